@@ -1,0 +1,162 @@
+/*
+ * blockbp.h -- C ABI of the GB300 blockBP decoder for the planar surface code.
+ *
+ * The library decodes batches of syndromes of the distance-d planar surface
+ * code under i.i.d. depolarizing noise with the blockBP decoder of Kaufmann
+ * and Arad, "Blockbp decoder for the surface code" (arXiv:2402.04834):
+ * for each syndrome and each of the four logical cosets I, X, Y, Z it runs
+ * block belief propagation with boundary-MPS messages on the coset tensor
+ * network (Sec. III.D, Algorithm 1), reads the coset log-probability out with
+ * the Bethe formula of Lemma 1, and picks a coset (Algorithm 1, Remark 6).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Lattice (Sec. II.B, Fig. 1): the code lives on a (2d-1) x (2d-1) grid;
+ *    (even, even) = horizontal-edge qubit, (odd, odd) = vertical-edge qubit,
+ *    (even, odd) = site check A_u (Z type), (odd, even) = plaquette check
+ *    B_p (X type).  n = d^2 + (d-1)^2 qubits, m = 2d(d-1) checks.
+ *  - Qubit order: row-major over the grid positions with i + j even.
+ *  - Syndrome order: all A_(r,c) row-major (r < d, c < d-1), then all
+ *    B_(r,j) row-major (r < d-1, j < d); one byte per bit, values 0/1.
+ *  - Coset order: 0 = I, 1 = X, 2 = Y, 3 = Z, relative to the library's pure
+ *    error f_s (X strings from a flagged A_(r,c) to the right boundary along
+ *    row r, Z strings from a flagged B_(r,j) to the bottom boundary along
+ *    column j).  X-bar is X on the horizontal edges of row 0, Z-bar is Z on
+ *    the horizontal edges of column 0.  A decision c means the correction
+ *    f_s * L_c.
+ *  - Every pointer argument is owned by the caller.  "Device" pointers are
+ *    CUDA global memory of the current device; "host" pointers are ordinary
+ *    (preferably pinned) host memory.  Calls are asynchronous on ``stream``
+ *    (a cudaStream_t, NULL = legacy default stream) unless stated otherwise.
+ *  - Return value: BBP_OK (0) or a negative BBP_E* code; bbp_strerror() gives
+ *    its text.  Numerical trouble of a single syndrome never fails a call:
+ *    it is reported in that syndrome's flags.
+ */
+#ifndef BLOCKBP_H
+#define BLOCKBP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define BBP_OK 0
+#define BBP_EINVAL (-1)        /* bad argument (null pointer, size, parameter) */
+#define BBP_ECUDA (-2)         /* a CUDA runtime call failed */
+#define BBP_ENOSPACE (-3)      /* workspace smaller than bbp_workspace_bytes() */
+#define BBP_EUNSUPPORTED (-4)  /* (k, D, precision) outside the compiled kernels */
+
+/* Per-coset flags (bit mask, Algorithm 1 and Remark 6). */
+#define BBP_FLAG_UNTRUSTED 1   /* Delta >= delta1: the Bethe value is not trusted */
+#define BBP_FLAG_OVERLAP 2     /* some edge overlap <m_uv|m_vu> <= 0 */
+#define BBP_FLAG_BLOCK 4       /* some block contraction Z_v <= 0 */
+#define BBP_FLAG_NONFINITE 8   /* a norm or a log went non-finite */
+
+/* Precisions. */
+#define BBP_FP64 0             /* all arithmetic in double */
+#define BBP_FP32 1             /* tensors and linear algebra in float; logs, Delta and
+                                  the read-out sums in double */
+
+/*
+ * Decoder parameters (Sec. III.E "Decoder Parameters"; values of Sec. IV).
+ *   d         code distance, d >= 2
+ *   k         block side in tensor-network nodes (Algorithm 1 "Partition into
+ *             k x k blocks"); blocks on the far edges take the remainder (Remark 1)
+ *   D         maximal MPS bond dimension chi of messages and in-block contraction
+ *   max_iter  maximal number of BP iterations (one iteration = two half-rounds,
+ *             Remark 8)
+ *   p         depolarizing probability, 0 < p < 0.75 (Sec. IV)
+ *   eta       damping parameter (Remark 7; the paper uses 0.1)
+ *   delta0    exit threshold on Delta (Remark 4); 0 runs exactly max_iter
+ *   delta1    trust threshold on Delta (Remark 6)
+ *   cutoff    relative singular-value cutoff: at every truncation the
+ *             singular values below cutoff * sigma_1 are dropped as numerical
+ *             zeros (the paper is silent; 1e-13 for BBP_FP64, 1e-7 for BBP_FP32)
+ *   precision BBP_FP64 or BBP_FP32
+ */
+typedef struct bbp_params {
+  int32_t d;
+  int32_t k;
+  int32_t D;
+  int32_t max_iter;
+  double p;
+  double eta;
+  double delta0;
+  double delta1;
+  double cutoff;
+  int32_t precision;
+  int32_t reserved;
+} bbp_params;
+
+/*
+ * bbp_workspace_bytes -- device scratch needed by bbp_decode_batch for B
+ * syndromes (MPS messages of every syndrome x coset, Sec. III.D).  With
+ * include_io != 0 it also counts room for device copies of the inputs and
+ * outputs, as bbp_decode_batch_host needs.  Writes the size to *bytes.
+ * Errors: BBP_EINVAL for invalid parameters or a null pointer.
+ */
+int bbp_workspace_bytes(const bbp_params* prm, int64_t B, int include_io, size_t* bytes);
+
+/*
+ * bbp_decode_batch -- blockBP decoding of B syndromes (Algorithm 1).
+ *   syndromes  device, [B][m] bytes 0/1 (order above)
+ *   logp       device, [B][4] doubles: natural log of the Bethe estimate of
+ *              pi(f_s L G) (Lemma 1) for the cosets I, X, Y, Z
+ *   delta      device, [B][4] doubles: final Delta of each coset (Remark 4)
+ *   iters      device, [B][4] int32: BP iterations run
+ *   flags      device, [B][4] int32: BBP_FLAG_* bits
+ *   decision   device, [B] int8: chosen coset index (Algorithm 1 / Remark 6):
+ *              largest logp among unflagged cosets, else smallest Delta,
+ *              ties to the lowest index
+ *   workspace  device scratch of at least bbp_workspace_bytes(prm, B, 0)
+ *              bytes, 256-byte aligned; contents on entry are ignored
+ * Asynchronous on ``stream``.  Returns BBP_EINVAL for bad arguments,
+ * BBP_ENOSPACE for a short workspace, BBP_EUNSUPPORTED when no compiled
+ * kernel covers (k, D, precision), BBP_ECUDA when a launch fails.
+ */
+int bbp_decode_batch(const uint8_t* syndromes, int64_t B, const bbp_params* prm,
+                     double* logp, double* delta, int32_t* iters, int32_t* flags,
+                     int8_t* decision, void* workspace, size_t workspace_bytes,
+                     void* stream);
+
+/*
+ * bbp_decode_batch_host -- the same decode with HOST buffers: copies the
+ * syndromes to the device, decodes, copies every output back and
+ * synchronises ``stream`` before returning.  ``workspace`` is device memory
+ * of at least bbp_workspace_bytes(prm, B, 1) bytes.  Any output pointer
+ * except decision may be NULL to skip its copy.  Errors as bbp_decode_batch.
+ */
+int bbp_decode_batch_host(const uint8_t* syndromes, int64_t B, const bbp_params* prm,
+                          double* logp, double* delta, int32_t* iters, int32_t* flags,
+                          int8_t* decision, void* workspace, size_t workspace_bytes,
+                          void* stream);
+
+/*
+ * bbp_sample -- seeded depolarizing errors and their syndromes on the device
+ * (Sec. IV workload).  Shot t in [first_shot, first_shot + B) draws, for each
+ * qubit q, r = mix(mix(mix(seed) ^ t) ^ q) with mix the SplitMix64 output
+ * function; identity iff (r >> 11) < floor((1 - p) 2^53), otherwise
+ * ((mix(r) >> 32) * 3) >> 32 selects X, Y, Z.
+ *   ex, ez      device [B][n] bytes: X and Z bit planes of the error
+ *   syndromes   device [B][m] bytes
+ *   true_class  device [B] int8: coset index of the error relative to f_s
+ * Any of ex / ez may be NULL.  Asynchronous on ``stream``.
+ */
+int bbp_sample(uint64_t seed, int64_t first_shot, int64_t B, int32_t d, double p,
+               uint8_t* ex, uint8_t* ez, uint8_t* syndromes, int8_t* true_class,
+               void* stream);
+
+/* Static text for a return code. */
+const char* bbp_strerror(int code);
+
+/* Library version string. */
+const char* bbp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BLOCKBP_H */

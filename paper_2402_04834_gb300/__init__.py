@@ -1,0 +1,12 @@
+"""GB300 blockBP decoder for the planar surface code (arXiv:2402.04834).
+
+The compute path is libblockbp.so (hand-written sm_103a CUDA, C ABI in
+include/blockbp.h); this package only marshals arguments and provides
+device memory and streams through PyTorch.
+"""
+
+from ._lib import FP32, FP64, BbpError, DecoderParams, lib, workspace_bytes  # noqa: F401
+from .decoder import Workspace, decode, decode_host, sample  # noqa: F401
+
+__all__ = ["DecoderParams", "decode", "decode_host", "sample", "workspace_bytes", "Workspace",
+           "lib", "BbpError", "FP32", "FP64"]

@@ -1,0 +1,98 @@
+"""ctypes binding of libblockbp.so (include/blockbp.h); argument marshalling only.
+
+Every step of the decoder runs in the library's CUDA kernels.  If the library
+is missing this module raises instead of falling back to anything else.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libblockbp.so")
+
+BBP_OK = 0
+FP64, FP32 = 0, 1
+FLAG_UNTRUSTED, FLAG_OVERLAP, FLAG_BLOCK, FLAG_NONFINITE = 1, 2, 4, 8
+
+# Exported symbols, as declared in include/blockbp.h.
+SYMBOLS = ("bbp_workspace_bytes", "bbp_decode_batch", "bbp_decode_batch_host", "bbp_sample",
+           "bbp_strerror", "bbp_version")
+
+
+class BbpParams(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("k", ctypes.c_int32), ("D", ctypes.c_int32),
+                ("max_iter", ctypes.c_int32), ("p", ctypes.c_double), ("eta", ctypes.c_double),
+                ("delta0", ctypes.c_double), ("delta1", ctypes.c_double), ("cutoff", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+@dataclass
+class DecoderParams:
+    """Decoder parameters (Sec. III.E); defaults are the values of Sec. IV."""
+    d: int
+    k: int = 4
+    D: int = 8
+    p: float = 0.1
+    max_iter: int = 20
+    eta: float = 0.1
+    delta0: float = 1e-4
+    delta1: float = 1e-2
+    cutoff: float | None = None
+    precision: str = "fp64"
+
+    def c(self) -> BbpParams:
+        prec = FP64 if self.precision == "fp64" else FP32
+        cut = self.cutoff if self.cutoff is not None else (1e-13 if prec == FP64 else 1e-7)
+        return BbpParams(self.d, self.k, self.D, self.max_iter, self.p, self.eta, self.delta0,
+                         self.delta1, cut, prec, 0)
+
+    @property
+    def m(self) -> int:
+        return 2 * self.d * (self.d - 1)
+
+
+class BbpError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise BbpError(f"{LIB_PATH} is missing: build it with paper_2402_04834_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        P = ctypes.POINTER(BbpParams)
+        L.bbp_workspace_bytes.argtypes = [P, i64, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+        L.bbp_workspace_bytes.restype = ctypes.c_int
+        L.bbp_decode_batch.argtypes = [vp, i64, P, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+        L.bbp_decode_batch.restype = ctypes.c_int
+        L.bbp_decode_batch_host.argtypes = [vp, i64, P, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+        L.bbp_decode_batch_host.restype = ctypes.c_int
+        L.bbp_sample.argtypes = [ctypes.c_uint64, i64, i64, i32, ctypes.c_double, vp, vp, vp, vp, vp]
+        L.bbp_sample.restype = ctypes.c_int
+        L.bbp_strerror.argtypes = [ctypes.c_int]
+        L.bbp_strerror.restype = ctypes.c_char_p
+        L.bbp_version.argtypes = []
+        L.bbp_version.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def check(rc: int):
+    if rc != BBP_OK:
+        raise BbpError(f"blockbp error {rc}: {lib().bbp_strerror(rc).decode()}")
+
+
+def workspace_bytes(prm: DecoderParams, B: int, include_io: bool = False) -> int:
+    out = ctypes.c_size_t(0)
+    cp = prm.c()
+    check(lib().bbp_workspace_bytes(ctypes.byref(cp), B, int(include_io), ctypes.byref(out)))
+    return int(out.value)

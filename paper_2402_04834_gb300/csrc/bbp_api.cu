@@ -1,0 +1,143 @@
+// C ABI of the blockBP decoder: argument checks, workspace sizing and the
+// kernel launches.  See include/blockbp.h for the contract of each call.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/blockbp.h"
+#include "bbp_launch.h"
+
+namespace {
+
+using bbp::Geo;
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+int check_params(const bbp_params* p) {
+  if (!p) return BBP_EINVAL;
+  if (p->d < 2 || p->d > 64) return BBP_EINVAL;
+  if (p->k < 1 || p->D < 1 || p->max_iter < 0 || p->max_iter > 100000) return BBP_EINVAL;
+  if (!(p->p > 0.0 && p->p < 0.75)) return BBP_EINVAL;
+  if (!(p->eta >= 0.0 && p->eta < 1.0)) return BBP_EINVAL;
+  if (!(p->delta0 >= 0.0) || !(p->delta1 >= 0.0) || !(p->cutoff >= 0.0 && p->cutoff < 1.0)) return BBP_EINVAL;
+  if (p->precision != BBP_FP64 && p->precision != BBP_FP32) return BBP_EINVAL;
+  if (p->k > bbp::kMaxK || p->D > bbp::kMaxD) return BBP_EUNSUPPORTED;
+  return BBP_OK;
+}
+
+struct Sizes {
+  Geo g;
+  int M, arena_elems, m;
+  size_t elem, arena_bytes, io_bytes;
+};
+
+Sizes sizes_for(const bbp_params* p, int64_t B) {
+  Sizes s;
+  s.g = bbp::make_geo(p->d, p->k);
+  bbp::count_messages(s.g, p->D, &s.M, &s.arena_elems);
+  s.m = 2 * p->d * (p->d - 1);
+  s.elem = p->precision == BBP_FP64 ? sizeof(double) : sizeof(float);
+  s.arena_bytes = align256((size_t)B * 4 * (size_t)s.arena_elems * s.elem);
+  s.io_bytes = align256((size_t)B * s.m) + align256((size_t)B * 4 * 8) * 2 +
+               align256((size_t)B * 4 * 4) * 2 + align256((size_t)B);
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bbp_version(void) { return "blockbp-gb300 0.1 (sm_103a)"; }
+
+const char* bbp_strerror(int code) {
+  switch (code) {
+    case BBP_OK: return "ok";
+    case BBP_EINVAL: return "invalid argument";
+    case BBP_ECUDA: return "CUDA runtime error";
+    case BBP_ENOSPACE: return "workspace too small";
+    case BBP_EUNSUPPORTED: return "block size or bond dimension outside the compiled kernels";
+    default: return "unknown error";
+  }
+}
+
+int bbp_workspace_bytes(const bbp_params* prm, int64_t B, int include_io, size_t* bytes) {
+  const int rc = check_params(prm);
+  if (rc != BBP_OK) return rc;
+  if (!bytes || B < 0 || B > (int64_t(1) << 29)) return BBP_EINVAL;
+  const Sizes s = sizes_for(prm, B);
+  *bytes = s.arena_bytes + (include_io ? s.io_bytes : 0);
+  return BBP_OK;
+}
+
+int bbp_decode_batch(const uint8_t* syndromes, int64_t B, const bbp_params* prm, double* logp,
+                     double* delta, int32_t* iters, int32_t* flags, int8_t* decision, void* workspace,
+                     size_t workspace_bytes, void* stream) {
+  const int rc = check_params(prm);
+  if (rc != BBP_OK) return rc;
+  if (B < 0 || B > (int64_t(1) << 29)) return BBP_EINVAL;
+  if (B == 0) return BBP_OK;
+  if (!syndromes || !logp || !delta || !iters || !flags || !decision || !workspace) return BBP_EINVAL;
+  if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return BBP_EINVAL;
+  const Sizes s = sizes_for(prm, B);
+  if (workspace_bytes < s.arena_bytes) return BBP_ENOSPACE;
+  bbp::LaunchArgs a;
+  a.geo = s.g; a.M = s.M; a.D = prm->D; a.max_iter = prm->max_iter; a.arena_elems = s.arena_elems;
+  a.p = prm->p; a.eta = prm->eta; a.delta0 = prm->delta0; a.delta1 = prm->delta1; a.cutoff = prm->cutoff;
+  a.synd = syndromes; a.arena = workspace; a.logp = logp; a.delta = delta; a.iters = iters;
+  a.flags = flags; a.decision = decision; a.B = B;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = prm->precision == BBP_FP64 ? bbp::launch_decode_f64(a, st) : bbp::launch_decode_f32(a, st);
+  if (e != cudaSuccess) return BBP_ECUDA;
+  e = bbp::launch_decide(a, st);
+  return e == cudaSuccess ? BBP_OK : BBP_ECUDA;
+}
+
+int bbp_decode_batch_host(const uint8_t* syndromes, int64_t B, const bbp_params* prm, double* logp,
+                          double* delta, int32_t* iters, int32_t* flags, int8_t* decision,
+                          void* workspace, size_t workspace_bytes, void* stream) {
+  const int rc = check_params(prm);
+  if (rc != BBP_OK) return rc;
+  if (B < 0 || B > (int64_t(1) << 29)) return BBP_EINVAL;
+  if (B == 0) return BBP_OK;
+  if (!syndromes || !decision || !workspace) return BBP_EINVAL;
+  if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return BBP_EINVAL;
+  const Sizes s = sizes_for(prm, B);
+  if (workspace_bytes < s.arena_bytes + s.io_bytes) return BBP_ENOSPACE;
+  char* base = static_cast<char*>(workspace) + s.arena_bytes;
+  uint8_t* d_synd = reinterpret_cast<uint8_t*>(base);  base += align256((size_t)B * s.m);
+  double* d_logp = reinterpret_cast<double*>(base);    base += align256((size_t)B * 4 * 8);
+  double* d_delta = reinterpret_cast<double*>(base);   base += align256((size_t)B * 4 * 8);
+  int32_t* d_iters = reinterpret_cast<int32_t*>(base); base += align256((size_t)B * 4 * 4);
+  int32_t* d_flags = reinterpret_cast<int32_t*>(base); base += align256((size_t)B * 4 * 4);
+  int8_t* d_dec = reinterpret_cast<int8_t*>(base);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(d_synd, syndromes, (size_t)B * s.m, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return BBP_ECUDA;
+  const int r = bbp_decode_batch(d_synd, B, prm, d_logp, d_delta, d_iters, d_flags, d_dec, workspace,
+                                 s.arena_bytes, stream);
+  if (r != BBP_OK) return r;
+  if (cudaMemcpyAsync(decision, d_dec, (size_t)B, cudaMemcpyDeviceToHost, st) != cudaSuccess) return BBP_ECUDA;
+  if (logp && cudaMemcpyAsync(logp, d_logp, (size_t)B * 32, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return BBP_ECUDA;
+  if (delta && cudaMemcpyAsync(delta, d_delta, (size_t)B * 32, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return BBP_ECUDA;
+  if (iters && cudaMemcpyAsync(iters, d_iters, (size_t)B * 16, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return BBP_ECUDA;
+  if (flags && cudaMemcpyAsync(flags, d_flags, (size_t)B * 16, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return BBP_ECUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? BBP_OK : BBP_ECUDA;
+}
+
+int bbp_sample(uint64_t seed, int64_t first_shot, int64_t B, int32_t d, double p, uint8_t* ex,
+               uint8_t* ez, uint8_t* syndromes, int8_t* true_class, void* stream) {
+  if (d < 2 || d > 64 || B < 0 || B > (int64_t(1) << 31) - 1 || first_shot < 0) return BBP_EINVAL;
+  if (!(p > 0.0 && p < 0.75) || !syndromes || !true_class) return BBP_EINVAL;
+  if (B == 0) return BBP_OK;
+  const unsigned long long thr = (unsigned long long)((1.0 - p) * 9007199254740992.0);
+  cudaError_t e = bbp::launch_sample(seed, first_shot, B, d, thr, ex, ez, syndromes, true_class,
+                                     static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? BBP_OK : BBP_ECUDA;
+}
+
+}  // extern "C"

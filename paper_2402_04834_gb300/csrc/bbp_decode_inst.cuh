@@ -1,0 +1,30 @@
+// Instantiation of the decoder kernel for one scalar type.
+#pragma once
+
+#include "bbp_kernels.cuh"
+#include "bbp_launch.h"
+
+namespace bbp {
+
+template <typename T>
+int smem_bytes_for(const Geo& g, int M) {
+  return cta_layout(g, M, kMaxK, kWarps, (int)sizeof(WarpWS<T, kMaxK, kMaxD>)).total;
+}
+
+template <typename T>
+cudaError_t launch_decode_t(const LaunchArgs& a, cudaStream_t st) {
+  KArgs<T> k;
+  k.geo = a.geo; k.M = a.M; k.D = a.D; k.max_iter = a.max_iter; k.arena_elems = a.arena_elems;
+  k.p = a.p; k.eta = a.eta; k.delta0 = a.delta0; k.delta1 = a.delta1; k.cutoff = a.cutoff;
+  k.synd = a.synd; k.arena = static_cast<T*>(a.arena);
+  k.logp = a.logp; k.delta = a.delta; k.iters = a.iters; k.flags = a.flags;
+  const int smem = smem_bytes_for<T>(a.geo, a.M);
+  auto kern = decode_kernel<T, kMaxK, kMaxD, kWarps>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)(a.B * 4);
+  kern<<<grid, kWarps * 32, smem, st>>>(k);
+  return cudaGetLastError();
+}
+
+}  // namespace bbp

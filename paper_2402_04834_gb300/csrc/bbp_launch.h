@@ -1,0 +1,43 @@
+// Launchers of the compiled decoder instances (one translation unit per
+// precision), called by the C ABI in bbp_api.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "bbp_geometry.h"
+
+namespace bbp {
+
+// Compile-time capacity of the instances: block side k <= kMaxK and bond
+// dimension D <= kMaxD; kWarps warps (message updates in flight) per CTA.
+constexpr int kMaxK = 4;
+constexpr int kMaxD = 8;
+constexpr int kWarps = 4;
+
+struct LaunchArgs {
+  Geo geo;
+  int M, D, max_iter, arena_elems;
+  double p, eta, delta0, delta1, cutoff;
+  const uint8_t* synd;
+  void* arena;
+  double* logp;
+  double* delta;
+  int32_t* iters;
+  int32_t* flags;
+  int8_t* decision;
+  long long B;
+};
+
+// Shared memory of one CTA in bytes for the given precision (0 = fp64, 1 = fp32).
+int cta_smem_bytes(int precision, const Geo& g, int M);
+
+cudaError_t launch_decode_f64(const LaunchArgs& a, cudaStream_t st);
+cudaError_t launch_decode_f32(const LaunchArgs& a, cudaStream_t st);
+cudaError_t launch_decide(const LaunchArgs& a, cudaStream_t st);
+cudaError_t launch_sample(uint64_t seed, long long first_shot, long long B, int d,
+                          unsigned long long id_threshold, uint8_t* ex, uint8_t* ez,
+                          uint8_t* synd, int8_t* true_class, cudaStream_t st);
+
+}  // namespace bbp

@@ -1,0 +1,78 @@
+"""The C-ABI library: loads, exports every declared symbol, validates arguments (no GPU)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2402_04834_gb300 as pkg
+from paper_2402_04834_gb300 import _lib
+from paper_2402_04834_gb300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build()
+    return pkg.lib()
+
+
+def declared_functions():
+    with open(os.path.join(ROOT, "include", "blockbp.h")) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^(?:int|const char\*)\s+(bbp_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 6
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(_lib.SYMBOLS)
+
+
+def test_version_and_strerror(L):
+    assert b"sm_103a" in L.bbp_version()
+    for code in (0, -1, -2, -3, -4):
+        assert len(L.bbp_strerror(code)) > 0
+
+
+def test_workspace_sizes_scale_with_batch(L):
+    p = pkg.DecoderParams(d=11, k=4, D=8)
+    a = pkg.workspace_bytes(p, 100)
+    b = pkg.workspace_bytes(p, 200)
+    assert b >= 2 * a - 256 and a > 0
+    p32 = pkg.DecoderParams(d=11, k=4, D=8, precision="fp32")
+    assert pkg.workspace_bytes(p32, 100) < a
+    assert pkg.workspace_bytes(p, 100, include_io=True) > a
+
+
+@pytest.mark.parametrize("field,val", [("d", 1), ("k", 0), ("D", 0), ("p", 0.0), ("p", 0.8),
+                                       ("eta", 1.0), ("precision", 7), ("max_iter", -1)])
+def test_invalid_parameters_rejected(L, field, val):
+    c = pkg.DecoderParams(d=5, k=3, D=4).c()
+    setattr(c, field, val)
+    out = ctypes.c_size_t(0)
+    assert L.bbp_workspace_bytes(ctypes.byref(c), 10, 0, ctypes.byref(out)) == -1
+
+
+def test_unsupported_sizes_reported(L):
+    c = pkg.DecoderParams(d=11, k=9, D=8).c()
+    out = ctypes.c_size_t(0)
+    assert L.bbp_workspace_bytes(ctypes.byref(c), 10, 0, ctypes.byref(out)) == -4
+
+
+def test_decode_null_pointers_rejected_before_any_cuda_call(L):
+    c = pkg.DecoderParams(d=5, k=3, D=4).c()
+    rc = L.bbp_decode_batch(None, 4, ctypes.byref(c), None, None, None, None, None, None, 0, None)
+    assert rc == -1
+    rc = L.bbp_decode_batch_host(None, 4, ctypes.byref(c), None, None, None, None, None, None, 0, None)
+    assert rc == -1
+    assert L.bbp_sample(1, 0, 4, 1, 0.1, None, None, None, None, None) == -1
+
+
+def test_empty_batch_is_a_no_op(L):
+    c = pkg.DecoderParams(d=5, k=3, D=4).c()
+    assert L.bbp_decode_batch(None, 0, ctypes.byref(c), None, None, None, None, None, None, 0, None) == 0

@@ -1,0 +1,209 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances (written from the arithmetic): FP64 |d log P| <= 1e-9 per coset
+(the target of the decoder); Delta within 1e-7 absolute (Delta is
+sqrt(sum 2 - 2<a|b>^2)/M, which cancels near convergence and carries
+~sqrt(M eps)/M of rounding); decisions identical wherever the oracle's
+log-likelihood margin among eligible cosets exceeds 1e-2.  FP32
+|d log P| <= 1e-3.  Shots whose oracle run met a near-degenerate truncation
+(relative Schmidt gap <= 1e-8) may legitimately keep a different subspace
+and are only checked for validity.
+"""
+
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import paper_2402_04834_gb300 as pkg
+import synth
+from oracle import blockbp as bb
+from oracle.lattice import Lattice
+from paper_2402_04834_gb300.build import build
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def dev():
+    build()
+    pkg.lib()
+    return torch.device("cuda:0")
+
+
+def load_golden(name):
+    with open(os.path.join(HERE, "golden", name)) as f:
+        return json.load(f)
+
+
+def margin(logp, flags):
+    el = sorted((logp[i] for i in range(4) if flags[i] == 0), reverse=True)
+    return el[0] - el[1] if len(el) >= 2 else math.inf
+
+
+def gpu_decode(S, prm, dev):
+    out = pkg.decode(torch.from_numpy(np.ascontiguousarray(S)).to(dev), prm)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def compare(out, rows, offset, tol_logp, check_iters=True, tol_delta=1e-7):
+    n_checked = 0
+    for r in rows:
+        b = r["shot"] - offset
+        gap = r["min_gap"]
+        degenerate = gap is not None and gap <= 1e-8
+        lp = np.array(r["logp"])
+        if not degenerate:
+            np.testing.assert_allclose(out["logp"][b], lp, rtol=0, atol=tol_logp, err_msg=f"shot {r['shot']}")
+            np.testing.assert_allclose(out["delta"][b], r["delta"], rtol=0, atol=tol_delta)
+            if check_iters:
+                assert list(out["iters"][b]) == r["iters"]
+            if margin(r["logp"], r["flags"]) > 1e-2 and list(out["flags"][b]) == r["flags"]:
+                assert int(out["decision"][b]) == r["decision"], f"shot {r['shot']}"
+            n_checked += 1
+        assert 0 <= int(out["decision"][b]) < 4
+    return n_checked
+
+
+def test_sampler_bit_exact_with_workload_module(dev):
+    for d in (3, 5, 11):
+        ex, ez, s, tc = pkg.sample(1234, 7, 64, d, 0.1, device=dev)
+        torch.cuda.synchronize()
+        rx, rz, rs = synth.sample_syndromes(1234, 7, 64, d, 0.1)
+        assert np.array_equal(ex.cpu().numpy(), rx)
+        assert np.array_equal(ez.cpu().numpy(), rz)
+        assert np.array_equal(s.cpu().numpy(), rs)
+        lat = Lattice(d)
+        tcn = tc.cpu().numpy()
+        for b in range(16):
+            assert tcn[b] == lat.true_class(rx[b], rz[b], rs[b])
+
+
+def test_fp64_parity_d5_config(dev):
+    g = load_golden("oracle_d5_k3_D4_p010.json")
+    w = g["workload"]
+    _, _, S = synth.sample_syndromes(w["seed"], w["first_shot"], w["shots"], w["d"], w["p"])
+    prm = pkg.DecoderParams(d=w["d"], k=w["k"], D=w["D"], p=w["p"], max_iter=w["max_iter"],
+                            delta0=w["delta0"], precision="fp64")
+    out = gpu_decode(S, prm, dev)
+    assert compare(out, g["shots"], w["first_shot"], 1e-9) == w["shots"]
+
+
+def test_fp64_parity_d11_config(dev):
+    g = load_golden("oracle_d11_k4_D8_p010.json")
+    w = g["workload"]
+    _, _, S = synth.sample_syndromes(w["seed"], w["first_shot"], w["shots"], w["d"], w["p"])
+    prm = pkg.DecoderParams(d=w["d"], k=w["k"], D=w["D"], p=w["p"], max_iter=w["max_iter"],
+                            delta0=w["delta0"], precision="fp64")
+    out = gpu_decode(S, prm, dev)
+    assert compare(out, g["shots"], w["first_shot"], 1e-9) >= len(g["shots"]) - 1
+
+
+@pytest.mark.parametrize("d,k,D,iters,p", [
+    (3, 2, 4, 5, 0.1),     # W = 5: blocks 2, 2, 1 (ragged tail)
+    (4, 3, 2, 4, 0.12),    # W = 7: blocks 3, 3, 1; D = 2 truncates
+    (5, 4, 8, 5, 0.1),     # W = 9: blocks 4, 4, 1
+    (7, 4, 2, 4, 0.08),    # W = 13: blocks 4, 4, 4, 1; D = 2 truncates
+    (7, 3, 2, 3, 0.08),    # W = 13: blocks 3, 3, 3, 3, 1
+    (2, 3, 4, 3, 0.2),     # W = 3: one block, no messages (bMPS limit)
+])
+def test_fp64_parity_ragged_live_oracle(dev, d, k, D, iters, p):
+    _, _, S = synth.sample_syndromes(4242, 0, 3, d, p)
+    prm = pkg.DecoderParams(d=d, k=k, D=D, p=p, max_iter=iters, delta0=0.0)
+    out = gpu_decode(S, prm, dev)
+    rows = []
+    for b in range(S.shape[0]):
+        r = bb.decode(S[b], bb.Params(d=d, k=k, D=D, p=p, max_iter=iters, delta0=0.0))
+        st = r["stats"]
+        rows.append(dict(shot=b, logp=list(r["logp"]), delta=list(r["delta"]), iters=list(r["iters"]),
+                         flags=list(r["flags"]), decision=r["decision"],
+                         min_gap=None if not np.isfinite(st.min_gap) else st.min_gap))
+    assert compare(out, rows, 0, 1e-9) >= 1
+
+
+def test_fp64_early_exit_matches_oracle(dev):
+    d, k, D, p = 5, 3, 4, 0.06
+    _, _, S = synth.sample_syndromes(99, 0, 4, d, p)
+    prm = pkg.DecoderParams(d=d, k=k, D=D, p=p, max_iter=40, delta0=1e-4)
+    out = gpu_decode(S, prm, dev)
+    for b in range(4):
+        r = bb.decode(S[b], bb.Params(d=d, k=k, D=D, p=p, max_iter=40, delta0=1e-4))
+        for L in range(4):
+            # Delta is compared against delta0 on both sides; only a Delta within
+            # rounding of delta0 could exit on a different iteration.
+            if abs(r["cosets"][L].delta - 1e-4) > 1e-6:
+                assert out["iters"][b][L] == r["iters"][L]
+                assert abs(out["logp"][b][L] - r["logp"][L]) < 1e-9
+
+
+def test_fp32_within_reduced_precision_tolerance(dev):
+    for name in ("oracle_d5_k3_D4_p010.json", "oracle_d11_k4_D8_p010.json"):
+        g = load_golden(name)
+        w = g["workload"]
+        _, _, S = synth.sample_syndromes(w["seed"], w["first_shot"], w["shots"], w["d"], w["p"])
+        prm = pkg.DecoderParams(d=w["d"], k=w["k"], D=w["D"], p=w["p"], max_iter=w["max_iter"],
+                                delta0=w["delta0"], precision="fp32")
+        out = gpu_decode(S, prm, dev)
+        errs = []
+        for r in g["shots"]:
+            b = r["shot"] - w["first_shot"]
+            errs.append(np.max(np.abs(out["logp"][b] - np.array(r["logp"]))))
+            if margin(r["logp"], r["flags"]) > 1e-2 and list(out["flags"][b]) == r["flags"]:
+                assert int(out["decision"][b]) == r["decision"]
+        assert max(errs) <= 1e-3, (name, max(errs))
+
+
+def test_host_entry_point_matches_device_entry_point(dev):
+    _, _, S = synth.sample_syndromes(5, 0, 9, 5, 0.1)
+    prm = pkg.DecoderParams(d=5, k=3, D=4, p=0.1, max_iter=6, delta0=0.0)
+    a = gpu_decode(S, prm, dev)
+    h = pkg.decode_host(S, prm, device=dev)
+    for key in ("logp", "delta", "iters", "flags", "decision"):
+        assert np.array_equal(a[key], h[key]), key
+
+
+def test_deterministic_reruns(dev):
+    _, _, S = synth.sample_syndromes(6, 0, 16, 7, 0.1)
+    prm = pkg.DecoderParams(d=7, k=4, D=8, p=0.1, max_iter=5, delta0=0.0)
+    a = gpu_decode(S, prm, dev)
+    b = gpu_decode(S, prm, dev)
+    for key in a:
+        assert np.array_equal(a[key], b[key]), key
+
+
+def test_zero_syndrome_and_single_shot(dev):
+    d = 5
+    S = np.zeros((1, 2 * d * (d - 1)), dtype=np.uint8)
+    prm = pkg.DecoderParams(d=d, k=3, D=4, p=0.05, max_iter=8, delta0=0.0)
+    out = gpu_decode(S, prm, dev)
+    assert int(out["decision"][0]) == 0
+    r = bb.decode(S[0], bb.Params(d=d, k=3, D=4, p=0.05, max_iter=8, delta0=0.0))
+    np.testing.assert_allclose(out["logp"][0], r["logp"], rtol=0, atol=1e-9)
+
+
+def test_full_size_batch_in_bench_configuration(dev):
+    # The benchmark's batch: 10^4 syndromes at d = 11, p = 0.10, k = 4, D = 8,
+    # decoded in one launch; the first shots are compared with the oracle.
+    g = load_golden("oracle_d11_k4_D8_p010.json")
+    w = g["workload"]
+    B = 10000
+    _, _, S = synth.sample_syndromes(w["seed"], 0, B, w["d"], w["p"])
+    prm = pkg.DecoderParams(d=w["d"], k=w["k"], D=w["D"], p=w["p"], max_iter=w["max_iter"],
+                            delta0=w["delta0"], precision="fp32")
+    out = gpu_decode(S, prm, dev)
+    for r in g["shots"]:
+        b = r["shot"]
+        assert np.max(np.abs(out["logp"][b] - np.array(r["logp"]))) <= 1e-3
+    # Properties at any size: valid decisions, probabilities <= 1, finite logs.
+    assert np.all((out["decision"] >= 0) & (out["decision"] < 4))
+    assert np.all(out["iters"] == w["max_iter"])
+    fin = np.isfinite(out["logp"])
+    assert fin.mean() > 0.999
+    lse = np.log(np.sum(np.exp(np.where(fin, out["logp"], -np.inf)), axis=1))
+    assert np.all(lse < 1e-6)
