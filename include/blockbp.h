@@ -48,6 +48,10 @@ extern "C" {
 #define BBP_ECUDA (-2)         /* a CUDA runtime call failed */
 #define BBP_ENOSPACE (-3)      /* workspace smaller than bbp_workspace_bytes() */
 #define BBP_EUNSUPPORTED (-4)  /* (k, D, precision) outside the compiled kernels */
+#define BBP_ETOOLARGE (-5)     /* batch needs more than the static workspace holds */
+
+/* Size of the static workspace used by bbp_decode_batch_static (32 MiB). */
+#define BBP_STATIC_WORKSPACE_BYTES (32u << 20)
 
 /* Per-coset flags (bit mask, Algorithm 1 and Remark 6). */
 #define BBP_FLAG_UNTRUSTED 1   /* Delta >= delta1: the Bethe value is not trusted */
@@ -148,6 +152,35 @@ int bbp_decode_batch_host(const uint8_t* syndromes, int64_t B, const bbp_params*
 int bbp_sample(uint64_t seed, int64_t first_shot, int64_t B, int32_t d, double p,
                uint8_t* ex, uint8_t* ez, uint8_t* syndromes, int8_t* true_class,
                void* stream);
+
+/*
+ * bbp_decode_batch_static -- the decode of bbp_decode_batch without any
+ * allocation, for callers that cannot allocate device memory: code inside a
+ * CUDA graph being captured or replayed, real-time loops that must not take
+ * the allocator's locks or fail for lack of memory mid-run, and hosts that
+ * own only the input and output buffers.  The paper has no counterpart; this
+ * is an interface of this library.
+ *   Arguments and outputs are those of bbp_decode_batch, minus the workspace:
+ *   the message arena is a file-scope device array of
+ *   BBP_STATIC_WORKSPACE_BYTES (32 MiB) that every GPU loading the library
+ *   reserves until the process exits.
+ *   Size limit: the batch may need at most BBP_STATIC_WORKSPACE_BYTES of
+ *   workspace (bbp_workspace_bytes(prm, B, 0)); beyond that the call returns
+ *   BBP_ETOOLARGE and launches nothing (d = 11, k = 4, D = 8: up to 512
+ *   syndromes in FP32, 256 in FP64).
+ *   The first call on a device looks up the array's device address (once per
+ *   device, with that device current); make that first call before any
+ *   stream capture begins.  No call allocates or frees memory.
+ *   Every call shares the one array, and the kernel initialises each message
+ *   before it reads it, so nothing must start at zero and the last call's
+ *   contents are simply overwritten.  Calls whose kernels overlap on the GPU
+ *   (different streams, or several host threads) race on the array and give
+ *   undefined results: serialise them.
+ * Errors as bbp_decode_batch, plus BBP_ETOOLARGE.
+ */
+int bbp_decode_batch_static(const uint8_t* syndromes, int64_t B, const bbp_params* prm,
+                            double* logp, double* delta, int32_t* iters, int32_t* flags,
+                            int8_t* decision, void* stream);
 
 /* Static text for a return code. */
 const char* bbp_strerror(int code);

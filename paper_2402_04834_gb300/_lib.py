@@ -19,7 +19,9 @@ FLAG_UNTRUSTED, FLAG_OVERLAP, FLAG_BLOCK, FLAG_NONFINITE = 1, 2, 4, 8
 
 # Exported symbols, as declared in include/blockbp.h.
 SYMBOLS = ("bbp_workspace_bytes", "bbp_decode_batch", "bbp_decode_batch_host", "bbp_sample",
-           "bbp_strerror", "bbp_version")
+           "bbp_strerror", "bbp_version", "bbp_decode_batch_static")
+BBP_ETOOLARGE = -5
+STATIC_WORKSPACE_BYTES = 32 << 20
 
 
 class BbpParams(ctypes.Structure):
@@ -76,6 +78,8 @@ def lib():
         L.bbp_decode_batch.restype = ctypes.c_int
         L.bbp_decode_batch_host.argtypes = [vp, i64, P, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
         L.bbp_decode_batch_host.restype = ctypes.c_int
+        L.bbp_decode_batch_static.argtypes = [vp, i64, P, vp, vp, vp, vp, vp, vp]
+        L.bbp_decode_batch_static.restype = ctypes.c_int
         L.bbp_sample.argtypes = [ctypes.c_uint64, i64, i64, i32, ctypes.c_double, vp, vp, vp, vp, vp]
         L.bbp_sample.restype = ctypes.c_int
         L.bbp_strerror.argtypes = [ctypes.c_int]

@@ -57,6 +57,7 @@ const char* bbp_strerror(int code) {
     case BBP_ECUDA: return "CUDA runtime error";
     case BBP_ENOSPACE: return "workspace too small";
     case BBP_EUNSUPPORTED: return "block size or bond dimension outside the compiled kernels";
+    case BBP_ETOOLARGE: return "batch needs more than the 32 MiB static workspace";
     default: return "unknown error";
   }
 }
