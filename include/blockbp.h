@@ -59,6 +59,10 @@ extern "C" {
 #define BBP_FLAG_BLOCK 4       /* some block contraction Z_v <= 0 */
 #define BBP_FLAG_NONFINITE 8   /* a norm or a log went non-finite */
 
+/* Algorithms. */
+#define BBP_ALG_MPS 0          /* blockBP with boundary-MPS messages of bond D (Sec. III.D) */
+#define BBP_ALG_FUSED 1        /* fused-block BP with dense messages of 2^k (Remark 9), k <= 4 */
+
 /* Precisions. */
 #define BBP_FP64 0             /* all arithmetic in double */
 #define BBP_FP32 1             /* tensors and linear algebra in float; logs, Delta and
@@ -80,6 +84,11 @@ extern "C" {
  *             singular values below cutoff * sigma_1 are dropped as numerical
  *             zeros (the paper is silent; 1e-13 for BBP_FP64, 1e-7 for BBP_FP32)
  *   precision BBP_FP64 or BBP_FP32
+ *   algorithm BBP_ALG_MPS, or BBP_ALG_FUSED: every k x k block fused into one
+ *             vertex with dense messages (Remark 9; the form the paper ran for
+ *             k = 1, 2, 4).  Nothing is truncated, D and cutoff are unused,
+ *             and the result equals BBP_ALG_MPS whenever that truncates
+ *             nothing.  Needs k <= 4 and no workspace.
  */
 typedef struct bbp_params {
   int32_t d;
@@ -92,7 +101,7 @@ typedef struct bbp_params {
   double delta1;
   double cutoff;
   int32_t precision;
-  int32_t reserved;
+  int32_t algorithm;
 } bbp_params;
 
 /*

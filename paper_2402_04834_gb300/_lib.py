@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libblockbp.so")
 
 BBP_OK = 0
 FP64, FP32 = 0, 1
+ALG_MPS, ALG_FUSED = 0, 1
 FLAG_UNTRUSTED, FLAG_OVERLAP, FLAG_BLOCK, FLAG_NONFINITE = 1, 2, 4, 8
 
 # Exported symbols, as declared in include/blockbp.h.
@@ -28,7 +29,7 @@ class BbpParams(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int32), ("k", ctypes.c_int32), ("D", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("p", ctypes.c_double), ("eta", ctypes.c_double),
                 ("delta0", ctypes.c_double), ("delta1", ctypes.c_double), ("cutoff", ctypes.c_double),
-                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("algorithm", ctypes.c_int32)]
 
 
 @dataclass
@@ -44,12 +45,14 @@ class DecoderParams:
     delta1: float = 1e-2
     cutoff: float | None = None
     precision: str = "fp64"
+    algorithm: str = "mps"          # "mps" (Sec. III.D) or "fused" (Remark 9, k <= 4)
 
     def c(self) -> BbpParams:
         prec = FP64 if self.precision == "fp64" else FP32
         cut = self.cutoff if self.cutoff is not None else (1e-13 if prec == FP64 else 1e-7)
+        alg = ALG_MPS if self.algorithm == "mps" else ALG_FUSED
         return BbpParams(self.d, self.k, self.D, self.max_iter, self.p, self.eta, self.delta0,
-                         self.delta1, cut, prec, 0)
+                         self.delta1, cut, prec, alg)
 
     @property
     def m(self) -> int:

@@ -22,7 +22,15 @@ int check_params(const bbp_params* p) {
   if (!(p->eta >= 0.0 && p->eta < 1.0)) return BBP_EINVAL;
   if (!(p->delta0 >= 0.0) || !(p->delta1 >= 0.0) || !(p->cutoff >= 0.0 && p->cutoff < 1.0)) return BBP_EINVAL;
   if (p->precision != BBP_FP64 && p->precision != BBP_FP32) return BBP_EINVAL;
-  if (p->k > bbp::kMaxK || p->D > bbp::kMaxD) return BBP_EUNSUPPORTED;
+  if (p->algorithm != BBP_ALG_MPS && p->algorithm != BBP_ALG_FUSED) return BBP_EINVAL;
+  if (p->algorithm == BBP_ALG_MPS && (p->k > bbp::kMaxK || p->D > bbp::kMaxD)) return BBP_EUNSUPPORTED;
+  if (p->algorithm == BBP_ALG_FUSED) {
+    if (p->k > bbp::kFusedMaxK) return BBP_EUNSUPPORTED;
+    const bbp::Geo g = bbp::make_geo(p->d, p->k);
+    int M = 0, ae = 0;
+    bbp::count_messages(g, 1, &M, &ae);
+    if (bbp::fused_smem_bytes(p->precision, g, M) > 227 * 1024) return BBP_EUNSUPPORTED;
+  }
   return BBP_OK;
 }
 
@@ -38,7 +46,7 @@ Sizes sizes_for(const bbp_params* p, int64_t B) {
   bbp::count_messages(s.g, p->D, &s.M, &s.arena_elems);
   s.m = 2 * p->d * (p->d - 1);
   s.elem = p->precision == BBP_FP64 ? sizeof(double) : sizeof(float);
-  s.arena_bytes = align256((size_t)B * 4 * (size_t)s.arena_elems * s.elem);
+  s.arena_bytes = p->algorithm == BBP_ALG_FUSED ? 0 : align256((size_t)B * 4 * (size_t)s.arena_elems * s.elem);
   s.io_bytes = align256((size_t)B * s.m) + align256((size_t)B * 4 * 8) * 2 +
                align256((size_t)B * 4 * 4) * 2 + align256((size_t)B);
   return s;
@@ -78,9 +86,10 @@ int bbp_decode_batch(const uint8_t* syndromes, int64_t B, const bbp_params* prm,
   if (rc != BBP_OK) return rc;
   if (B < 0 || B > (int64_t(1) << 29)) return BBP_EINVAL;
   if (B == 0) return BBP_OK;
-  if (!syndromes || !logp || !delta || !iters || !flags || !decision || !workspace) return BBP_EINVAL;
-  if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return BBP_EINVAL;
   const Sizes s = sizes_for(prm, B);
+  if (!syndromes || !logp || !delta || !iters || !flags || !decision) return BBP_EINVAL;
+  if (s.arena_bytes > 0 && !workspace) return BBP_EINVAL;
+  if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return BBP_EINVAL;
   if (workspace_bytes < s.arena_bytes) return BBP_ENOSPACE;
   bbp::LaunchArgs a;
   a.geo = s.g; a.M = s.M; a.D = prm->D; a.max_iter = prm->max_iter; a.arena_elems = s.arena_elems;
@@ -88,7 +97,11 @@ int bbp_decode_batch(const uint8_t* syndromes, int64_t B, const bbp_params* prm,
   a.synd = syndromes; a.arena = workspace; a.logp = logp; a.delta = delta; a.iters = iters;
   a.flags = flags; a.decision = decision; a.B = B;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = prm->precision == BBP_FP64 ? bbp::launch_decode_f64(a, st) : bbp::launch_decode_f32(a, st);
+  cudaError_t e;
+  if (prm->algorithm == BBP_ALG_FUSED)
+    e = prm->precision == BBP_FP64 ? bbp::launch_fused_f64(a, st) : bbp::launch_fused_f32(a, st);
+  else
+    e = prm->precision == BBP_FP64 ? bbp::launch_decode_f64(a, st) : bbp::launch_decode_f32(a, st);
   if (e != cudaSuccess) return BBP_ECUDA;
   e = bbp::launch_decide(a, st);
   return e == cudaSuccess ? BBP_OK : BBP_ECUDA;

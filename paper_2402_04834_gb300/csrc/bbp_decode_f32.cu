@@ -5,9 +5,14 @@
 namespace bbp {
 
 cudaError_t launch_decode_f32(const LaunchArgs& a, cudaStream_t st) { return launch_decode_t<float>(a, st); }
+cudaError_t launch_fused_f32(const LaunchArgs& a, cudaStream_t st) { return launch_fused_t<float>(a, st); }
 
 int cta_smem_bytes(int precision, const Geo& g, int M) {
   return precision == 0 ? smem_bytes_for<double>(g, M) : smem_bytes_for<float>(g, M);
+}
+
+int fused_smem_bytes(int precision, const Geo& g, int M) {
+  return precision == 0 ? fused_smem_for<double>(g, M) : fused_smem_for<float>(g, M);
 }
 
 }  // namespace bbp

@@ -1,6 +1,7 @@
 // Instantiation of the decoder kernel for one scalar type.
 #pragma once
 
+#include "bbp_fused.cuh"
 #include "bbp_kernels.cuh"
 #include "bbp_launch.h"
 
@@ -24,6 +25,27 @@ cudaError_t launch_decode_t(const LaunchArgs& a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)(a.B * 4);
   kern<<<grid, kWarps * 32, smem, st>>>(k);
+  return cudaGetLastError();
+}
+
+template <typename T>
+int fused_smem_for(const Geo& g, int M) {
+  return fused_layout<T>(g, M, kFusedWarps).total;
+}
+
+template <typename T>
+cudaError_t launch_fused_t(const LaunchArgs& a, cudaStream_t st) {
+  KArgs<T> k;
+  k.geo = a.geo; k.M = a.M; k.D = a.D; k.max_iter = a.max_iter; k.arena_elems = 0;
+  k.p = a.p; k.eta = a.eta; k.delta0 = a.delta0; k.delta1 = a.delta1; k.cutoff = a.cutoff;
+  k.synd = a.synd; k.arena = nullptr;
+  k.logp = a.logp; k.delta = a.delta; k.iters = a.iters; k.flags = a.flags;
+  const int smem = fused_smem_for<T>(a.geo, a.M);
+  auto kern = fused_kernel<T, kFusedWarps>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)(a.B * 4);
+  kern<<<grid, kFusedWarps * 32, smem, st>>>(k);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,412 @@
+// Fused-block BP (Remark 9; the form the paper ran for k = 1, 2, 4): every
+// k x k block acts as one vertex with four legs of dimension 2^k and the
+// messages are dense vectors, so there is no MPS truncation at all.  Where
+// the MPS form of Sec. III.D truncates nothing, both compute the same
+// numbers.
+//
+// One CTA decodes one (syndrome, coset); all messages live in shared memory
+// (M dense vectors of 2^k).  A warp contracts one block with its incoming
+// messages node by node on a dense state indexed by
+//     [a | rows of the chain | b | v]   (most to least significant bits)
+// where v is the vertical leg inside the current column and a / b carry the
+// top / bottom side message.  A side message m(t_0 .. t_{w-1}) is fed one
+// leg per column through its exact copy / data / copy factorisation: the
+// first floor(w/2) legs are recorded in a, the middle column contracts a
+// with m and leaves in a the values expected for the remaining legs, which
+// the last columns check off.  All dimensions are powers of two, so every
+// index is a bit field.  Every loop is bounded and no CTA waits on another.
+#pragma once
+
+#include "bbp_kernels.cuh"
+
+namespace bbp {
+
+constexpr int kFusedK = 4;                 // largest block side of the fused path
+constexpr int kFusedVec = 1 << kFusedK;    // dense message length
+constexpr int kFusedState = 512;           // 2^(2 + 4 + 2 + 1)
+
+template <typename T>
+struct FusedWS {
+  T s0[kFusedState];
+  T s1[kFusedState];
+  T wn[kFusedK * 16];      // node tensors of the current column
+  T mt[kFusedVec];         // side message A in consumption order
+  T mb[kFusedVec];         // side message B in consumption order
+};
+
+// Shared-memory layout of one fused CTA.
+struct FusedLayout {
+  int synd, frame, msg_of, meta, work, ovl, rlog, misc, msgs, ws, total;
+};
+
+template <typename T>
+BBP_HD FusedLayout fused_layout(const Geo& g, int M, int nwarps) {
+  FusedLayout L;
+  const int m = 2 * g.d * (g.d - 1);
+  int o = 0;
+  L.synd = o;   o = align_up(o + m, 16);
+  L.frame = o;  o = align_up(o + g.W * g.W, 16);
+  L.msg_of = o; o = align_up(o + 2 * g.nb * g.nb * 4, 16);
+  L.meta = o;   o = align_up(o + 2 * M, 16);
+  L.work = o;   o = align_up(o + 2 * 2 * M, 16);
+  L.ovl = o;    o = align_up(o + 8 * M, 16);
+  L.rlog = o;   o = align_up(o + 8 * (g.nb * g.nb + M), 16);
+  L.misc = o;   o = align_up(o + 64, 16);
+  L.msgs = o;   o = align_up(o + (int)sizeof(T) * kFusedVec * M, 16);
+  L.ws = o;     o = align_up(o + nwarps * (int)sizeof(FusedWS<T>), 16);
+  L.total = o;
+  return L;
+}
+
+__device__ __forceinline__ int bitrev(int x, int w) {
+  return (int)(__brev((unsigned)x) >> (32 - w));
+}
+
+struct FState {
+  int ab, h, bb, hv;   // bit widths of a, rows, b, v
+  __device__ __forceinline__ int size() const { return 1 << (ab + h + bb + hv); }
+  __device__ __forceinline__ int idx(int a, int H, int b, int v) const {
+    return ((((a << h) | H) << bb | b) << hv) | v;
+  }
+};
+
+// Contract block f (rotated so that f.dir points right) with its incoming
+// dense messages; leaves the outgoing vector over the chain in ws.s0 and
+// returns the log of the norms taken out (read-out only).
+template <typename T, int K>
+__device__ __noinline__ double fused_sweep(FusedWS<T>& ws, const Ctx<T, K>& c, const T* msgs, const Frame& f,
+                                           bool readout, int lane) {
+  const int h = f.h, nc = f.ncols;
+  T* cur = ws.s0;
+  T* nxt = ws.s1;
+  // Initial state: the message on the side opposite the outgoing one.
+  for (int H = lane; H < (1 << h); H += 32)
+    cur[H] = f.in_idx >= 0 ? msgs[f.in_idx * kFusedVec + H] : (H == 0 ? T(1) : T(0));
+  // Side messages in consumption order.
+  for (int i = lane; i < (1 << nc); i += 32) {
+    const int j = f.rev ? bitrev(i, nc) : i;
+    ws.mt[i] = f.a_idx >= 0 ? msgs[f.a_idx * kFusedVec + j] : T(0);
+    ws.mb[i] = f.b_idx >= 0 ? msgs[f.b_idx * kFusedVec + j] : T(0);
+  }
+  __syncwarp();
+  FState st{0, h, 0, 0};
+  const int sd = nc >> 1;               // the column that holds the data site
+  const int nf = nc - sd - 1;           // legs still expected after it
+  double log_scale = 0.0;
+  for (int t = 0; t < nc; ++t) {
+    for (int e = lane; e < h * 16; e += 32) {
+      const int s = e >> 4, q = e & 15;
+      int i, j;
+      f.node(t, s, &i, &j);
+      ws.wn[e] = node_value<T>(c.frame, c.g.W, c.pI, c.pE, i, j, f.dir, (q >> 3) & 1, (q >> 2) & 1,
+                               (q >> 1) & 1, q & 1);
+    }
+    // Side message A: enters the column as its vertical leg v.
+    {
+      FState ns = st;
+      ns.hv = 1;
+      if (f.a_idx < 0) ns.ab = 0;
+      else if (t < sd) ns.ab = st.ab + 1;
+      else if (t == sd) ns.ab = nf;
+      else ns.ab = st.ab - 1;
+      const int n = ns.size();
+      for (int e = lane; e < n; e += 32) {
+        const int v = e & 1, b = (e >> 1) & ((1 << ns.bb) - 1);
+        const int H = (e >> (1 + ns.bb)) & ((1 << h) - 1), a2 = e >> (1 + ns.bb + h);
+        T val;
+        if (f.a_idx < 0) {
+          val = v == 0 ? cur[st.idx(0, H, b, 0)] : T(0);
+        } else if (t < sd) {
+          val = v == (a2 & 1) ? cur[st.idx(a2 >> 1, H, b, 0)] : T(0);
+        } else if (t == sd) {
+          val = T(0);
+          for (int a = 0; a < (1 << st.ab); ++a)
+            val += ws.mt[(((a << 1) | v) << nf) | a2] * cur[st.idx(a, H, b, 0)];
+        } else {
+          val = cur[st.idx((v << (st.ab - 1)) | a2, H, b, 0)];
+        }
+        nxt[e] = val;
+      }
+      __syncwarp();
+      T* tmp = cur; cur = nxt; nxt = tmp;
+      st = ns;
+    }
+    // The column's nodes, top to bottom: chain position s is row bit h-1-s.
+    for (int s = 0; s < h; ++s) {
+      const int pos = h - 1 - s;
+      const T* w = ws.wn + s * 16;
+      const int n = st.size();
+      for (int e = lane; e < n; e += 32) {
+        const int d = e & 1, b = (e >> 1) & ((1 << st.bb) - 1);
+        const int H = (e >> (1 + st.bb)) & ((1 << h) - 1), a = e >> (1 + st.bb + h);
+        const int r = (H >> pos) & 1, H0 = H & ~(1 << pos);
+        T acc = T(0);
+#pragma unroll
+        for (int l = 0; l < 2; ++l)
+#pragma unroll
+          for (int u = 0; u < 2; ++u)
+            acc += cur[st.idx(a, H0 | (l << pos), b, u)] * w[((l * 2 + r) * 2 + u) * 2 + d];
+        nxt[e] = acc;
+      }
+      __syncwarp();
+      T* tmp = cur; cur = nxt; nxt = tmp;
+    }
+    // Side message B: closes the column's vertical leg.
+    {
+      FState ns = st;
+      ns.hv = 0;
+      if (f.b_idx < 0) ns.bb = 0;
+      else if (t < sd) ns.bb = st.bb + 1;
+      else if (t == sd) ns.bb = nf;
+      else ns.bb = st.bb - 1;
+      const int n = ns.size();
+      for (int e = lane; e < n; e += 32) {
+        const int b2 = e & ((1 << ns.bb) - 1);
+        const int H = (e >> ns.bb) & ((1 << h) - 1), a = e >> (ns.bb + h);
+        T val;
+        if (f.b_idx < 0) {
+          val = cur[st.idx(a, H, 0, 0)];
+        } else if (t < sd) {
+          val = cur[st.idx(a, H, b2 >> 1, b2 & 1)];
+        } else if (t == sd) {
+          val = T(0);
+          for (int b = 0; b < (1 << st.bb); ++b)
+            for (int v = 0; v < 2; ++v)
+              val += ws.mb[(((b << 1) | v) << nf) | b2] * cur[st.idx(a, H, b, v)];
+        } else {
+          val = T(0);
+          for (int v = 0; v < 2; ++v) val += cur[st.idx(a, H, (v << (st.bb - 1)) | b2, v)];
+        }
+        nxt[e] = val;
+      }
+      __syncwarp();
+      T* tmp = cur; cur = nxt; nxt = tmp;
+      st = ns;
+    }
+    if (readout) {   // keep the block value in range; its log goes to the read-out
+      const int n = st.size();
+      T acc = 0;
+      for (int e = lane; e < n; e += 32) acc += cur[e] * cur[e];
+      acc = warp_sum(acc);
+      const T nrm = xsqrt(acc);
+      if (nrm > T(0)) {
+        const T inv = T(1) / nrm;
+        for (int e = lane; e < n; e += 32) cur[e] *= inv;
+        log_scale += log((double)nrm);
+      }
+      __syncwarp();
+    }
+  }
+  if (cur != ws.s0) {
+    for (int H = lane; H < (1 << h); H += 32) ws.s0[H] = cur[H];
+    __syncwarp();
+  }
+  return log_scale;
+}
+
+// Unit L2 norm (Remark 3) of the 2^w vector x; returns the norm.
+template <typename T>
+__device__ __forceinline__ T fused_normalize(T* x, int n, int lane) {
+  T acc = 0;
+  for (int e = lane; e < n; e += 32) acc += x[e] * x[e];
+  acc = warp_sum(acc);
+  const T nrm = xsqrt(acc);
+  const T inv = nrm > T(0) ? T(1) / nrm : T(0);
+  __syncwarp();
+  for (int e = lane; e < n; e += 32) x[e] *= inv;
+  __syncwarp();
+  return nrm;
+}
+
+template <typename T>
+__device__ __forceinline__ double fused_dot(const T* x, const T* y, int n, int lane) {
+  double acc = 0.0;
+  for (int e = lane; e < n; e += 32) acc += (double)x[e] * (double)y[e];
+  return warp_sum(acc);
+}
+
+template <typename T, int NW>
+__global__ void __launch_bounds__(NW * 32) fused_kernel(KArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  using WS = FusedWS<T>;
+  const Geo g = a.geo;
+  const int W = g.W, d = g.d, nb = g.nb, M = a.M;
+  const int m = 2 * d * (d - 1);
+  const FusedLayout Lo = fused_layout<T>(g, M, NW);
+  uint8_t* synd = smem + Lo.synd;
+  uint8_t* frame = smem + Lo.frame;
+  int16_t* msg_of = reinterpret_cast<int16_t*>(smem + Lo.msg_of);
+  int16_t* meta = reinterpret_cast<int16_t*>(smem + Lo.meta);
+  int16_t* work = reinterpret_cast<int16_t*>(smem + Lo.work);
+  double* ovl = reinterpret_cast<double*>(smem + Lo.ovl);
+  double* rlog = reinterpret_cast<double*>(smem + Lo.rlog);
+  int* misc = reinterpret_cast<int*>(smem + Lo.misc);
+  double* dsh = reinterpret_cast<double*>(smem + Lo.misc + 48);
+  T* msgs = reinterpret_cast<T*>(smem + Lo.msgs);
+  WS* wsa = reinterpret_cast<WS*>(smem + Lo.ws);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const long long cta = blockIdx.x;
+  const long long shot = cta >> 2;
+  const int coset = (int)(cta & 3);
+
+  for (int i = tid; i < m; i += NW * 32) synd[i] = a.synd[shot * m + i];
+  __syncthreads();
+  const int bx = (coset == 1 || coset == 2), bz = (coset == 2 || coset == 3);
+  for (int e = tid; e < W * W; e += NW * 32) {
+    const int i = e / W, j = e % W;
+    int fx = 0, fz = 0;
+    if ((i & 1) == 0 && (j & 1) == 0) {
+      const int r = i >> 1, cc = j >> 1;
+      for (int c2 = 0; c2 < cc; ++c2) fx ^= synd[r * (d - 1) + c2];
+      for (int r2 = 0; r2 < r; ++r2) fz ^= synd[d * (d - 1) + r2 * d + cc];
+      if (bx && r == 0) fx ^= 1;
+      if (bz && cc == 0) fz ^= 1;
+    }
+    frame[e] = (uint8_t)(fx | (fz << 1));
+  }
+  if (tid == 0) {
+    int idx = 0, n0 = 0, n1 = 0;
+    for (int I = 0; I < nb; ++I)
+      for (int J = 0; J < nb; ++J)
+        for (int dir = 0; dir < 4; ++dir) {
+          const int key = (I * nb + J) * 4 + dir;
+          if (g.has(I, J, dir)) {
+            msg_of[key] = (int16_t)idx;
+            meta[idx] = (int16_t)key;
+            if (((I + J) & 1) == 0) work[n0++] = (int16_t)idx;
+            else work[M + n1++] = (int16_t)idx;
+            ++idx;
+          } else {
+            msg_of[key] = -1;
+          }
+        }
+    misc[0] = 0; misc[1] = 0; misc[2] = n0; misc[3] = n1;
+  }
+  __syncthreads();
+
+  Ctx<T, kFusedK> c;
+  c.g = g; c.D = 0; c.cutoff2 = T(0);
+  c.pI = (T)(1.0 - a.p); c.pE = (T)(a.p / 3.0);
+  c.frame = frame; c.msg_of = msg_of; c.msg_off = nullptr; c.dims = nullptr;
+  c.arena = nullptr; c.e0 = nullptr; c.cta_flags = &misc[1];
+
+  // Remark 2: uniform messages of unit norm.
+  for (int idx = warp; idx < M; idx += NW) {
+    const int key = meta[idx];
+    const int w = g.side_len(key / 4 / nb, (key / 4) % nb, key & 3);
+    const T u = (T)rsqrt((double)(1 << w));
+    for (int i = lane; i < kFusedVec; i += 32) msgs[idx * kFusedVec + i] = i < (1 << w) ? u : T(0);
+  }
+  __syncthreads();
+
+  WS& ws = wsa[warp];
+  double delta = 0.0;
+  int it_done = 0;
+  for (int it = 1; it <= a.max_iter && M > 0; ++it) {
+    for (int color = 0; color < 2; ++color) {       // Remark 8
+      const int nwork = misc[2 + color];
+      const int16_t* lst = work + color * M;
+      for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(&misc[0], 1);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= nwork) break;
+        const int idx = lst[item];
+        const int key = meta[idx];
+        const int I = key / 4 / nb, J = (key / 4) % nb, dir = key & 3;
+        const Frame f = make_frame(c, I, J, dir);
+        fused_sweep(ws, c, msgs, f, false, lane);
+        const int n = 1 << f.h;
+        T* x = ws.s0;
+        T* old = msgs + idx * kFusedVec;
+        fused_normalize(x, n, lane);                                  // Remark 3
+        const T eta = (T)a.eta;
+        for (int e = lane; e < n; e += 32) x[e] = (T(1) - eta) * x[e] + eta * old[e];   // Remark 7
+        __syncwarp();
+        fused_normalize(x, n, lane);
+        const double o = fused_dot(x, old, n, lane);
+        __syncwarp();
+        for (int e = lane; e < n; e += 32) old[e] = x[e];
+        if (lane == 0) ovl[idx] = o;
+        __syncwarp();
+      }
+      __syncthreads();
+      if (tid == 0) misc[0] = 0;
+      __syncthreads();
+    }
+    if (warp == 0) {                                   // Remark 4
+      double acc = 0.0;
+      for (int i = lane; i < M; i += 32) acc += 2.0 - 2.0 * ovl[i] * ovl[i];
+      acc = warp_sum(acc);
+      if (lane == 0) dsh[0] = sqrt(fmax(acc, 0.0)) / M;
+    }
+    __syncthreads();
+    delta = dsh[0];
+    it_done = it;
+    if (delta < a.delta0) break;
+  }
+
+  // Lemma 1 read-out.
+  if (tid == 0) {
+    int ne = 0;
+    for (int idx = 0; idx < M; ++idx) {
+      const int dir = meta[idx] & 3;
+      if (dir == kDirR || dir == kDirD) work[ne++] = (int16_t)idx;
+    }
+    misc[4] = ne;
+    misc[0] = 0;
+  }
+  __syncthreads();
+  const int nedge = misc[4];
+  const int nblk = nb * nb;
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(&misc[0], 1);
+    item = __shfl_sync(kFull, item, 0);
+    if (item >= nblk + nedge) break;
+    if (item < nblk) {
+      const int I = item / nb, J = item % nb;
+      const Frame f = make_frame(c, I, J, kDirR);
+      const double ls = fused_sweep(ws, c, msgs, f, true, lane);
+      const int right = J + 1 < nb ? msg_index(c, I, J + 1, kDirL) : -1;
+      double z;
+      if (right >= 0) z = fused_dot(ws.s0, msgs + right * kFusedVec, 1 << f.h, lane);
+      else z = (double)ws.s0[0];
+      if (lane == 0) {
+        rlog[item] = ls + log(fabs(z));
+        if (!(z > 0.0)) atomicOr(&misc[1], kFlagBlock);
+      }
+      __syncwarp();
+    } else {
+      const int e = item - nblk;
+      const int idx = work[e];
+      const int key = meta[idx];
+      const int I = key / 4 / nb, J = (key / 4) % nb, dir = key & 3;
+      const int other = dir == kDirR ? msg_index(c, I, J + 1, kDirL) : msg_index(c, I + 1, J, kDirU);
+      const int w = g.side_len(I, J, dir);
+      const double o = fused_dot(msgs + idx * kFusedVec, msgs + other * kFusedVec, 1 << w, lane);
+      if (lane == 0) {
+        rlog[item] = -log(fabs(o));
+        if (!(o > 0.0)) atomicOr(&misc[1], kFlagOverlap);
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double acc = 0.0;
+    for (int i = lane; i < nblk + nedge; i += 32) acc += rlog[i];
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      int fl = misc[1];
+      if (!isfinite(acc)) fl |= kFlagNonfinite;
+      if (!(delta < a.delta1)) fl |= kFlagUntrusted;
+      a.logp[cta] = acc;
+      a.delta[cta] = delta;
+      a.iters[cta] = it_done;
+      a.flags[cta] = fl;
+    }
+  }
+}
+
+}  // namespace bbp

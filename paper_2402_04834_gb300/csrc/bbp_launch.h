@@ -33,6 +33,13 @@ struct LaunchArgs {
 // Shared memory of one CTA in bytes for the given precision (0 = fp64, 1 = fp32).
 int cta_smem_bytes(int precision, const Geo& g, int M);
 
+// Fused-block path (Remark 9): block side k <= kFusedMaxK, messages in shared memory.
+constexpr int kFusedMaxK = 4;
+constexpr int kFusedWarps = 8;
+int fused_smem_bytes(int precision, const Geo& g, int M);
+
+cudaError_t launch_fused_f64(const LaunchArgs& a, cudaStream_t st);
+cudaError_t launch_fused_f32(const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_decode_f64(const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_decode_f32(const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_decide(const LaunchArgs& a, cudaStream_t st);

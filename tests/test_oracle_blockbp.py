@@ -108,3 +108,17 @@ def test_uniform_noise_free_network_logp():
     p = 1e-6
     r = bb.run_blockbp(coset_network(lat, s, 0, p), bb.Params(d=d, k=3, D=4, p=p, max_iter=5, delta0=0.0))
     assert abs(r.logp - lat.n * math.log(1 - p)) < 1e-4
+
+
+def test_dense_and_mps_oracles_agree_at_d11_k4_D8():
+    # At d = 11, k = 4, D = 8 the MPS form truncates nothing on this shot, so
+    # the two independent implementations must give the same log P.
+    d, p = 11, 0.10
+    lat = Lattice(d)
+    _, _, S = synth.sample_syndromes(synth.workload_seed(2, 2), 5, 1, d, p)
+    stats = M.Stats()
+    T = coset_network(lat, S[0], 1, p)
+    r = bb.run_blockbp(T, bb.Params(d=d, k=4, D=8, p=p, max_iter=4, delta0=0.0), stats)
+    lp, dl, it, _ = run_naive(T, 4, 4, 0.1, 0.0)
+    assert stats.truncations == 0
+    assert abs(r.logp - lp) < 1e-9
