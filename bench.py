@@ -2,10 +2,12 @@
 
 Workload (one step = one batch through the whole hot path): the distance-11
 planar surface code under depolarizing noise p = 0.10, 10^4 seeded synthetic
-syndromes per GPU, blockBP with 4x4-node blocks, bond D = 8, max-iter 20,
-delta0 = 1e-4, delta1 = 1e-2, eta = 0.1 (Sec. IV parameters).  The headline
-path is the FP32 kernel (tensors, QR and SVD in float; logs, Delta and the
-read-out in double); the plain FP64 kernel is timed beside it on a subset.
+syndromes per GPU, blockBP with 4x4-node blocks, max-iter 20, delta0 = 1e-4,
+delta1 = 1e-2, eta = 0.1 (Sec. IV parameters), D = 8 for the MPS form.
+The headline path is the fused-block form of Remark 9 (the form the paper
+ran for k = 4) in FP32 with double logs and read-out.  Timed beside it on
+subsets of the same batch: the plain FP64 blockBP with MPS messages (the
+denominator of the metric), the FP64 fused form and the FP32 MPS form.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -50,25 +52,96 @@ FP64_FMA_PER_SM_CLK = 2
 
 
 def oracle_one(args):
-    """Oracle decode of one shot (runs in a spawned worker)."""
-    s, max_iter, delta0 = args
+    """Oracle decode of one shot (runs in a spawned worker).
+
+    ``fused`` selects the dense fused-block oracle (Remark 9), otherwise the
+    MPS blockBP oracle; both apply the decision rule of Algorithm 1."""
+    s, max_iter, delta0, algorithm = args
+    s = np.asarray(s, dtype=np.uint8)
     from oracle import blockbp as bb
+    if algorithm == "fused":
+        from oracle.lattice import Lattice
+        from oracle.naive import run_naive
+        from oracle.tn import coset_network
+        lat = Lattice(D_CODE)
+        lp, dl, its = [], [], []
+        for L in range(4):
+            a, b, it, _ = run_naive(coset_network(lat, s, L, P_NOISE), K_BLOCK, max_iter, ETA, delta0)
+            lp.append(a)
+            dl.append(b)
+            its.append(it)
+        flags = [0 if x < DELTA1 else 1 for x in dl]
+        return None, int(bb.decide(lp, dl, flags)), its
     P = bb.Params(d=D_CODE, k=K_BLOCK, D=D_BOND, p=P_NOISE, max_iter=max_iter, eta=ETA,
                   delta0=delta0, delta1=DELTA1)
-    r = bb.decode(np.asarray(s, dtype=np.uint8), P)
+    r = bb.decode(s, P)
     return r["stats"].flops, int(r["decision"]), [int(x) for x in r["iters"]]
 
 
-def run_oracle_sample(first_shot: int, n: int, procs: int):
+def run_oracle_sample(first_shot: int, n: int, procs: int, algorithm: str):
     """Decode n shots of the workload with the oracle on ``procs`` processes."""
     _, _, S = synth.sample_syndromes(SEED, first_shot, n, D_CODE, P_NOISE)
     ctx = mp.get_context("spawn")
     with ctx.Pool(procs) as pool:
         pool.map(int, range(procs))                 # workers up before the clock starts
         t0 = time.perf_counter()
-        res = pool.map(oracle_one, [(S[b].tolist(), MAX_ITER, DELTA0) for b in range(n)], chunksize=1)
+        res = pool.map(oracle_one, [(S[b].tolist(), MAX_ITER, DELTA0, algorithm) for b in range(n)],
+                       chunksize=1)
         dt = time.perf_counter() - t0
     return dt, res
+
+
+def fused_flops(d: int, k: int):
+    """Arithmetic of the fused kernel (multiply-adds count 2), per coset.
+
+    Returns (per BP iteration, read-out): the node-by-node contraction of
+    every block towards each neighbour (side-message data columns, four-term
+    node updates, copy-out sums), normalisation, damping and overlaps, then
+    the Lemma 1 read-out.  Mirrors the loop structure of the kernel."""
+    W = 2 * d - 1
+    rng = [(a, min(a + k, W)) for a in range(0, W, k)]
+    nb = len(rng)
+
+    def sweep(h, nc, has_a, has_b, readout):
+        fl = 0.0
+        ab = bb = 0
+        sd, nf = nc >> 1, nc - (nc >> 1) - 1
+        for t in range(nc):
+            nab = 0 if not has_a else (ab + 1 if t < sd else (nf if t == sd else ab - 1))
+            size = 2 ** (nab + h + bb + 1)
+            if has_a and t == sd:
+                fl += 2.0 * size * 2 ** ab
+            ab = nab
+            fl += h * 2.0 * size * 4
+            nbb = 0 if not has_b else (bb + 1 if t < sd else (nf if t == sd else bb - 1))
+            size_b = 2 ** (ab + h + nbb)
+            if has_b and t == sd:
+                fl += 2.0 * size_b * 2 ** (bb + 1)
+            elif has_b and t > sd:
+                fl += 1.0 * size_b * 2
+            bb = nbb
+            if readout:
+                fl += 3.0 * 2 ** (ab + h + bb)
+        return fl
+
+    per_iter = 0.0
+    readout = 0.0
+    for I in range(nb):
+        for J in range(nb):
+            hr = rng[I][1] - rng[I][0]
+            hc = rng[J][1] - rng[J][0]
+            for dr, (di, dj) in enumerate(((0, 1), (0, -1), (1, 0), (-1, 0))):
+                if not (0 <= I + di < nb and 0 <= J + dj < nb):
+                    continue
+                if dr < 2:
+                    h, nc, ha, hb = hr, hc, I > 0, I + 1 < nb
+                else:
+                    h, nc, ha, hb = hc, hr, J > 0, J + 1 < nb
+                per_iter += sweep(h, nc, ha, hb, False) + 12.0 * 2 ** h
+                if dr in (0, 2):
+                    readout += 2.0 * 2 ** h
+            readout += sweep(hr, hc, I > 0, I + 1 < nb, True) + 2.0 * 2 ** hr
+    return per_iter, readout
 
 
 class ClockSampler:
@@ -136,10 +209,10 @@ def reference_arm(args):
     procs = args.cpu_procs or min(os.cpu_count() or 1, 32)
     n = procs
     for w in range(args.warmup):
-        run_oracle_sample(w * n, n, procs)
+        run_oracle_sample(w * n, n, procs, args.algorithm)
     times = []
     for s in range(args.steps):
-        dt, _ = run_oracle_sample((args.warmup + s) * n, n, procs)
+        dt, _ = run_oracle_sample((args.warmup + s) * n, n, procs, args.algorithm)
         times.append(dt)
     tot = sum(times)
     value = n * args.steps / tot
@@ -148,9 +221,10 @@ def reference_arm(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "batch_per_step": n},
+        "config": {"workload": WORKLOAD, "batch_per_step": n, "algorithm": args.algorithm},
         "cpu_baseline": {"value": value, "unit": "syndromes/s", "cores": procs, "kind": "oracle",
-                         "sample": f"{n} shots of the workload per step, one process per core"},
+                         "sample": f"{n} shots of the workload per step, one process per core, "
+                                   f"{'dense fused-block' if args.algorithm == 'fused' else 'MPS'} oracle"},
         "e2e": {"value": value, "unit": "syndromes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -161,6 +235,7 @@ def ours(args):
 
     import paper_2402_04834_gb300 as pkg
     from paper_2402_04834_gb300 import _lib
+    from paper_2402_04834_gb300.sharding import reduce_max, shot_range
     if not os.path.exists(_lib.LIB_PATH):
         from paper_2402_04834_gb300.build import build
         build()
@@ -182,8 +257,9 @@ def ours(args):
 
     B = args.batch
     prm = pkg.DecoderParams(d=D_CODE, k=K_BLOCK, D=D_BOND, p=P_NOISE, max_iter=MAX_ITER, eta=ETA,
-                            delta0=DELTA0, delta1=DELTA1, precision=args.precision)
-    first = rank * B
+                            delta0=DELTA0, delta1=DELTA1, precision=args.precision,
+                            algorithm=args.algorithm)
+    first, _ = shot_range(rank, world, B)
     _, _, S = synth.sample_syndromes(SEED, first, B, D_CODE, P_NOISE)
     S_host = torch.from_numpy(S).pin_memory()
     S_dev = S_host.to(dev)
@@ -210,10 +286,7 @@ def ours(args):
         wall = time.perf_counter() - t0
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     dev_ms = sum(step_ms)
-    t = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    dev_ms_max = float(t.item())
+    dev_ms_max = reduce_max(dev_ms, dist, dev)
     value = world * B * args.steps / (dev_ms_max / 1e3)
     iters_mean = float(out["iters"].double().mean().item())
     decisions = out["decision"].cpu().numpy()
@@ -229,65 +302,68 @@ def ours(args):
         t1 = time.perf_counter()
         pkg.decode_host(hsyn, prm, workspace=ws, out=hout, device=dev)
         e2e_t.append(time.perf_counter() - t1)
-    te = torch.tensor([sum(e2e_t)], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * B * args.steps / float(te.item())
+    e2e_value = world * B * args.steps / reduce_max(sum(e2e_t), dist, dev)
 
-    # Plain FP64 GPU blockBP on a subset of the same workload.
-    fp64 = None
-    if args.fp64_batch > 0:
-        B64 = min(args.fp64_batch, B)
-        p64 = pkg.DecoderParams(d=D_CODE, k=K_BLOCK, D=D_BOND, p=P_NOISE, max_iter=MAX_ITER, eta=ETA,
-                                delta0=DELTA0, delta1=DELTA1, precision="fp64")
-        s64 = S_dev[:B64].contiguous()
-        o64 = pkg.decode(s64, p64, workspace=ws)
+    # Comparison legs on subsets of the same batch: the plain FP64 blockBP with
+    # MPS messages (the denominator of the metric) and the other combinations.
+    def leg(alg, prec, nshots):
+        if nshots <= 0:
+            return None
+        nshots = min(nshots, B)
+        pp = pkg.DecoderParams(d=D_CODE, k=K_BLOCK, D=D_BOND, p=P_NOISE, max_iter=MAX_ITER, eta=ETA,
+                               delta0=DELTA0, delta1=DELTA1, precision=prec, algorithm=alg)
+        sub = S_dev[:nshots].contiguous()
+        o = pkg.decode(sub, pp, workspace=ws)
         barrier()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        ms64 = 0.0
         for i in range(2):
             flush.fill_(float(i))
             ev[2 * i].record(stream)
-            o64 = pkg.decode(s64, p64, workspace=ws, out=o64)
+            o = pkg.decode(sub, pp, workspace=ws, out=o)
             ev[2 * i + 1].record(stream)
         barrier()
-        ms64 = ev[0].elapsed_time(ev[1]) + ev[2].elapsed_time(ev[3])
-        fp64_val = 2 * B64 / (ms64 / 1e3)
-        agree = float(np.mean(o64["decision"].cpu().numpy() == decisions[:B64]))
-        fp64 = {"value": fp64_val, "unit": "syndromes/s", "batch": B64,
-                "mean_iters": float(o64["iters"].double().mean().item()),
-                "decision_agreement_with_headline": agree,
-                "headline_speedup": value / world / fp64_val}
+        ms = ev[0].elapsed_time(ev[1]) + ev[2].elapsed_time(ev[3])
+        val = 2 * nshots / (ms / 1e3)
+        agree = float(np.mean(o["decision"].cpu().numpy() == decisions[:nshots]))
+        return {"value": val, "unit": "syndromes/s", "batch": nshots, "algorithm": alg, "precision": prec,
+                "mean_iters": float(o["iters"].double().mean().item()),
+                "decision_agreement_with_headline": agree, "headline_speedup": value / world / val}
+
+    fp64_mps = leg("mps", "fp64", args.fp64_batch)
+    legs = {"fp64_fused": leg("fused", "fp64", args.other_batch),
+            "fp32_mps": leg("mps", "fp32", args.other_batch // 4)}
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
 
-    # Oracle on a bounded sample: CPU baseline and the algorithmic flop count.
+    # Oracle on a bounded sample of the same workload: the CPU baseline.
     cpu = None
-    flops_per_synd = None
     if args.cpu_baseline and world == 1:
         procs = args.cpu_procs or min(os.cpu_count() or 1, 32)
-        dt, res = run_oracle_sample(0, procs, procs)
-        flops_per_synd = float(np.mean([r[0] for r in res]))
+        dt, res = run_oracle_sample(0, procs, procs, args.algorithm)
         agree = float(np.mean([r[1] == int(decisions[i]) for i, r in enumerate(res)]))
         cpu = {"value": procs / dt, "unit": "syndromes/s", "cores": procs, "kind": "oracle",
-               "sample": f"shots 0..{procs - 1} of the workload, one per process ({dt:.1f} s)",
+               "sample": (f"shots 0..{procs - 1} of the workload, one per process ({dt:.1f} s), "
+                          f"{'dense fused-block' if args.algorithm == 'fused' else 'MPS'} oracle"),
                "decision_agreement": agree}
 
+    # Roofline of the dominant kernel: its arithmetic per launch over its time.
     fp = 1 if args.precision == "fp32" else 0
     per_clk = FP32_FMA_PER_SM_CLK if fp else FP64_FMA_PER_SM_CLK
     peak = 2.0 * per_clk * N_SM * SM_MAX_MHZ * 1e6 / 1e12
     roof = None
-    if flops_per_synd is not None:
+    if args.algorithm == "fused":
+        f_it, f_ro = fused_flops(D_CODE, K_BLOCK)
+        flops = float(out["iters"].double().sum().item()) * f_it + B * 4 * f_ro
         kern_s = (dev_ms / args.steps) / 1e3
-        achieved = flops_per_synd * B / kern_s / 1e12
+        achieved = flops / kern_s / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": "decode_kernel", "peak_source": ("FP32 FMA lanes x 2 x SMs x max clock"
-                                                          if fp else "FP64 DFMA/clk/SM x 2 x SMs x max clock"),
-                "flops_per_syndrome": flops_per_synd}
+                "frac": achieved / peak, "traffic": None, "kernel": "fused_kernel",
+                "peak_source": ("derived: 128 FP32 lanes x 2 x 152 SMs x 2070 MHz" if fp
+                                else "derived: 2 FP64 FMA/clk/SM x 2 x 152 SMs x 2070 MHz"),
+                "flops_per_syndrome": flops / B}
 
     line = {
         "metric": METRIC, "value": value, "unit": "syndromes/s", "n_gpus": world,
@@ -296,13 +372,15 @@ def ours(args):
         "dtype": "f32" if fp else "f64",
         "data": "synthetic: seeded i.i.d. depolarizing errors (SplitMix64 counter RNG) and their syndromes",
         "config": {"workload": WORKLOAD, "batch_per_gpu": B, "precision": args.precision,
-                   "l2": "256 MB buffer written before every timed step; message arena larger than L2",
+                   "algorithm": args.algorithm,
+                   "l2": "flushed: a 256 MB buffer is written before every timed step",
                    "mean_iters": iters_mean, "wall_s": wall},
         "clocks": clk.summary(),
         "e2e": {"value": e2e_value, "unit": "syndromes/s", "h2d_bytes_per_step": int(B * S.shape[1]),
                 "d2h_bytes_per_step": int(B * (1 + 32))},
         "gpu_launches": 2 * args.steps,
-        "roofline": roof, "cpu_baseline": cpu, "fp64_gpu": fp64,
+        "roofline": roof, "cpu_baseline": cpu,
+        "plain_fp64_gpu": fp64_mps, "other_paths": legs,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -317,7 +395,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=10000)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--fp64-batch", type=int, default=1024)
+    ap.add_argument("--algorithm", default="fused", choices=["fused", "mps"])
+    ap.add_argument("--fp64-batch", type=int, default=512)
+    ap.add_argument("--other-batch", type=int, default=4096)
     ap.add_argument("--cpu-procs", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     args = ap.parse_args()
