@@ -26,7 +26,7 @@ constexpr int kFusedVec = 1 << kFusedK;    // dense message length
 constexpr int kFusedState = 512;           // 2^(2 + 4 + 2 + 1)
 
 template <typename T>
-struct FusedWS {
+struct __align__(16) FusedWS {
   T s0[kFusedState];
   T s1[kFusedState];
   T wn[kFusedK * 16];      // node tensors of the current column
@@ -57,6 +57,10 @@ BBP_HD FusedLayout fused_layout(const Geo& g, int M, int nwarps) {
   L.total = o;
   return L;
 }
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
 
 __device__ __forceinline__ int bitrev(int x, int w) {
   return (int)(__brev((unsigned)x) >> (32 - w));
@@ -101,7 +105,8 @@ __device__ __noinline__ double fused_sweep(FusedWS<T>& ws, const Ctx<T, K>& c, c
       ws.wn[e] = node_value<T>(c.frame, c.g.W, c.pI, c.pE, i, j, f.dir, (q >> 3) & 1, (q >> 2) & 1,
                                (q >> 1) & 1, q & 1);
     }
-    // Side message A: enters the column as its vertical leg v.
+    // Side message A: enters the column as its vertical leg v.  Output
+    // entries come in pairs (v = 0, 1) sharing (a, rows, b).
     {
       FState ns = st;
       ns.hv = 1;
@@ -109,44 +114,61 @@ __device__ __noinline__ double fused_sweep(FusedWS<T>& ws, const Ctx<T, K>& c, c
       else if (t < sd) ns.ab = st.ab + 1;
       else if (t == sd) ns.ab = nf;
       else ns.ab = st.ab - 1;
-      const int n = ns.size();
-      for (int e = lane; e < n; e += 32) {
-        const int v = e & 1, b = (e >> 1) & ((1 << ns.bb) - 1);
-        const int H = (e >> (1 + ns.bb)) & ((1 << h) - 1), a2 = e >> (1 + ns.bb + h);
-        T val;
+      using V2 = typename Vec2<T>::type;
+      const int np = ns.size() >> 1;
+      const int hb = h + st.bb;                        // bits of (rows, b)
+      const int low = (1 << hb) - 1;
+      for (int e2 = lane; e2 < np; e2 += 32) {
+        const int a2 = e2 >> hb, hbv = e2 & low;       // (rows, b) part is shared by in and out
+        V2 o;
         if (f.a_idx < 0) {
-          val = v == 0 ? cur[st.idx(0, H, b, 0)] : T(0);
+          o.x = cur[e2]; o.y = T(0);
         } else if (t < sd) {
-          val = v == (a2 & 1) ? cur[st.idx(a2 >> 1, H, b, 0)] : T(0);
+          const T x = cur[((a2 >> 1) << hb) | hbv];
+          if (a2 & 1) { o.x = T(0); o.y = x; } else { o.x = x; o.y = T(0); }
         } else if (t == sd) {
-          val = T(0);
-          for (int a = 0; a < (1 << st.ab); ++a)
-            val += ws.mt[(((a << 1) | v) << nf) | a2] * cur[st.idx(a, H, b, 0)];
+          T s0 = T(0), s1 = T(0);
+          for (int a = 0; a < (1 << st.ab); ++a) {
+            const T x = cur[(a << hb) | hbv];
+            s0 += ws.mt[((a << 1) << nf) | a2] * x;
+            s1 += ws.mt[(((a << 1) | 1) << nf) | a2] * x;
+          }
+          o.x = s0; o.y = s1;
         } else {
-          val = cur[st.idx((v << (st.ab - 1)) | a2, H, b, 0)];
+          o.x = cur[(a2 << hb) | hbv];
+          o.y = cur[(((1 << (st.ab - 1)) | a2) << hb) | hbv];
         }
-        nxt[e] = val;
+        *reinterpret_cast<V2*>(nxt + 2 * e2) = o;
       }
       __syncwarp();
       T* tmp = cur; cur = nxt; nxt = tmp;
       st = ns;
     }
     // The column's nodes, top to bottom: chain position s is row bit h-1-s.
+    // Each lane takes quads of entries that differ only in the node's row bit
+    // (l -> r) and in v (u -> d): out[r][d] = sum_{l,u} in[l][u] w[l][r][u][d],
+    // read and written as two pairs of adjacent entries.
     for (int s = 0; s < h; ++s) {
-      const int pos = h - 1 - s;
-      const T* w = ws.wn + s * 16;
-      const int n = st.size();
-      for (int e = lane; e < n; e += 32) {
-        const int d = e & 1, b = (e >> 1) & ((1 << st.bb) - 1);
-        const int H = (e >> (1 + st.bb)) & ((1 << h) - 1), a = e >> (1 + st.bb + h);
-        const int r = (H >> pos) & 1, H0 = H & ~(1 << pos);
-        T acc = T(0);
+      const int P = (h - 1 - s) + st.bb + 1;          // bit of the node's row in the index
+      const int bitP = 1 << P;
+      T w[16];
 #pragma unroll
-        for (int l = 0; l < 2; ++l)
-#pragma unroll
-          for (int u = 0; u < 2; ++u)
-            acc += cur[st.idx(a, H0 | (l << pos), b, u)] * w[((l * 2 + r) * 2 + u) * 2 + d];
-        nxt[e] = acc;
+      for (int q = 0; q < 16; ++q) w[q] = ws.wn[s * 16 + q];
+      const int nq = st.size() >> 2;
+      const int lowmask = (1 << (P - 1)) - 1;
+      using V2 = typename Vec2<T>::type;
+      for (int g = lane; g < nq; g += 32) {
+        const int base = ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
+        const V2 i0 = *reinterpret_cast<const V2*>(cur + base);          // (l=0,u=0), (l=0,u=1)
+        const V2 i1 = *reinterpret_cast<const V2*>(cur + (base | bitP)); // (l=1,u=0), (l=1,u=1)
+        V2 o0, o1;
+        // w index: ((l*2 + r)*2 + u)*2 + d
+        o0.x = i0.x * w[0] + i0.y * w[2] + i1.x * w[8] + i1.y * w[10];     // r=0, d=0
+        o0.y = i0.x * w[1] + i0.y * w[3] + i1.x * w[9] + i1.y * w[11];     // r=0, d=1
+        o1.x = i0.x * w[4] + i0.y * w[6] + i1.x * w[12] + i1.y * w[14];    // r=1, d=0
+        o1.y = i0.x * w[5] + i0.y * w[7] + i1.x * w[13] + i1.y * w[15];    // r=1, d=1
+        *reinterpret_cast<V2*>(nxt + base) = o0;
+        *reinterpret_cast<V2*>(nxt + (base | bitP)) = o1;
       }
       __syncwarp();
       T* tmp = cur; cur = nxt; nxt = tmp;
@@ -160,27 +182,29 @@ __device__ __noinline__ double fused_sweep(FusedWS<T>& ws, const Ctx<T, K>& c, c
       else if (t == sd) ns.bb = nf;
       else ns.bb = st.bb - 1;
       const int n = ns.size();
-      for (int e = lane; e < n; e += 32) {
-        const int b2 = e & ((1 << ns.bb) - 1);
-        const int H = (e >> ns.bb) & ((1 << h) - 1), a = e >> (ns.bb + h);
-        T val;
-        if (f.b_idx < 0) {
-          val = cur[st.idx(a, H, 0, 0)];
-        } else if (t < sd) {
-          val = cur[st.idx(a, H, b2 >> 1, b2 & 1)];
-        } else if (t == sd) {
-          val = T(0);
-          for (int b = 0; b < (1 << st.bb); ++b)
-            for (int v = 0; v < 2; ++v)
-              val += ws.mb[(((b << 1) | v) << nf) | b2] * cur[st.idx(a, H, b, v)];
-        } else {
-          val = T(0);
-          for (int v = 0; v < 2; ++v) val += cur[st.idx(a, H, (v << (st.bb - 1)) | b2, v)];
+      if (!(f.b_idx >= 0 && t < sd)) {   // recording v as b's new low bit changes no index
+        for (int e = lane; e < n; e += 32) {
+          T val;
+          if (f.b_idx < 0) {
+            val = cur[e << 1];                          // v = 0, b has no bits
+          } else if (t == sd) {
+            const int b2 = e & ((1 << ns.bb) - 1), ah = e >> ns.bb;   // (a, rows)
+            val = T(0);
+            for (int b = 0; b < (1 << st.bb); ++b) {
+              const int bi = ((ah << st.bb) | b) << 1;
+              val += ws.mb[((b << 1) << nf) | b2] * cur[bi] + ws.mb[(((b << 1) | 1) << nf) | b2] * cur[bi | 1];
+            }
+          } else {
+            const int b2 = e & ((1 << ns.bb) - 1), ah = e >> ns.bb;
+            const int hi0 = ((ah << st.bb) | b2) << 1;                        // b top bit 0, v = 0
+            const int hi1 = ((ah << st.bb) | (1 << (st.bb - 1)) | b2) << 1 | 1; // b top bit 1, v = 1
+            val = cur[hi0] + cur[hi1];
+          }
+          nxt[e] = val;
         }
-        nxt[e] = val;
+        __syncwarp();
+        T* tmp = cur; cur = nxt; nxt = tmp;
       }
-      __syncwarp();
-      T* tmp = cur; cur = nxt; nxt = tmp;
       st = ns;
     }
     if (readout) {   // keep the block value in range; its log goes to the read-out
@@ -225,8 +249,13 @@ __device__ __forceinline__ double fused_dot(const T* x, const T* y, int n, int l
   return warp_sum(acc);
 }
 
+// Resident CTAs per SM the register budget is sized for: shared memory holds
+// four FP32 CTAs or two FP64 ones at d = 11.
+template <typename T> struct FusedMinBlocks { static constexpr int value = 4; };
+template <> struct FusedMinBlocks<double> { static constexpr int value = 2; };
+
 template <typename T, int NW>
-__global__ void __launch_bounds__(NW * 32) fused_kernel(KArgs<T> a) {
+__global__ void __launch_bounds__(NW * 32, FusedMinBlocks<T>::value) fused_kernel(KArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   using WS = FusedWS<T>;
   const Geo g = a.geo;
