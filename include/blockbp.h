@@ -191,6 +191,73 @@ int bbp_decode_batch_static(const uint8_t* syndromes, int64_t B, const bbp_param
                             double* logp, double* delta, int32_t* iters, int32_t* flags,
                             int8_t* decision, void* stream);
 
+/*
+ * Learned warm start (fused path only).  The paper starts BP from uniform
+ * messages (Remark 2); these calls let a small network propose the initial
+ * message of every directed block edge instead, and train that network on
+ * converged messages.  Rows are ordered (syndrome, coset, message); M is the
+ * number of directed block edges (bbp_message_count).  Cold start remains
+ * the default and the fallback.
+ */
+#define BBP_WARM_FEATURES 256        /* features per message */
+#define BBP_WARM_HIDDEN 256          /* width of the two hidden layers */
+#define BBP_WARM_OUT 16              /* outputs: logits of a 2^k <= 16 message */
+#define BBP_WARM_MAX_ROWS 4194240    /* rows per infer / train call */
+
+/* Number of directed block edges M of (d, k). */
+int bbp_message_count(const bbp_params* prm, int32_t* M);
+
+/*
+ * bbp_message_features -- features of every message of B syndromes: a 7 x 7
+ * window of the coset network around the message's side, read in the frame
+ * rotated so the message points right (channels: inside the grid, qubit,
+ * coset-frame x bit, z bit, syndrome bit of a check), one-hot direction,
+ * one-hot message length, 10 p, 1.
+ *   feats  device [B*4*M][BBP_WARM_FEATURES] float
+ *   lens   device [B*4*M] int32 message lengths 2^w, or NULL
+ * Requires k <= 4.  Asynchronous on ``stream``.
+ */
+int bbp_message_features(const uint8_t* syndromes, int64_t B, const bbp_params* prm, float* feats,
+                         int32_t* lens, void* stream);
+
+/* Parameters of the network: W1 (F x H), b1, W2 (H x H), b2, W3 (H x O), b3, row-major. */
+int bbp_warm_param_count(void);
+
+/* Device scratch of one infer or train call over N rows. */
+int bbp_warm_workspace_bytes(int64_t N, size_t* bytes);
+
+/*
+ * bbp_warm_infer -- initial messages from the network: msgs[N][16] are
+ * non-negative unit vectors over the first lens[row] entries (exp of the
+ * logits, normalised), zero beyond.  GEMM operands are rounded to bf16,
+ * accumulation is FP32.  All pointers device memory; N <= BBP_WARM_MAX_ROWS.
+ */
+int bbp_warm_infer(const float* theta, const float* feats, const int32_t* lens, int64_t N, float* msgs,
+                   void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * bbp_warm_train_step -- one FP32 training step on N rows: forward, the loss
+ * 1 - <u, t>^2 per message (the Delta term of Remark 4) averaged over rows,
+ * backward into grad (bbp_warm_param_count floats), and, when step > 0 and
+ * adam_m / adam_v are given, one Adam update of theta with learning rate lr.
+ * loss_sum receives the sum of the per-row losses.  targets [N][16] are unit
+ * vectors.  All pointers device memory.
+ */
+int bbp_warm_train_step(float* theta, float* adam_m, float* adam_v, int32_t step, float lr, const float* feats,
+                        const float* targets, const int32_t* lens, int64_t N, float* grad, float* loss_sum,
+                        void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * bbp_decode_batch_ex -- bbp_decode_batch for algorithm BBP_ALG_FUSED with
+ * optional initial messages init_msgs [B][4][M][16] (renormalised; an
+ * all-zero message falls back to uniform) and optional export of the
+ * messages after the BP loop into final_msgs [B][4][M][16] (float).
+ * Errors as bbp_decode_batch; BBP_EINVAL for the MPS algorithm.
+ */
+int bbp_decode_batch_ex(const uint8_t* syndromes, int64_t B, const bbp_params* prm, const float* init_msgs,
+                        float* final_msgs, double* logp, double* delta, int32_t* iters, int32_t* flags,
+                        int8_t* decision, void* workspace, size_t workspace_bytes, void* stream);
+
 /* Static text for a return code. */
 const char* bbp_strerror(int code);
 

@@ -58,8 +58,11 @@ def fuse_block(T, rows, cols):
     return F.reshape(dl, dr, dt, db)
 
 
-def run_naive(tensors, k, max_iter, eta, delta0, k_cols=None):
-    """Dense fused-block BP; returns (logp, delta, iters, messages)."""
+def run_naive(tensors, k, max_iter, eta, delta0, k_cols=None, init=None):
+    """Dense fused-block BP; returns (logp, delta, iters, messages).
+
+    ``init`` optionally maps (I, J, dir) to an initial message (normalised
+    here); the default is the uniform start of Remark 2."""
     W = len(tensors)
     kc = k_cols if k_cols is not None else k
     rows, cols = ranges(W, k), ranges(W, kc)
@@ -75,7 +78,11 @@ def run_naive(tensors, k, max_iter, eta, delta0, k_cols=None):
     msgs = {}
     for (I, J, dr) in edges:
         dim = F[(I, J)].shape[axis[dr]]
-        msgs[(I, J, dr)] = np.full(dim, 1.0 / math.sqrt(dim))
+        if init is not None:
+            v = np.asarray(init[(I, J, dr)], dtype=np.float64)[:dim]
+            msgs[(I, J, dr)] = v / np.linalg.norm(v)
+        else:
+            msgs[(I, J, dr)] = np.full(dim, 1.0 / math.sqrt(dim))
 
     def incoming(I, J, side):
         if has(I, J, side):

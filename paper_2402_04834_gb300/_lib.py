@@ -20,7 +20,10 @@ FLAG_UNTRUSTED, FLAG_OVERLAP, FLAG_BLOCK, FLAG_NONFINITE = 1, 2, 4, 8
 
 # Exported symbols, as declared in include/blockbp.h.
 SYMBOLS = ("bbp_workspace_bytes", "bbp_decode_batch", "bbp_decode_batch_host", "bbp_sample",
-           "bbp_strerror", "bbp_version", "bbp_decode_batch_static")
+           "bbp_strerror", "bbp_version", "bbp_decode_batch_static", "bbp_message_count",
+           "bbp_message_features", "bbp_warm_param_count", "bbp_warm_workspace_bytes", "bbp_warm_infer",
+           "bbp_warm_train_step", "bbp_decode_batch_ex")
+WARM_F, WARM_H, WARM_O, WARM_MAX_ROWS = 256, 256, 16, 4194240
 BBP_ETOOLARGE = -5
 STATIC_WORKSPACE_BYTES = 32 << 20
 
@@ -81,6 +84,21 @@ def lib():
         L.bbp_decode_batch.restype = ctypes.c_int
         L.bbp_decode_batch_host.argtypes = [vp, i64, P, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
         L.bbp_decode_batch_host.restype = ctypes.c_int
+        L.bbp_decode_batch_ex.argtypes = [vp, i64, P, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+        L.bbp_decode_batch_ex.restype = ctypes.c_int
+        L.bbp_message_count.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+        L.bbp_message_count.restype = ctypes.c_int
+        L.bbp_message_features.argtypes = [vp, i64, P, vp, vp, vp]
+        L.bbp_message_features.restype = ctypes.c_int
+        L.bbp_warm_param_count.argtypes = []
+        L.bbp_warm_param_count.restype = ctypes.c_int
+        L.bbp_warm_workspace_bytes.argtypes = [i64, ctypes.POINTER(ctypes.c_size_t)]
+        L.bbp_warm_workspace_bytes.restype = ctypes.c_int
+        L.bbp_warm_infer.argtypes = [vp, vp, vp, i64, vp, vp, ctypes.c_size_t, vp]
+        L.bbp_warm_infer.restype = ctypes.c_int
+        L.bbp_warm_train_step.argtypes = [vp, vp, vp, i32, ctypes.c_float, vp, vp, vp, i64, vp, vp, vp,
+                                          ctypes.c_size_t, vp]
+        L.bbp_warm_train_step.restype = ctypes.c_int
         L.bbp_decode_batch_static.argtypes = [vp, i64, P, vp, vp, vp, vp, vp, vp]
         L.bbp_decode_batch_static.restype = ctypes.c_int
         L.bbp_sample.argtypes = [ctypes.c_uint64, i64, i64, i32, ctypes.c_double, vp, vp, vp, vp, vp]

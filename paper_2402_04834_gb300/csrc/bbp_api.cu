@@ -82,6 +82,13 @@ int bbp_workspace_bytes(const bbp_params* prm, int64_t B, int include_io, size_t
 int bbp_decode_batch(const uint8_t* syndromes, int64_t B, const bbp_params* prm, double* logp,
                      double* delta, int32_t* iters, int32_t* flags, int8_t* decision, void* workspace,
                      size_t workspace_bytes, void* stream) {
+  return bbp_decode_batch_ex(syndromes, B, prm, nullptr, nullptr, logp, delta, iters, flags, decision,
+                             workspace, workspace_bytes, stream);
+}
+
+int bbp_decode_batch_ex(const uint8_t* syndromes, int64_t B, const bbp_params* prm, const float* init_msgs,
+                        float* final_msgs, double* logp, double* delta, int32_t* iters, int32_t* flags,
+                        int8_t* decision, void* workspace, size_t workspace_bytes, void* stream) {
   const int rc = check_params(prm);
   if (rc != BBP_OK) return rc;
   if (B < 0 || B > (int64_t(1) << 29)) return BBP_EINVAL;
@@ -96,6 +103,8 @@ int bbp_decode_batch(const uint8_t* syndromes, int64_t B, const bbp_params* prm,
   a.p = prm->p; a.eta = prm->eta; a.delta0 = prm->delta0; a.delta1 = prm->delta1; a.cutoff = prm->cutoff;
   a.synd = syndromes; a.arena = workspace; a.logp = logp; a.delta = delta; a.iters = iters;
   a.flags = flags; a.decision = decision; a.B = B;
+  if ((init_msgs || final_msgs) && prm->algorithm != BBP_ALG_FUSED) return BBP_EINVAL;
+  a.init_msgs = init_msgs; a.final_msgs = final_msgs;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   if (prm->algorithm == BBP_ALG_FUSED)

@@ -19,6 +19,7 @@ cudaError_t launch_decode_t(const LaunchArgs& a, cudaStream_t st) {
   k.p = a.p; k.eta = a.eta; k.delta0 = a.delta0; k.delta1 = a.delta1; k.cutoff = a.cutoff;
   k.synd = a.synd; k.arena = static_cast<T*>(a.arena);
   k.logp = a.logp; k.delta = a.delta; k.iters = a.iters; k.flags = a.flags;
+  k.init_msgs = nullptr; k.final_msgs = nullptr;
   const int smem = smem_bytes_for<T>(a.geo, a.M);
   auto kern = decode_kernel<T, kMaxK, kMaxD, kWarps>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -40,6 +41,7 @@ cudaError_t launch_fused_t(const LaunchArgs& a, cudaStream_t st) {
   k.p = a.p; k.eta = a.eta; k.delta0 = a.delta0; k.delta1 = a.delta1; k.cutoff = a.cutoff;
   k.synd = a.synd; k.arena = nullptr;
   k.logp = a.logp; k.delta = a.delta; k.iters = a.iters; k.flags = a.flags;
+  k.init_msgs = a.init_msgs; k.final_msgs = a.final_msgs;
   const int smem = fused_smem_for<T>(a.geo, a.M);
   auto kern = fused_kernel<T, kFusedWarps>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -320,12 +320,26 @@ __global__ void __launch_bounds__(NW * 32, FusedMinBlocks<T>::value) fused_kerne
   c.frame = frame; c.msg_of = msg_of; c.msg_off = nullptr; c.dims = nullptr;
   c.arena = nullptr; c.e0 = nullptr; c.cta_flags = &misc[1];
 
-  // Remark 2: uniform messages of unit norm.
+  // Remark 2: uniform messages of unit norm, unless initial messages are
+  // given (learned warm start): those are renormalised on entry.
   for (int idx = warp; idx < M; idx += NW) {
     const int key = meta[idx];
     const int w = g.side_len(key / 4 / nb, (key / 4) % nb, key & 3);
-    const T u = (T)rsqrt((double)(1 << w));
-    for (int i = lane; i < kFusedVec; i += 32) msgs[idx * kFusedVec + i] = i < (1 << w) ? u : T(0);
+    T* x = msgs + idx * kFusedVec;
+    if (a.init_msgs) {
+      const float* src = a.init_msgs + (cta * M + idx) * kFusedVec;
+      for (int i = lane; i < kFusedVec; i += 32) x[i] = i < (1 << w) ? (T)src[i] : T(0);
+      __syncwarp();
+      const T nrm = fused_normalize(x, 1 << w, lane);
+      if (!(nrm > T(0))) {                            // unusable proposal: fall back to uniform
+        const T u = (T)rsqrt((double)(1 << w));
+        for (int i = lane; i < (1 << w); i += 32) x[i] = u;
+        __syncwarp();
+      }
+    } else {
+      const T u = (T)rsqrt((double)(1 << w));
+      for (int i = lane; i < kFusedVec; i += 32) x[i] = i < (1 << w) ? u : T(0);
+    }
   }
   __syncthreads();
 
@@ -375,6 +389,9 @@ __global__ void __launch_bounds__(NW * 32, FusedMinBlocks<T>::value) fused_kerne
     it_done = it;
     if (delta < a.delta0) break;
   }
+
+  if (a.final_msgs)
+    for (int e = tid; e < M * kFusedVec; e += NW * 32) a.final_msgs[cta * M * kFusedVec + e] = (float)msgs[e];
 
   // Lemma 1 read-out.
   if (tid == 0) {

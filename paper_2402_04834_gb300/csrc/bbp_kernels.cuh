@@ -84,6 +84,8 @@ struct KArgs {
   double* delta;
   int32_t* iters;
   int32_t* flags;
+  const float* init_msgs;   // fused path: [cta][M][16] initial messages, or null (uniform)
+  float* final_msgs;        // fused path: [cta][M][16] messages after the BP loop, or null
 };
 
 // Everything a warp needs to reach the CTA's shared tables.

@@ -28,6 +28,8 @@ struct LaunchArgs {
   int32_t* flags;
   int8_t* decision;
   long long B;
+  const float* init_msgs = nullptr;
+  float* final_msgs = nullptr;
 };
 
 // Shared memory of one CTA in bytes for the given precision (0 = fp64, 1 = fp32).

@@ -1,0 +1,386 @@
+// Learned warm start for the fused-block decoder: message features, the
+// network F -> H -> H -> O with GELU (forward, backward, Adam), and its
+// inference into initial messages.  The paper initialises every message to
+// the uniform distribution (Remark 2) and names learned techniques as a way
+// to improve BP (Sec. V); cold start stays the default and the fallback.
+//
+// Features of the message from block v towards direction dir are read in
+// the frame rotated so that dir points right: a 7 x 7 window of grid nodes,
+// columns t = ncols-7 .. ncols-1 (the block's last columns and what lies
+// behind it), rows s = -1 .. 5 of the chain, with five channels per node --
+// inside the grid, qubit, the coset frame's x bit and z bit (qubits), the
+// syndrome bit (checks) -- then one-hot direction, one-hot message length,
+// 10 p and a constant 1.
+//
+// All kernels are plain FP32 CUDA-core code: a 64 x 64-tile GEMM with bias /
+// GELU epilogues and transposed operands for the backward pass.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "../../include/blockbp.h"
+#include "bbp_fused.cuh"
+#include "bbp_launch.h"
+
+namespace bbp {
+namespace warm {
+
+constexpr int F = BBP_WARM_FEATURES;   // 256
+constexpr int H = BBP_WARM_HIDDEN;     // 256
+constexpr int O = BBP_WARM_OUT;        // 16
+constexpr int kParams = F * H + H + H * H + H + H * O + O;
+
+// ---------------------------------------------------------------------------
+// Features.
+__global__ void features_kernel(Geo g, int M, double p, const uint8_t* synd, float* feats, int32_t* lens) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int W = g.W, d = g.d, nb = g.nb;
+  const int m = 2 * d * (d - 1);
+  uint8_t* s = smem;
+  uint8_t* frame = smem + align_up(m, 16);
+  int16_t* msg_of = reinterpret_cast<int16_t*>(frame + align_up(W * W, 16));
+  int16_t* meta = msg_of + align_up(nb * nb * 4, 8);
+  const long long cta = blockIdx.x;
+  const long long shot = cta >> 2;
+  const int coset = (int)(cta & 3);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) s[i] = synd[shot * m + i];
+  __syncthreads();
+  const int bx = (coset == 1 || coset == 2), bz = (coset == 2 || coset == 3);
+  for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
+    const int i = e / W, j = e % W;
+    int fx = 0, fz = 0;
+    if ((i & 1) == 0 && (j & 1) == 0) {
+      const int r = i >> 1, cc = j >> 1;
+      for (int c2 = 0; c2 < cc; ++c2) fx ^= s[r * (d - 1) + c2];
+      for (int r2 = 0; r2 < r; ++r2) fz ^= s[d * (d - 1) + r2 * d + cc];
+      if (bx && r == 0) fx ^= 1;
+      if (bz && cc == 0) fz ^= 1;
+    }
+    frame[e] = (uint8_t)(fx | (fz << 1));
+  }
+  if (threadIdx.x == 0) {
+    int idx = 0;
+    for (int I = 0; I < nb; ++I)
+      for (int J = 0; J < nb; ++J)
+        for (int dir = 0; dir < 4; ++dir) {
+          const int key = (I * nb + J) * 4 + dir;
+          if (g.has(I, J, dir)) { msg_of[key] = (int16_t)idx; meta[idx] = (int16_t)key; ++idx; }
+          else msg_of[key] = -1;
+        }
+  }
+  __syncthreads();
+  Ctx<float, kFusedK> c;
+  c.g = g; c.msg_of = msg_of;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int idx = warp; idx < M; idx += nw) {
+    const int key = meta[idx];
+    const int I = key / 4 / nb, J = (key / 4) % nb, dir = key & 3;
+    const Frame f = make_frame(c, I, J, dir);
+    const long long row = cta * M + idx;
+    for (int q = lane; q < F; q += 32) {
+      float v = 0.f;
+      if (q < 5 * 49) {
+        const int ch = q / 49, pos = q % 49;
+        const int t = f.ncols - 7 + pos / 7, sp = -1 + pos % 7;
+        int i, j;
+        f.node(t, sp, &i, &j);
+        const bool in = i >= 0 && j >= 0 && i < W && j < W;
+        if (in) {
+          const bool qubit = ((i + j) & 1) == 0;
+          if (ch == 0) v = 1.f;
+          else if (ch == 1) v = qubit ? 1.f : 0.f;
+          else if (ch == 2) v = qubit ? (float)(frame[i * W + j] & 1) : 0.f;
+          else if (ch == 3) v = qubit ? (float)((frame[i * W + j] >> 1) & 1) : 0.f;
+          else if (!qubit) {
+            const int bit = (i & 1) == 0 ? (i >> 1) * (d - 1) + (j >> 1)              // A_(r,c)
+                                         : d * (d - 1) + (i >> 1) * d + (j >> 1);     // B_(r,j)
+            v = (float)s[bit];
+          }
+        }
+      } else if (q < 245 + 4) {
+        v = (q - 245 == dir) ? 1.f : 0.f;
+      } else if (q < 249 + 4) {
+        v = (q - 249 == f.h - 1) ? 1.f : 0.f;
+      } else if (q == 253) {
+        v = (float)(10.0 * p);
+      } else if (q == 254) {
+        v = 1.f;
+      }
+      feats[row * F + q] = v;
+    }
+    if (lane == 0 && lens) lens[row] = 1 << f.h;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// GEMM: C[M x N] = op(A) op(B) (+ bias) with optional GELU, FP32.
+// op(A) is A (M x K, row-major, lda) or A^T with A stored K x M; op(B) is B
+// (K x N, ldb) or B^T with B stored N x K.  Optional outputs: the
+// pre-activation Z and the activation C; accumulate adds into C.
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float x) {
+  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) gemm_kernel(int Mr, int N, int K, const float* __restrict__ A, int lda,
+                                                   const float* __restrict__ B, int ldb, float* C, int ldc,
+                                                   const float* __restrict__ bias, float* Z, int act, int accumulate,
+                                                   int bf16_operands) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ float As[BK][BM + 4];
+  __shared__ float Bs[BK][BN + 4];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int e = threadIdx.x; e < BM * BK; e += 256) {
+      // Walk the tile along the operand's contiguous dimension (coalesced).
+      const int mm = TA ? e % BM : e / BK, kk = TA ? e / BM : e % BK;
+      const int gm = m0 + mm, gk = k0 + kk;
+      float v = 0.f;
+      if (gm < Mr && gk < K) v = TA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
+      if (bf16_operands) v = __bfloat162float(__float2bfloat16(v));
+      As[kk][mm] = v;
+    }
+    for (int e = threadIdx.x; e < BN * BK; e += 256) {
+      const int nn = TB ? e / BK : e % BN, kk = TB ? e % BK : e / BN;
+      const int gn = n0 + nn, gk = k0 + kk;
+      float v = 0.f;
+      if (gn < N && gk < K) v = TB ? B[(long long)gn * ldb + gk] : B[(long long)gk * ldb + gn];
+      if (bf16_operands) v = __bfloat162float(__float2bfloat16(v));
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + ty * 4 + i;
+    if (gm >= Mr) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx * 4 + j;
+      if (gn >= N) continue;
+      float v = acc[i][j] + (bias ? bias[gn] : 0.f);
+      if (Z) Z[(long long)gm * ldc + gn] = v;
+      if (act) v = gelu(v);
+      float* cp = C + (long long)gm * ldc + gn;
+      *cp = accumulate ? *cp + v : v;
+    }
+  }
+}
+
+template <bool TA, bool TB>
+cudaError_t gemm(int Mr, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
+                 const float* bias, float* Z, int act, int accumulate, int bf16, cudaStream_t st) {
+  dim3 grid((N + 63) / 64, (Mr + 63) / 64);
+  gemm_kernel<TA, TB><<<grid, 256, 0, st>>>(Mr, N, K, A, lda, B, ldb, C, ldc, bias, Z, act, accumulate, bf16);
+  return cudaGetLastError();
+}
+
+// u = masked exp(o - max) / norm; per-row loss 1 - <u,t>^2 and dL/do (mean over N).
+__global__ void head_kernel(const float* logits, const int32_t* lens, const float* targets, long long N,
+                            float* msgs, float* gO, float* loss_sum) {
+  const long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (row >= N) return;
+  const int n = lens[row];
+  float o[O], mm[O];
+  float mx = -INFINITY;
+  for (int i = 0; i < O; ++i) { o[i] = logits[row * O + i]; if (i < n) mx = fmaxf(mx, o[i]); }
+  float s2 = 0.f;
+  for (int i = 0; i < O; ++i) { mm[i] = i < n ? expf(o[i] - mx) : 0.f; s2 += mm[i] * mm[i]; }
+  const float nm = sqrtf(s2), inv = 1.f / nm;
+  if (msgs)
+    for (int i = 0; i < O; ++i) msgs[row * O + i] = mm[i] * inv;
+  if (targets) {
+    float cdot = 0.f;
+    for (int i = 0; i < O; ++i) cdot += mm[i] * inv * targets[row * O + i];
+    atomicAdd(loss_sum, 1.f - cdot * cdot);
+    // dL/du = -2 c t / N; dL/dm = (gu - <gu,u> u) / |m|; dL/do = dL/dm * m.
+    const float sc = -2.f * cdot / (float)N;
+    float gu_u = 0.f;
+    for (int i = 0; i < O; ++i) gu_u += sc * targets[row * O + i] * mm[i] * inv;
+    for (int i = 0; i < O; ++i) {
+      const float gu = sc * targets[row * O + i];
+      gO[row * O + i] = (gu - gu_u * mm[i] * inv) * inv * mm[i];
+    }
+  }
+}
+
+__global__ void gelu_back_kernel(float* gA, const float* Z, long long n) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e < n) gA[e] *= gelu_grad(Z[e]);
+}
+
+// Column sums of G [N x C] into out[C] (overwrites).
+__global__ void colsum_kernel(const float* G, long long N, int C, float* out) {
+  const int c = blockIdx.x;
+  float acc = 0.f;
+  for (long long r = threadIdx.x; r < N; r += blockDim.x) acc += G[r * C + c];
+  __shared__ float sh[256];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = sh[0];
+}
+
+__global__ void adam_kernel(float* th, const float* gr, float* m, float* v, long long n, float lr, float b1,
+                            float b2, float eps, float c1, float c2) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const float g = gr[e];
+  const float mm = b1 * m[e] + (1.f - b1) * g;
+  const float vv = b2 * v[e] + (1.f - b2) * g * g;
+  m[e] = mm;
+  v[e] = vv;
+  th[e] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+}
+
+struct Params {
+  const float *W1, *b1, *W2, *b2, *W3, *b3;
+};
+__host__ __device__ inline Params split(const float* th) {
+  Params P;
+  P.W1 = th; P.b1 = P.W1 + F * H; P.W2 = P.b1 + H; P.b2 = P.W2 + H * H; P.W3 = P.b2 + H; P.b3 = P.W3 + H * O;
+  return P;
+}
+
+}  // namespace warm
+}  // namespace bbp
+
+using namespace bbp;
+using namespace bbp::warm;
+
+namespace {
+size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+// Scratch of a forward (+ backward) pass over N rows: Z1, A1, Z2, A2 [N x H],
+// logits and dL/dlogits [N x O], and two [N x H] gradient buffers.
+size_t pass_bytes(long long N) { return al256((size_t)N * H * 4) * 6 + al256((size_t)N * O * 4) * 2 + 256; }
+}  // namespace
+
+extern "C" {
+
+int bbp_warm_param_count(void) { return kParams; }
+
+int bbp_message_count(const bbp_params* prm, int32_t* M) {
+  if (!prm || !M || prm->d < 2 || prm->k < 1) return BBP_EINVAL;
+  const Geo g = make_geo(prm->d, prm->k);
+  int m = 0, ae = 0;
+  count_messages(g, 1, &m, &ae);
+  *M = m;
+  return BBP_OK;
+}
+
+int bbp_message_features(const uint8_t* syndromes, int64_t B, const bbp_params* prm, float* feats,
+                         int32_t* lens, void* stream) {
+  if (!prm || !syndromes || !feats || B < 0 || prm->d < 2 || prm->k < 1 || prm->k > kFusedK) return BBP_EINVAL;
+  if (B == 0) return BBP_OK;
+  const Geo g = make_geo(prm->d, prm->k);
+  int M = 0, ae = 0;
+  count_messages(g, 1, &M, &ae);
+  const int m = 2 * g.d * (g.d - 1);
+  const int smem = align_up(m, 16) + align_up(g.W * g.W, 16) + 2 * align_up(g.nb * g.nb * 4, 8) + 2 * M + 64;
+  features_kernel<<<(unsigned)(B * 4), 256, smem, static_cast<cudaStream_t>(stream)>>>(g, M, prm->p, syndromes,
+                                                                                      feats, lens);
+  return cudaGetLastError() == cudaSuccess ? BBP_OK : BBP_ECUDA;
+}
+
+int bbp_warm_workspace_bytes(int64_t N, size_t* bytes) {
+  if (!bytes || N < 0) return BBP_EINVAL;
+  *bytes = pass_bytes(N);
+  return BBP_OK;
+}
+
+int bbp_warm_infer(const float* theta, const float* feats, const int32_t* lens, int64_t N, float* msgs,
+                   void* workspace, size_t workspace_bytes, void* stream) {
+  if (!theta || !feats || !lens || !msgs || N < 0 || N > BBP_WARM_MAX_ROWS) return BBP_EINVAL;
+  if (N == 0) return BBP_OK;
+  if (!workspace || workspace_bytes < pass_bytes(N)) return BBP_ENOSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Params P = split(theta);
+  char* w = static_cast<char*>(workspace);
+  float* A1 = reinterpret_cast<float*>(w);
+  float* A2 = reinterpret_cast<float*>(w + al256((size_t)N * H * 4));
+  float* L = reinterpret_cast<float*>(w + 2 * al256((size_t)N * H * 4));
+  // BF16 operands, FP32 accumulation (weights kept in FP32).
+  if (gemm<false, false>((int)N, H, F, feats, F, P.W1, H, A1, H, P.b1, nullptr, 1, 0, 1, st) != cudaSuccess ||
+      gemm<false, false>((int)N, H, H, A1, H, P.W2, H, A2, H, P.b2, nullptr, 1, 0, 1, st) != cudaSuccess ||
+      gemm<false, false>((int)N, O, H, A2, H, P.W3, O, L, O, P.b3, nullptr, 0, 0, 1, st) != cudaSuccess)
+    return BBP_ECUDA;
+  head_kernel<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(L, lens, nullptr, N, msgs, nullptr, nullptr);
+  return cudaGetLastError() == cudaSuccess ? BBP_OK : BBP_ECUDA;
+}
+
+int bbp_warm_train_step(float* theta, float* adam_m, float* adam_v, int32_t step, float lr, const float* feats,
+                        const float* targets, const int32_t* lens, int64_t N, float* grad, float* loss_sum,
+                        void* workspace, size_t workspace_bytes, void* stream) {
+  if (!theta || !feats || !targets || !lens || !grad || !loss_sum || N <= 0 || N > BBP_WARM_MAX_ROWS)
+    return BBP_EINVAL;
+  if (!workspace || workspace_bytes < pass_bytes(N)) return BBP_ENOSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Params P = split(theta);
+  float* gW1 = grad;
+  float* gb1 = gW1 + F * H;
+  float* gW2 = gb1 + H;
+  float* gb2 = gW2 + H * H;
+  float* gW3 = gb2 + H;
+  float* gb3 = gW3 + H * O;
+  char* w = static_cast<char*>(workspace);
+  const size_t nh = al256((size_t)N * H * 4), no = al256((size_t)N * O * 4);
+  float* Z1 = reinterpret_cast<float*>(w);
+  float* A1 = reinterpret_cast<float*>(w + nh);
+  float* Z2 = reinterpret_cast<float*>(w + 2 * nh);
+  float* A2 = reinterpret_cast<float*>(w + 3 * nh);
+  float* G1 = reinterpret_cast<float*>(w + 4 * nh);
+  float* G2 = reinterpret_cast<float*>(w + 5 * nh);
+  float* L = reinterpret_cast<float*>(w + 6 * nh);
+  float* gO = reinterpret_cast<float*>(w + 6 * nh + no);
+  const int n = (int)N;
+  bool ok = true;
+  ok = ok && gemm<false, false>(n, H, F, feats, F, P.W1, H, A1, H, P.b1, Z1, 1, 0, 0, st) == cudaSuccess;
+  ok = ok && gemm<false, false>(n, H, H, A1, H, P.W2, H, A2, H, P.b2, Z2, 1, 0, 0, st) == cudaSuccess;
+  ok = ok && gemm<false, false>(n, O, H, A2, H, P.W3, O, L, O, P.b3, nullptr, 0, 0, 0, st) == cudaSuccess;
+  if (!ok) return BBP_ECUDA;
+  if (cudaMemsetAsync(loss_sum, 0, sizeof(float), st) != cudaSuccess) return BBP_ECUDA;
+  head_kernel<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(L, lens, targets, N, nullptr, gO, loss_sum);
+  // Layer 3: gW3 = A2^T gO, gb3 = colsum gO, gA2 = gO W3^T.
+  ok = ok && gemm<true, false>(H, O, n, A2, H, gO, O, gW3, O, nullptr, nullptr, 0, 0, 0, st) == cudaSuccess;
+  colsum_kernel<<<O, 256, 0, st>>>(gO, N, O, gb3);
+  ok = ok && gemm<false, true>(n, H, O, gO, O, P.W3, O, G2, H, nullptr, nullptr, 0, 0, 0, st) == cudaSuccess;
+  gelu_back_kernel<<<(unsigned)(((long long)N * H + 255) / 256), 256, 0, st>>>(G2, Z2, (long long)N * H);
+  // Layer 2.
+  ok = ok && gemm<true, false>(H, H, n, A1, H, G2, H, gW2, H, nullptr, nullptr, 0, 0, 0, st) == cudaSuccess;
+  colsum_kernel<<<H, 256, 0, st>>>(G2, N, H, gb2);
+  ok = ok && gemm<false, true>(n, H, H, G2, H, P.W2, H, G1, H, nullptr, nullptr, 0, 0, 0, st) == cudaSuccess;
+  gelu_back_kernel<<<(unsigned)(((long long)N * H + 255) / 256), 256, 0, st>>>(G1, Z1, (long long)N * H);
+  // Layer 1.
+  ok = ok && gemm<true, false>(F, H, n, feats, F, G1, H, gW1, H, nullptr, nullptr, 0, 0, 0, st) == cudaSuccess;
+  colsum_kernel<<<H, 256, 0, st>>>(G1, N, H, gb1);
+  if (!ok || cudaGetLastError() != cudaSuccess) return BBP_ECUDA;
+  if (step > 0 && adam_m && adam_v) {
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+    adam_kernel<<<(unsigned)((kParams + 255) / 256), 256, 0, st>>>(theta, grad, adam_m, adam_v, kParams, lr, b1,
+                                                                  b2, 1e-8f, c1, c2);
+  }
+  return cudaGetLastError() == cudaSuccess ? BBP_OK : BBP_ECUDA;
+}
+
+}  // extern "C"

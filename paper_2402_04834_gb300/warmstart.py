@@ -1,0 +1,239 @@
+"""Learned warm start for the fused-block decoder (argument marshalling only).
+
+A network proposes the initial message of every directed block edge from
+local features; it is trained on messages that the GPU decoder itself
+produces at convergence.  Features, training steps, inference and decoding
+all run in libblockbp (include/blockbp.h); PyTorch provides device memory.
+Cold start (uniform messages, Remark 2) stays the default and the fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+import torch
+
+from ._lib import WARM_F, WARM_H, WARM_MAX_ROWS, WARM_O, DecoderParams, check, lib
+from .decoder import Workspace, _ptr, _stream, decode
+
+
+def message_count(prm: DecoderParams) -> int:
+    M = ctypes.c_int32(0)
+    cp = prm.c()
+    check(lib().bbp_message_count(ctypes.byref(cp), ctypes.byref(M)))
+    return int(M.value)
+
+
+def features(syndromes: torch.Tensor, prm: DecoderParams, stream=None):
+    """Features [B*4*M, 256] (float32) and message lengths [B*4*M] (int32)."""
+    B = syndromes.shape[0]
+    M = message_count(prm)
+    N = B * 4 * M
+    feats = torch.empty(N, WARM_F, dtype=torch.float32, device=syndromes.device)
+    lens = torch.empty(N, dtype=torch.int32, device=syndromes.device)
+    cp = prm.c()
+    check(lib().bbp_message_features(_ptr(syndromes.contiguous()), B, ctypes.byref(cp), _ptr(feats), _ptr(lens),
+                                     _stream(stream)))
+    return feats, lens
+
+
+def _ws_bytes(N: int) -> int:
+    out = ctypes.c_size_t(0)
+    check(lib().bbp_warm_workspace_bytes(N, ctypes.byref(out)))
+    return int(out.value)
+
+
+class WarmStart:
+    """Parameters and Adam state of the network, on one device."""
+
+    def __init__(self, device="cuda", seed: int = 0):
+        n = int(lib().bbp_warm_param_count())
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        parts = []
+        for fan_in, fan_out in ((WARM_F, WARM_H), (WARM_H, WARM_H), (WARM_H, WARM_O)):
+            w = torch.randn(fan_in, fan_out, generator=g) * math.sqrt(2.0 / (fan_in + fan_out))
+            parts += [w.reshape(-1), torch.zeros(fan_out)]
+        theta = torch.cat(parts)
+        assert theta.numel() == n
+        self.device = torch.device(device)
+        self.theta = theta.to(self.device, torch.float32).contiguous()
+        self.m = torch.zeros_like(self.theta)
+        self.v = torch.zeros_like(self.theta)
+        self.grad = torch.zeros_like(self.theta)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        self.step = 0
+        self.ws = Workspace()
+
+    def train_step(self, feats, targets, lens, lr=1e-3, stream=None) -> float:
+        """One Adam step on a minibatch; returns the mean loss before the step."""
+        N = feats.shape[0]
+        ws = self.ws.get(_ws_bytes(N), self.device)
+        self.step += 1
+        check(lib().bbp_warm_train_step(_ptr(self.theta), _ptr(self.m), _ptr(self.v), self.step, lr, _ptr(feats),
+                                        _ptr(targets), _ptr(lens), N, _ptr(self.grad), _ptr(self.loss), _ptr(ws),
+                                        ws.numel(), _stream(stream)))
+        return float(self.loss.item()) / N
+
+    def gradient(self, feats, targets, lens, stream=None):
+        """Loss and gradient without an update (used by the gradient check)."""
+        N = feats.shape[0]
+        ws = self.ws.get(_ws_bytes(N), self.device)
+        check(lib().bbp_warm_train_step(_ptr(self.theta), None, None, 0, 0.0, _ptr(feats), _ptr(targets),
+                                        _ptr(lens), N, _ptr(self.grad), _ptr(self.loss), _ptr(ws), ws.numel(),
+                                        _stream(stream)))
+        torch.cuda.synchronize(self.device)
+        return float(self.loss.item()) / N, self.grad.clone()
+
+    def infer(self, feats, lens, out=None, stream=None):
+        """Initial messages [N, 16] for the given feature rows (chunked)."""
+        N = feats.shape[0]
+        out = out if out is not None else torch.empty(N, WARM_O, dtype=torch.float32, device=feats.device)
+        step = min(N, WARM_MAX_ROWS, 1 << 20)
+        ws = self.ws.get(_ws_bytes(step), self.device)
+        for a in range(0, N, step):
+            b = min(N, a + step)
+            check(lib().bbp_warm_infer(_ptr(self.theta), _ptr(feats[a:b]), _ptr(lens[a:b]), b - a, _ptr(out[a:b]),
+                                       _ptr(ws), ws.numel(), _stream(stream)))
+        return out
+
+    def train(self, feats, targets, lens, epochs=4, batch=8192, lr=1e-3, seed=0, log=None):
+        N = feats.shape[0]
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        hist = []
+        for ep in range(epochs):
+            perm = torch.randperm(N, generator=g).to(feats.device)
+            tot, cnt = 0.0, 0
+            for a in range(0, N - batch + 1, batch):
+                idx = perm[a:a + batch]
+                lo = self.train_step(feats[idx].contiguous(), targets[idx].contiguous(), lens[idx].contiguous(), lr)
+                tot += lo
+                cnt += 1
+            hist.append(tot / max(cnt, 1))
+            if log:
+                log(f"epoch {ep}: mean loss {hist[-1]:.4e}")
+        return hist
+
+
+def decode_ex(syndromes, prm: DecoderParams, init_msgs=None, final_msgs=None, workspace=None, stream=None,
+              out=None):
+    """Fused-path decode with optional initial messages and message export."""
+    B = syndromes.shape[0]
+    dev = syndromes.device
+    if out is None:
+        out = {
+            "logp": torch.empty(B, 4, dtype=torch.float64, device=dev),
+            "delta": torch.empty(B, 4, dtype=torch.float64, device=dev),
+            "iters": torch.empty(B, 4, dtype=torch.int32, device=dev),
+            "flags": torch.empty(B, 4, dtype=torch.int32, device=dev),
+            "decision": torch.empty(B, dtype=torch.int8, device=dev),
+        }
+    cp = prm.c()
+    ws = (workspace or Workspace()).get(256, dev)
+    check(lib().bbp_decode_batch_ex(_ptr(syndromes), B, ctypes.byref(cp),
+                                    _ptr(init_msgs) if init_msgs is not None else None,
+                                    _ptr(final_msgs) if final_msgs is not None else None,
+                                    _ptr(out["logp"]), _ptr(out["delta"]), _ptr(out["iters"]), _ptr(out["flags"]),
+                                    _ptr(out["decision"]), _ptr(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+def decode_warm(syndromes, prm: DecoderParams, net: WarmStart, stream=None, out=None, buffers=None):
+    """Learned warm start: features -> network -> fused decode."""
+    feats, lens = features(syndromes, prm, stream)
+    init = net.infer(feats, lens, stream=stream)
+    return decode_ex(syndromes, prm, init_msgs=init, stream=stream, out=out)
+
+
+def collect(syndromes, prm: DecoderParams, max_delta=1e-3):
+    """Training rows from one batch: features and the decoder's converged
+    messages, keeping the (syndrome, coset) pairs whose final Delta is below
+    ``max_delta`` (converged)."""
+    B = syndromes.shape[0]
+    M = message_count(prm)
+    final = torch.empty(B * 4 * M, WARM_O, dtype=torch.float32, device=syndromes.device)
+    out = decode_ex(syndromes, prm, final_msgs=final)
+    feats, lens = features(syndromes, prm)
+    ok = (out["delta"] < max_delta).reshape(-1).repeat_interleave(M)
+    return feats[ok], final[ok], lens[ok]
+
+
+def wilson(k: int, n: int, z: float = 1.959963984540054):
+    """Wilson score interval of a binomial proportion k / n (95% by default)."""
+    if n == 0:
+        return (0.0, 1.0)
+    ph = k / n
+    den = 1 + z * z / n
+    c = (ph + z * z / (2 * n)) / den
+    h = z * math.sqrt(ph * (1 - ph) / n + z * z / (4 * n * n)) / den
+    return (max(0.0, c - h), min(1.0, c + h))
+
+
+def build_training_set(device="cuda", d_list=(11, 15), shots=(1500, 800), p_grid=(0.05, 0.075, 0.10, 0.125, 0.15),
+                       k=4, seed_base=4000, max_rows=1_000_000):
+    """Converged messages of seeded decodes (the decoder labels its own data)."""
+    feats, targets, lens = [], [], []
+    for d, n in zip(d_list, shots):
+        per_p = max(1, n // len(p_grid))
+        for ip, p in enumerate(p_grid):
+            prm = DecoderParams(d=d, k=k, p=p, max_iter=40, delta0=1e-6, precision="fp32", algorithm="fused")
+            from .decoder import sample
+            _, _, s, _ = sample(seed_base + 100 * d + ip, 0, per_p, d, p, device=device, with_errors=False)
+            f, t, ln = collect(s, prm)
+            feats.append(f)
+            targets.append(t)
+            lens.append(ln)
+    F = torch.cat(feats)[:max_rows].contiguous()
+    T = torch.cat(targets)[:max_rows].contiguous()
+    L = torch.cat(lens)[:max_rows].contiguous()
+    return F, T, L
+
+
+def evaluate(net: WarmStart, d=13, p=0.10, shots=10000, k=4, seed=5000, device="cuda", max_iter=20, delta0=1e-4):
+    """Cold versus warm start on fresh syndromes: iterations, P_L, throughput."""
+    from .decoder import sample
+    _, _, s, tc = sample(seed, 0, shots, d, p, device=device, with_errors=False)
+    prm = DecoderParams(d=d, k=k, p=p, max_iter=max_iter, delta0=delta0, precision="fp32", algorithm="fused")
+    res = {}
+    for name in ("cold", "warm"):
+        run = (lambda: decode(s, prm)) if name == "cold" else (lambda: decode_warm(s, prm, net))
+        out = run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        fails = int((out["decision"].to(torch.int64) != tc.to(torch.int64)).sum().item())
+        lo, hi = wilson(fails, shots)
+        res[name] = {"mean_iters": float(out["iters"].double().mean().item()), "failures": fails, "shots": shots,
+                     "P_L": fails / shots, "P_L_wilson95": [lo, hi], "ms": ms, "syndromes_per_s": shots / ms * 1e3}
+        res[name + "_decision"] = out["decision"]
+    agree = float((res["cold_decision"] == res["warm_decision"]).double().mean().item())
+    for key in ("cold_decision", "warm_decision"):
+        res.pop(key)
+    res["decision_agreement"] = agree
+    res["iterations_saved_fraction"] = 1.0 - res["warm"]["mean_iters"] / res["cold"]["mean_iters"]
+    return res
+
+
+def main():
+    import json
+    import time
+    dev = torch.device("cuda")
+    t0 = time.time()
+    F, T, L = build_training_set(device=dev)
+    t1 = time.time()
+    net = WarmStart(device=dev, seed=0)
+    hist = net.train(F, T, L, epochs=8, batch=8192, lr=1e-3)
+    torch.cuda.synchronize()
+    t2 = time.time()
+    ev = evaluate(net, device=dev)
+    print(json.dumps({"training_rows": int(F.shape[0]), "data_s": t1 - t0, "train_s": t2 - t1,
+                      "loss_per_epoch": hist, "evaluation_d13_p010": ev}))
+
+
+if __name__ == "__main__":
+    main()

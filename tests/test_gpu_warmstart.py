@@ -1,0 +1,175 @@
+"""GPU checks of the learned warm start: gradients and inference against the
+numpy oracle of the network, features against a direct re-derivation, and
+warm-started decoding against the dense oracle started from the same
+messages."""
+
+import numpy as np
+import pytest
+
+import paper_2402_04834_gb300 as pkg
+import synth
+from oracle import mlp
+from oracle.blockbp import BlockNetwork, DIRS
+from oracle.lattice import Lattice
+from oracle.naive import run_naive
+from oracle.tn import coset_network
+from paper_2402_04834_gb300 import warmstart as wsm
+from paper_2402_04834_gb300.build import build
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    build()
+    pkg.lib()
+    return torch.device("cuda:0")
+
+
+def random_rows(N, seed):
+    rng = np.random.default_rng(seed)
+    X = (rng.random((N, 256)) < 0.3).astype(np.float32)
+    lens = rng.choice([2, 16], size=N).astype(np.int32)
+    T = np.abs(rng.standard_normal((N, 16))) * (np.arange(16)[None, :] < lens[:, None])
+    T = (T / np.linalg.norm(T, axis=1, keepdims=True)).astype(np.float32)
+    return X, T, lens
+
+
+def test_gradient_matches_oracle(dev):
+    net = wsm.WarmStart(device=dev, seed=1)
+    X, T, lens = random_rows(96, 2)
+    loss, g = net.gradient(torch.from_numpy(X).to(dev), torch.from_numpy(T).to(dev), torch.from_numpy(lens).to(dev))
+    theta = net.theta.double().cpu().numpy()
+    L, g_ref = mlp.loss_and_grad(theta, X.astype(np.float64), T.astype(np.float64), lens)
+    assert abs(loss - L) <= 1e-5 + 1e-4 * abs(L)
+    g = g.double().cpu().numpy()
+    err = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
+    assert err < 1e-4, err
+    # And per block of parameters, the largest entries agree closely.
+    i = np.argmax(np.abs(g_ref))
+    assert abs(g[i] - g_ref[i]) <= 1e-4 * abs(g_ref[i])
+
+
+def test_adam_step_matches_oracle(dev):
+    net = wsm.WarmStart(device=dev, seed=3)
+    X, T, lens = random_rows(64, 4)
+    theta0 = net.theta.double().cpu().numpy()
+    net.train_step(torch.from_numpy(X).to(dev), torch.from_numpy(T).to(dev), torch.from_numpy(lens).to(dev), lr=1e-3)
+    torch.cuda.synchronize()
+    _, g_ref = mlp.loss_and_grad(theta0, X.astype(np.float64), T.astype(np.float64), lens)
+    m, v = np.zeros_like(theta0), np.zeros_like(theta0)
+    ref = mlp.adam(theta0.copy(), g_ref, m, v, 1, lr=1e-3)
+    got = net.theta.double().cpu().numpy()
+    # The first Adam step moves each weight by ~lr sign(g); FP32 gradients may
+    # flip the sign of entries whose gradient is at rounding level only.
+    big = np.abs(g_ref) > 1e-3 * np.abs(g_ref).max()
+    np.testing.assert_allclose(got[big], ref[big], rtol=0, atol=2e-6)
+
+
+def test_bf16_inference_close_to_oracle(dev):
+    net = wsm.WarmStart(device=dev, seed=5)
+    X, T, lens = random_rows(128, 6)
+    u = net.infer(torch.from_numpy(X).to(dev), torch.from_numpy(lens).to(dev))
+    torch.cuda.synchronize()
+    o, _ = mlp.forward(net.theta.double().cpu().numpy(), X.astype(np.float64))
+    ref, _ = mlp.message_from_logits(o, lens)
+    assert np.max(np.abs(u.cpu().numpy() - ref)) < 2e-2
+    assert np.allclose(np.linalg.norm(u.cpu().numpy(), axis=1), 1.0, atol=1e-5)
+
+
+def expected_features(d, k, p, s, coset):
+    """Direct re-derivation of the feature rows of one (syndrome, coset)."""
+    lat = Lattice(d)
+    fx, fz = lat.coset_frame(s, coset)
+    W = 2 * d - 1
+    net = BlockNetwork([[None] * W for _ in range(W)], k, k)
+    rows = []
+    for (I, J, dr) in net.directed_edges():
+        r0, r1 = net.rows[I]
+        c0, c1 = net.cols[J]
+        if dr in ("R", "L"):
+            h, nc = r1 - r0, c1 - c0
+        else:
+            h, nc = c1 - c0, r1 - r0
+
+        def node(t, sp):
+            if dr == "R":
+                return r0 + sp, c0 + t
+            if dr == "L":
+                return r0 + sp, c1 - 1 - t
+            if dr == "D":
+                return r0 + t, c0 + sp
+            return r1 - 1 - t, c0 + sp
+
+        f = np.zeros(256, dtype=np.float32)
+        for pos in range(49):
+            i, j = node(nc - 7 + pos // 7, -1 + pos % 7)
+            if not (0 <= i < W and 0 <= j < W):
+                continue
+            f[pos] = 1
+            if (i + j) % 2 == 0:
+                q = lat.qidx[i, j]
+                f[49 + pos] = 1
+                f[98 + pos] = fx[q]
+                f[147 + pos] = fz[q]
+            else:
+                f[196 + pos] = s[lat.cidx[i, j]]
+        f[245 + DIRS.index(dr)] = 1
+        f[249 + h - 1] = 1
+        f[253] = 10 * p
+        f[254] = 1
+        rows.append(f)
+    return np.array(rows)
+
+
+def test_features_match_rederivation(dev):
+    d, k, p = 7, 4, 0.1
+    _, _, S = synth.sample_syndromes(3, 0, 2, d, p)
+    prm = pkg.DecoderParams(d=d, k=k, p=p, algorithm="fused")
+    feats, lens = wsm.features(torch.from_numpy(S).to(dev), prm)
+    torch.cuda.synchronize()
+    M = wsm.message_count(prm)
+    F = feats.cpu().numpy().reshape(2, 4, M, 256)
+    for b in range(2):
+        for L in range(4):
+            np.testing.assert_array_equal(F[b, L], expected_features(d, k, p, S[b], L))
+
+
+def test_warm_started_decode_matches_dense_oracle(dev):
+    # Any initial messages: the GPU and the dense oracle started from the same
+    # ones must agree (FP64, 1e-9).
+    d, k, p, iters = 5, 4, 0.1, 5
+    _, _, S = synth.sample_syndromes(9, 0, 2, d, p)
+    prm = pkg.DecoderParams(d=d, k=k, p=p, max_iter=iters, delta0=0.0, precision="fp64", algorithm="fused")
+    M = wsm.message_count(prm)
+    rng = np.random.default_rng(0)
+    init = np.abs(rng.standard_normal((2, 4, M, 16))).astype(np.float32)
+    out = wsm.decode_ex(torch.from_numpy(S).to(dev), prm, init_msgs=torch.from_numpy(init).to(dev))
+    torch.cuda.synchronize()
+    lat = Lattice(d)
+    W = 2 * d - 1
+    edges = BlockNetwork([[None] * W for _ in range(W)], k, k).directed_edges()
+    for b in range(2):
+        for L in range(4):
+            ini = {e: init[b, L, i].astype(np.float64) for i, e in enumerate(edges)}
+            lp, dl, it, _ = run_naive(coset_network(lat, S[b], L, p), k, iters, 0.1, 0.0, init=ini)
+            assert abs(out["logp"][b, L].item() - lp) < 1e-9
+            assert abs(out["delta"][b, L].item() - dl) < 1e-7
+
+
+def test_converged_messages_restart_in_one_iteration(dev):
+    d, k, p = 11, 4, 0.1
+    _, _, S = synth.sample_syndromes(synth.workload_seed(2, 2), 0, 64, d, p)
+    s = torch.from_numpy(S).to(dev)
+    prm = pkg.DecoderParams(d=d, k=k, p=p, max_iter=40, delta0=1e-6, precision="fp32", algorithm="fused")
+    M = wsm.message_count(prm)
+    final = torch.empty(64 * 4 * M, 16, dtype=torch.float32, device=dev)
+    cold = wsm.decode_ex(s, prm, final_msgs=final)
+    warm = wsm.decode_ex(s, prm, init_msgs=final)
+    torch.cuda.synchronize()
+    conv = cold["delta"] < 1e-6
+    assert conv.float().mean() > 0.5
+    assert torch.all(warm["iters"][conv] <= 2)
+    assert torch.max(torch.abs(warm["logp"][conv] - cold["logp"][conv])).item() < 1e-3
