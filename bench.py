@@ -365,6 +365,27 @@ def ours(args):
                                 else "derived: 2 FP64 FMA/clk/SM x 2 x 152 SMs x 2070 MHz"),
                 "flops_per_syndrome": flops / B}
 
+    # Learned warm start (the network is trained here, untimed, on converged
+    # messages of seeded d = 11 and d = 15 decodes); cold versus warm on the
+    # same shots of this workload, inference cost included in its time.
+    learned = None
+    if args.warm and world == 1 and args.algorithm == "fused":
+        from paper_2402_04834_gb300 import warmstart as wsm
+        t_w = time.perf_counter()
+        Ftr, Ttr, Ltr = wsm.build_training_set(device=dev)
+        net = wsm.WarmStart(device=dev, seed=0)
+        hist = net.train(Ftr, Ttr, Ltr, epochs=12, batch=8192, lr=3e-3)
+        hist += net.train(Ftr, Ttr, Ltr, epochs=8, batch=8192, lr=5e-4, seed=1)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t_w
+        del Ftr, Ttr, Ltr
+        ev = wsm.evaluate(net, d=D_CODE, p=P_NOISE, shots=B, k=K_BLOCK, seed=SEED, device=dev,
+                          max_iter=MAX_ITER, delta0=DELTA0, alpha=wsm.DEFAULT_ALPHA)
+        learned = {"training_rows": 1_000_000, "train_s": train_s, "final_loss": hist[-1],
+                   "alpha": ev["alpha"], "cold": ev["cold"], "warm": ev["warm"],
+                   "iterations_saved_fraction": ev["iterations_saved_fraction"],
+                   "decision_agreement": ev["decision_agreement"]}
+
     line = {
         "metric": METRIC, "value": value, "unit": "syndromes/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms_max / args.steps,
@@ -380,7 +401,7 @@ def ours(args):
                 "d2h_bytes_per_step": int(B * (1 + 32))},
         "gpu_launches": 2 * args.steps,
         "roofline": roof, "cpu_baseline": cpu,
-        "plain_fp64_gpu": fp64_mps, "other_paths": legs,
+        "plain_fp64_gpu": fp64_mps, "other_paths": legs, "learned_warm_start": learned,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -400,6 +421,7 @@ def main():
     ap.add_argument("--other-batch", type=int, default=4096)
     ap.add_argument("--cpu-procs", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-warm", dest="warm", action="store_false")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

@@ -84,6 +84,8 @@ extern "C" {
  *             singular values below cutoff * sigma_1 are dropped as numerical
  *             zeros (the paper is silent; 1e-13 for BBP_FP64, 1e-7 for BBP_FP32)
  *   precision BBP_FP64 or BBP_FP32
+ *   launch_warps, launch_ctas_per_sm  launch shape of the fused path (tuning
+ *             only; results do not depend on them)
  *   algorithm BBP_ALG_MPS, or BBP_ALG_FUSED: every k x k block fused into one
  *             vertex with dense messages (Remark 9; the form the paper ran for
  *             k = 1, 2, 4).  Nothing is truncated, D and cutoff are unused,
@@ -102,6 +104,8 @@ typedef struct bbp_params {
   double cutoff;
   int32_t precision;
   int32_t algorithm;
+  int32_t launch_warps;        /* fused path: warps per CTA, 0 = default (8); 4, 8 or 16 in FP32 */
+  int32_t launch_ctas_per_sm;  /* bbp_decode_mixed: resident CTAs per SM, 0 = the occupancy limit */
 } bbp_params;
 
 /*
@@ -227,13 +231,15 @@ int bbp_warm_param_count(void);
 int bbp_warm_workspace_bytes(int64_t N, size_t* bytes);
 
 /*
- * bbp_warm_infer -- initial messages from the network: msgs[N][16] are
- * non-negative unit vectors over the first lens[row] entries (exp of the
- * logits, normalised), zero beyond.  GEMM operands are rounded to bf16,
- * accumulation is FP32.  All pointers device memory; N <= BBP_WARM_MAX_ROWS.
+ * bbp_warm_infer -- initial messages from the network: the proposal u (exp
+ * of the logits over the first lens[row] entries, unit norm) is blended with
+ * the uniform start, msgs = normalise((1 - alpha) uniform + alpha u), zero
+ * beyond lens[row]; alpha in [0, 1] (0 = cold start).  GEMM operands are
+ * rounded to bf16, accumulation is FP32.  All pointers device memory;
+ * N <= BBP_WARM_MAX_ROWS.
  */
-int bbp_warm_infer(const float* theta, const float* feats, const int32_t* lens, int64_t N, float* msgs,
-                   void* workspace, size_t workspace_bytes, void* stream);
+int bbp_warm_infer(const float* theta, const float* feats, const int32_t* lens, int64_t N, float alpha,
+                   float* msgs, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * bbp_warm_train_step -- one FP32 training step on N rows: forward, the loss
@@ -257,6 +263,23 @@ int bbp_warm_train_step(float* theta, float* adam_m, float* adam_v, int32_t step
 int bbp_decode_batch_ex(const uint8_t* syndromes, int64_t B, const bbp_params* prm, const float* init_msgs,
                         float* final_msgs, double* logp, double* delta, int32_t* iters, int32_t* flags,
                         int8_t* decision, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * bbp_decode_mixed -- syndromes of different distances in one persistent
+ * launch (fused path).  CTAs take (syndrome, coset) items from a counter in
+ * ``order`` (e.g. largest distance first); outputs are indexed by syndrome.
+ *   syndromes  device, packed: syndrome b starts at byte offsets[b] and has
+ *              m(d_of[b]) = 2 d (d-1) bytes
+ *   offsets    device [B] int64;  d_of  device [B] int32 (2 <= d <= d_max)
+ *   order      device [B] int32 permutation of 0..B-1, or NULL (natural order)
+ *   prm        k, p, eta, delta0, delta1, max_iter, precision; d is ignored;
+ *              algorithm must be BBP_ALG_FUSED
+ *   workspace  device, at least 256 bytes (the work counter)
+ * Errors as bbp_decode_batch.
+ */
+int bbp_decode_mixed(const uint8_t* syndromes, const int64_t* offsets, const int32_t* d_of, const int32_t* order,
+                     int64_t B, int32_t d_max, const bbp_params* prm, double* logp, double* delta, int32_t* iters,
+                     int32_t* flags, int8_t* decision, void* workspace, size_t workspace_bytes, void* stream);
 
 /* Static text for a return code. */
 const char* bbp_strerror(int code);

@@ -22,7 +22,7 @@ FLAG_UNTRUSTED, FLAG_OVERLAP, FLAG_BLOCK, FLAG_NONFINITE = 1, 2, 4, 8
 SYMBOLS = ("bbp_workspace_bytes", "bbp_decode_batch", "bbp_decode_batch_host", "bbp_sample",
            "bbp_strerror", "bbp_version", "bbp_decode_batch_static", "bbp_message_count",
            "bbp_message_features", "bbp_warm_param_count", "bbp_warm_workspace_bytes", "bbp_warm_infer",
-           "bbp_warm_train_step", "bbp_decode_batch_ex")
+           "bbp_warm_train_step", "bbp_decode_batch_ex", "bbp_decode_mixed")
 WARM_F, WARM_H, WARM_O, WARM_MAX_ROWS = 256, 256, 16, 4194240
 BBP_ETOOLARGE = -5
 STATIC_WORKSPACE_BYTES = 32 << 20
@@ -32,7 +32,8 @@ class BbpParams(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int32), ("k", ctypes.c_int32), ("D", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("p", ctypes.c_double), ("eta", ctypes.c_double),
                 ("delta0", ctypes.c_double), ("delta1", ctypes.c_double), ("cutoff", ctypes.c_double),
-                ("precision", ctypes.c_int32), ("algorithm", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("algorithm", ctypes.c_int32),
+                ("launch_warps", ctypes.c_int32), ("launch_ctas_per_sm", ctypes.c_int32)]
 
 
 @dataclass
@@ -49,13 +50,15 @@ class DecoderParams:
     cutoff: float | None = None
     precision: str = "fp64"
     algorithm: str = "mps"          # "mps" (Sec. III.D) or "fused" (Remark 9, k <= 4)
+    warps: int = 0                  # fused launch shape (tuning only): warps per CTA
+    ctas_per_sm: int = 0            # persistent mixed launch: resident CTAs per SM (0 = occupancy)
 
     def c(self) -> BbpParams:
         prec = FP64 if self.precision == "fp64" else FP32
         cut = self.cutoff if self.cutoff is not None else (1e-13 if prec == FP64 else 1e-7)
         alg = ALG_MPS if self.algorithm == "mps" else ALG_FUSED
         return BbpParams(self.d, self.k, self.D, self.max_iter, self.p, self.eta, self.delta0,
-                         self.delta1, cut, prec, alg)
+                         self.delta1, cut, prec, alg, self.warps, self.ctas_per_sm)
 
     @property
     def m(self) -> int:
@@ -85,6 +88,8 @@ def lib():
         L.bbp_decode_batch_host.argtypes = [vp, i64, P, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
         L.bbp_decode_batch_host.restype = ctypes.c_int
         L.bbp_decode_batch_ex.argtypes = [vp, i64, P, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+        L.bbp_decode_mixed.argtypes = [vp, vp, vp, vp, i64, i32, P, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+        L.bbp_decode_mixed.restype = ctypes.c_int
         L.bbp_decode_batch_ex.restype = ctypes.c_int
         L.bbp_message_count.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
         L.bbp_message_count.restype = ctypes.c_int
@@ -94,7 +99,7 @@ def lib():
         L.bbp_warm_param_count.restype = ctypes.c_int
         L.bbp_warm_workspace_bytes.argtypes = [i64, ctypes.POINTER(ctypes.c_size_t)]
         L.bbp_warm_workspace_bytes.restype = ctypes.c_int
-        L.bbp_warm_infer.argtypes = [vp, vp, vp, i64, vp, vp, ctypes.c_size_t, vp]
+        L.bbp_warm_infer.argtypes = [vp, vp, vp, i64, ctypes.c_float, vp, vp, ctypes.c_size_t, vp]
         L.bbp_warm_infer.restype = ctypes.c_int
         L.bbp_warm_train_step.argtypes = [vp, vp, vp, i32, ctypes.c_float, vp, vp, vp, i64, vp, vp, vp,
                                           ctypes.c_size_t, vp]

@@ -14,6 +14,11 @@ using bbp::Geo;
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
+int warps_of(const bbp_params* p) {
+  if (p->precision == BBP_FP64) return 8;
+  return p->launch_warps == 0 ? bbp::kFusedWarps : p->launch_warps;
+}
+
 int check_params(const bbp_params* p) {
   if (!p) return BBP_EINVAL;
   if (p->d < 2 || p->d > 64) return BBP_EINVAL;
@@ -24,12 +29,15 @@ int check_params(const bbp_params* p) {
   if (p->precision != BBP_FP64 && p->precision != BBP_FP32) return BBP_EINVAL;
   if (p->algorithm != BBP_ALG_MPS && p->algorithm != BBP_ALG_FUSED) return BBP_EINVAL;
   if (p->algorithm == BBP_ALG_MPS && (p->k > bbp::kMaxK || p->D > bbp::kMaxD)) return BBP_EUNSUPPORTED;
+  if (p->launch_warps != 0 && p->launch_warps != 4 && p->launch_warps != 8 && p->launch_warps != 16)
+    return BBP_EINVAL;
+  if (p->launch_ctas_per_sm < 0 || p->launch_ctas_per_sm > 32) return BBP_EINVAL;
   if (p->algorithm == BBP_ALG_FUSED) {
     if (p->k > bbp::kFusedMaxK) return BBP_EUNSUPPORTED;
     const bbp::Geo g = bbp::make_geo(p->d, p->k);
     int M = 0, ae = 0;
     bbp::count_messages(g, 1, &M, &ae);
-    if (bbp::fused_smem_bytes(p->precision, g, M) > 227 * 1024) return BBP_EUNSUPPORTED;
+    if (bbp::fused_smem_bytes(p->precision, g, M, warps_of(p)) > 227 * 1024) return BBP_EUNSUPPORTED;
   }
   return BBP_OK;
 }
@@ -108,7 +116,7 @@ int bbp_decode_batch_ex(const uint8_t* syndromes, int64_t B, const bbp_params* p
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   if (prm->algorithm == BBP_ALG_FUSED)
-    e = prm->precision == BBP_FP64 ? bbp::launch_fused_f64(a, st) : bbp::launch_fused_f32(a, st);
+    e = prm->precision == BBP_FP64 ? bbp::launch_fused_f64(a, 8, st) : bbp::launch_fused_f32(a, warps_of(prm), st);
   else
     e = prm->precision == BBP_FP64 ? bbp::launch_decode_f64(a, st) : bbp::launch_decode_f32(a, st);
   if (e != cudaSuccess) return BBP_ECUDA;
@@ -150,6 +158,37 @@ int bbp_decode_batch_host(const uint8_t* syndromes, int64_t B, const bbp_params*
   if (flags && cudaMemcpyAsync(flags, d_flags, (size_t)B * 16, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return BBP_ECUDA;
   return cudaStreamSynchronize(st) == cudaSuccess ? BBP_OK : BBP_ECUDA;
+}
+
+int bbp_decode_mixed(const uint8_t* syndromes, const int64_t* offsets, const int32_t* d_of, const int32_t* order,
+                     int64_t B, int32_t d_max, const bbp_params* prm, double* logp, double* delta, int32_t* iters,
+                     int32_t* flags, int8_t* decision, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!prm || prm->algorithm != BBP_ALG_FUSED) return BBP_EINVAL;
+  bbp_params q = *prm;
+  q.d = d_max;                                   // validate the largest geometry
+  const int rc = check_params(&q);
+  if (rc != BBP_OK) return rc;
+  if (B < 0 || B > (int64_t(1) << 29)) return BBP_EINVAL;
+  if (B == 0) return BBP_OK;
+  if (!syndromes || !offsets || !d_of || !logp || !delta || !iters || !flags || !decision || !workspace)
+    return BBP_EINVAL;
+  if (workspace_bytes < 256 || reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return BBP_ENOSPACE;
+  bbp::LaunchArgs a;
+  a.geo = bbp::make_geo(d_max, prm->k);
+  a.M = 0; a.D = prm->D; a.max_iter = prm->max_iter; a.arena_elems = 0;
+  a.p = prm->p; a.eta = prm->eta; a.delta0 = prm->delta0; a.delta1 = prm->delta1; a.cutoff = prm->cutoff;
+  a.synd = syndromes; a.arena = nullptr; a.logp = logp; a.delta = delta; a.iters = iters;
+  a.flags = flags; a.decision = decision; a.B = B;
+  bbp::MixedLaunch m;
+  m.d_of = d_of; m.offsets = offsets; m.order = order;
+  m.counter = static_cast<unsigned long long*>(workspace);
+  m.d_max = d_max; m.ctas_per_sm = prm->launch_ctas_per_sm;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = prm->precision == BBP_FP64 ? bbp::launch_fused_mixed_f64(a, m, 8, st)
+                                             : bbp::launch_fused_mixed_f32(a, m, warps_of(prm), st);
+  if (e != cudaSuccess) return BBP_ECUDA;
+  e = bbp::launch_decide(a, st);
+  return e == cudaSuccess ? BBP_OK : BBP_ECUDA;
 }
 
 int bbp_sample(uint64_t seed, int64_t first_shot, int64_t B, int32_t d, double p, uint8_t* ex,

@@ -30,24 +30,59 @@ cudaError_t launch_decode_t(const LaunchArgs& a, cudaStream_t st) {
 }
 
 template <typename T>
-int fused_smem_for(const Geo& g, int M) {
-  return fused_layout<T>(g, M, kFusedWarps).total;
+int fused_smem_for(const Geo& g, int M, int warps = kFusedWarps) {
+  return fused_layout<T>(g, M, warps).total;
 }
 
 template <typename T>
-cudaError_t launch_fused_t(const LaunchArgs& a, cudaStream_t st) {
+KArgs<T> fused_args(const LaunchArgs& a) {
   KArgs<T> k;
   k.geo = a.geo; k.M = a.M; k.D = a.D; k.max_iter = a.max_iter; k.arena_elems = 0;
   k.p = a.p; k.eta = a.eta; k.delta0 = a.delta0; k.delta1 = a.delta1; k.cutoff = a.cutoff;
   k.synd = a.synd; k.arena = nullptr;
   k.logp = a.logp; k.delta = a.delta; k.iters = a.iters; k.flags = a.flags;
   k.init_msgs = a.init_msgs; k.final_msgs = a.final_msgs;
-  const int smem = fused_smem_for<T>(a.geo, a.M);
-  auto kern = fused_kernel<T, kFusedWarps>;
+  return k;
+}
+
+template <typename T, int NW>
+cudaError_t launch_fused_nw(const LaunchArgs& a, cudaStream_t st) {
+  const KArgs<T> k = fused_args<T>(a);
+  const int smem = fused_smem_for<T>(a.geo, a.M, NW);
+  auto kern = fused_kernel<T, NW>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)(a.B * 4);
-  kern<<<grid, kFusedWarps * 32, smem, st>>>(k);
+  kern<<<grid, NW * 32, smem, st>>>(k);
+  return cudaGetLastError();
+}
+
+template <typename T, int NW>
+cudaError_t launch_fused_mixed_nw(const LaunchArgs& a, const MixedLaunch& m, cudaStream_t st) {
+  const KArgs<T> k = fused_args<T>(a);
+  const Geo gmax = make_geo(m.d_max, a.geo.k);
+  int Mmax = 0, ae = 0;
+  count_messages(gmax, 1, &Mmax, &ae);
+  const int smem = fused_smem_for<T>(gmax, Mmax, NW);
+  auto kern = fused_mixed_kernel<T, NW>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = m.ctas_per_sm;
+  if (per_sm <= 0) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NW * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+  }
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  MixedArgs mx;
+  mx.d_of = m.d_of; mx.offsets = m.offsets; mx.order = m.order; mx.counter = m.counter;
+  mx.n_items = a.B * 4; mx.k = a.geo.k;
+  long long grid = (long long)sms * per_sm;
+  if (grid > mx.n_items) grid = mx.n_items;
+  if ((e = cudaMemsetAsync(m.counter, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+  kern<<<(unsigned)grid, NW * 32, smem, st>>>(k, mx);
   return cudaGetLastError();
 }
 

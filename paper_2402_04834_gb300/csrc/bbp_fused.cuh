@@ -78,7 +78,7 @@ struct FState {
 // dense messages; leaves the outgoing vector over the chain in ws.s0 and
 // returns the log of the norms taken out (read-out only).
 template <typename T, int K>
-__device__ __noinline__ double fused_sweep(FusedWS<T>& ws, const Ctx<T, K>& c, const T* msgs, const Frame& f,
+__device__ __forceinline__ double fused_sweep(FusedWS<T>& ws, const Ctx<T, K>& c, const T* msgs, const Frame& f,
                                            bool readout, int lane) {
   const int h = f.h, nc = f.ncols;
   T* cur = ws.s0;
@@ -151,12 +151,30 @@ __device__ __noinline__ double fused_sweep(FusedWS<T>& ws, const Ctx<T, K>& c, c
     for (int s = 0; s < h; ++s) {
       const int P = (h - 1 - s) + st.bb + 1;          // bit of the node's row in the index
       const int bitP = 1 << P;
-      T w[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) w[q] = ws.wn[s * 16 + q];
       const int nq = st.size() >> 2;
       const int lowmask = (1 << (P - 1)) - 1;
       using V2 = typename Vec2<T>::type;
+      int ni, nj;
+      f.node(t, s, &ni, &nj);
+      if (((ni + nj) & 1) && ni > 0 && nj > 0 && ni < c.g.W - 1 && nj < c.g.W - 1) {
+        // Interior check: a copy tensor over four legs, out[r][d] = [r = d] in[r][r].
+        for (int g = lane; g < nq; g += 32) {
+          const int base = ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
+          const V2 i0 = *reinterpret_cast<const V2*>(cur + base);
+          const V2 i1 = *reinterpret_cast<const V2*>(cur + (base | bitP));
+          V2 o0, o1;
+          o0.x = i0.x; o0.y = T(0);
+          o1.x = T(0); o1.y = i1.y;
+          *reinterpret_cast<V2*>(nxt + base) = o0;
+          *reinterpret_cast<V2*>(nxt + (base | bitP)) = o1;
+        }
+        __syncwarp();
+        T* tmp = cur; cur = nxt; nxt = tmp;
+        continue;
+      }
+      T w[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) w[q] = ws.wn[s * 16 + q];
       for (int g = lane; g < nq; g += 32) {
         const int base = ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
         const V2 i0 = *reinterpret_cast<const V2*>(cur + base);          // (l=0,u=0), (l=0,u=1)
@@ -249,17 +267,18 @@ __device__ __forceinline__ double fused_dot(const T* x, const T* y, int n, int l
   return warp_sum(acc);
 }
 
-// Resident CTAs per SM the register budget is sized for: shared memory holds
-// four FP32 CTAs or two FP64 ones at d = 11.
-template <typename T> struct FusedMinBlocks { static constexpr int value = 4; };
-template <> struct FusedMinBlocks<double> { static constexpr int value = 2; };
+// Resident CTAs per SM the register budget is sized for: 32 warps per SM in
+// FP32 (64 registers a thread), 16 in FP64; shared memory at d = 11 allows it.
+template <typename T, int NW> struct FusedMinBlocks { static constexpr int value = 32 / NW > 1 ? 32 / NW : 1; };
+template <int NW> struct FusedMinBlocks<double, NW> { static constexpr int value = 16 / NW > 1 ? 16 / NW : 1; };
 
+// One (syndrome, coset) decoded by the whole CTA: syn_src holds the
+// syndrome's m bytes and ``cta`` indexes the outputs (syndrome * 4 + coset).
 template <typename T, int NW>
-__global__ void __launch_bounds__(NW * 32, FusedMinBlocks<T>::value) fused_kernel(KArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const int M, const uint8_t* syn_src,
+                                           const long long cta, const int coset, unsigned char* smem) {
   using WS = FusedWS<T>;
-  const Geo g = a.geo;
-  const int W = g.W, d = g.d, nb = g.nb, M = a.M;
+  const int W = g.W, d = g.d, nb = g.nb;
   const int m = 2 * d * (d - 1);
   const FusedLayout Lo = fused_layout<T>(g, M, NW);
   uint8_t* synd = smem + Lo.synd;
@@ -275,11 +294,8 @@ __global__ void __launch_bounds__(NW * 32, FusedMinBlocks<T>::value) fused_kerne
   WS* wsa = reinterpret_cast<WS*>(smem + Lo.ws);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const long long cta = blockIdx.x;
-  const long long shot = cta >> 2;
-  const int coset = (int)(cta & 3);
 
-  for (int i = tid; i < m; i += NW * 32) synd[i] = a.synd[shot * m + i];
+  for (int i = tid; i < m; i += NW * 32) synd[i] = syn_src[i];
   __syncthreads();
   const int bx = (coset == 1 || coset == 2), bz = (coset == 2 || coset == 3);
   for (int e = tid; e < W * W; e += NW * 32) {
@@ -452,6 +468,47 @@ __global__ void __launch_bounds__(NW * 32, FusedMinBlocks<T>::value) fused_kerne
       a.iters[cta] = it_done;
       a.flags[cta] = fl;
     }
+  }
+}
+
+
+template <typename T, int NW>
+__global__ void __launch_bounds__(NW * 32, (FusedMinBlocks<T, NW>::value)) fused_kernel(KArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const long long cta = blockIdx.x;
+  const int m = 2 * a.geo.d * (a.geo.d - 1);
+  fused_item<T, NW>(a, a.geo, a.M, a.synd + (cta >> 2) * m, cta, (int)(cta & 3), smem);
+}
+
+// A batch of syndromes of different distances in one persistent launch: CTAs
+// take (syndrome, coset) items from a global counter in the order given
+// (largest distance first balances the tail) until the batch is done.
+struct MixedArgs {
+  const int32_t* d_of;          // distance of each syndrome
+  const int64_t* offsets;       // byte offset of each syndrome in the packed buffer
+  const int32_t* order;         // syndrome order of the items, or null
+  unsigned long long* counter;  // zero before the launch
+  long long n_items;            // 4 * B
+  int k;
+};
+
+template <typename T, int NW>
+__global__ void __launch_bounds__(NW * 32, (FusedMinBlocks<T, NW>::value)) fused_mixed_kernel(KArgs<T> a, MixedArgs mx) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long item_sh;
+  for (;;) {
+    if (threadIdx.x == 0) item_sh = (long long)atomicAdd(mx.counter, 1ull);
+    __syncthreads();
+    const long long item = item_sh;
+    __syncthreads();
+    if (item >= mx.n_items) break;
+    const long long shot = mx.order ? (long long)mx.order[item >> 2] : (item >> 2);
+    const int coset = (int)(item & 3);
+    const Geo g = make_geo(mx.d_of[shot], mx.k);
+    int M = 0, ae = 0;
+    count_messages(g, 1, &M, &ae);
+    fused_item<T, NW>(a, g, M, a.synd + mx.offsets[shot], shot * 4 + coset, coset, smem);
+    __syncthreads();
   }
 }
 

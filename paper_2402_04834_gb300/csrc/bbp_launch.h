@@ -38,10 +38,21 @@ int cta_smem_bytes(int precision, const Geo& g, int M);
 // Fused-block path (Remark 9): block side k <= kFusedMaxK, messages in shared memory.
 constexpr int kFusedMaxK = 4;
 constexpr int kFusedWarps = 8;
-int fused_smem_bytes(int precision, const Geo& g, int M);
+int fused_smem_bytes(int precision, const Geo& g, int M, int warps = kFusedWarps);
 
-cudaError_t launch_fused_f64(const LaunchArgs& a, cudaStream_t st);
-cudaError_t launch_fused_f32(const LaunchArgs& a, cudaStream_t st);
+struct MixedLaunch {
+  const int32_t* d_of;
+  const int64_t* offsets;
+  const int32_t* order;
+  unsigned long long* counter;
+  int d_max;
+  int ctas_per_sm;
+};
+
+cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, cudaStream_t st);
+cudaError_t launch_fused_f32(const LaunchArgs& a, int warps, cudaStream_t st);
+cudaError_t launch_fused_mixed_f64(const LaunchArgs& a, const MixedLaunch& mx, int warps, cudaStream_t st);
+cudaError_t launch_fused_mixed_f32(const LaunchArgs& a, const MixedLaunch& mx, int warps, cudaStream_t st);
 cudaError_t launch_decode_f64(const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_decode_f32(const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_decide(const LaunchArgs& a, cudaStream_t st);

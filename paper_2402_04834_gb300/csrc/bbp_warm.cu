@@ -194,7 +194,7 @@ cudaError_t gemm(int Mr, int N, int K, const float* A, int lda, const float* B, 
 
 // u = masked exp(o - max) / norm; per-row loss 1 - <u,t>^2 and dL/do (mean over N).
 __global__ void head_kernel(const float* logits, const int32_t* lens, const float* targets, long long N,
-                            float* msgs, float* gO, float* loss_sum) {
+                            float* msgs, float* gO, float* loss_sum, float alpha) {
   const long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (row >= N) return;
   const int n = lens[row];
@@ -204,8 +204,17 @@ __global__ void head_kernel(const float* logits, const int32_t* lens, const floa
   float s2 = 0.f;
   for (int i = 0; i < O; ++i) { mm[i] = i < n ? expf(o[i] - mx) : 0.f; s2 += mm[i] * mm[i]; }
   const float nm = sqrtf(s2), inv = 1.f / nm;
-  if (msgs)
-    for (int i = 0; i < O; ++i) msgs[row * O + i] = mm[i] * inv;
+  if (msgs) {
+    // Proposal blended with the uniform start: (1 - alpha) uniform + alpha u.
+    const float un = rsqrtf((float)n);
+    float b[O], s2b = 0.f;
+    for (int i = 0; i < O; ++i) {
+      b[i] = i < n ? (1.f - alpha) * un + alpha * mm[i] * inv : 0.f;
+      s2b += b[i] * b[i];
+    }
+    const float ib = rsqrtf(s2b);
+    for (int i = 0; i < O; ++i) msgs[row * O + i] = b[i] * ib;
+  }
   if (targets) {
     float cdot = 0.f;
     for (int i = 0; i < O; ++i) cdot += mm[i] * inv * targets[row * O + i];
@@ -308,9 +317,10 @@ int bbp_warm_workspace_bytes(int64_t N, size_t* bytes) {
   return BBP_OK;
 }
 
-int bbp_warm_infer(const float* theta, const float* feats, const int32_t* lens, int64_t N, float* msgs,
-                   void* workspace, size_t workspace_bytes, void* stream) {
+int bbp_warm_infer(const float* theta, const float* feats, const int32_t* lens, int64_t N, float alpha,
+                   float* msgs, void* workspace, size_t workspace_bytes, void* stream) {
   if (!theta || !feats || !lens || !msgs || N < 0 || N > BBP_WARM_MAX_ROWS) return BBP_EINVAL;
+  if (!(alpha >= 0.f && alpha <= 1.f)) return BBP_EINVAL;
   if (N == 0) return BBP_OK;
   if (!workspace || workspace_bytes < pass_bytes(N)) return BBP_ENOSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -324,7 +334,7 @@ int bbp_warm_infer(const float* theta, const float* feats, const int32_t* lens, 
       gemm<false, false>((int)N, H, H, A1, H, P.W2, H, A2, H, P.b2, nullptr, 1, 0, 1, st) != cudaSuccess ||
       gemm<false, false>((int)N, O, H, A2, H, P.W3, O, L, O, P.b3, nullptr, 0, 0, 1, st) != cudaSuccess)
     return BBP_ECUDA;
-  head_kernel<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(L, lens, nullptr, N, msgs, nullptr, nullptr);
+  head_kernel<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(L, lens, nullptr, N, msgs, nullptr, nullptr, alpha);
   return cudaGetLastError() == cudaSuccess ? BBP_OK : BBP_ECUDA;
 }
 
@@ -359,7 +369,7 @@ int bbp_warm_train_step(float* theta, float* adam_m, float* adam_v, int32_t step
   ok = ok && gemm<false, false>(n, O, H, A2, H, P.W3, O, L, O, P.b3, nullptr, 0, 0, 0, st) == cudaSuccess;
   if (!ok) return BBP_ECUDA;
   if (cudaMemsetAsync(loss_sum, 0, sizeof(float), st) != cudaSuccess) return BBP_ECUDA;
-  head_kernel<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(L, lens, targets, N, nullptr, gO, loss_sum);
+  head_kernel<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(L, lens, targets, N, nullptr, gO, loss_sum, 1.f);
   // Layer 3: gW3 = A2^T gO, gb3 = colsum gO, gA2 = gO W3^T.
   ok = ok && gemm<true, false>(H, O, n, A2, H, gO, O, gW3, O, nullptr, nullptr, 0, 0, 0, st) == cudaSuccess;
   colsum_kernel<<<O, 256, 0, st>>>(gO, N, O, gb3);

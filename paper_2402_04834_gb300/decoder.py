@@ -100,3 +100,43 @@ def sample(seed: int, first_shot: int, B: int, d: int, p: float, device="cuda", 
     check(lib().bbp_sample(seed, first_shot, B, d, p, _ptr(ex) if ex is not None else None,
                            _ptr(ez) if ez is not None else None, _ptr(s), _ptr(tc), _stream(stream)))
     return ex, ez, s, tc
+
+
+def pack_mixed(syndromes_by_shot, device="cuda"):
+    """Pack per-shot syndromes of different lengths: (packed, offsets, d_of)."""
+    lens = [len(s) for s in syndromes_by_shot]
+    d_of = []
+    for m in lens:
+        d = int(round((1 + (1 + 2 * m) ** 0.5) / 2))     # m = 2 d (d - 1)
+        if 2 * d * (d - 1) != m:
+            raise ValueError(f"syndrome length {m} is not 2d(d-1)")
+        d_of.append(d)
+    offsets = np.zeros(len(lens), dtype=np.int64)
+    offsets[1:] = np.cumsum(lens)[:-1]
+    packed = np.concatenate([np.asarray(s, dtype=np.uint8) for s in syndromes_by_shot])
+    return (torch.from_numpy(packed).to(device), torch.from_numpy(offsets).to(device),
+            torch.tensor(d_of, dtype=torch.int32, device=device))
+
+
+def decode_mixed(packed, offsets, d_of, prm: DecoderParams, largest_first=True, stream=None, out=None,
+                 counter=None):
+    """Syndromes of different distances in one persistent launch (fused path)."""
+    B = d_of.shape[0]
+    dev = d_of.device
+    if out is None:
+        out = {
+            "logp": torch.empty(B, 4, dtype=torch.float64, device=dev),
+            "delta": torch.empty(B, 4, dtype=torch.float64, device=dev),
+            "iters": torch.empty(B, 4, dtype=torch.int32, device=dev),
+            "flags": torch.empty(B, 4, dtype=torch.int32, device=dev),
+            "decision": torch.empty(B, dtype=torch.int8, device=dev),
+        }
+    order = torch.argsort(d_of, descending=True, stable=True).to(torch.int32) if largest_first else None
+    d_max = int(d_of.max().item())
+    counter = counter if counter is not None else torch.empty(256, dtype=torch.uint8, device=dev)
+    cp = prm.c()
+    check(lib().bbp_decode_mixed(_ptr(packed), _ptr(offsets), _ptr(d_of), _ptr(order) if order is not None else None,
+                                 B, d_max, ctypes.byref(cp), _ptr(out["logp"]), _ptr(out["delta"]),
+                                 _ptr(out["iters"]), _ptr(out["flags"]), _ptr(out["decision"]), _ptr(counter),
+                                 counter.numel(), _stream(stream)))
+    return out

@@ -86,16 +86,17 @@ class WarmStart:
         torch.cuda.synchronize(self.device)
         return float(self.loss.item()) / N, self.grad.clone()
 
-    def infer(self, feats, lens, out=None, stream=None):
-        """Initial messages [N, 16] for the given feature rows (chunked)."""
+    def infer(self, feats, lens, out=None, stream=None, alpha=1.0):
+        """Initial messages [N, 16] for the given feature rows (chunked),
+        blended with the uniform start by ``alpha``."""
         N = feats.shape[0]
         out = out if out is not None else torch.empty(N, WARM_O, dtype=torch.float32, device=feats.device)
         step = min(N, WARM_MAX_ROWS, 1 << 20)
         ws = self.ws.get(_ws_bytes(step), self.device)
         for a in range(0, N, step):
             b = min(N, a + step)
-            check(lib().bbp_warm_infer(_ptr(self.theta), _ptr(feats[a:b]), _ptr(lens[a:b]), b - a, _ptr(out[a:b]),
-                                       _ptr(ws), ws.numel(), _stream(stream)))
+            check(lib().bbp_warm_infer(_ptr(self.theta), _ptr(feats[a:b]), _ptr(lens[a:b]), b - a, alpha,
+                                       _ptr(out[a:b]), _ptr(ws), ws.numel(), _stream(stream)))
         return out
 
     def train(self, feats, targets, lens, epochs=4, batch=8192, lr=1e-3, seed=0, log=None):
@@ -139,10 +140,13 @@ def decode_ex(syndromes, prm: DecoderParams, init_msgs=None, final_msgs=None, wo
     return out
 
 
-def decode_warm(syndromes, prm: DecoderParams, net: WarmStart, stream=None, out=None, buffers=None):
+DEFAULT_ALPHA = 0.1     # blend weight of the proposal (measured: larger weights raise P_L)
+
+
+def decode_warm(syndromes, prm: DecoderParams, net: WarmStart, stream=None, out=None, alpha=DEFAULT_ALPHA):
     """Learned warm start: features -> network -> fused decode."""
     feats, lens = features(syndromes, prm, stream)
-    init = net.infer(feats, lens, stream=stream)
+    init = net.infer(feats, lens, stream=stream, alpha=alpha)
     return decode_ex(syndromes, prm, init_msgs=init, stream=stream, out=out)
 
 
@@ -190,14 +194,15 @@ def build_training_set(device="cuda", d_list=(11, 15), shots=(1500, 800), p_grid
     return F, T, L
 
 
-def evaluate(net: WarmStart, d=13, p=0.10, shots=10000, k=4, seed=5000, device="cuda", max_iter=20, delta0=1e-4):
+def evaluate(net: WarmStart, d=13, p=0.10, shots=10000, k=4, seed=5000, device="cuda", max_iter=20, delta0=1e-4,
+             alpha=DEFAULT_ALPHA):
     """Cold versus warm start on fresh syndromes: iterations, P_L, throughput."""
     from .decoder import sample
     _, _, s, tc = sample(seed, 0, shots, d, p, device=device, with_errors=False)
     prm = DecoderParams(d=d, k=k, p=p, max_iter=max_iter, delta0=delta0, precision="fp32", algorithm="fused")
-    res = {}
+    res = {"alpha": alpha}
     for name in ("cold", "warm"):
-        run = (lambda: decode(s, prm)) if name == "cold" else (lambda: decode_warm(s, prm, net))
+        run = (lambda: decode(s, prm)) if name == "cold" else (lambda: decode_warm(s, prm, net, alpha=alpha))
         out = run()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -227,12 +232,13 @@ def main():
     F, T, L = build_training_set(device=dev)
     t1 = time.time()
     net = WarmStart(device=dev, seed=0)
-    hist = net.train(F, T, L, epochs=8, batch=8192, lr=1e-3)
+    hist = net.train(F, T, L, epochs=12, batch=8192, lr=3e-3)
+    hist += net.train(F, T, L, epochs=8, batch=8192, lr=5e-4, seed=1)
     torch.cuda.synchronize()
     t2 = time.time()
-    ev = evaluate(net, device=dev)
+    evs = [evaluate(net, device=dev, alpha=a) for a in (0.1, 0.25, 0.5, 1.0)]
     print(json.dumps({"training_rows": int(F.shape[0]), "data_s": t1 - t0, "train_s": t2 - t1,
-                      "loss_per_epoch": hist, "evaluation_d13_p010": ev}))
+                      "loss_per_epoch": hist, "evaluation_d13_p010": evs}))
 
 
 if __name__ == "__main__":

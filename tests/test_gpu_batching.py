@@ -1,0 +1,116 @@
+"""Batching: mixed distances in one persistent launch, CUDA-graph capture,
+autotuned launch shapes.  Results must not depend on any of them."""
+
+import numpy as np
+import pytest
+
+import paper_2402_04834_gb300 as pkg
+import synth
+from oracle.lattice import Lattice
+from oracle.naive import run_naive
+from oracle.tn import coset_network
+from paper_2402_04834_gb300 import autotune
+from paper_2402_04834_gb300.build import build
+from paper_2402_04834_gb300.decoder import decode_mixed, pack_mixed
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    build()
+    pkg.lib()
+    return torch.device("cuda:0")
+
+
+def mixed_batch(B, dists, p, seed):
+    rng = np.random.default_rng(seed)
+    ds = rng.choice(dists, size=B)
+    shots = []
+    for b, d in enumerate(ds):
+        _, _, S = synth.sample_syndromes(seed, b, 1, int(d), p)
+        shots.append(S[0])
+    return ds, shots
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_mixed_batch_equals_per_distance_decodes(dev, precision):
+    p = 0.1
+    ds, shots = mixed_batch(96, [3, 5, 7, 9, 11], p, 17)
+    packed, offsets, d_of = pack_mixed(shots, device=dev)
+    prm = pkg.DecoderParams(d=0, k=4, p=p, max_iter=8, delta0=1e-4, precision=precision, algorithm="fused")
+    for largest_first in (True, False):
+        out = decode_mixed(packed, offsets, d_of, prm, largest_first=largest_first)
+        torch.cuda.synchronize()
+        for d in sorted(set(ds.tolist())):
+            idx = np.nonzero(ds == d)[0]
+            S = np.stack([shots[i] for i in idx])
+            ref = pkg.decode(torch.from_numpy(S).to(dev), pkg.DecoderParams(**{**prm.__dict__, "d": int(d)}))
+            torch.cuda.synchronize()
+            for key in ("logp", "delta", "iters", "flags", "decision"):
+                assert torch.equal(out[key][torch.from_numpy(idx).to(dev)], ref[key]), (d, key)
+
+
+def test_mixed_batch_matches_dense_oracle_on_a_sample(dev):
+    p = 0.1
+    ds, shots = mixed_batch(16, [3, 5, 7], p, 23)
+    packed, offsets, d_of = pack_mixed(shots, device=dev)
+    prm = pkg.DecoderParams(d=0, k=4, p=p, max_iter=5, delta0=0.0, precision="fp64", algorithm="fused")
+    out = decode_mixed(packed, offsets, d_of, prm)
+    torch.cuda.synchronize()
+    for b in (0, 5, 11):
+        d = int(ds[b])
+        lat = Lattice(d)
+        for L in range(4):
+            lp, _, _, _ = run_naive(coset_network(lat, shots[b], L, p), 4, 5, 0.1, 0.0)
+            assert abs(out["logp"][b, L].item() - lp) < 1e-9
+
+
+def test_cuda_graph_capture_replays_the_decode(dev):
+    d, p = 11, 0.1
+    prm = pkg.DecoderParams(d=d, k=4, p=p, max_iter=20, delta0=1e-4, precision="fp32", algorithm="fused")
+    _, _, S1 = synth.sample_syndromes(31, 0, 512, d, p)
+    _, _, S2 = synth.sample_syndromes(32, 0, 512, d, p)
+    s_static = torch.from_numpy(S1).to(dev)
+    out = pkg.decode(s_static, prm)                      # warm up: buffers exist before capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(g, stream=stream):
+            pkg.decode(s_static, prm, out=out, stream=stream)
+    torch.cuda.current_stream().wait_stream(stream)
+    for S in (S2, S1):
+        s_static.copy_(torch.from_numpy(S).to(dev))
+        g.replay()
+        torch.cuda.synchronize()
+        ref = pkg.decode(torch.from_numpy(S).to(dev), prm)
+        torch.cuda.synchronize()
+        for key in ("logp", "iters", "decision"):
+            assert torch.equal(out[key], ref[key]), key
+
+
+def test_autotuned_shapes_give_identical_results(dev):
+    d, p = 9, 0.1
+    _, _, S = synth.sample_syndromes(41, 0, 256, d, p)
+    s = torch.from_numpy(S).to(dev)
+    prm = pkg.DecoderParams(d=d, k=4, p=p, max_iter=10, precision="fp32", algorithm="fused")
+    best, table = autotune.tune_uniform(s, prm)
+    assert len(table) == 3 and best.warps in (4, 8, 16)
+    ref = pkg.decode(s, prm)
+    for w in (4, 16):
+        got = pkg.decode(s, pkg.DecoderParams(**{**prm.__dict__, "warps": w}))
+        torch.cuda.synchronize()
+        assert torch.equal(got["logp"], ref["logp"])
+    ds, shots = mixed_batch(128, [7, 9, 13], p, 5)
+    packed, offsets, d_of = pack_mixed(shots, device=dev)
+    mp = pkg.DecoderParams(d=0, k=4, p=p, max_iter=10, precision="fp32", algorithm="fused")
+    best, table = autotune.tune_mixed(packed, offsets, d_of, mp, ctas=(0, 2))
+    assert len(table) >= 2
+    a = decode_mixed(packed, offsets, d_of, best)
+    b = decode_mixed(packed, offsets, d_of, mp)
+    torch.cuda.synchronize()
+    assert torch.equal(a["logp"], b["logp"])
