@@ -97,14 +97,12 @@ __device__ __forceinline__ double fused_sweep(FusedWS<T>& ws, const Ctx<T, K>& c
   const int sd = nc >> 1;               // the column that holds the data site
   const int nf = nc - sd - 1;           // legs still expected after it
   double log_scale = 0.0;
+  // Which parity the in/out legs carry: a qubit's tensor is pi(f (+) (x, z))
+  // with one of x, z the parity of its in/out legs (alpha) and the other the
+  // parity of its chain legs (beta); alpha is z for horizontal-edge qubits
+  // swept along rows and for vertical-edge qubits swept along columns.
+  const bool rowwise = f.dir == kDirR || f.dir == kDirL;
   for (int t = 0; t < nc; ++t) {
-    for (int e = lane; e < h * 16; e += 32) {
-      const int s = e >> 4, q = e & 15;
-      int i, j;
-      f.node(t, s, &i, &j);
-      ws.wn[e] = node_value<T>(c.frame, c.g.W, c.pI, c.pE, i, j, f.dir, (q >> 3) & 1, (q >> 2) & 1,
-                               (q >> 1) & 1, q & 1);
-    }
     // Side message A: enters the column as its vertical leg v.  Output
     // entries come in pairs (v = 0, 1) sharing (a, rows, b).
     {
@@ -156,7 +154,37 @@ __device__ __forceinline__ double fused_sweep(FusedWS<T>& ws, const Ctx<T, K>& c
       using V2 = typename Vec2<T>::type;
       int ni, nj;
       f.node(t, s, &ni, &nj);
-      if (((ni + nj) & 1) && ni > 0 && nj > 0 && ni < c.g.W - 1 && nj < c.g.W - 1) {
+      const bool interior = ni > 0 && nj > 0 && ni < c.g.W - 1 && nj < c.g.W - 1;
+      if (interior && !((ni + nj) & 1)) {
+        // Interior qubit: out[r][d] = sum_{l,u} in[l][u] g[l^r][u^d], an XOR
+        // convolution with the 2 x 2 table g[alpha][beta].
+        const int fr = c.frame[ni * c.g.W + nj];
+        const int fx = fr & 1, fz = (fr >> 1) & 1;
+        const bool alpha_is_z = ((ni & 1) == 0) == rowwise;
+        T gt[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int al = q >> 1, be = q & 1;
+          const int xb = alpha_is_z ? be : al, zb = alpha_is_z ? al : be;
+          gt[q] = ((fx ^ xb) | (fz ^ zb)) ? c.pE : c.pI;
+        }
+        for (int g = lane; g < nq; g += 32) {
+          const int base = ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
+          const V2 i0 = *reinterpret_cast<const V2*>(cur + base);          // in[0][0], in[0][1]
+          const V2 i1 = *reinterpret_cast<const V2*>(cur + (base | bitP)); // in[1][0], in[1][1]
+          V2 o0, o1;
+          o0.x = i0.x * gt[0] + i0.y * gt[1] + i1.x * gt[2] + i1.y * gt[3];
+          o0.y = i0.x * gt[1] + i0.y * gt[0] + i1.x * gt[3] + i1.y * gt[2];
+          o1.x = i0.x * gt[2] + i0.y * gt[3] + i1.x * gt[0] + i1.y * gt[1];
+          o1.y = i0.x * gt[3] + i0.y * gt[2] + i1.x * gt[1] + i1.y * gt[0];
+          *reinterpret_cast<V2*>(nxt + base) = o0;
+          *reinterpret_cast<V2*>(nxt + (base | bitP)) = o1;
+        }
+        __syncwarp();
+        T* tmp = cur; cur = nxt; nxt = tmp;
+        continue;
+      }
+      if (interior) {
         // Interior check: a copy tensor over four legs, out[r][d] = [r = d] in[r][r].
         for (int g = lane; g < nq; g += 32) {
           const int base = ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
@@ -172,9 +200,15 @@ __device__ __forceinline__ double fused_sweep(FusedWS<T>& ws, const Ctx<T, K>& c
         T* tmp = cur; cur = nxt; nxt = tmp;
         continue;
       }
+      // Border node: the general 16-entry tensor (missing legs carry 0).
+      if (lane < 16)
+        ws.wn[lane] = node_value<T>(c.frame, c.g.W, c.pI, c.pE, ni, nj, f.dir, (lane >> 3) & 1, (lane >> 2) & 1,
+                                    (lane >> 1) & 1, lane & 1);
+      __syncwarp();
       T w[16];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) w[q] = ws.wn[s * 16 + q];
+      for (int q = 0; q < 16; ++q) w[q] = ws.wn[q];
+      __syncwarp();
       for (int g = lane; g < nq; g += 32) {
         const int base = ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
         const V2 i0 = *reinterpret_cast<const V2*>(cur + base);          // (l=0,u=0), (l=0,u=1)
