@@ -76,7 +76,7 @@ struct FState {
 
 // Contract block f (rotated so that f.dir points right) with its incoming
 // dense messages; leaves the outgoing vector over the chain in ws.s0 and
-// returns the log of the norms taken out (read-out only).
+// returns the log of the norms taken out (read-out only; FP64, in lane 0).
 template <typename T, int K>
 __device__ __forceinline__ double fused_sweep(FusedWS<T>& ws, const Ctx<T, K>& c, const T* msgs, const Frame& f,
                                            bool readout, int lane) {
@@ -96,7 +96,7 @@ __device__ __forceinline__ double fused_sweep(FusedWS<T>& ws, const Ctx<T, K>& c
   FState st{0, h, 0, 0};
   const int sd = nc >> 1;               // the column that holds the data site
   const int nf = nc - sd - 1;           // legs still expected after it
-  double log_scale = 0.0;
+  double log_scale = 0.0;               // accumulated by lane 0 only
   // Which parity the in/out legs carry: a qubit's tensor is pi(f (+) (x, z))
   // with one of x, z the parity of its in/out legs (alpha) and the other the
   // parity of its chain legs (beta); alpha is z for horizontal-edge qubits
@@ -155,6 +155,70 @@ __device__ __forceinline__ double fused_sweep(FusedWS<T>& ws, const Ctx<T, K>& c
       int ni, nj;
       f.node(t, s, &ni, &nj);
       const bool interior = ni > 0 && nj > 0 && ni < c.g.W - 1 && nj < c.g.W - 1;
+      if (interior && s + 1 < h) {
+        int mi, mj;
+        f.node(t, s + 1, &mi, &mj);
+        if (mi > 0 && mj > 0 && mi < c.g.W - 1 && mj < c.g.W - 1) {
+          // Two interior chain neighbours, one check and one qubit, in one
+          // pass: the check's copy tensor ties the vertical leg between them
+          // to the check's own row bit c.
+          const bool check_first = (ni + nj) & 1;
+          const int qi = check_first ? mi : ni, qj = check_first ? mj : nj;
+          const int fr = c.frame[qi * c.g.W + qj];
+          const int fx = fr & 1, fz = (fr >> 1) & 1;
+          const bool alpha_is_z = ((qi & 1) == 0) == rowwise;
+          T gt[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int al = q >> 1, be = q & 1;
+            const int xb = alpha_is_z ? be : al, zb = alpha_is_z ? al : be;
+            gt[q] = ((fx ^ xb) | (fz ^ zb)) ? c.pE : c.pI;
+          }
+          if (check_first) {
+            // out[c, r, d] = sum_l in[c, l, v=c] g[l^r][c^d]; rows bits P (c) and P-1 (qubit).
+            const int Q = P - 1, bitQ = 1 << Q, lowq = (1 << (Q - 1)) - 1;
+            for (int g = lane; g < nq; g += 32) {
+              const int base = ((g >> (Q - 1)) << (Q + 1)) | ((g & lowq) << 1);
+              const int cb = (base >> P) & 1;
+              const T x0 = cur[base | cb];
+              const T x1 = cur[base | bitQ | cb];
+              // g[a][c ^ d] by selects (a dynamic index would put gt in local memory)
+              const T g00 = cb ? gt[1] : gt[0], g01 = cb ? gt[0] : gt[1];
+              const T g10 = cb ? gt[3] : gt[2], g11 = cb ? gt[2] : gt[3];
+              V2 o0, o1;
+              o0.x = x0 * g00 + x1 * g10;   // r = 0, d = 0
+              o0.y = x0 * g01 + x1 * g11;   // r = 0, d = 1
+              o1.x = x0 * g10 + x1 * g00;   // r = 1, d = 0
+              o1.y = x0 * g11 + x1 * g01;   // r = 1, d = 1
+              *reinterpret_cast<V2*>(nxt + base) = o0;
+              *reinterpret_cast<V2*>(nxt + (base | bitQ)) = o1;
+            }
+          } else {
+            // out[r, c, v] = [v = c] sum_{l,u} in[l, c, u] g[l^r][u^c]; qubit bit P, check bit P-1.
+            const int cpos = P - 1;
+            for (int g = lane; g < nq; g += 32) {
+              const int base = ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
+              const int cb = (base >> cpos) & 1;
+              const V2 i0 = *reinterpret_cast<const V2*>(cur + base);          // in[0][u=0,1]
+              const V2 i1 = *reinterpret_cast<const V2*>(cur + (base | bitP)); // in[1][u=0,1]
+              // g[l ^ r][u ^ c]
+              const T g00 = cb ? gt[1] : gt[0], g01 = cb ? gt[0] : gt[1];
+              const T g10 = cb ? gt[3] : gt[2], g11 = cb ? gt[2] : gt[3];
+              const T r0 = i0.x * g00 + i0.y * g01 + i1.x * g10 + i1.y * g11;
+              const T r1 = i0.x * g10 + i0.y * g11 + i1.x * g00 + i1.y * g01;
+              V2 o0, o1;
+              o0.x = cb ? T(0) : r0; o0.y = cb ? r0 : T(0);
+              o1.x = cb ? T(0) : r1; o1.y = cb ? r1 : T(0);
+              *reinterpret_cast<V2*>(nxt + base) = o0;
+              *reinterpret_cast<V2*>(nxt + (base | bitP)) = o1;
+            }
+          }
+          __syncwarp();
+          T* tmp = cur; cur = nxt; nxt = tmp;
+          ++s;
+          continue;
+        }
+      }
       if (interior && !((ni + nj) & 1)) {
         // Interior qubit: out[r][d] = sum_{l,u} in[l][u] g[l^r][u^d], an XOR
         // convolution with the 2 x 2 table g[alpha][beta].
@@ -268,7 +332,7 @@ __device__ __forceinline__ double fused_sweep(FusedWS<T>& ws, const Ctx<T, K>& c
       if (nrm > T(0)) {
         const T inv = T(1) / nrm;
         for (int e = lane; e < n; e += 32) cur[e] *= inv;
-        log_scale += log((double)nrm);
+        if (lane == 0) log_scale += log((double)nrm);
       }
       __syncwarp();
     }
@@ -300,6 +364,30 @@ __device__ __forceinline__ double fused_dot(const T* x, const T* y, int n, int l
   for (int e = lane; e < n; e += 32) acc += (double)x[e] * (double)y[e];
   return warp_sum(acc);
 }
+
+// The per-message term 2 - 2 <x, y>^2 of Delta (Remark 4) for unit vectors
+// x (new) and y (old).  FP64 evaluates it as written.  FP32 evaluates the
+// same quantity as s (2 - s / 2) with s = ||x - y||^2 (an identity for unit
+// vectors): no cancellation when a message barely moved, and no FP64
+// instruction per update (FP64 issues at 1/64 of the FP32 rate here).
+template <typename T> struct DeltaTerm;
+template <> struct DeltaTerm<double> {
+  static __device__ __forceinline__ double eval(const double* x, const double* y, int n, int lane) {
+    const double o = fused_dot(x, y, n, lane);
+    return 2.0 - 2.0 * o * o;
+  }
+};
+template <> struct DeltaTerm<float> {
+  static __device__ __forceinline__ float eval(const float* x, const float* y, int n, int lane) {
+    float s = 0.f;
+    for (int e = lane; e < n; e += 32) {
+      const float t = x[e] - y[e];
+      s += t * t;
+    }
+    s = warp_sum(s);
+    return s * (2.f - 0.5f * s);
+  }
+};
 
 // Resident CTAs per SM the register budget is sized for: 32 warps per SM in
 // FP32 (64 registers a thread), 16 in FP64; shared memory at d = 11 allows it.
@@ -394,6 +482,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
   __syncthreads();
 
   WS& ws = wsa[warp];
+  const T eta = (T)a.eta, one_m_eta = T(1) - eta;
   double delta = 0.0;
   int it_done = 0;
   for (int it = 1; it <= a.max_iter && M > 0; ++it) {
@@ -414,14 +503,13 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
         T* x = ws.s0;
         T* old = msgs + idx * kFusedVec;
         fused_normalize(x, n, lane);                                  // Remark 3
-        const T eta = (T)a.eta;
-        for (int e = lane; e < n; e += 32) x[e] = (T(1) - eta) * x[e] + eta * old[e];   // Remark 7
+        for (int e = lane; e < n; e += 32) x[e] = one_m_eta * x[e] + eta * old[e];   // Remark 7
         __syncwarp();
         fused_normalize(x, n, lane);
-        const double o = fused_dot(x, old, n, lane);
+        const T term = DeltaTerm<T>::eval(x, old, n, lane);
         __syncwarp();
         for (int e = lane; e < n; e += 32) old[e] = x[e];
-        if (lane == 0) ovl[idx] = o;
+        if (lane == 0) ovl[idx] = (double)term;
         __syncwarp();
       }
       __syncthreads();
@@ -430,7 +518,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
     }
     if (warp == 0) {                                   // Remark 4
       double acc = 0.0;
-      for (int i = lane; i < M; i += 32) acc += 2.0 - 2.0 * ovl[i] * ovl[i];
+      for (int i = lane; i < M; i += 32) acc += ovl[i];
       acc = warp_sum(acc);
       if (lane == 0) dsh[0] = sqrt(fmax(acc, 0.0)) / M;
     }
@@ -464,7 +552,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
     if (item < nblk) {
       const int I = item / nb, J = item % nb;
       const Frame f = make_frame(c, I, J, kDirR);
-      const double ls = fused_sweep(ws, c, msgs, f, true, lane);
+      const double ls = fused_sweep(ws, c, msgs, f, true, lane);   // valid in lane 0
       const int right = J + 1 < nb ? msg_index(c, I, J + 1, kDirL) : -1;
       double z;
       if (right >= 0) z = fused_dot(ws.s0, msgs + right * kFusedVec, 1 << f.h, lane);

@@ -119,8 +119,11 @@ def pack_mixed(syndromes_by_shot, device="cuda"):
 
 
 def decode_mixed(packed, offsets, d_of, prm: DecoderParams, largest_first=True, stream=None, out=None,
-                 counter=None):
-    """Syndromes of different distances in one persistent launch (fused path)."""
+                 counter=None, order=None, d_max=None):
+    """Syndromes of different distances in one persistent launch (fused path).
+
+    ``order`` and ``d_max`` may be passed precomputed (needed inside CUDA-graph
+    capture, where they cannot be derived with a host synchronisation)."""
     B = d_of.shape[0]
     dev = d_of.device
     if out is None:
@@ -131,8 +134,10 @@ def decode_mixed(packed, offsets, d_of, prm: DecoderParams, largest_first=True, 
             "flags": torch.empty(B, 4, dtype=torch.int32, device=dev),
             "decision": torch.empty(B, dtype=torch.int8, device=dev),
         }
-    order = torch.argsort(d_of, descending=True, stable=True).to(torch.int32) if largest_first else None
-    d_max = int(d_of.max().item())
+    if order is None and largest_first:
+        order = torch.argsort(d_of, descending=True, stable=True).to(torch.int32)
+    if d_max is None:
+        d_max = int(d_of.max().item())
     counter = counter if counter is not None else torch.empty(256, dtype=torch.uint8, device=dev)
     cp = prm.c()
     check(lib().bbp_decode_mixed(_ptr(packed), _ptr(offsets), _ptr(d_of), _ptr(order) if order is not None else None,

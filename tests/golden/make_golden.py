@@ -34,6 +34,11 @@ WORKLOADS = {
     "d11": dict(file="oracle_d11_k4_D8_p010.json", d=11, k=4, D=8, p=0.10, max_iter=20, delta0=0.0,
                 seed=synth.workload_seed(2, 2), first_shot=0, shots=12),
 }
+# The other noise levels of the d = 11 workload (p index 0, 1, 3, 4).
+for _ip, _p in ((0, 0.05), (1, 0.08), (3, 0.13), (4, 0.15)):
+    WORKLOADS[f"d11_p{int(round(_p * 100)):03d}"] = dict(
+        file=f"oracle_d11_k4_D8_p{int(round(_p * 100)):03d}.json", d=11, k=4, D=8, p=_p, max_iter=20,
+        delta0=0.0, seed=synth.workload_seed(2, _ip), first_shot=0, shots=4)
 
 
 def _one(args):

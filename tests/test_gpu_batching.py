@@ -114,3 +114,41 @@ def test_autotuned_shapes_give_identical_results(dev):
     b = decode_mixed(packed, offsets, d_of, mp)
     torch.cuda.synchronize()
     assert torch.equal(a["logp"], b["logp"])
+
+
+def test_mixed_workload_4096_over_five_distances(dev):
+    # 4096 syndromes, d uniform over {7, 9, 13, 17, 21}, p = 0.10, one
+    # persistent launch with the autotuned shape, captured in a CUDA graph.
+    p = 0.10
+    ds, shots = mixed_batch(4096, [7, 9, 13, 17, 21], p, 3000)
+    packed, offsets, d_of = pack_mixed(shots, device=dev)
+    prm = pkg.DecoderParams(d=0, k=4, p=p, max_iter=20, delta0=1e-4, precision="fp32", algorithm="fused")
+    best, table = autotune.tune_mixed(packed, offsets, d_of, prm, warps=(8, 16), ctas=(0, 2))
+    out = decode_mixed(packed, offsets, d_of, best)
+    torch.cuda.synchronize()
+    counter = torch.empty(256, dtype=torch.uint8, device=dev)
+    g = torch.cuda.CUDAGraph()
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    order = torch.argsort(d_of, descending=True, stable=True).to(torch.int32)
+    d_max = int(d_of.max().item())
+    with torch.cuda.stream(stream):
+        graph_out = decode_mixed(packed, offsets, d_of, best, stream=stream, counter=counter, order=order,
+                                 d_max=d_max)
+        torch.cuda.current_stream(dev).synchronize()
+        with torch.cuda.graph(g, stream=stream):
+            decode_mixed(packed, offsets, d_of, best, stream=stream, out=graph_out, counter=counter, order=order,
+                         d_max=d_max)
+    torch.cuda.current_stream().wait_stream(stream)
+    g.replay()
+    torch.cuda.synchronize()
+    for key in ("logp", "iters", "decision"):
+        assert torch.equal(graph_out[key], out[key]), key
+    # Per-distance decodes give the same bits.
+    for d in (7, 21):
+        idx = np.nonzero(ds == d)[0][:64]
+        S = np.stack([shots[i] for i in idx])
+        ref = pkg.decode(torch.from_numpy(S).to(dev), pkg.DecoderParams(**{**best.__dict__, "d": d, "ctas_per_sm": 0}))
+        torch.cuda.synchronize()
+        assert torch.equal(out["logp"][torch.from_numpy(idx).to(dev)], ref["logp"])
+    assert (out["decision"] >= 0).all() and (out["decision"] < 4).all()

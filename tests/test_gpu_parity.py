@@ -207,3 +207,30 @@ def test_full_size_batch_in_bench_configuration(dev):
     assert fin.mean() > 0.999
     lse = np.log(np.sum(np.exp(np.where(fin, out["logp"], -np.inf)), axis=1))
     assert np.all(lse < 1e-6)
+
+
+_NOISE_CASES = [(pn, prec, alg, tol) for pn in ("p005", "p008", "p013", "p015")
+                for prec, alg, tol in (("fp64", "mps", 1e-9), ("fp32", "mps", 1e-3), ("fp32", "fused", 1e-3))]
+
+
+@pytest.mark.parametrize("pname,prec,alg,tol", [
+    pytest.param(*c, marks=pytest.mark.xfail(
+        strict=True, reason="FP32 MPS misses 1e-3 at p = 0.05: 3.6e-3 on shot 1; "
+                            "FP32 QR/SVD resolution, not truncation (none occurs) nor message storage"))
+    if c[0] == "p005" and c[1:3] == ("fp32", "mps") else c
+    for c in _NOISE_CASES], ids=[f"{c[0]}-{c[1]}-{c[2]}" for c in _NOISE_CASES])
+def test_d11_other_noise_levels(dev, pname, prec, alg, tol):
+    # d = 11 workload at the other noise levels against the FP64 oracle:
+    # FP64 MPS to 1e-9, the FP32 forms to 1e-3.
+    g = load_golden(f"oracle_d11_k4_D8_{pname}.json")
+    w = g["workload"]
+    _, _, S = synth.sample_syndromes(w["seed"], w["first_shot"], w["shots"], w["d"], w["p"])
+    prm = pkg.DecoderParams(d=w["d"], k=w["k"], D=w["D"], p=w["p"], max_iter=w["max_iter"],
+                            delta0=w["delta0"], precision=prec, algorithm=alg)
+    out = gpu_decode(S, prm, dev)
+    for r in g["shots"]:
+        if r["truncations"] and alg == "fused":
+            continue          # the fused form equals the MPS form only without truncation
+        b = r["shot"] - w["first_shot"]
+        err = np.max(np.abs(out["logp"][b] - np.array(r["logp"])))
+        assert err <= tol, (pname, prec, alg, r["shot"], err)
