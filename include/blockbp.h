@@ -84,8 +84,15 @@ extern "C" {
  *             singular values below cutoff * sigma_1 are dropped as numerical
  *             zeros (the paper is silent; 1e-13 for BBP_FP64, 1e-7 for BBP_FP32)
  *   precision BBP_FP64 or BBP_FP32
- *   launch_warps, launch_ctas_per_sm  launch shape of the fused path (tuning
- *             only; results do not depend on them)
+ *   launch_warps, launch_cosets, launch_ctas_per_sm  launch shape of the
+ *             fused path (tuning only; results do not depend on them): warps
+ *             per CTA, cosets decoded together by one CTA (1, 2 or 4; they
+ *             share the block geometry and, off row 0 and column 0, the node
+ *             tensors) and resident CTAs per SM of bbp_decode_mixed.  0 picks
+ *             the fastest compiled shape whose shared memory fits; compiled
+ *             (warps, cosets): FP32 (8,4) (8,2) (4,2) (4,4) (16,1) (8,1)
+ *             (4,1), FP64 (4,2) (8,2) (8,1) (4,4); other requests give
+ *             BBP_EUNSUPPORTED.
  *   algorithm BBP_ALG_MPS, or BBP_ALG_FUSED: every k x k block fused into one
  *             vertex with dense messages (Remark 9; the form the paper ran for
  *             k = 1, 2, 4).  Nothing is truncated, D and cutoff are unused,
@@ -104,8 +111,9 @@ typedef struct bbp_params {
   double cutoff;
   int32_t precision;
   int32_t algorithm;
-  int32_t launch_warps;        /* fused path: warps per CTA, 0 = default (8); 4, 8 or 16 in FP32 */
+  int32_t launch_warps;        /* fused path: warps per CTA (4, 8, 16), 0 = default */
   int32_t launch_ctas_per_sm;  /* bbp_decode_mixed: resident CTAs per SM, 0 = the occupancy limit */
+  int32_t launch_cosets;       /* fused path: cosets per CTA (1, 2, 4), 0 = default */
 } bbp_params;
 
 /*

@@ -24,6 +24,9 @@ SYMBOLS = ("bbp_workspace_bytes", "bbp_decode_batch", "bbp_decode_batch_host", "
            "bbp_message_features", "bbp_warm_param_count", "bbp_warm_workspace_bytes", "bbp_warm_infer",
            "bbp_warm_train_step", "bbp_decode_batch_ex", "bbp_decode_mixed")
 WARM_F, WARM_H, WARM_O, WARM_MAX_ROWS = 256, 256, 16, 4194240
+# Compiled launch shapes (warps per CTA, cosets per CTA) of the fused kernel.
+FUSED_SHAPES = {"fp32": ((8, 4), (8, 2), (4, 2), (4, 4), (16, 1), (8, 1), (4, 1)),
+                "fp64": ((4, 2), (8, 2), (8, 1), (4, 4))}
 BBP_ETOOLARGE = -5
 STATIC_WORKSPACE_BYTES = 32 << 20
 
@@ -33,7 +36,8 @@ class BbpParams(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("p", ctypes.c_double), ("eta", ctypes.c_double),
                 ("delta0", ctypes.c_double), ("delta1", ctypes.c_double), ("cutoff", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("algorithm", ctypes.c_int32),
-                ("launch_warps", ctypes.c_int32), ("launch_ctas_per_sm", ctypes.c_int32)]
+                ("launch_warps", ctypes.c_int32), ("launch_ctas_per_sm", ctypes.c_int32),
+                ("launch_cosets", ctypes.c_int32)]
 
 
 @dataclass
@@ -52,13 +56,14 @@ class DecoderParams:
     algorithm: str = "mps"          # "mps" (Sec. III.D) or "fused" (Remark 9, k <= 4)
     warps: int = 0                  # fused launch shape (tuning only): warps per CTA
     ctas_per_sm: int = 0            # persistent mixed launch: resident CTAs per SM (0 = occupancy)
+    cosets: int = 0                 # fused launch shape (tuning only): cosets per CTA (1, 2, 4)
 
     def c(self) -> BbpParams:
         prec = FP64 if self.precision == "fp64" else FP32
         cut = self.cutoff if self.cutoff is not None else (1e-13 if prec == FP64 else 1e-7)
         alg = ALG_MPS if self.algorithm == "mps" else ALG_FUSED
         return BbpParams(self.d, self.k, self.D, self.max_iter, self.p, self.eta, self.delta0,
-                         self.delta1, cut, prec, alg, self.warps, self.ctas_per_sm)
+                         self.delta1, cut, prec, alg, self.warps, self.ctas_per_sm, self.cosets)
 
     @property
     def m(self) -> int:

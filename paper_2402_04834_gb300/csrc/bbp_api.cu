@@ -14,9 +14,11 @@ using bbp::Geo;
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-int warps_of(const bbp_params* p) {
-  if (p->precision == BBP_FP64) return 8;
-  return p->launch_warps == 0 ? bbp::kFusedWarps : p->launch_warps;
+// Launch shape of the fused kernel for this request at geometry g.
+bool shape_of(const bbp_params* p, const Geo& g, int M, int* warps, int* cosets) {
+  *warps = p->launch_warps;
+  *cosets = p->launch_cosets;
+  return bbp::fused_shape(p->precision, g, M, warps, cosets);
 }
 
 int check_params(const bbp_params* p) {
@@ -31,13 +33,15 @@ int check_params(const bbp_params* p) {
   if (p->algorithm == BBP_ALG_MPS && (p->k > bbp::kMaxK || p->D > bbp::kMaxD)) return BBP_EUNSUPPORTED;
   if (p->launch_warps != 0 && p->launch_warps != 4 && p->launch_warps != 8 && p->launch_warps != 16)
     return BBP_EINVAL;
+  if (p->launch_cosets != 0 && p->launch_cosets != 1 && p->launch_cosets != 2 && p->launch_cosets != 4)
+    return BBP_EINVAL;
   if (p->launch_ctas_per_sm < 0 || p->launch_ctas_per_sm > 32) return BBP_EINVAL;
   if (p->algorithm == BBP_ALG_FUSED) {
     if (p->k > bbp::kFusedMaxK) return BBP_EUNSUPPORTED;
     const bbp::Geo g = bbp::make_geo(p->d, p->k);
-    int M = 0, ae = 0;
+    int M = 0, ae = 0, w = 0, c = 0;
     bbp::count_messages(g, 1, &M, &ae);
-    if (bbp::fused_smem_bytes(p->precision, g, M, warps_of(p)) > 227 * 1024) return BBP_EUNSUPPORTED;
+    if (!shape_of(p, g, M, &w, &c)) return BBP_EUNSUPPORTED;
   }
   return BBP_OK;
 }
@@ -115,9 +119,11 @@ int bbp_decode_batch_ex(const uint8_t* syndromes, int64_t B, const bbp_params* p
   a.init_msgs = init_msgs; a.final_msgs = final_msgs;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;
-  if (prm->algorithm == BBP_ALG_FUSED)
-    e = prm->precision == BBP_FP64 ? bbp::launch_fused_f64(a, 8, st) : bbp::launch_fused_f32(a, warps_of(prm), st);
-  else
+  if (prm->algorithm == BBP_ALG_FUSED) {
+    int w = 0, c = 0;
+    if (!shape_of(prm, s.g, s.M, &w, &c)) return BBP_EUNSUPPORTED;
+    e = prm->precision == BBP_FP64 ? bbp::launch_fused_f64(a, w, c, st) : bbp::launch_fused_f32(a, w, c, st);
+  } else
     e = prm->precision == BBP_FP64 ? bbp::launch_decode_f64(a, st) : bbp::launch_decode_f32(a, st);
   if (e != cudaSuccess) return BBP_ECUDA;
   e = bbp::launch_decide(a, st);
@@ -184,8 +190,11 @@ int bbp_decode_mixed(const uint8_t* syndromes, const int64_t* offsets, const int
   m.counter = static_cast<unsigned long long*>(workspace);
   m.d_max = d_max; m.ctas_per_sm = prm->launch_ctas_per_sm;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = prm->precision == BBP_FP64 ? bbp::launch_fused_mixed_f64(a, m, 8, st)
-                                             : bbp::launch_fused_mixed_f32(a, m, warps_of(prm), st);
+  int Mmax = 0, ae = 0, w = 0, c = 0;
+  bbp::count_messages(a.geo, 1, &Mmax, &ae);
+  if (!shape_of(prm, a.geo, Mmax, &w, &c)) return BBP_EUNSUPPORTED;
+  cudaError_t e = prm->precision == BBP_FP64 ? bbp::launch_fused_mixed_f64(a, m, w, c, st)
+                                             : bbp::launch_fused_mixed_f32(a, m, w, c, st);
   if (e != cudaSuccess) return BBP_ECUDA;
   e = bbp::launch_decide(a, st);
   return e == cudaSuccess ? BBP_OK : BBP_ECUDA;

@@ -23,15 +23,6 @@ __global__ void decide_kernel(const double* logp, const double* delta, const int
 
 
 cudaError_t launch_decode_f64(const LaunchArgs& a, cudaStream_t st) { return launch_decode_t<double>(a, st); }
-cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, cudaStream_t st) {
-  (void)warps;
-  return launch_fused_nw<double, 8>(a, st);
-}
-cudaError_t launch_fused_mixed_f64(const LaunchArgs& a, const MixedLaunch& m, int warps, cudaStream_t st) {
-  (void)warps;
-  return launch_fused_mixed_nw<double, 8>(a, m, st);
-}
-
 cudaError_t launch_decide(const LaunchArgs& a, cudaStream_t st) {
   const int tpb = 128;
   const unsigned grid = (unsigned)((a.B + tpb - 1) / tpb);

@@ -30,8 +30,8 @@ cudaError_t launch_decode_t(const LaunchArgs& a, cudaStream_t st) {
 }
 
 template <typename T>
-int fused_smem_for(const Geo& g, int M, int warps = kFusedWarps) {
-  return fused_layout<T>(g, M, warps).total;
+int fused_smem_for(const Geo& g, int M, int warps, int cosets) {
+  return fused_layout<T>(g, M, warps, cosets).total;
 }
 
 template <typename T>
@@ -45,26 +45,26 @@ KArgs<T> fused_args(const LaunchArgs& a) {
   return k;
 }
 
-template <typename T, int NW>
+template <typename T, int NW, int G>
 cudaError_t launch_fused_nw(const LaunchArgs& a, cudaStream_t st) {
   const KArgs<T> k = fused_args<T>(a);
-  const int smem = fused_smem_for<T>(a.geo, a.M, NW);
-  auto kern = fused_kernel<T, NW>;
+  const int smem = fused_smem_for<T>(a.geo, a.M, NW, G);
+  auto kern = fused_kernel<T, NW, G>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  const unsigned grid = (unsigned)(a.B * 4);
+  const unsigned grid = (unsigned)(a.B * (4 / G));
   kern<<<grid, NW * 32, smem, st>>>(k);
   return cudaGetLastError();
 }
 
-template <typename T, int NW>
+template <typename T, int NW, int G>
 cudaError_t launch_fused_mixed_nw(const LaunchArgs& a, const MixedLaunch& m, cudaStream_t st) {
   const KArgs<T> k = fused_args<T>(a);
   const Geo gmax = make_geo(m.d_max, a.geo.k);
   int Mmax = 0, ae = 0;
   count_messages(gmax, 1, &Mmax, &ae);
-  const int smem = fused_smem_for<T>(gmax, Mmax, NW);
-  auto kern = fused_mixed_kernel<T, NW>;
+  const int smem = fused_smem_for<T>(gmax, Mmax, NW, G);
+  auto kern = fused_mixed_kernel<T, NW, G>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   int per_sm = m.ctas_per_sm;
@@ -78,7 +78,7 @@ cudaError_t launch_fused_mixed_nw(const LaunchArgs& a, const MixedLaunch& m, cud
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   MixedArgs mx;
   mx.d_of = m.d_of; mx.offsets = m.offsets; mx.order = m.order; mx.counter = m.counter;
-  mx.n_items = a.B * 4; mx.k = a.geo.k;
+  mx.n_items = a.B * (4 / G); mx.k = a.geo.k;
   long long grid = (long long)sms * per_sm;
   if (grid > mx.n_items) grid = mx.n_items;
   if ((e = cudaMemsetAsync(m.counter, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;

@@ -4,17 +4,27 @@
 // the MPS form of Sec. III.D truncates nothing, both compute the same
 // numbers.
 //
-// One CTA decodes one (syndrome, coset); all messages live in shared memory
-// (M dense vectors of 2^k).  A warp contracts one block with its incoming
-// messages node by node on a dense state indexed by
-//     [a | rows of the chain | b | v]   (most to least significant bits)
-// where v is the vertical leg inside the current column and a / b carry the
-// top / bottom side message.  A side message m(t_0 .. t_{w-1}) is fed one
-// leg per column through its exact copy / data / copy factorisation: the
-// first floor(w/2) legs are recorded in a, the middle column contracts a
-// with m and leaves in a the values expected for the remaining legs, which
-// the last columns check off.  All dimensions are powers of two, so every
-// index is a bit field.  Every loop is bounded and no CTA waits on another.
+// One CTA decodes G of the four cosets of one syndrome (G = 1, 2 or 4); all
+// their messages live in shared memory (G x M dense vectors of 2^k).  The
+// cosets share the network's geometry, and every node off the first row
+// and column has the same Pauli frame in all of them (the logical strings
+// of Sec. II run along row 0 and column 0), so a warp updates one directed
+// block edge for all cosets of the CTA that are still iterating at once:
+// index arithmetic, node tables and synchronisation are paid once for G
+// vectors.  A coset whose Delta drops below delta0 is frozen (its messages
+// and iteration count stay as they were), exactly as if it ran alone.
+//
+// A warp contracts one block with its incoming messages node by node on a
+// dense state indexed by
+//     [slot | a | rows of the chain | b | v]   (most to least significant bits)
+// where slot picks the coset, v is the vertical leg inside the current
+// column and a / b carry the top / bottom side message.  A side message
+// m(t_0 .. t_{w-1}) is fed one leg per column through its exact copy / data /
+// copy factorisation: the first floor(w/2) legs are recorded in a, the
+// middle column contracts a with m and leaves in a the values expected for
+// the remaining legs, which the last columns check off.  All dimensions are
+// powers of two, so every index is a bit field.  Every loop is bounded and
+// no CTA waits on another.
 #pragma once
 
 #include "bbp_kernels.cuh"
@@ -23,37 +33,61 @@ namespace bbp {
 
 constexpr int kFusedK = 4;                 // largest block side of the fused path
 constexpr int kFusedVec = 1 << kFusedK;    // dense message length
-constexpr int kFusedState = 512;           // 2^(2 + 4 + 2 + 1)
+// Largest state of one coset: with k <= 4 the side-message bits a and b
+// together never exceed 3 at a node pass nor 4 at a side step, so
+// a + rows + b + v <= 8 bits.
+constexpr int kFusedSlot = 256;
+constexpr int kFusedMaxG = 4;              // cosets per CTA
+
+// Per-warp scratch for G cosets, carved from shared memory.
+template <typename T>
+struct FusedWS {
+  T* s0;   // state, G * kFusedSlot
+  T* s1;   // state, G * kFusedSlot
+  T* wn;   // node tensors, 16 per coset
+  T* mt;   // side message A in consumption order, kFusedVec per coset
+  T* mb;   // side message B in consumption order, kFusedVec per coset
+};
 
 template <typename T>
-struct __align__(16) FusedWS {
-  T s0[kFusedState];
-  T s1[kFusedState];
-  T wn[kFusedK * 16];      // node tensors of the current column
-  T mt[kFusedVec];         // side message A in consumption order
-  T mb[kFusedVec];         // side message B in consumption order
-};
+BBP_HD int fused_ws_bytes(int G) {
+  return align_up((int)sizeof(T) * G * (2 * kFusedSlot + 16 + 2 * kFusedVec), 16);
+}
+
+template <typename T>
+__device__ __forceinline__ FusedWS<T> fused_ws_at(unsigned char* base, int G) {
+  FusedWS<T> w;
+  T* p = reinterpret_cast<T*>(base);
+  w.s0 = p;
+  w.s1 = p + G * kFusedSlot;
+  w.wn = p + 2 * G * kFusedSlot;
+  w.mt = w.wn + 16 * G;
+  w.mb = w.mt + kFusedVec * G;
+  return w;
+}
 
 // Shared-memory layout of one fused CTA.
 struct FusedLayout {
-  int synd, frame, msg_of, meta, work, ovl, rlog, misc, msgs, ws, total;
+  int synd, frame, msg_of, meta, work, ovl, rlog, misc, msgs, ws, ws_stride, total;
 };
 
 template <typename T>
-BBP_HD FusedLayout fused_layout(const Geo& g, int M, int nwarps) {
+BBP_HD FusedLayout fused_layout(const Geo& g, int M, int nwarps, int G) {
   FusedLayout L;
   const int m = 2 * g.d * (g.d - 1);
   int o = 0;
   L.synd = o;   o = align_up(o + m, 16);
-  L.frame = o;  o = align_up(o + g.W * g.W, 16);
+  L.frame = o;  o = align_up(o + G * g.W * g.W, 16);
   L.msg_of = o; o = align_up(o + 2 * g.nb * g.nb * 4, 16);
   L.meta = o;   o = align_up(o + 2 * M, 16);
   L.work = o;   o = align_up(o + 2 * 2 * M, 16);
-  L.ovl = o;    o = align_up(o + 8 * M, 16);
-  L.rlog = o;   o = align_up(o + 8 * (g.nb * g.nb + M), 16);
-  L.misc = o;   o = align_up(o + 64, 16);
-  L.msgs = o;   o = align_up(o + (int)sizeof(T) * kFusedVec * M, 16);
-  L.ws = o;     o = align_up(o + nwarps * (int)sizeof(FusedWS<T>), 16);
+  L.ovl = o;    o = align_up(o + 8 * G * M, 16);
+  L.rlog = o;   o = align_up(o + 8 * G * (g.nb * g.nb + M), 16);
+  L.misc = o;   o = align_up(o + 128, 16);
+  L.msgs = o;   o = align_up(o + (int)sizeof(T) * kFusedVec * G * M, 16);
+  L.ws = o;
+  L.ws_stride = fused_ws_bytes<T>(G);
+  o = align_up(o + nwarps * L.ws_stride, 16);
   L.total = o;
   return L;
 }
@@ -67,44 +101,69 @@ __device__ __forceinline__ int bitrev(int x, int w) {
 }
 
 struct FState {
-  int ab, h, bb, hv;   // bit widths of a, rows, b, v
-  __device__ __forceinline__ int size() const { return 1 << (ab + h + bb + hv); }
-  __device__ __forceinline__ int idx(int a, int H, int b, int v) const {
-    return ((((a << h) | H) << bb | b) << hv) | v;
-  }
+  int ab, h, bb, hv;   // bit widths of a, rows, b, v (per coset)
+  __device__ __forceinline__ int bits() const { return ab + h + bb + hv; }
+  __device__ __forceinline__ int size() const { return 1 << bits(); }
 };
 
-// Contract block f (rotated so that f.dir points right) with its incoming
-// dense messages; leaves the outgoing vector over the chain in ws.s0 and
-// returns the log of the norms taken out (read-out only; FP64, in lane 0).
+// Coset (0 .. G-1 within the CTA) held by slot s; slots are packed 2 bits each.
+__device__ __forceinline__ int slot_coset(unsigned cos_of, int s) { return (int)((cos_of >> (2 * s)) & 3u); }
+
+// The qubit table g[alpha][beta] = pi(f (+) (x, z)) of an interior qubit:
+// one of x, z is the parity of its in/out legs (alpha), the other the
+// parity of its chain legs (beta); alpha is z for horizontal-edge qubits
+// swept along rows and for vertical-edge qubits swept along columns.
 template <typename T, int K>
-__device__ __forceinline__ double fused_sweep(FusedWS<T>& ws, const Ctx<T, K>& c, const T* msgs, const Frame& f,
+__device__ __forceinline__ void qubit_table(const Ctx<T, K>& c, int qi, int qj, bool rowwise, T gt[4]) {
+  const int fr = c.frame[qi * c.g.W + qj];
+  const int fx = fr & 1, fz = (fr >> 1) & 1;
+  const bool alpha_is_z = ((qi & 1) == 0) == rowwise;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int al = q >> 1, be = q & 1;
+    const int xb = alpha_is_z ? be : al, zb = alpha_is_z ? al : be;
+    gt[q] = ((fx ^ xb) | (fz ^ zb)) ? c.pE : c.pI;
+  }
+}
+
+// Contract block f (rotated so that f.dir points right) with its incoming
+// dense messages for the n cosets of cos_of (messages of coset q at
+// msgs + q * stride; c.frame is the frame of slot 0's coset and frames holds
+// all G frames).  Leaves the outgoing vectors over the chain in ws.s0, slot
+// s at s << h, and returns the log of the norms taken out (read-out only,
+// which runs with n = 1; FP64, in lane 0).
+template <typename T, int K>
+__device__ __forceinline__ double fused_sweep(const FusedWS<T>& ws, const Ctx<T, K>& c, const T* msgs, int stride,
+                                           unsigned cos_of, int n, const uint8_t* frames, const Frame& f,
                                            bool readout, int lane) {
+  using V2 = typename Vec2<T>::type;
   const int h = f.h, nc = f.ncols;
   T* cur = ws.s0;
   T* nxt = ws.s1;
   // Initial state: the message on the side opposite the outgoing one.
-  for (int H = lane; H < (1 << h); H += 32)
-    cur[H] = f.in_idx >= 0 ? msgs[f.in_idx * kFusedVec + H] : (H == 0 ? T(1) : T(0));
+  for (int e = lane; e < (n << h); e += 32) {
+    const int H = e & ((1 << h) - 1);
+    const T* ms = msgs + slot_coset(cos_of, e >> h) * stride;
+    cur[e] = f.in_idx >= 0 ? ms[f.in_idx * kFusedVec + H] : (H == 0 ? T(1) : T(0));
+  }
   // Side messages in consumption order.
-  for (int i = lane; i < (1 << nc); i += 32) {
+  for (int e = lane; e < (n << nc); e += 32) {
+    const int i = e & ((1 << nc) - 1);
     const int j = f.rev ? bitrev(i, nc) : i;
-    ws.mt[i] = f.a_idx >= 0 ? msgs[f.a_idx * kFusedVec + j] : T(0);
-    ws.mb[i] = f.b_idx >= 0 ? msgs[f.b_idx * kFusedVec + j] : T(0);
+    const T* ms = msgs + slot_coset(cos_of, e >> nc) * stride;
+    ws.mt[e] = f.a_idx >= 0 ? ms[f.a_idx * kFusedVec + j] : T(0);
+    ws.mb[e] = f.b_idx >= 0 ? ms[f.b_idx * kFusedVec + j] : T(0);
   }
   __syncwarp();
   FState st{0, h, 0, 0};
   const int sd = nc >> 1;               // the column that holds the data site
   const int nf = nc - sd - 1;           // legs still expected after it
   double log_scale = 0.0;               // accumulated by lane 0 only
-  // Which parity the in/out legs carry: a qubit's tensor is pi(f (+) (x, z))
-  // with one of x, z the parity of its in/out legs (alpha) and the other the
-  // parity of its chain legs (beta); alpha is z for horizontal-edge qubits
-  // swept along rows and for vertical-edge qubits swept along columns.
   const bool rowwise = f.dir == kDirR || f.dir == kDirL;
+  const int WW = c.g.W * c.g.W;
   for (int t = 0; t < nc; ++t) {
     // Side message A: enters the column as its vertical leg v.  Output
-    // entries come in pairs (v = 0, 1) sharing (a, rows, b).
+    // entries come in pairs (v = 0, 1) sharing (slot, a, rows, b).
     {
       FState ns = st;
       ns.hv = 1;
@@ -112,29 +171,32 @@ __device__ __forceinline__ double fused_sweep(FusedWS<T>& ws, const Ctx<T, K>& c
       else if (t < sd) ns.ab = st.ab + 1;
       else if (t == sd) ns.ab = nf;
       else ns.ab = st.ab - 1;
-      using V2 = typename Vec2<T>::type;
-      const int np = ns.size() >> 1;
+      const int np = n << (ns.bits() - 1);
       const int hb = h + st.bb;                        // bits of (rows, b)
       const int low = (1 << hb) - 1;
       for (int e2 = lane; e2 < np; e2 += 32) {
-        const int a2 = e2 >> hb, hbv = e2 & low;       // (rows, b) part is shared by in and out
+        const int a2f = e2 >> hb, hbv = e2 & low;      // a2f = (slot, a); (rows, b) is shared by in and out
         V2 o;
         if (f.a_idx < 0) {
           o.x = cur[e2]; o.y = T(0);
         } else if (t < sd) {
-          const T x = cur[((a2 >> 1) << hb) | hbv];
-          if (a2 & 1) { o.x = T(0); o.y = x; } else { o.x = x; o.y = T(0); }
+          const T x = cur[((a2f >> 1) << hb) | hbv];
+          if (a2f & 1) { o.x = T(0); o.y = x; } else { o.x = x; o.y = T(0); }
         } else if (t == sd) {
+          const int s = a2f >> nf, a2 = a2f & ((1 << nf) - 1);
+          const T* mt = ws.mt + (s << nc);
+          const int ib = s << (st.ab + hb);
           T s0 = T(0), s1 = T(0);
           for (int a = 0; a < (1 << st.ab); ++a) {
-            const T x = cur[(a << hb) | hbv];
-            s0 += ws.mt[((a << 1) << nf) | a2] * x;
-            s1 += ws.mt[(((a << 1) | 1) << nf) | a2] * x;
+            const T x = cur[ib | (a << hb) | hbv];
+            s0 += mt[((a << 1) << nf) | a2] * x;
+            s1 += mt[(((a << 1) | 1) << nf) | a2] * x;
           }
           o.x = s0; o.y = s1;
         } else {
-          o.x = cur[(a2 << hb) | hbv];
-          o.y = cur[(((1 << (st.ab - 1)) | a2) << hb) | hbv];
+          const int ai = ((a2f >> ns.ab) << st.ab) | (a2f & ((1 << ns.ab) - 1));
+          o.x = cur[(ai << hb) | hbv];
+          o.y = cur[((ai | (1 << (st.ab - 1))) << hb) | hbv];
         }
         *reinterpret_cast<V2*>(nxt + 2 * e2) = o;
       }
@@ -146,12 +208,12 @@ __device__ __forceinline__ double fused_sweep(FusedWS<T>& ws, const Ctx<T, K>& c
     // Each lane takes quads of entries that differ only in the node's row bit
     // (l -> r) and in v (u -> d): out[r][d] = sum_{l,u} in[l][u] w[l][r][u][d],
     // read and written as two pairs of adjacent entries.
+    const int lnq = st.bits() - 2;                    // quads per coset, log2
+    const int nq = n << lnq;
     for (int s = 0; s < h; ++s) {
       const int P = (h - 1 - s) + st.bb + 1;          // bit of the node's row in the index
       const int bitP = 1 << P;
-      const int nq = st.size() >> 2;
       const int lowmask = (1 << (P - 1)) - 1;
-      using V2 = typename Vec2<T>::type;
       int ni, nj;
       f.node(t, s, &ni, &nj);
       const bool interior = ni > 0 && nj > 0 && ni < c.g.W - 1 && nj < c.g.W - 1;
@@ -163,17 +225,8 @@ __device__ __forceinline__ double fused_sweep(FusedWS<T>& ws, const Ctx<T, K>& c
           // pass: the check's copy tensor ties the vertical leg between them
           // to the check's own row bit c.
           const bool check_first = (ni + nj) & 1;
-          const int qi = check_first ? mi : ni, qj = check_first ? mj : nj;
-          const int fr = c.frame[qi * c.g.W + qj];
-          const int fx = fr & 1, fz = (fr >> 1) & 1;
-          const bool alpha_is_z = ((qi & 1) == 0) == rowwise;
           T gt[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int al = q >> 1, be = q & 1;
-            const int xb = alpha_is_z ? be : al, zb = alpha_is_z ? al : be;
-            gt[q] = ((fx ^ xb) | (fz ^ zb)) ? c.pE : c.pI;
-          }
+          qubit_table(c, check_first ? mi : ni, check_first ? mj : nj, rowwise, gt);
           if (check_first) {
             // out[c, r, d] = sum_l in[c, l, v=c] g[l^r][c^d]; rows bits P (c) and P-1 (qubit).
             const int Q = P - 1, bitQ = 1 << Q, lowq = (1 << (Q - 1)) - 1;
@@ -222,16 +275,8 @@ __device__ __forceinline__ double fused_sweep(FusedWS<T>& ws, const Ctx<T, K>& c
       if (interior && !((ni + nj) & 1)) {
         // Interior qubit: out[r][d] = sum_{l,u} in[l][u] g[l^r][u^d], an XOR
         // convolution with the 2 x 2 table g[alpha][beta].
-        const int fr = c.frame[ni * c.g.W + nj];
-        const int fx = fr & 1, fz = (fr >> 1) & 1;
-        const bool alpha_is_z = ((ni & 1) == 0) == rowwise;
         T gt[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int al = q >> 1, be = q & 1;
-          const int xb = alpha_is_z ? be : al, zb = alpha_is_z ? al : be;
-          gt[q] = ((fx ^ xb) | (fz ^ zb)) ? c.pE : c.pI;
-        }
+        qubit_table(c, ni, nj, rowwise, gt);
         for (int g = lane; g < nq; g += 32) {
           const int base = ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
           const V2 i0 = *reinterpret_cast<const V2*>(cur + base);          // in[0][0], in[0][1]
@@ -264,16 +309,28 @@ __device__ __forceinline__ double fused_sweep(FusedWS<T>& ws, const Ctx<T, K>& c
         T* tmp = cur; cur = nxt; nxt = tmp;
         continue;
       }
-      // Border node: the general 16-entry tensor (missing legs carry 0).
-      if (lane < 16)
-        ws.wn[lane] = node_value<T>(c.frame, c.g.W, c.pI, c.pE, ni, nj, f.dir, (lane >> 3) & 1, (lane >> 2) & 1,
-                                    (lane >> 1) & 1, lane & 1);
+      // Border node: the general 16-entry tensor (missing legs carry 0).  On
+      // row 0 and column 0 the frame, hence the tensor, depends on the coset.
+      const bool per_coset = n > 1 && (ni == 0 || nj == 0);
+      if (!per_coset) {
+        if (lane < 16)
+          ws.wn[lane] = node_value<T>(c.frame, c.g.W, c.pI, c.pE, ni, nj, f.dir, (lane >> 3) & 1,
+                                      (lane >> 2) & 1, (lane >> 1) & 1, lane & 1);
+      } else {
+        for (int q = lane; q < 16 * n; q += 32)
+          ws.wn[q] = node_value<T>(frames + slot_coset(cos_of, q >> 4) * WW, c.g.W, c.pI, c.pE, ni, nj, f.dir,
+                                   (q >> 3) & 1, (q >> 2) & 1, (q >> 1) & 1, q & 1);
+      }
       __syncwarp();
       T w[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) w[q] = ws.wn[q];
-      __syncwarp();
       for (int g = lane; g < nq; g += 32) {
+        if (per_coset) {
+          const T* wq = ws.wn + ((g >> lnq) << 4);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) w[q] = wq[q];
+        }
         const int base = ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
         const V2 i0 = *reinterpret_cast<const V2*>(cur + base);          // (l=0,u=0), (l=0,u=1)
         const V2 i1 = *reinterpret_cast<const V2*>(cur + (base | bitP)); // (l=1,u=0), (l=1,u=1)
@@ -297,18 +354,19 @@ __device__ __forceinline__ double fused_sweep(FusedWS<T>& ws, const Ctx<T, K>& c
       else if (t < sd) ns.bb = st.bb + 1;
       else if (t == sd) ns.bb = nf;
       else ns.bb = st.bb - 1;
-      const int n = ns.size();
+      const int nt = n << ns.bits();
       if (!(f.b_idx >= 0 && t < sd)) {   // recording v as b's new low bit changes no index
-        for (int e = lane; e < n; e += 32) {
+        for (int e = lane; e < nt; e += 32) {
           T val;
           if (f.b_idx < 0) {
             val = cur[e << 1];                          // v = 0, b has no bits
           } else if (t == sd) {
-            const int b2 = e & ((1 << ns.bb) - 1), ah = e >> ns.bb;   // (a, rows)
+            const int b2 = e & ((1 << ns.bb) - 1), ah = e >> ns.bb;   // (slot, a, rows)
+            const T* mb = ws.mb + ((ah >> (st.ab + h)) << nc);
             val = T(0);
             for (int b = 0; b < (1 << st.bb); ++b) {
               const int bi = ((ah << st.bb) | b) << 1;
-              val += ws.mb[((b << 1) << nf) | b2] * cur[bi] + ws.mb[(((b << 1) | 1) << nf) | b2] * cur[bi | 1];
+              val += mb[((b << 1) << nf) | b2] * cur[bi] + mb[(((b << 1) | 1) << nf) | b2] * cur[bi | 1];
             }
           } else {
             const int b2 = e & ((1 << ns.bb) - 1), ah = e >> ns.bb;
@@ -323,39 +381,25 @@ __device__ __forceinline__ double fused_sweep(FusedWS<T>& ws, const Ctx<T, K>& c
       }
       st = ns;
     }
-    if (readout) {   // keep the block value in range; its log goes to the read-out
-      const int n = st.size();
+    if (readout) {   // keep the block value in range; its log goes to the read-out (n = 1)
+      const int nt = st.size();
       T acc = 0;
-      for (int e = lane; e < n; e += 32) acc += cur[e] * cur[e];
+      for (int e = lane; e < nt; e += 32) acc += cur[e] * cur[e];
       acc = warp_sum(acc);
       const T nrm = xsqrt(acc);
       if (nrm > T(0)) {
         const T inv = T(1) / nrm;
-        for (int e = lane; e < n; e += 32) cur[e] *= inv;
+        for (int e = lane; e < nt; e += 32) cur[e] *= inv;
         if (lane == 0) log_scale += log((double)nrm);
       }
       __syncwarp();
     }
   }
   if (cur != ws.s0) {
-    for (int H = lane; H < (1 << h); H += 32) ws.s0[H] = cur[H];
+    for (int e = lane; e < (n << h); e += 32) ws.s0[e] = cur[e];
     __syncwarp();
   }
   return log_scale;
-}
-
-// Unit L2 norm (Remark 3) of the 2^w vector x; returns the norm.
-template <typename T>
-__device__ __forceinline__ T fused_normalize(T* x, int n, int lane) {
-  T acc = 0;
-  for (int e = lane; e < n; e += 32) acc += x[e] * x[e];
-  acc = warp_sum(acc);
-  const T nrm = xsqrt(acc);
-  const T inv = nrm > T(0) ? T(1) / nrm : T(0);
-  __syncwarp();
-  for (int e = lane; e < n; e += 32) x[e] *= inv;
-  __syncwarp();
-  return nrm;
 }
 
 template <typename T>
@@ -366,62 +410,102 @@ __device__ __forceinline__ double fused_dot(const T* x, const T* y, int n, int l
 }
 
 // The per-message term 2 - 2 <x, y>^2 of Delta (Remark 4) for unit vectors
-// x (new) and y (old).  FP64 evaluates it as written.  FP32 evaluates the
-// same quantity as s (2 - s / 2) with s = ||x - y||^2 (an identity for unit
-// vectors): no cancellation when a message barely moved, and no FP64
-// instruction per update (FP64 issues at 1/64 of the FP32 rate here).
+// x (new) and y (old), each held one entry per lane in a group of lanes.
+// FP64 evaluates it as written.  FP32 evaluates the same quantity as
+// s (2 - s / 2) with s = ||x - y||^2 (an identity for unit vectors): no
+// cancellation when a message barely moved, and no FP64 instruction per
+// update (FP64 issues at 1/64 of the FP32 rate here).
 template <typename T> struct DeltaTerm;
 template <> struct DeltaTerm<double> {
-  static __device__ __forceinline__ double eval(const double* x, const double* y, int n, int lane) {
-    const double o = fused_dot(x, y, n, lane);
+  static __device__ __forceinline__ double eval(double x, double y, int width) {
+    const double o = group_sum(x * y, width);
     return 2.0 - 2.0 * o * o;
   }
 };
 template <> struct DeltaTerm<float> {
-  static __device__ __forceinline__ float eval(const float* x, const float* y, int n, int lane) {
-    float s = 0.f;
-    for (int e = lane; e < n; e += 32) {
-      const float t = x[e] - y[e];
-      s += t * t;
-    }
-    s = warp_sum(s);
+  static __device__ __forceinline__ float eval(float x, float y, int width) {
+    const float t = x - y;
+    const float s = group_sum(t * t, width);
     return s * (2.f - 0.5f * s);
   }
 };
 
-// Resident CTAs per SM the register budget is sized for: 32 warps per SM in
-// FP32 (64 registers a thread), 16 in FP64; shared memory at d = 11 allows it.
-template <typename T, int NW> struct FusedMinBlocks { static constexpr int value = 32 / NW > 1 ? 32 / NW : 1; };
-template <int NW> struct FusedMinBlocks<double, NW> { static constexpr int value = 16 / NW > 1 ? 16 / NW : 1; };
+// Unit L2 norm (Remark 3) of the vector held by a group of lanes.
+template <typename T>
+__device__ __forceinline__ T group_normalize(T v, int width) {
+  const T nrm = xsqrt(group_sum(v * v, width));
+  return v * (nrm > T(0) ? T(1) / nrm : T(0));
+}
 
-// One (syndrome, coset) decoded by the whole CTA: syn_src holds the
-// syndrome's m bytes and ``cta`` indexes the outputs (syndrome * 4 + coset).
-template <typename T, int NW>
+// After a sweep: normalise the new messages in ws.s0 (Remark 3), damp them
+// with the stored ones (Remark 7), normalise again, record each coset's
+// Delta term in ovl[coset * M + idx] and store the result.  Entry e of the
+// n x 2^h outgoing vectors sits in lane e % 32 (e < 64: G <= 4, h <= 4).
+template <typename T>
+__device__ __forceinline__ void fused_update(const FusedWS<T>& ws, T* msgs, int stride, unsigned cos_of, int n,
+                                             int idx, int h, T eta, T one_m_eta, double* ovl, int M, int lane) {
+  const int width = 1 << h, tot = n << h;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    if (r == 1 && tot <= 32) break;
+    const int e = lane + 32 * r;
+    const bool on = e < tot;
+    const int q = on ? slot_coset(cos_of, e >> h) : 0;
+    T* old = msgs + q * stride + idx * kFusedVec + (e & (width - 1));
+    T x = on ? ws.s0[e] : T(0);
+    const T y = on ? *old : T(0);
+    x = group_normalize(x, width);
+    x = one_m_eta * x + eta * y;
+    x = group_normalize(x, width);
+    const T term = DeltaTerm<T>::eval(x, y, width);
+    if (on) {
+      *old = x;
+      if ((e & (width - 1)) == 0) ovl[q * M + idx] = (double)term;
+    }
+  }
+  __syncwarp();
+}
+
+// Resident CTAs per SM the register budget is sized for: with one coset per
+// CTA, 32 warps per SM in FP32 (64 registers a thread) and 16 in FP64; with
+// more cosets per CTA shared memory allows half as many.
+template <typename T, int NW, int G> struct FusedMinBlocks {
+  static constexpr int warps = (sizeof(T) == 4 ? 32 : 16) / (G > 1 ? 2 : 1);
+  static constexpr int value = warps / NW > 1 ? warps / NW : 1;
+};
+
+// Cosets c0 .. c0 + G - 1 of one syndrome decoded by the whole CTA: syn_src
+// holds the syndrome's m bytes and outputs go to row syn * 4 + coset.
+template <typename T, int NW, int G>
 __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const int M, const uint8_t* syn_src,
-                                           const long long cta, const int coset, unsigned char* smem) {
-  using WS = FusedWS<T>;
-  const int W = g.W, d = g.d, nb = g.nb;
+                                           const long long syn, const int c0, unsigned char* smem) {
+  const int W = g.W, d = g.d, nb = g.nb, WW = W * W;
   const int m = 2 * d * (d - 1);
-  const FusedLayout Lo = fused_layout<T>(g, M, NW);
+  const FusedLayout Lo = fused_layout<T>(g, M, NW, G);
   uint8_t* synd = smem + Lo.synd;
-  uint8_t* frame = smem + Lo.frame;
+  uint8_t* frames = smem + Lo.frame;
   int16_t* msg_of = reinterpret_cast<int16_t*>(smem + Lo.msg_of);
   int16_t* meta = reinterpret_cast<int16_t*>(smem + Lo.meta);
   int16_t* work = reinterpret_cast<int16_t*>(smem + Lo.work);
   double* ovl = reinterpret_cast<double*>(smem + Lo.ovl);
   double* rlog = reinterpret_cast<double*>(smem + Lo.rlog);
-  int* misc = reinterpret_cast<int*>(smem + Lo.misc);
-  double* dsh = reinterpret_cast<double*>(smem + Lo.misc + 48);
+  int* misc = reinterpret_cast<int*>(smem + Lo.misc);      // [0] counter, [2..4] list sizes, [8 + q] flags
+  double* dsh = reinterpret_cast<double*>(smem + Lo.misc + 64);
   T* msgs = reinterpret_cast<T*>(smem + Lo.msgs);
-  WS* wsa = reinterpret_cast<WS*>(smem + Lo.ws);
+  const int stride = M * kFusedVec;                          // messages of one coset
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const FusedWS<T> ws = fused_ws_at<T>(smem + Lo.ws + warp * Lo.ws_stride, G);
 
   for (int i = tid; i < m; i += NW * 32) synd[i] = syn_src[i];
   __syncthreads();
-  const int bx = (coset == 1 || coset == 2), bz = (coset == 2 || coset == 3);
-  for (int e = tid; e < W * W; e += NW * 32) {
-    const int i = e / W, j = e % W;
+  // Pauli frame f_s L of each coset: pure error strings from the syndrome
+  // plus the logical string (X on row 0, Z on column 0).
+  for (int e = tid; e < G * WW; e += NW * 32) {
+    const int q = e / WW, ij = e - q * WW;
+    const int coset = c0 + q;
+    const int bx = (coset == 1 || coset == 2), bz = (coset == 2 || coset == 3);
+    const int i = ij / W, j = ij % W;
     int fx = 0, fz = 0;
     if ((i & 1) == 0 && (j & 1) == 0) {
       const int r = i >> 1, cc = j >> 1;
@@ -430,7 +514,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
       if (bx && r == 0) fx ^= 1;
       if (bz && cc == 0) fz ^= 1;
     }
-    frame[e] = (uint8_t)(fx | (fz << 1));
+    frames[e] = (uint8_t)(fx | (fz << 1));
   }
   if (tid == 0) {
     int idx = 0, n0 = 0, n1 = 0;
@@ -448,44 +532,52 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
             msg_of[key] = -1;
           }
         }
-    misc[0] = 0; misc[1] = 0; misc[2] = n0; misc[3] = n1;
+    misc[0] = 0; misc[2] = n0; misc[3] = n1;
+    for (int q = 0; q < 4; ++q) misc[8 + q] = 0;
   }
   __syncthreads();
 
   Ctx<T, kFusedK> c;
   c.g = g; c.D = 0; c.cutoff2 = T(0);
   c.pI = (T)(1.0 - a.p); c.pE = (T)(a.p / 3.0);
-  c.frame = frame; c.msg_of = msg_of; c.msg_off = nullptr; c.dims = nullptr;
-  c.arena = nullptr; c.e0 = nullptr; c.cta_flags = &misc[1];
+  c.frame = frames; c.msg_of = msg_of; c.msg_off = nullptr; c.dims = nullptr;
+  c.arena = nullptr; c.e0 = nullptr; c.cta_flags = &misc[8];
 
   // Remark 2: uniform messages of unit norm, unless initial messages are
   // given (learned warm start): those are renormalised on entry.
-  for (int idx = warp; idx < M; idx += NW) {
+  for (int qi = warp; qi < G * M; qi += NW) {
+    const int q = qi / M, idx = qi - q * M;
     const int key = meta[idx];
     const int w = g.side_len(key / 4 / nb, (key / 4) % nb, key & 3);
-    T* x = msgs + idx * kFusedVec;
+    T* x = msgs + q * stride + idx * kFusedVec;
+    bool uniform = true;
     if (a.init_msgs) {
-      const float* src = a.init_msgs + (cta * M + idx) * kFusedVec;
-      for (int i = lane; i < kFusedVec; i += 32) x[i] = i < (1 << w) ? (T)src[i] : T(0);
-      __syncwarp();
-      const T nrm = fused_normalize(x, 1 << w, lane);
-      if (!(nrm > T(0))) {                            // unusable proposal: fall back to uniform
-        const T u = (T)rsqrt((double)(1 << w));
-        for (int i = lane; i < (1 << w); i += 32) x[i] = u;
-        __syncwarp();
-      }
-    } else {
+      const float* src = a.init_msgs + ((syn * 4 + c0 + q) * M + idx) * kFusedVec;
+      const T v = lane < (1 << w) ? (T)src[lane] : T(0);
+      const T nrm = xsqrt(group_sum(v * v, 32));
+      uniform = !(nrm > T(0));
+      if (!uniform && lane < kFusedVec) x[lane] = v * (T(1) / nrm);
+    }
+    if (uniform) {                                   // no (or an unusable) proposal
       const T u = (T)rsqrt((double)(1 << w));
-      for (int i = lane; i < kFusedVec; i += 32) x[i] = i < (1 << w) ? u : T(0);
+      if (lane < kFusedVec) x[lane] = lane < (1 << w) ? u : T(0);
     }
   }
   __syncthreads();
 
-  WS& ws = wsa[warp];
   const T eta = (T)a.eta, one_m_eta = T(1) - eta;
-  double delta = 0.0;
-  int it_done = 0;
-  for (int it = 1; it <= a.max_iter && M > 0; ++it) {
+  unsigned act = (1u << G) - 1;                      // cosets still iterating
+  double delta[G];
+  int it_done[G];
+#pragma unroll
+  for (int q = 0; q < G; ++q) { delta[q] = 0.0; it_done[q] = 0; }
+  for (int it = 1; it <= a.max_iter && M > 0 && act; ++it) {
+    int n = 0;
+    unsigned cos_of = 0;
+#pragma unroll
+    for (int q = 0; q < G; ++q)
+      if ((act >> q) & 1u) { cos_of |= (unsigned)q << (2 * n); ++n; }
+    c.frame = frames + (cos_of & 3u) * WW;
     for (int color = 0; color < 2; ++color) {       // Remark 8
       const int nwork = misc[2 + color];
       const int16_t* lst = work + color * M;
@@ -498,40 +590,36 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
         const int key = meta[idx];
         const int I = key / 4 / nb, J = (key / 4) % nb, dir = key & 3;
         const Frame f = make_frame(c, I, J, dir);
-        fused_sweep(ws, c, msgs, f, false, lane);
-        const int n = 1 << f.h;
-        T* x = ws.s0;
-        T* old = msgs + idx * kFusedVec;
-        fused_normalize(x, n, lane);                                  // Remark 3
-        for (int e = lane; e < n; e += 32) x[e] = one_m_eta * x[e] + eta * old[e];   // Remark 7
-        __syncwarp();
-        fused_normalize(x, n, lane);
-        const T term = DeltaTerm<T>::eval(x, old, n, lane);
-        __syncwarp();
-        for (int e = lane; e < n; e += 32) old[e] = x[e];
-        if (lane == 0) ovl[idx] = (double)term;
-        __syncwarp();
+        fused_sweep(ws, c, msgs, stride, cos_of, n, frames, f, false, lane);
+        fused_update(ws, msgs, stride, cos_of, n, idx, f.h, eta, one_m_eta, ovl, M, lane);
       }
       __syncthreads();
       if (tid == 0) misc[0] = 0;
       __syncthreads();
     }
-    if (warp == 0) {                                   // Remark 4
+    if (warp < G && ((act >> warp) & 1u)) {          // Remark 4, one warp per coset
       double acc = 0.0;
-      for (int i = lane; i < M; i += 32) acc += ovl[i];
+      for (int i = lane; i < M; i += 32) acc += ovl[warp * M + i];
       acc = warp_sum(acc);
-      if (lane == 0) dsh[0] = sqrt(fmax(acc, 0.0)) / M;
+      if (lane == 0) dsh[warp] = sqrt(fmax(acc, 0.0)) / M;
     }
     __syncthreads();
-    delta = dsh[0];
-    it_done = it;
-    if (delta < a.delta0) break;
+#pragma unroll
+    for (int q = 0; q < G; ++q)
+      if ((act >> q) & 1u) {
+        delta[q] = dsh[q];
+        it_done[q] = it;
+        if (delta[q] < a.delta0) act &= ~(1u << q);
+      }
   }
 
   if (a.final_msgs)
-    for (int e = tid; e < M * kFusedVec; e += NW * 32) a.final_msgs[cta * M * kFusedVec + e] = (float)msgs[e];
+    for (int e = tid; e < G * stride; e += NW * 32) {
+      const int q = e / stride;
+      a.final_msgs[(syn * 4 + c0 + q) * stride + (e - q * stride)] = (float)msgs[e];
+    }
 
-  // Lemma 1 read-out.
+  // Lemma 1 read-out, coset by coset.
   if (tid == 0) {
     int ne = 0;
     for (int idx = 0; idx < M; ++idx) {
@@ -544,92 +632,105 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
   __syncthreads();
   const int nedge = misc[4];
   const int nblk = nb * nb;
+  const int per = nblk + nedge;
   for (;;) {
     int item = 0;
     if (lane == 0) item = atomicAdd(&misc[0], 1);
     item = __shfl_sync(kFull, item, 0);
-    if (item >= nblk + nedge) break;
-    if (item < nblk) {
-      const int I = item / nb, J = item % nb;
+    if (item >= G * per) break;
+    const int q = item / per, r = item - q * per;
+    const T* mq = msgs + q * stride;
+    if (r < nblk) {
+      const int I = r / nb, J = r % nb;
+      c.frame = frames + q * WW;
       const Frame f = make_frame(c, I, J, kDirR);
-      const double ls = fused_sweep(ws, c, msgs, f, true, lane);   // valid in lane 0
+      const double ls = fused_sweep(ws, c, msgs, stride, (unsigned)q, 1, frames, f, true, lane);  // lane 0
       const int right = J + 1 < nb ? msg_index(c, I, J + 1, kDirL) : -1;
       double z;
-      if (right >= 0) z = fused_dot(ws.s0, msgs + right * kFusedVec, 1 << f.h, lane);
+      if (right >= 0) z = fused_dot(ws.s0, mq + right * kFusedVec, 1 << f.h, lane);
       else z = (double)ws.s0[0];
       if (lane == 0) {
         rlog[item] = ls + log(fabs(z));
-        if (!(z > 0.0)) atomicOr(&misc[1], kFlagBlock);
+        if (!(z > 0.0)) atomicOr(&misc[8 + q], kFlagBlock);
       }
       __syncwarp();
     } else {
-      const int e = item - nblk;
-      const int idx = work[e];
+      const int idx = work[r - nblk];
       const int key = meta[idx];
       const int I = key / 4 / nb, J = (key / 4) % nb, dir = key & 3;
       const int other = dir == kDirR ? msg_index(c, I, J + 1, kDirL) : msg_index(c, I + 1, J, kDirU);
       const int w = g.side_len(I, J, dir);
-      const double o = fused_dot(msgs + idx * kFusedVec, msgs + other * kFusedVec, 1 << w, lane);
+      const double o = fused_dot(mq + idx * kFusedVec, mq + other * kFusedVec, 1 << w, lane);
       if (lane == 0) {
         rlog[item] = -log(fabs(o));
-        if (!(o > 0.0)) atomicOr(&misc[1], kFlagOverlap);
+        if (!(o > 0.0)) atomicOr(&misc[8 + q], kFlagOverlap);
       }
     }
   }
   __syncthreads();
-  if (warp == 0) {
+  if (warp < G) {
     double acc = 0.0;
-    for (int i = lane; i < nblk + nedge; i += 32) acc += rlog[i];
+    for (int i = lane; i < per; i += 32) acc += rlog[warp * per + i];
     acc = warp_sum(acc);
+    double dq = 0.0;
+    int iq = 0;
+#pragma unroll
+    for (int q = 0; q < G; ++q)
+      if (q == warp) { dq = delta[q]; iq = it_done[q]; }
     if (lane == 0) {
-      int fl = misc[1];
+      int fl = misc[8 + warp];
       if (!isfinite(acc)) fl |= kFlagNonfinite;
-      if (!(delta < a.delta1)) fl |= kFlagUntrusted;
-      a.logp[cta] = acc;
-      a.delta[cta] = delta;
-      a.iters[cta] = it_done;
-      a.flags[cta] = fl;
+      if (!(dq < a.delta1)) fl |= kFlagUntrusted;
+      const long long row = syn * 4 + c0 + warp;
+      a.logp[row] = acc;
+      a.delta[row] = dq;
+      a.iters[row] = iq;
+      a.flags[row] = fl;
     }
   }
 }
 
-
-template <typename T, int NW>
-__global__ void __launch_bounds__(NW * 32, (FusedMinBlocks<T, NW>::value)) fused_kernel(KArgs<T> a) {
+// One CTA per (syndrome, group of G cosets).
+template <typename T, int NW, int G>
+__global__ void __launch_bounds__(NW * 32, (FusedMinBlocks<T, NW, G>::value)) fused_kernel(KArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const long long cta = blockIdx.x;
+  constexpr int NG = 4 / G;
+  const long long syn = blockIdx.x / NG;
+  const int c0 = (int)(blockIdx.x % NG) * G;
   const int m = 2 * a.geo.d * (a.geo.d - 1);
-  fused_item<T, NW>(a, a.geo, a.M, a.synd + (cta >> 2) * m, cta, (int)(cta & 3), smem);
+  fused_item<T, NW, G>(a, a.geo, a.M, a.synd + syn * m, syn, c0, smem);
 }
 
 // A batch of syndromes of different distances in one persistent launch: CTAs
-// take (syndrome, coset) items from a global counter in the order given
-// (largest distance first balances the tail) until the batch is done.
+// take (syndrome, coset group) items from a global counter in the order
+// given (largest distance first balances the tail) until the batch is done.
 struct MixedArgs {
   const int32_t* d_of;          // distance of each syndrome
   const int64_t* offsets;       // byte offset of each syndrome in the packed buffer
   const int32_t* order;         // syndrome order of the items, or null
   unsigned long long* counter;  // zero before the launch
-  long long n_items;            // 4 * B
+  long long n_items;            // B * (4 / G)
   int k;
 };
 
-template <typename T, int NW>
-__global__ void __launch_bounds__(NW * 32, (FusedMinBlocks<T, NW>::value)) fused_mixed_kernel(KArgs<T> a, MixedArgs mx) {
+template <typename T, int NW, int G>
+__global__ void __launch_bounds__(NW * 32, (FusedMinBlocks<T, NW, G>::value))
+    fused_mixed_kernel(KArgs<T> a, MixedArgs mx) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long item_sh;
+  constexpr int NG = 4 / G;
   for (;;) {
     if (threadIdx.x == 0) item_sh = (long long)atomicAdd(mx.counter, 1ull);
     __syncthreads();
     const long long item = item_sh;
     __syncthreads();
     if (item >= mx.n_items) break;
-    const long long shot = mx.order ? (long long)mx.order[item >> 2] : (item >> 2);
-    const int coset = (int)(item & 3);
+    const long long shot = mx.order ? (long long)mx.order[item / NG] : (item / NG);
+    const int c0 = (int)(item % NG) * G;
     const Geo g = make_geo(mx.d_of[shot], mx.k);
     int M = 0, ae = 0;
     count_messages(g, 1, &M, &ae);
-    fused_item<T, NW>(a, g, M, a.synd + mx.offsets[shot], shot * 4 + coset, coset, smem);
+    fused_item<T, NW, G>(a, g, M, a.synd + mx.offsets[shot], shot, c0, smem);
     __syncthreads();
   }
 }

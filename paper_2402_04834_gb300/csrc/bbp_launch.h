@@ -37,8 +37,12 @@ int cta_smem_bytes(int precision, const Geo& g, int M);
 
 // Fused-block path (Remark 9): block side k <= kFusedMaxK, messages in shared memory.
 constexpr int kFusedMaxK = 4;
-constexpr int kFusedWarps = 8;
-int fused_smem_bytes(int precision, const Geo& g, int M, int warps = kFusedWarps);
+constexpr int kMaxSmemBytes = 227 * 1024;       // opt-in shared memory of one CTA
+int fused_smem_bytes(int precision, const Geo& g, int M, int warps, int cosets);
+// Launch shape of the fused kernel: *warps / *cosets are requests (0 = any);
+// on success they hold the first compiled shape that matches them and
+// whose shared memory fits, in the order of measured speed.
+bool fused_shape(int precision, const Geo& g, int M, int* warps, int* cosets);
 
 struct MixedLaunch {
   const int32_t* d_of;
@@ -49,10 +53,12 @@ struct MixedLaunch {
   int ctas_per_sm;
 };
 
-cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, cudaStream_t st);
-cudaError_t launch_fused_f32(const LaunchArgs& a, int warps, cudaStream_t st);
-cudaError_t launch_fused_mixed_f64(const LaunchArgs& a, const MixedLaunch& mx, int warps, cudaStream_t st);
-cudaError_t launch_fused_mixed_f32(const LaunchArgs& a, const MixedLaunch& mx, int warps, cudaStream_t st);
+cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, int cosets, cudaStream_t st);
+cudaError_t launch_fused_f32(const LaunchArgs& a, int warps, int cosets, cudaStream_t st);
+cudaError_t launch_fused_mixed_f64(const LaunchArgs& a, const MixedLaunch& mx, int warps, int cosets,
+                                   cudaStream_t st);
+cudaError_t launch_fused_mixed_f32(const LaunchArgs& a, const MixedLaunch& mx, int warps, int cosets,
+                                   cudaStream_t st);
 cudaError_t launch_decode_f64(const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_decode_f32(const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_decide(const LaunchArgs& a, cudaStream_t st);

@@ -50,7 +50,8 @@ def test_workspace_sizes_scale_with_batch(L):
 
 
 @pytest.mark.parametrize("field,val", [("d", 1), ("k", 0), ("D", 0), ("p", 0.0), ("p", 0.8),
-                                       ("eta", 1.0), ("precision", 7), ("max_iter", -1)])
+                                       ("eta", 1.0), ("precision", 7), ("max_iter", -1),
+                                       ("launch_warps", 5), ("launch_cosets", 3)])
 def test_invalid_parameters_rejected(L, field, val):
     c = pkg.DecoderParams(d=5, k=3, D=4).c()
     setattr(c, field, val)
@@ -62,6 +63,22 @@ def test_unsupported_sizes_reported(L):
     c = pkg.DecoderParams(d=11, k=9, D=8).c()
     out = ctypes.c_size_t(0)
     assert L.bbp_workspace_bytes(ctypes.byref(c), 10, 0, ctypes.byref(out)) == -4
+
+
+def test_fused_launch_shapes_checked_on_the_host(L):
+    # Compiled shapes are accepted; uncompiled ones, and shapes whose shared
+    # memory cannot fit one CTA, are reported before any CUDA call.
+    out = ctypes.c_size_t(0)
+    for prec, shapes in pkg.FUSED_SHAPES.items():
+        for w, g in shapes:
+            c = pkg.DecoderParams(d=7, k=4, precision=prec, algorithm="fused", warps=w, cosets=g).c()
+            assert L.bbp_workspace_bytes(ctypes.byref(c), 10, 0, ctypes.byref(out)) == 0, (prec, w, g)
+    c = pkg.DecoderParams(d=7, k=4, precision="fp64", algorithm="fused", warps=16, cosets=4).c()
+    assert L.bbp_workspace_bytes(ctypes.byref(c), 10, 0, ctypes.byref(out)) == -4
+    c = pkg.DecoderParams(d=31, k=4, precision="fp64", algorithm="fused", warps=4, cosets=4).c()
+    assert L.bbp_workspace_bytes(ctypes.byref(c), 10, 0, ctypes.byref(out)) == -4
+    c = pkg.DecoderParams(d=31, k=4, precision="fp64", algorithm="fused").c()
+    assert L.bbp_workspace_bytes(ctypes.byref(c), 10, 0, ctypes.byref(out)) == 0
 
 
 def test_decode_null_pointers_rejected_before_any_cuda_call(L):

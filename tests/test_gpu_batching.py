@@ -99,16 +99,17 @@ def test_autotuned_shapes_give_identical_results(dev):
     s = torch.from_numpy(S).to(dev)
     prm = pkg.DecoderParams(d=d, k=4, p=p, max_iter=10, precision="fp32", algorithm="fused")
     best, table = autotune.tune_uniform(s, prm)
-    assert len(table) == 3 and best.warps in (4, 8, 16)
+    assert len(table) == len(pkg.FUSED_SHAPES["fp32"]) and (best.warps, best.cosets) in pkg.FUSED_SHAPES["fp32"]
     ref = pkg.decode(s, prm)
-    for w in (4, 16):
-        got = pkg.decode(s, pkg.DecoderParams(**{**prm.__dict__, "warps": w}))
+    for w, c in pkg.FUSED_SHAPES["fp32"]:
+        got = pkg.decode(s, pkg.DecoderParams(**{**prm.__dict__, "warps": w, "cosets": c}))
         torch.cuda.synchronize()
-        assert torch.equal(got["logp"], ref["logp"])
+        for key in ("logp", "delta", "iters", "flags"):
+            assert torch.equal(got[key], ref[key]), (w, c, key)
     ds, shots = mixed_batch(128, [7, 9, 13], p, 5)
     packed, offsets, d_of = pack_mixed(shots, device=dev)
     mp = pkg.DecoderParams(d=0, k=4, p=p, max_iter=10, precision="fp32", algorithm="fused")
-    best, table = autotune.tune_mixed(packed, offsets, d_of, mp, ctas=(0, 2))
+    best, table = autotune.tune_mixed(packed, offsets, d_of, mp, shapes=((8, 4), (8, 2), (8, 1)), ctas=(0, 2))
     assert len(table) >= 2
     a = decode_mixed(packed, offsets, d_of, best)
     b = decode_mixed(packed, offsets, d_of, mp)
@@ -123,7 +124,7 @@ def test_mixed_workload_4096_over_five_distances(dev):
     ds, shots = mixed_batch(4096, [7, 9, 13, 17, 21], p, 3000)
     packed, offsets, d_of = pack_mixed(shots, device=dev)
     prm = pkg.DecoderParams(d=0, k=4, p=p, max_iter=20, delta0=1e-4, precision="fp32", algorithm="fused")
-    best, table = autotune.tune_mixed(packed, offsets, d_of, prm, warps=(8, 16), ctas=(0, 2))
+    best, table = autotune.tune_mixed(packed, offsets, d_of, prm, shapes=((8, 4), (8, 2), (8, 1)), ctas=(0, 2))
     out = decode_mixed(packed, offsets, d_of, best)
     torch.cuda.synchronize()
     counter = torch.empty(256, dtype=torch.uint8, device=dev)
