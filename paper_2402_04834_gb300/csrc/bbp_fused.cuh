@@ -126,14 +126,37 @@ __device__ __forceinline__ void qubit_table(const Ctx<T, K>& c, int qi, int qj, 
   }
 }
 
+// Log of a product of positive factors, for the read-out (Lemma 1).  FP64
+// sums the factors' logs; FP32 keeps the product as a float mantissa and a
+// binary exponent and takes one FP64 log at the end (FP64 issues at 1/64
+// of the FP32 rate here).  Used by one lane.
+template <typename T> struct LogAcc;
+template <> struct LogAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void mul(double x) { s += log(x); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct LogAcc<float> {
+  float m = 1.f;
+  int e = 0;
+  __device__ __forceinline__ void mul(float x) {
+    int ex;
+    m *= frexpf(x, &ex);
+    e += ex;
+    m = frexpf(m, &ex);
+    e += ex;
+  }
+  __device__ __forceinline__ double value() const { return log((double)m) + (double)e * 0.6931471805599453; }
+};
+
 // Contract block f (rotated so that f.dir points right) with its incoming
 // dense messages for the n cosets of cos_of (messages of coset q at
 // msgs + q * stride; c.frame is the frame of slot 0's coset and frames holds
 // all G frames).  Leaves the outgoing vectors over the chain in ws.s0, slot
-// s at s << h, and returns the log of the norms taken out (read-out only,
-// which runs with n = 1; FP64, in lane 0).
+// s at s << h, and returns the norms taken out (read-out only, which runs
+// with n = 1; in lane 0).
 template <typename T, int K>
-__device__ __forceinline__ double fused_sweep(const FusedWS<T>& ws, const Ctx<T, K>& c, const T* msgs, int stride,
+__device__ __forceinline__ LogAcc<T> fused_sweep(const FusedWS<T>& ws, const Ctx<T, K>& c, const T* msgs, int stride,
                                            unsigned cos_of, int n, const uint8_t* frames, const Frame& f,
                                            bool readout, int lane) {
   using V2 = typename Vec2<T>::type;
@@ -158,7 +181,7 @@ __device__ __forceinline__ double fused_sweep(const FusedWS<T>& ws, const Ctx<T,
   FState st{0, h, 0, 0};
   const int sd = nc >> 1;               // the column that holds the data site
   const int nf = nc - sd - 1;           // legs still expected after it
-  double log_scale = 0.0;               // accumulated by lane 0 only
+  LogAcc<T> log_scale;                  // accumulated by lane 0 only
   const bool rowwise = f.dir == kDirR || f.dir == kDirL;
   const int WW = c.g.W * c.g.W;
   for (int t = 0; t < nc; ++t) {
@@ -390,7 +413,7 @@ __device__ __forceinline__ double fused_sweep(const FusedWS<T>& ws, const Ctx<T,
       if (nrm > T(0)) {
         const T inv = T(1) / nrm;
         for (int e = lane; e < nt; e += 32) cur[e] *= inv;
-        if (lane == 0) log_scale += log((double)nrm);
+        if (lane == 0) log_scale.mul(nrm);
       }
       __syncwarp();
     }
@@ -402,11 +425,10 @@ __device__ __forceinline__ double fused_sweep(const FusedWS<T>& ws, const Ctx<T,
   return log_scale;
 }
 
+// <x, y> over n <= 32 entries for the read-out, in the working precision.
 template <typename T>
-__device__ __forceinline__ double fused_dot(const T* x, const T* y, int n, int lane) {
-  double acc = 0.0;
-  for (int e = lane; e < n; e += 32) acc += (double)x[e] * (double)y[e];
-  return warp_sum(acc);
+__device__ __forceinline__ T read_dot(const T* x, const T* y, int n, int lane) {
+  return warp_sum(lane < n ? x[lane] * y[lane] : T(0));
 }
 
 // The per-message term 2 - 2 <x, y>^2 of Delta (Remark 4) for unit vectors
@@ -644,14 +666,13 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
       const int I = r / nb, J = r % nb;
       c.frame = frames + q * WW;
       const Frame f = make_frame(c, I, J, kDirR);
-      const double ls = fused_sweep(ws, c, msgs, stride, (unsigned)q, 1, frames, f, true, lane);  // lane 0
+      LogAcc<T> ls = fused_sweep(ws, c, msgs, stride, (unsigned)q, 1, frames, f, true, lane);  // lane 0
       const int right = J + 1 < nb ? msg_index(c, I, J + 1, kDirL) : -1;
-      double z;
-      if (right >= 0) z = fused_dot(ws.s0, mq + right * kFusedVec, 1 << f.h, lane);
-      else z = (double)ws.s0[0];
+      const T z = right >= 0 ? read_dot(ws.s0, mq + right * kFusedVec, 1 << f.h, lane) : ws.s0[0];
       if (lane == 0) {
-        rlog[item] = ls + log(fabs(z));
-        if (!(z > 0.0)) atomicOr(&misc[8 + q], kFlagBlock);
+        ls.mul(z < T(0) ? -z : z);
+        rlog[item] = ls.value();
+        if (!(z > T(0))) atomicOr(&misc[8 + q], kFlagBlock);
       }
       __syncwarp();
     } else {
@@ -660,10 +681,10 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
       const int I = key / 4 / nb, J = (key / 4) % nb, dir = key & 3;
       const int other = dir == kDirR ? msg_index(c, I, J + 1, kDirL) : msg_index(c, I + 1, J, kDirU);
       const int w = g.side_len(I, J, dir);
-      const double o = fused_dot(mq + idx * kFusedVec, mq + other * kFusedVec, 1 << w, lane);
+      const T o = read_dot(mq + idx * kFusedVec, mq + other * kFusedVec, 1 << w, lane);
       if (lane == 0) {
-        rlog[item] = -log(fabs(o));
-        if (!(o > 0.0)) atomicOr(&misc[8 + q], kFlagOverlap);
+        rlog[item] = -log(fabs((double)o));
+        if (!(o > T(0))) atomicOr(&misc[8 + q], kFlagOverlap);
       }
     }
   }
