@@ -197,6 +197,47 @@ __device__ __forceinline__ LogAcc<T> fused_sweep(const FusedWS<T>& ws, const Ctx
       const int np = n << (ns.bits() - 1);
       const int hb = h + st.bb;                        // bits of (rows, b)
       const int low = (1 << hb) - 1;
+      if (t == sd && f.a_idx >= 0 && hb >= 5 && nf <= 1) {
+        // The data column, one coset at a time with its side message in
+        // registers: each lane reads the 2^ab values in[a, rows, b] of its
+        // (rows, b) once and writes all outputs (a2, v) of that group.
+        const int na = 1 << st.ab;                     // st.ab = sd <= 2
+        for (int s = 0; s < n; ++s) {
+          T mr[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) mr[i] = i < (1 << nc) ? ws.mt[(s << nc) + i] : T(0);
+          const int ib = s << (st.ab + hb), ob = s << (nf + hb);
+          for (int hbv = lane; hbv <= low; hbv += 32) {
+            T x[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) x[a] = a < na ? cur[ib | (a << hb) | hbv] : T(0);
+            if (nf == 1) {
+#pragma unroll
+              for (int a2 = 0; a2 < 2; ++a2) {
+                T s0 = T(0), s1 = T(0);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                  s0 += mr[(a << 2) | a2] * x[a];
+                  s1 += mr[(((a << 1) | 1) << 1) | a2] * x[a];
+                }
+                V2 o;
+                o.x = s0; o.y = s1;
+                *reinterpret_cast<V2*>(nxt + 2 * (ob | (a2 << hb) | hbv)) = o;
+              }
+            } else {
+              T s0 = T(0), s1 = T(0);
+#pragma unroll
+              for (int a = 0; a < 4; ++a) {
+                s0 += mr[a << 1] * x[a];
+                s1 += mr[(a << 1) | 1] * x[a];
+              }
+              V2 o;
+              o.x = s0; o.y = s1;
+              *reinterpret_cast<V2*>(nxt + 2 * (ob | hbv)) = o;
+            }
+          }
+        }
+      } else
       for (int e2 = lane; e2 < np; e2 += 32) {
         const int a2f = e2 >> hb, hbv = e2 & low;      // a2f = (slot, a); (rows, b) is shared by in and out
         V2 o;
@@ -378,7 +419,49 @@ __device__ __forceinline__ LogAcc<T> fused_sweep(const FusedWS<T>& ws, const Ctx
       else if (t == sd) ns.bb = nf;
       else ns.bb = st.bb - 1;
       const int nt = n << ns.bits();
-      if (!(f.b_idx >= 0 && t < sd)) {   // recording v as b's new low bit changes no index
+      const int hah = st.ab + h;                       // bits of (a, rows)
+      if (t == sd && f.b_idx >= 0 && hah >= 5 && nf <= 1) {
+        // The data column, one coset at a time with its side message in
+        // registers: each lane reads the 2^bb pairs in[a, rows, b, v] of its
+        // (a, rows) once and writes all outputs b2 of that group.
+        const int nbb = 1 << st.bb;                    // st.bb = sd <= 2
+        for (int s = 0; s < n; ++s) {
+          T mr[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) mr[i] = i < (1 << nc) ? ws.mb[(s << nc) + i] : T(0);
+          for (int al = lane; al < (1 << hah); al += 32) {
+            const int ah = (s << hah) | al;
+            V2 x[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              if (b < nbb) {
+                x[b] = *reinterpret_cast<const V2*>(cur + (((ah << st.bb) | b) << 1));
+              } else {
+                x[b].x = T(0); x[b].y = T(0);
+              }
+            }
+            if (nf == 1) {
+              V2 o;
+              T val = T(0);
+#pragma unroll
+              for (int b = 0; b < 4; ++b) val += mr[(b << 2)] * x[b].x + mr[(((b << 1) | 1) << 1)] * x[b].y;
+              o.x = val;
+              val = T(0);
+#pragma unroll
+              for (int b = 0; b < 4; ++b) val += mr[(b << 2) | 1] * x[b].x + mr[(((b << 1) | 1) << 1) | 1] * x[b].y;
+              o.y = val;
+              *reinterpret_cast<V2*>(nxt + (ah << 1)) = o;
+            } else {
+              T val = T(0);
+#pragma unroll
+              for (int b = 0; b < 4; ++b) val += mr[b << 1] * x[b].x + mr[(b << 1) | 1] * x[b].y;
+              nxt[ah] = val;
+            }
+          }
+        }
+        __syncwarp();
+        T* tmp = cur; cur = nxt; nxt = tmp;
+      } else if (!(f.b_idx >= 0 && t < sd)) {   // recording v as b's new low bit changes no index
         for (int e = lane; e < nt; e += 32) {
           T val;
           if (f.b_idx < 0) {
