@@ -215,6 +215,8 @@ int bbp_decode_batch_static(const uint8_t* syndromes, int64_t B, const bbp_param
 #define BBP_WARM_HIDDEN 256          /* width of the two hidden layers */
 #define BBP_WARM_OUT 16              /* outputs: logits of a 2^k <= 16 message */
 #define BBP_WARM_MAX_ROWS 4194240    /* rows per infer / train call */
+#define BBP_WARM_STATUS_OFFSET 270336 /* bbp_warm_infer: int32 status word in the workspace */
+#define BBP_WARM_INFER_WORKSPACE_BYTES 270592 /* bbp_warm_infer needs this much, for any N */
 
 /* Number of directed block edges M of (d, k). */
 int bbp_message_count(const bbp_params* prm, int32_t* M);
@@ -242,9 +244,14 @@ int bbp_warm_workspace_bytes(int64_t N, size_t* bytes);
  * bbp_warm_infer -- initial messages from the network: the proposal u (exp
  * of the logits over the first lens[row] entries, unit norm) is blended with
  * the uniform start, msgs = normalise((1 - alpha) uniform + alpha u), zero
- * beyond lens[row]; alpha in [0, 1] (0 = cold start).  GEMM operands are
- * rounded to bf16, accumulation is FP32.  All pointers device memory;
- * N <= BBP_WARM_MAX_ROWS.
+ * beyond lens[row]; alpha in [0, 1] (0 = cold start).  The layers run on
+ * the tensor cores (tcgen05): operands (features, weights, hidden
+ * activations) rounded to BF16, FP32 accumulation.  All pointers device
+ * memory; N <= BBP_WARM_MAX_ROWS; workspace 256-byte aligned.  A
+ * device-side wait that gives up (none is expected) leaves NaN rows, which
+ * the decoder replaces by the uniform start, and sets the int32 at byte
+ * BBP_WARM_STATUS_OFFSET of the workspace to 1 (0 otherwise); the call is
+ * asynchronous, so read it after the stream has finished.
  */
 int bbp_warm_infer(const float* theta, const float* feats, const int32_t* lens, int64_t N, float alpha,
                    float* msgs, void* workspace, size_t workspace_bytes, void* stream);

@@ -24,6 +24,8 @@ SYMBOLS = ("bbp_workspace_bytes", "bbp_decode_batch", "bbp_decode_batch_host", "
            "bbp_message_features", "bbp_warm_param_count", "bbp_warm_workspace_bytes", "bbp_warm_infer",
            "bbp_warm_train_step", "bbp_decode_batch_ex", "bbp_decode_mixed")
 WARM_F, WARM_H, WARM_O, WARM_MAX_ROWS = 256, 256, 16, 4194240
+WARM_STATUS_OFFSET = 270336       # int32 status word of bbp_warm_infer in its workspace
+WARM_INFER_WS_BYTES = 270592      # workspace of bbp_warm_infer, for any N
 # Compiled launch shapes (warps per CTA, cosets per CTA) of the fused kernel.
 FUSED_SHAPES = {"fp32": ((8, 4), (8, 2), (4, 2), (4, 4), (16, 1), (8, 1), (4, 1)),
                 "fp64": ((4, 2), (8, 2), (8, 1), (4, 4))}

@@ -12,8 +12,9 @@
 // syndrome bit (checks) -- then one-hot direction, one-hot message length,
 // 10 p and a constant 1.
 //
-// All kernels are plain FP32 CUDA-core code: a 64 x 64-tile GEMM with bias /
-// GELU epilogues and transposed operands for the backward pass.
+// Training is FP32 CUDA-core code: a 64 x 64-tile GEMM with bias / GELU
+// epilogues and transposed operands for the backward pass.  Inference runs
+// on the tensor cores (bbp_warm_tc.cu).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -22,6 +23,7 @@
 #include "../../include/blockbp.h"
 #include "bbp_fused.cuh"
 #include "bbp_launch.h"
+#include "bbp_warm_tc.h"
 
 namespace bbp {
 namespace warm {
@@ -126,8 +128,7 @@ __device__ __forceinline__ float gelu_grad(float x) {
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(256) gemm_kernel(int Mr, int N, int K, const float* __restrict__ A, int lda,
                                                    const float* __restrict__ B, int ldb, float* C, int ldc,
-                                                   const float* __restrict__ bias, float* Z, int act, int accumulate,
-                                                   int bf16_operands) {
+                                                   const float* __restrict__ bias, float* Z, int act, int accumulate) {
   constexpr int BM = 64, BN = 64, BK = 16;
   __shared__ float As[BK][BM + 4];
   __shared__ float Bs[BK][BN + 4];
@@ -141,7 +142,6 @@ __global__ void __launch_bounds__(256) gemm_kernel(int Mr, int N, int K, const f
       const int gm = m0 + mm, gk = k0 + kk;
       float v = 0.f;
       if (gm < Mr && gk < K) v = TA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
-      if (bf16_operands) v = __bfloat162float(__float2bfloat16(v));
       As[kk][mm] = v;
     }
     for (int e = threadIdx.x; e < BN * BK; e += 256) {
@@ -149,7 +149,6 @@ __global__ void __launch_bounds__(256) gemm_kernel(int Mr, int N, int K, const f
       const int gn = n0 + nn, gk = k0 + kk;
       float v = 0.f;
       if (gn < N && gk < K) v = TB ? B[(long long)gn * ldb + gk] : B[(long long)gk * ldb + gn];
-      if (bf16_operands) v = __bfloat162float(__float2bfloat16(v));
       Bs[kk][nn] = v;
     }
     __syncthreads();
@@ -186,15 +185,15 @@ __global__ void __launch_bounds__(256) gemm_kernel(int Mr, int N, int K, const f
 
 template <bool TA, bool TB>
 cudaError_t gemm(int Mr, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
-                 const float* bias, float* Z, int act, int accumulate, int bf16, cudaStream_t st) {
+                 const float* bias, float* Z, int act, int accumulate, cudaStream_t st) {
   dim3 grid((N + 63) / 64, (Mr + 63) / 64);
-  gemm_kernel<TA, TB><<<grid, 256, 0, st>>>(Mr, N, K, A, lda, B, ldb, C, ldc, bias, Z, act, accumulate, bf16);
+  gemm_kernel<TA, TB><<<grid, 256, 0, st>>>(Mr, N, K, A, lda, B, ldb, C, ldc, bias, Z, act, accumulate);
   return cudaGetLastError();
 }
 
 // u = masked exp(o - max) / norm; per-row loss 1 - <u,t>^2 and dL/do (mean over N).
 __global__ void head_kernel(const float* logits, const int32_t* lens, const float* targets, long long N,
-                            float* msgs, float* gO, float* loss_sum, float alpha) {
+                            float* gO, float* loss_sum) {
   const long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (row >= N) return;
   const int n = lens[row];
@@ -204,17 +203,6 @@ __global__ void head_kernel(const float* logits, const int32_t* lens, const floa
   float s2 = 0.f;
   for (int i = 0; i < O; ++i) { mm[i] = i < n ? expf(o[i] - mx) : 0.f; s2 += mm[i] * mm[i]; }
   const float nm = sqrtf(s2), inv = 1.f / nm;
-  if (msgs) {
-    // Proposal blended with the uniform start: (1 - alpha) uniform + alpha u.
-    const float un = rsqrtf((float)n);
-    float b[O], s2b = 0.f;
-    for (int i = 0; i < O; ++i) {
-      b[i] = i < n ? (1.f - alpha) * un + alpha * mm[i] * inv : 0.f;
-      s2b += b[i] * b[i];
-    }
-    const float ib = rsqrtf(s2b);
-    for (int i = 0; i < O; ++i) msgs[row * O + i] = b[i] * ib;
-  }
   if (targets) {
     float cdot = 0.f;
     for (int i = 0; i < O; ++i) cdot += mm[i] * inv * targets[row * O + i];
@@ -281,7 +269,11 @@ namespace {
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 // Scratch of a forward (+ backward) pass over N rows: Z1, A1, Z2, A2 [N x H],
 // logits and dL/dlogits [N x O], and two [N x H] gradient buffers.
-size_t pass_bytes(long long N) { return al256((size_t)N * H * 4) * 6 + al256((size_t)N * O * 4) * 2 + 256; }
+size_t pass_bytes(long long N) {
+  const size_t train = al256((size_t)N * H * 4) * 6 + al256((size_t)N * O * 4) * 2 + 256;
+  const size_t infer = infer_tc_workspace_bytes();
+  return train > infer ? train : infer;
+}
 }  // namespace
 
 extern "C" {
@@ -322,20 +314,11 @@ int bbp_warm_infer(const float* theta, const float* feats, const int32_t* lens, 
   if (!theta || !feats || !lens || !msgs || N < 0 || N > BBP_WARM_MAX_ROWS) return BBP_EINVAL;
   if (!(alpha >= 0.f && alpha <= 1.f)) return BBP_EINVAL;
   if (N == 0) return BBP_OK;
-  if (!workspace || workspace_bytes < pass_bytes(N)) return BBP_ENOSPACE;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const Params P = split(theta);
-  char* w = static_cast<char*>(workspace);
-  float* A1 = reinterpret_cast<float*>(w);
-  float* A2 = reinterpret_cast<float*>(w + al256((size_t)N * H * 4));
-  float* L = reinterpret_cast<float*>(w + 2 * al256((size_t)N * H * 4));
-  // BF16 operands, FP32 accumulation (weights kept in FP32).
-  if (gemm<false, false>((int)N, H, F, feats, F, P.W1, H, A1, H, P.b1, nullptr, 1, 0, 1, st) != cudaSuccess ||
-      gemm<false, false>((int)N, H, H, A1, H, P.W2, H, A2, H, P.b2, nullptr, 1, 0, 1, st) != cudaSuccess ||
-      gemm<false, false>((int)N, O, H, A2, H, P.W3, O, L, O, P.b3, nullptr, 0, 0, 1, st) != cudaSuccess)
-    return BBP_ECUDA;
-  head_kernel<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(L, lens, nullptr, N, msgs, nullptr, nullptr, alpha);
-  return cudaGetLastError() == cudaSuccess ? BBP_OK : BBP_ECUDA;
+  if (!workspace || workspace_bytes < infer_tc_workspace_bytes()) return BBP_ENOSPACE;
+  if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return BBP_EINVAL;
+  return infer_tc(theta, feats, lens, N, alpha, msgs, workspace, static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? BBP_OK
+             : BBP_ECUDA;
 }
 
 int bbp_warm_train_step(float* theta, float* adam_m, float* adam_v, int32_t step, float lr, const float* feats,
@@ -364,24 +347,24 @@ int bbp_warm_train_step(float* theta, float* adam_m, float* adam_v, int32_t step
   float* gO = reinterpret_cast<float*>(w + 6 * nh + no);
   const int n = (int)N;
   bool ok = true;
-  ok = ok && gemm<false, false>(n, H, F, feats, F, P.W1, H, A1, H, P.b1, Z1, 1, 0, 0, st) == cudaSuccess;
-  ok = ok && gemm<false, false>(n, H, H, A1, H, P.W2, H, A2, H, P.b2, Z2, 1, 0, 0, st) == cudaSuccess;
-  ok = ok && gemm<false, false>(n, O, H, A2, H, P.W3, O, L, O, P.b3, nullptr, 0, 0, 0, st) == cudaSuccess;
+  ok = ok && gemm<false, false>(n, H, F, feats, F, P.W1, H, A1, H, P.b1, Z1, 1, 0, st) == cudaSuccess;
+  ok = ok && gemm<false, false>(n, H, H, A1, H, P.W2, H, A2, H, P.b2, Z2, 1, 0, st) == cudaSuccess;
+  ok = ok && gemm<false, false>(n, O, H, A2, H, P.W3, O, L, O, P.b3, nullptr, 0, 0, st) == cudaSuccess;
   if (!ok) return BBP_ECUDA;
   if (cudaMemsetAsync(loss_sum, 0, sizeof(float), st) != cudaSuccess) return BBP_ECUDA;
-  head_kernel<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(L, lens, targets, N, nullptr, gO, loss_sum, 1.f);
+  head_kernel<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(L, lens, targets, N, gO, loss_sum);
   // Layer 3: gW3 = A2^T gO, gb3 = colsum gO, gA2 = gO W3^T.
-  ok = ok && gemm<true, false>(H, O, n, A2, H, gO, O, gW3, O, nullptr, nullptr, 0, 0, 0, st) == cudaSuccess;
+  ok = ok && gemm<true, false>(H, O, n, A2, H, gO, O, gW3, O, nullptr, nullptr, 0, 0, st) == cudaSuccess;
   colsum_kernel<<<O, 256, 0, st>>>(gO, N, O, gb3);
-  ok = ok && gemm<false, true>(n, H, O, gO, O, P.W3, O, G2, H, nullptr, nullptr, 0, 0, 0, st) == cudaSuccess;
+  ok = ok && gemm<false, true>(n, H, O, gO, O, P.W3, O, G2, H, nullptr, nullptr, 0, 0, st) == cudaSuccess;
   gelu_back_kernel<<<(unsigned)(((long long)N * H + 255) / 256), 256, 0, st>>>(G2, Z2, (long long)N * H);
   // Layer 2.
-  ok = ok && gemm<true, false>(H, H, n, A1, H, G2, H, gW2, H, nullptr, nullptr, 0, 0, 0, st) == cudaSuccess;
+  ok = ok && gemm<true, false>(H, H, n, A1, H, G2, H, gW2, H, nullptr, nullptr, 0, 0, st) == cudaSuccess;
   colsum_kernel<<<H, 256, 0, st>>>(G2, N, H, gb2);
-  ok = ok && gemm<false, true>(n, H, H, G2, H, P.W2, H, G1, H, nullptr, nullptr, 0, 0, 0, st) == cudaSuccess;
+  ok = ok && gemm<false, true>(n, H, H, G2, H, P.W2, H, G1, H, nullptr, nullptr, 0, 0, st) == cudaSuccess;
   gelu_back_kernel<<<(unsigned)(((long long)N * H + 255) / 256), 256, 0, st>>>(G1, Z1, (long long)N * H);
   // Layer 1.
-  ok = ok && gemm<true, false>(F, H, n, feats, F, G1, H, gW1, H, nullptr, nullptr, 0, 0, 0, st) == cudaSuccess;
+  ok = ok && gemm<true, false>(F, H, n, feats, F, G1, H, gW1, H, nullptr, nullptr, 0, 0, st) == cudaSuccess;
   colsum_kernel<<<H, 256, 0, st>>>(G1, N, H, gb1);
   if (!ok || cudaGetLastError() != cudaSuccess) return BBP_ECUDA;
   if (step > 0 && adam_m && adam_v) {

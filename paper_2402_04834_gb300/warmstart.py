@@ -15,7 +15,8 @@ import math
 import numpy as np
 import torch
 
-from ._lib import WARM_F, WARM_H, WARM_MAX_ROWS, WARM_O, DecoderParams, check, lib
+from ._lib import (WARM_F, WARM_H, WARM_INFER_WS_BYTES, WARM_MAX_ROWS, WARM_O, WARM_STATUS_OFFSET as STATUS_OFFSET,
+                   DecoderParams, check, lib)
 from .decoder import Workspace, _ptr, _stream, decode
 
 
@@ -65,6 +66,7 @@ class WarmStart:
         self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
         self.step = 0
         self.ws = Workspace()
+        self.infer_ws = Workspace()
 
     def train_step(self, feats, targets, lens, lr=1e-3, stream=None) -> float:
         """One Adam step on a minibatch; returns the mean loss before the step."""
@@ -91,13 +93,21 @@ class WarmStart:
         blended with the uniform start by ``alpha``."""
         N = feats.shape[0]
         out = out if out is not None else torch.empty(N, WARM_O, dtype=torch.float32, device=feats.device)
-        step = min(N, WARM_MAX_ROWS, 1 << 20)
-        ws = self.ws.get(_ws_bytes(step), self.device)
+        step = max(1, min(N, WARM_MAX_ROWS))
+        ws = self.infer_ws.get(WARM_INFER_WS_BYTES, self.device)
         for a in range(0, N, step):
             b = min(N, a + step)
             check(lib().bbp_warm_infer(_ptr(self.theta), _ptr(feats[a:b]), _ptr(lens[a:b]), b - a, alpha,
                                        _ptr(out[a:b]), _ptr(ws), ws.numel(), _stream(stream)))
         return out
+
+    def status(self) -> int:
+        """Status word of the last inference (0 = every device wait completed)."""
+        torch.cuda.synchronize(self.device)
+        buf = self.infer_ws.buf
+        if buf is None or buf.numel() < STATUS_OFFSET + 4:
+            return 0
+        return int(buf[STATUS_OFFSET:STATUS_OFFSET + 4].view(torch.int32).item())
 
     def train(self, feats, targets, lens, epochs=4, batch=8192, lr=1e-3, seed=0, log=None):
         N = feats.shape[0]
@@ -148,6 +158,24 @@ def decode_warm(syndromes, prm: DecoderParams, net: WarmStart, stream=None, out=
     feats, lens = features(syndromes, prm, stream)
     init = net.infer(feats, lens, stream=stream, alpha=alpha)
     return decode_ex(syndromes, prm, init_msgs=init, stream=stream, out=out)
+
+
+def decode_warm_host(syndromes, prm: DecoderParams, net: WarmStart, out=None, alpha=DEFAULT_ALPHA, stream=None):
+    """decode_warm from host memory: syndromes [B, m] uint8 (numpy or CPU
+    tensor, pinned for asynchronous copies) in, decisions [B] and log P
+    [B, 4] back in host memory; synchronises the stream."""
+    syn = torch.as_tensor(syndromes)
+    st = stream or torch.cuda.current_stream(net.device)
+    with torch.cuda.stream(st):
+        dev_syn = syn.to(net.device, non_blocking=True)
+        res = decode_warm(dev_syn, prm, net, stream=st, alpha=alpha)
+        if out is None:
+            out = {"decision": torch.empty(syn.shape[0], dtype=torch.int8, pin_memory=True),
+                   "logp": torch.empty(syn.shape[0], 4, dtype=torch.float64, pin_memory=True)}
+        out["decision"].copy_(res["decision"], non_blocking=True)
+        out["logp"].copy_(res["logp"], non_blocking=True)
+    st.synchronize()
+    return out
 
 
 def collect(syndromes, prm: DecoderParams, max_delta=1e-3):
