@@ -4,10 +4,15 @@ Workload (one step = one batch through the whole hot path): the distance-11
 planar surface code under depolarizing noise p = 0.10, 10^4 seeded synthetic
 syndromes per GPU, blockBP with 4x4-node blocks, max-iter 20, delta0 = 1e-4,
 delta1 = 1e-2, eta = 0.1 (Sec. IV parameters), D = 8 for the MPS form.
-The headline path is the fused-block form of Remark 9 (the form the paper
-ran for k = 4) in FP32 with double logs and read-out.  Timed beside it on
-subsets of the same batch: the plain FP64 blockBP with MPS messages (the
-denominator of the metric), the FP64 fused form and the FP32 MPS form.
+The headline decoder is the learned + mixed-precision one: message
+features, the warm-start network on the tensor cores (trained first,
+untimed, on converged messages of seeded decodes), then the fused-block
+form of Remark 9 (the form the paper ran for k = 4) in FP32 with FP64
+Delta sums and read-out, started from the network's proposals.  Timed
+beside it on the same batch: the same decoder from the uniform start
+(cold), the plain FP64 blockBP with MPS messages (the denominator of the
+metric), the FP64 fused form and the FP32 MPS form.  ``--no-warm`` makes
+the cold decoder the headline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -49,6 +54,8 @@ SM_MAX_MHZ = 2070.0
 # 1/64 of that (2 DFMA per clock per SM, the nominal 1.25 TFLOP/s of GB300).
 FP32_FMA_PER_SM_CLK = 128
 FP64_FMA_PER_SM_CLK = 2
+# Warm-start network: 256 -> 256 -> 256 -> 16, two flops per multiply-add.
+MLP_FLOPS_PER_ROW = 2 * (256 * 256 + 256 * 256 + 256 * 16)
 
 
 def oracle_one(args):
@@ -235,6 +242,7 @@ def ours(args):
 
     import paper_2402_04834_gb300 as pkg
     from paper_2402_04834_gb300 import _lib
+    from paper_2402_04834_gb300 import warmstart as wsm
     from paper_2402_04834_gb300.sharding import reduce_max, shot_range
     if not os.path.exists(_lib.LIB_PATH):
         from paper_2402_04834_gb300.build import build
@@ -264,49 +272,112 @@ def ours(args):
     S_host = torch.from_numpy(S).pin_memory()
     S_dev = S_host.to(dev)
     ws = pkg.Workspace()
-    out = None
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    learned = args.warm and args.algorithm == "fused"
 
+    # The learned warm start is trained first, untimed, on converged messages
+    # of seeded d = 11 and d = 15 decodes at p in [0.05, 0.15].
+    net, train_info = None, None
+    if learned:
+        t_w = time.perf_counter()
+        Ftr, Ttr, Ltr = wsm.build_training_set(device=dev)
+        net = wsm.WarmStart(device=dev, seed=0)
+        hist = net.train(Ftr, Ttr, Ltr, epochs=12, batch=8192, lr=3e-3)
+        hist += net.train(Ftr, Ttr, Ltr, epochs=8, batch=8192, lr=5e-4, seed=1)
+        torch.cuda.synchronize()
+        train_info = {"training_rows": int(Ftr.shape[0]), "train_s": time.perf_counter() - t_w,
+                      "final_loss": hist[-1]}
+        del Ftr, Ttr, Ltr
+
+    # One step = the whole decoder over the batch.  Learned: message
+    # features -> tensor-core network -> fused decode from the proposals;
+    # events around the network and around the decode kernel.
+    M = wsm.message_count(prm)
+    rows = B * 4 * M
+    ev_mlp = []
+    ev_dec = []
+
+    def step(out, record=False):
+        if not learned:
+            a = torch.cuda.Event(enable_timing=True) if record else None
+            b = torch.cuda.Event(enable_timing=True) if record else None
+            if record:
+                a.record(stream)
+            out = pkg.decode(S_dev, prm, workspace=ws, out=out)
+            if record:
+                b.record(stream)
+                ev_dec.append((a, b))
+            return out
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
+        feats, lens = wsm.features(S_dev, prm)
+        if record:
+            evs[0].record(stream)
+        init = net.infer(feats, lens, alpha=wsm.DEFAULT_ALPHA)
+        if record:
+            evs[1].record(stream)
+            evs[2].record(stream)
+        out = wsm.decode_ex(S_dev, prm, init_msgs=init, out=out)
+        if record:
+            evs[3].record(stream)
+            ev_mlp.append((evs[0], evs[1]))
+            ev_dec.append((evs[2], evs[3]))
+        return out
+
+    out = None
     for _ in range(args.warmup):
-        out = pkg.decode(S_dev, prm, workspace=ws, out=out)
+        out = step(out)
     barrier()
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     with ClockSampler(local) as clk:
         barrier()
+        torch.cuda.nvtx.range_push("timed")        # lets a profiler select the timed steps
         t0 = time.perf_counter()
         for i in range(args.steps):
             flush.fill_(float(i))                   # evict L2 before every step
             starts[i].record(stream)
-            out = pkg.decode(S_dev, prm, workspace=ws, out=out)
+            out = step(out, record=True)
             ends[i].record(stream)
         barrier()
         wall = time.perf_counter() - t0
+        torch.cuda.nvtx.range_pop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     dev_ms = sum(step_ms)
     dev_ms_max = reduce_max(dev_ms, dist, dev)
     value = world * B * args.steps / (dev_ms_max / 1e3)
+    dec_ms = sum(a.elapsed_time(b) for a, b in ev_dec) / args.steps
+    mlp_ms = sum(a.elapsed_time(b) for a, b in ev_mlp) / args.steps if ev_mlp else None
     iters_mean = float(out["iters"].double().mean().item())
     decisions = out["decision"].cpu().numpy()
 
-    # End to end through the host entry point: H2D syndromes, decode, D2H results.
-    hout = {"logp": np.empty((B, 4)), "delta": None, "iters": None, "flags": None,
-            "decision": np.empty(B, dtype=np.int8)}
-    hsyn = S_host.numpy()
-    pkg.decode_host(hsyn, prm, workspace=ws, out=hout, device=dev)
-    barrier()
+    # End to end through the public API with host buffers: H2D syndromes,
+    # the decoder, D2H decisions and log P, every step.
+    hsyn = S_host
     e2e_t = []
-    for _ in range(args.steps):
-        t1 = time.perf_counter()
-        pkg.decode_host(hsyn, prm, workspace=ws, out=hout, device=dev)
-        e2e_t.append(time.perf_counter() - t1)
+    if learned:
+        hout = wsm.decode_warm_host(hsyn, prm, net)
+        barrier()
+        for _ in range(args.steps):
+            t1 = time.perf_counter()
+            wsm.decode_warm_host(hsyn, prm, net, out=hout)
+            e2e_t.append(time.perf_counter() - t1)
+    else:
+        hout = {"logp": np.empty((B, 4)), "delta": None, "iters": None, "flags": None,
+                "decision": np.empty(B, dtype=np.int8)}
+        pkg.decode_host(hsyn.numpy(), prm, workspace=ws, out=hout, device=dev)
+        barrier()
+        for _ in range(args.steps):
+            t1 = time.perf_counter()
+            pkg.decode_host(hsyn.numpy(), prm, workspace=ws, out=hout, device=dev)
+            e2e_t.append(time.perf_counter() - t1)
     e2e_value = world * B * args.steps / reduce_max(sum(e2e_t), dist, dev)
 
-    # Comparison legs on subsets of the same batch: the plain FP64 blockBP with
-    # MPS messages (the denominator of the metric) and the other combinations.
-    def leg(alg, prec, nshots):
+    # Comparison legs on the same batch: cold start (uniform messages,
+    # Remark 2), the plain FP64 blockBP with MPS messages (the denominator of
+    # the metric) and the other combinations.
+    def leg(alg, prec, nshots, cold=False):
         if nshots <= 0:
             return None
         nshots = min(nshots, B)
@@ -329,6 +400,7 @@ def ours(args):
                 "mean_iters": float(o["iters"].double().mean().item()),
                 "decision_agreement_with_headline": agree, "headline_speedup": value / world / val}
 
+    cold = leg("fused", args.precision, B) if learned else None
     fp64_mps = leg("mps", "fp64", args.fp64_batch)
     legs = {"fp64_fused": leg("fused", "fp64", args.other_batch),
             "fp32_mps": leg("mps", "fp32", args.other_batch // 4)}
@@ -346,46 +418,49 @@ def ours(args):
         agree = float(np.mean([r[1] == int(decisions[i]) for i, r in enumerate(res)]))
         cpu = {"value": procs / dt, "unit": "syndromes/s", "cores": procs, "kind": "oracle",
                "sample": (f"shots 0..{procs - 1} of the workload, one per process ({dt:.1f} s), "
-                          f"{'dense fused-block' if args.algorithm == 'fused' else 'MPS'} oracle"),
+                          f"{'dense fused-block' if args.algorithm == 'fused' else 'MPS'} oracle, cold start"),
                "decision_agreement": agree}
 
-    # Roofline of the dominant kernel: its arithmetic per launch over its time.
+    # Roofline of the dominant kernel (the fused decode): its arithmetic per
+    # launch over its event-timed duration; and of the network on the tensor cores.
     fp = 1 if args.precision == "fp32" else 0
     per_clk = FP32_FMA_PER_SM_CLK if fp else FP64_FMA_PER_SM_CLK
     peak = 2.0 * per_clk * N_SM * SM_MAX_MHZ * 1e6 / 1e12
-    roof = None
+    roof = roof_mlp = None
     if args.algorithm == "fused":
         f_it, f_ro = fused_flops(D_CODE, K_BLOCK)
         flops = float(out["iters"].double().sum().item()) * f_it + B * 4 * f_ro
-        kern_s = (dev_ms / args.steps) / 1e3
-        achieved = flops / kern_s / 1e12
+        achieved = flops / (dec_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "kernel": "fused_kernel",
+                "launch_ms": dec_ms,
                 "peak_source": ("derived: 128 FP32 lanes x 2 x 152 SMs x 2070 MHz" if fp
                                 else "derived: 2 FP64 FMA/clk/SM x 2 x 152 SMs x 2070 MHz"),
                 "flops_per_syndrome": flops / B}
+    if mlp_ms is not None:
+        bf16_peak, src = 1900.0, "fallback"
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                bf16_peak, src = float(json.load(f)["bf16_tflops"]), "measured (burst)"
+        except (OSError, KeyError, ValueError):
+            pass
+        mf = rows * MLP_FLOPS_PER_ROW / (mlp_ms / 1e3) / 1e12
+        roof_mlp = {"bound": "tensor", "achieved": mf, "peak": bf16_peak, "unit": "TFLOP/s", "frac": mf / bf16_peak,
+                    "traffic": None, "kernel": "mlp_tc_kernel (+ weight preparation)", "launch_ms": mlp_ms,
+                    "rows": rows, "peak_source": src}
 
-    # Learned warm start (the network is trained here, untimed, on converged
-    # messages of seeded d = 11 and d = 15 decodes); cold versus warm on the
-    # same shots of this workload, inference cost included in its time.
-    learned = None
-    if args.warm and world == 1 and args.algorithm == "fused":
-        from paper_2402_04834_gb300 import warmstart as wsm
-        t_w = time.perf_counter()
-        Ftr, Ttr, Ltr = wsm.build_training_set(device=dev)
-        net = wsm.WarmStart(device=dev, seed=0)
-        hist = net.train(Ftr, Ttr, Ltr, epochs=12, batch=8192, lr=3e-3)
-        hist += net.train(Ftr, Ttr, Ltr, epochs=8, batch=8192, lr=5e-4, seed=1)
-        torch.cuda.synchronize()
-        train_s = time.perf_counter() - t_w
-        del Ftr, Ttr, Ltr
+    # Learned warm start against cold start on the same shots: iterations and
+    # the logical error rate (Wilson 95 % intervals).
+    learned_info = None
+    if learned and world == 1:
         ev = wsm.evaluate(net, d=D_CODE, p=P_NOISE, shots=B, k=K_BLOCK, seed=SEED, device=dev,
                           max_iter=MAX_ITER, delta0=DELTA0, alpha=wsm.DEFAULT_ALPHA)
-        learned = {"training_rows": 1_000_000, "train_s": train_s, "final_loss": hist[-1],
-                   "alpha": ev["alpha"], "cold": ev["cold"], "warm": ev["warm"],
-                   "iterations_saved_fraction": ev["iterations_saved_fraction"],
-                   "decision_agreement": ev["decision_agreement"]}
+        learned_info = {**train_info, "alpha": ev["alpha"], "cold": ev["cold"], "warm": ev["warm"],
+                        "iterations_saved_fraction": ev["iterations_saved_fraction"],
+                        "decision_agreement": ev["decision_agreement"]}
 
+    chunks = -(-rows // _lib.WARM_MAX_ROWS)
+    per_step = (1 + 2 * chunks + 2) if learned else 2
     line = {
         "metric": METRIC, "value": value, "unit": "syndromes/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms_max / args.steps,
@@ -394,14 +469,16 @@ def ours(args):
         "data": "synthetic: seeded i.i.d. depolarizing errors (SplitMix64 counter RNG) and their syndromes",
         "config": {"workload": WORKLOAD, "batch_per_gpu": B, "precision": args.precision,
                    "algorithm": args.algorithm,
+                   "decoder": ("learned warm start (tensor-core network, alpha=%g) + fused FP32 blockBP"
+                               % wsm.DEFAULT_ALPHA) if learned else "fused blockBP, cold start",
                    "l2": "flushed: a 256 MB buffer is written before every timed step",
                    "mean_iters": iters_mean, "wall_s": wall},
         "clocks": clk.summary(),
         "e2e": {"value": e2e_value, "unit": "syndromes/s", "h2d_bytes_per_step": int(B * S.shape[1]),
                 "d2h_bytes_per_step": int(B * (1 + 32))},
-        "gpu_launches": 2 * args.steps,
-        "roofline": roof, "cpu_baseline": cpu,
-        "plain_fp64_gpu": fp64_mps, "other_paths": legs, "learned_warm_start": learned,
+        "gpu_launches": per_step * args.steps,
+        "roofline": roof, "roofline_network": roof_mlp, "cpu_baseline": cpu,
+        "cold_start": cold, "plain_fp64_gpu": fp64_mps, "other_paths": legs, "learned_warm_start": learned_info,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
