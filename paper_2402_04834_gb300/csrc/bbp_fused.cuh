@@ -153,12 +153,12 @@ template <> struct LogAcc<float> {
 // dense messages for the n cosets of cos_of (messages of coset q at
 // msgs + q * stride; c.frame is the frame of slot 0's coset and frames holds
 // all G frames).  Leaves the outgoing vectors over the chain in ws.s0, slot
-// s at s << h, and returns the norms taken out (read-out only, which runs
-// with n = 1; in lane 0).
+// s at s << h.  For the read-out (ls not null) every column's state is
+// renormalised per coset and the norms taken out go to ls[slot] (lane 0).
 template <typename T, int K>
-__device__ __forceinline__ LogAcc<T> fused_sweep(const FusedWS<T>& ws, const Ctx<T, K>& c, const T* msgs, int stride,
-                                           unsigned cos_of, int n, const uint8_t* frames, const Frame& f,
-                                           bool readout, int lane) {
+__device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K>& c, const T* msgs, int stride,
+                                         unsigned cos_of, int n, const uint8_t* frames, const Frame& f,
+                                         LogAcc<T>* ls, int lane) {
   using V2 = typename Vec2<T>::type;
   const int h = f.h, nc = f.ncols;
   T* cur = ws.s0;
@@ -181,7 +181,6 @@ __device__ __forceinline__ LogAcc<T> fused_sweep(const FusedWS<T>& ws, const Ctx
   FState st{0, h, 0, 0};
   const int sd = nc >> 1;               // the column that holds the data site
   const int nf = nc - sd - 1;           // legs still expected after it
-  LogAcc<T> log_scale;                  // accumulated by lane 0 only
   const bool rowwise = f.dir == kDirR || f.dir == kDirL;
   const int WW = c.g.W * c.g.W;
   for (int t = 0; t < nc; ++t) {
@@ -487,16 +486,22 @@ __device__ __forceinline__ LogAcc<T> fused_sweep(const FusedWS<T>& ws, const Ctx
       }
       st = ns;
     }
-    if (readout) {   // keep the block value in range; its log goes to the read-out (n = 1)
-      const int nt = st.size();
-      T acc = 0;
-      for (int e = lane; e < nt; e += 32) acc += cur[e] * cur[e];
-      acc = warp_sum(acc);
-      const T nrm = xsqrt(acc);
-      if (nrm > T(0)) {
-        const T inv = T(1) / nrm;
-        for (int e = lane; e < nt; e += 32) cur[e] *= inv;
-        if (lane == 0) log_scale.mul(nrm);
+    if (ls) {   // keep each coset's block value in range; the logs go to the read-out
+      const int S = st.size();
+#pragma unroll
+      for (int q = 0; q < kFusedMaxG; ++q) {
+        if (q < n) {
+          T* cq = cur + q * S;
+          T acc = 0;
+          for (int e = lane; e < S; e += 32) acc += cq[e] * cq[e];
+          acc = warp_sum(acc);
+          const T nrm = xsqrt(acc);
+          if (nrm > T(0)) {
+            const T inv = T(1) / nrm;
+            for (int e = lane; e < S; e += 32) cq[e] *= inv;
+            if (lane == 0) ls[q].mul(nrm);
+          }
+        }
       }
       __syncwarp();
     }
@@ -505,7 +510,6 @@ __device__ __forceinline__ LogAcc<T> fused_sweep(const FusedWS<T>& ws, const Ctx
     for (int e = lane; e < (n << h); e += 32) ws.s0[e] = cur[e];
     __syncwarp();
   }
-  return log_scale;
 }
 
 // <x, y> over n <= 32 entries for the read-out, in the working precision.
@@ -695,7 +699,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
         const int key = meta[idx];
         const int I = key / 4 / nb, J = (key / 4) % nb, dir = key & 3;
         const Frame f = make_frame(c, I, J, dir);
-        fused_sweep(ws, c, msgs, stride, cos_of, n, frames, f, false, lane);
+        fused_sweep(ws, c, msgs, stride, cos_of, n, frames, f, (LogAcc<T>*)nullptr, lane);
         fused_update(ws, msgs, stride, cos_of, n, idx, f.h, eta, one_m_eta, ovl, M, lane);
       }
       __syncthreads();
@@ -724,7 +728,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
       a.final_msgs[(syn * 4 + c0 + q) * stride + (e - q * stride)] = (float)msgs[e];
     }
 
-  // Lemma 1 read-out, coset by coset.
+  // Lemma 1 read-out, all G cosets of a block (or edge) at once.
   if (tid == 0) {
     int ne = 0;
     for (int idx = 0; idx < M; ++idx) {
@@ -738,36 +742,45 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
   const int nedge = misc[4];
   const int nblk = nb * nb;
   const int per = nblk + nedge;
+  const unsigned all = G == 1 ? 0u : (G == 2 ? 0x4u : 0xE4u);    // slot q holds coset q
+  c.frame = frames;
   for (;;) {
     int item = 0;
     if (lane == 0) item = atomicAdd(&misc[0], 1);
     item = __shfl_sync(kFull, item, 0);
-    if (item >= G * per) break;
-    const int q = item / per, r = item - q * per;
-    const T* mq = msgs + q * stride;
-    if (r < nblk) {
-      const int I = r / nb, J = r % nb;
-      c.frame = frames + q * WW;
+    if (item >= per) break;
+    if (item < nblk) {
+      const int I = item / nb, J = item % nb;
       const Frame f = make_frame(c, I, J, kDirR);
-      LogAcc<T> ls = fused_sweep(ws, c, msgs, stride, (unsigned)q, 1, frames, f, true, lane);  // lane 0
+      LogAcc<T> ls[kFusedMaxG];
+      fused_sweep(ws, c, msgs, stride, all, G, frames, f, ls, lane);
       const int right = J + 1 < nb ? msg_index(c, I, J + 1, kDirL) : -1;
-      const T z = right >= 0 ? read_dot(ws.s0, mq + right * kFusedVec, 1 << f.h, lane) : ws.s0[0];
-      if (lane == 0) {
-        ls.mul(z < T(0) ? -z : z);
-        rlog[item] = ls.value();
-        if (!(z > T(0))) atomicOr(&misc[8 + q], kFlagBlock);
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        const T* mq = msgs + q * stride;
+        const T z = right >= 0 ? read_dot(ws.s0 + (q << f.h), mq + right * kFusedVec, 1 << f.h, lane)
+                               : ws.s0[q << f.h];
+        if (lane == 0) {
+          ls[q].mul(z < T(0) ? -z : z);
+          rlog[q * per + item] = ls[q].value();
+          if (!(z > T(0))) atomicOr(&misc[8 + q], kFlagBlock);
+        }
       }
       __syncwarp();
     } else {
-      const int idx = work[r - nblk];
+      const int idx = work[item - nblk];
       const int key = meta[idx];
       const int I = key / 4 / nb, J = (key / 4) % nb, dir = key & 3;
       const int other = dir == kDirR ? msg_index(c, I, J + 1, kDirL) : msg_index(c, I + 1, J, kDirU);
       const int w = g.side_len(I, J, dir);
-      const T o = read_dot(mq + idx * kFusedVec, mq + other * kFusedVec, 1 << w, lane);
-      if (lane == 0) {
-        rlog[item] = -log(fabs((double)o));
-        if (!(o > T(0))) atomicOr(&misc[8 + q], kFlagOverlap);
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        const T* mq = msgs + q * stride;
+        const T o = read_dot(mq + idx * kFusedVec, mq + other * kFusedVec, 1 << w, lane);
+        if (lane == 0) {
+          rlog[q * per + item] = -log(fabs((double)o));
+          if (!(o > T(0))) atomicOr(&misc[8 + q], kFlagOverlap);
+        }
       }
     }
   }

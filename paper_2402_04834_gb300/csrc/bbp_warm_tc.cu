@@ -158,6 +158,7 @@ __device__ __forceinline__ void copy_tile(unsigned char* dst, const unsigned cha
                                           int tid) {
   const uint4* s = reinterpret_cast<const uint4*>(src);
   uint4* d = reinterpret_cast<uint4*>(dst);
+#pragma unroll 8
   for (int i = tid; i < bytes / 16; i += kThreads) d[i] = s[i];
 }
 
@@ -233,6 +234,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const long long r0 = tile * TM;
     // X: rows r0 .. r0 + 127 of the FP32 features, rounded to BF16 (one
     // 8-element chunk of one row per task; consecutive threads, consecutive rows).
+#pragma unroll 8
     for (int task = tid; task < TM * (KD / 8); task += kThreads) {
       const int row = task & (TM - 1), ch = task >> 7;
       const long long gr = r0 + row;

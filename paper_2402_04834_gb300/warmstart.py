@@ -252,9 +252,39 @@ def evaluate(net: WarmStart, d=13, p=0.10, shots=10000, k=4, seed=5000, device="
     return res
 
 
+def time_inference(syndromes_n=2500, d=11, p=0.10, k=4, seed=5000, reps=3):
+    """Features and tensor-core inference of an untrained network over the
+    messages of ``syndromes_n`` seeded syndromes (4 M rows per syndrome);
+    returns the rows and the best times in ms."""
+    from .decoder import sample
+    dev = torch.device("cuda")
+    _, _, s, _ = sample(seed, 0, syndromes_n, d, p, device=dev, with_errors=False)
+    prm = DecoderParams(d=d, k=k, p=p, precision="fp32", algorithm="fused")
+    net = WarmStart(device=dev, seed=0)
+    feats, lens = features(s, prm)
+    out = net.infer(feats, lens)
+    res = {"rows": int(feats.shape[0])}
+    for name, fn in (("features_ms", lambda: features(s, prm)), ("infer_ms", lambda: net.infer(feats, lens, out=out))):
+        best = float("inf")
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        res[name] = best
+    res["status"] = net.status()
+    return res
+
+
 def main():
     import json
+    import sys
     import time
+    if len(sys.argv) > 2 and sys.argv[1] == "--time-inference":
+        print(json.dumps(time_inference(int(sys.argv[2]))))
+        return
     dev = torch.device("cuda")
     t0 = time.time()
     F, T, L = build_training_set(device=dev)
