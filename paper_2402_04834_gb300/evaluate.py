@@ -1,0 +1,70 @@
+"""Logical error rate and throughput of the decoder on seeded syndromes.
+
+P_L is estimated as in Sec. IV: errors are drawn on the device
+(``decoder.sample``, which also returns each error's true logical class), the
+decoder picks a coset, and a shot fails when the pick is not the true
+class; the 95 % interval is Wilson's.  Throughput is timed with CUDA events
+around one decode of the whole batch.  The paper observes that BP converges
+faster at low noise, so max-iter can be lowered there (Sec. IV, last
+paragraph); ``sweep`` measures that trade-off.
+
+    python -m paper_2402_04834_gb300.evaluate --d 11 --p 0.05 0.10 --max-iter 5 10 20 --shots 10000
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+
+import torch
+
+from ._lib import DecoderParams
+from .decoder import decode, sample
+from .warmstart import wilson
+
+
+def logical_error_rate(d: int, p: float, shots: int, seed: int, **params) -> dict:
+    """Decode ``shots`` seeded syndromes; P_L with its Wilson 95 % interval,
+    mean iterations over cosets and syndromes per second."""
+    _, _, s, tc = sample(seed, 0, shots, d, p, with_errors=False)
+    prm = DecoderParams(d=d, p=p, **params)
+    out = decode(s, prm)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    out = decode(s, prm, out=out)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    fails = int((out["decision"].to(torch.int64) != tc.to(torch.int64)).sum().item())
+    lo, hi = wilson(fails, shots)
+    return {"d": d, "p": p, "shots": shots, **params, "failures": fails, "P_L": fails / shots,
+            "P_L_wilson95": [lo, hi], "mean_iters": float(out["iters"].double().mean().item()),
+            "syndromes_per_s": shots / ms * 1e3}
+
+
+def sweep(d_list, p_list, max_iters, shots, k=4, precision="fp32", algorithm="fused", seed_base=7000):
+    rows = []
+    for d in d_list:
+        for ip, p in enumerate(p_list):
+            for mi in max_iters:
+                rows.append(logical_error_rate(d, p, shots, seed_base + 100 * d + ip, k=k, max_iter=mi,
+                                               precision=precision, algorithm=algorithm))
+    return rows
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--d", type=int, nargs="+", default=[11])
+    ap.add_argument("--p", type=float, nargs="+", default=[0.05, 0.10])
+    ap.add_argument("--max-iter", type=int, nargs="+", default=[5, 10, 20])
+    ap.add_argument("--shots", type=int, default=10000)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--algorithm", default="fused", choices=["fused", "mps"])
+    args = ap.parse_args()
+    for r in sweep(args.d, args.p, args.max_iter, args.shots, precision=args.precision, algorithm=args.algorithm):
+        print(json.dumps(r), flush=True)
+
+
+if __name__ == "__main__":
+    main()
