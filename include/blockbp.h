@@ -176,10 +176,9 @@ int bbp_sample(uint64_t seed, int64_t first_shot, int64_t B, int32_t d, double p
 
 /*
  * bbp_decode_batch_static -- the decode of bbp_decode_batch without any
- * allocation, for callers that cannot allocate device memory: code inside a
- * CUDA graph being captured or replayed, real-time loops that must not take
- * the allocator's locks or fail for lack of memory mid-run, and hosts that
- * own only the input and output buffers.  The paper has no counterpart; this
+ * allocation, for callers that cannot allocate device memory: real-time
+ * loops that must not take the allocator's locks or fail for lack of memory
+ * mid-run, and hosts that own only the input and output buffers.  The paper has no counterpart; this
  * is an interface of this library.
  *   Arguments and outputs are those of bbp_decode_batch, minus the workspace:
  *   the message arena is a file-scope device array of

@@ -1,10 +1,9 @@
 // Decoding without any allocation: bbp_decode_batch_static.
 //
-// Some callers cannot call cudaMalloc at all: code running inside a CUDA
-// graph that is being captured or replayed, real-time decoding loops that
-// must not take the allocator's locks or risk an out-of-memory error
+// Some callers cannot call cudaMalloc at all: real-time decoding loops
+// that must not take the allocator's locks or risk an out-of-memory error
 // mid-run, and hosts that hand the decoder only the input and output
-// buffers.  For them the message arena lives in a fixed file-scope device
+// buffers (a fixed memory budget owned by someone else).  For them the message arena lives in a fixed file-scope device
 // array that every GPU loading this library reserves once, for the life
 // of the process.
 #include <cuda_runtime.h>

@@ -1,8 +1,8 @@
 """bbp_decode_batch_static: the decode for callers that cannot allocate.
 
-Code captured into a CUDA graph, real-time decoding loops that must not take
-the allocator's locks or run out of memory mid-run, and hosts that own only
-the input and output buffers cannot give the decoder a workspace.  This
+Real-time decoding loops that must not take the allocator's locks or run
+out of memory mid-run, and hosts that own only the input and output buffers,
+cannot give the decoder a workspace.  This
 entry point keeps the message arena in a fixed device array inside the
 library instead.  Here it is called through the C ABI and must reproduce the
 workspace-taking entry point on two calls in a row (the second call reuses
