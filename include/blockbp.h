@@ -256,6 +256,19 @@ int bbp_warm_infer(const float* theta, const float* feats, const int32_t* lens, 
                    float* msgs, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * bbp_warm_infer_syndromes -- bbp_warm_infer for every message of B
+ * syndromes (device [B][m] bytes), with the features of
+ * bbp_message_features computed inside the kernel instead of read from a
+ * features buffer: msgs [B*4*M][16], rows ordered (syndrome, coset,
+ * message), equal bit for bit to bbp_message_features followed by
+ * bbp_warm_infer.  Uses prm's d, k (<= 4) and p.  Workspace and status word
+ * as bbp_warm_infer; BBP_EUNSUPPORTED if the geometry's tables do not fit
+ * in shared memory next to the operand tiles.
+ */
+int bbp_warm_infer_syndromes(const float* theta, const uint8_t* syndromes, int64_t B, const bbp_params* prm,
+                             float alpha, float* msgs, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * bbp_warm_train_step -- one FP32 training step on N rows: forward, the loss
  * 1 - <u, t>^2 per message (the Delta term of Remark 4) averaged over rows,
  * backward into grad (bbp_warm_param_count floats), and, when step > 0 and

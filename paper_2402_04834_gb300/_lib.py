@@ -22,7 +22,7 @@ FLAG_UNTRUSTED, FLAG_OVERLAP, FLAG_BLOCK, FLAG_NONFINITE = 1, 2, 4, 8
 SYMBOLS = ("bbp_workspace_bytes", "bbp_decode_batch", "bbp_decode_batch_host", "bbp_sample",
            "bbp_strerror", "bbp_version", "bbp_decode_batch_static", "bbp_message_count",
            "bbp_message_features", "bbp_warm_param_count", "bbp_warm_workspace_bytes", "bbp_warm_infer",
-           "bbp_warm_train_step", "bbp_decode_batch_ex", "bbp_decode_mixed")
+           "bbp_warm_train_step", "bbp_decode_batch_ex", "bbp_decode_mixed", "bbp_warm_infer_syndromes")
 WARM_F, WARM_H, WARM_O, WARM_MAX_ROWS = 256, 256, 16, 4194240
 WARM_STATUS_OFFSET = 270336       # int32 status word of bbp_warm_infer in its workspace
 WARM_INFER_WS_BYTES = 270592      # workspace of bbp_warm_infer, for any N
@@ -107,6 +107,8 @@ def lib():
         L.bbp_warm_workspace_bytes.argtypes = [i64, ctypes.POINTER(ctypes.c_size_t)]
         L.bbp_warm_workspace_bytes.restype = ctypes.c_int
         L.bbp_warm_infer.argtypes = [vp, vp, vp, i64, ctypes.c_float, vp, vp, ctypes.c_size_t, vp]
+        L.bbp_warm_infer_syndromes.argtypes = [vp, vp, i64, P, ctypes.c_float, vp, vp, ctypes.c_size_t, vp]
+        L.bbp_warm_infer_syndromes.restype = ctypes.c_int
         L.bbp_warm_infer.restype = ctypes.c_int
         L.bbp_warm_train_step.argtypes = [vp, vp, vp, i32, ctypes.c_float, vp, vp, vp, i64, vp, vp, vp,
                                           ctypes.c_size_t, vp]

@@ -4,13 +4,7 @@
 // the uniform distribution (Remark 2) and names learned techniques as a way
 // to improve BP (Sec. V); cold start stays the default and the fallback.
 //
-// Features of the message from block v towards direction dir are read in
-// the frame rotated so that dir points right: a 7 x 7 window of grid nodes,
-// columns t = ncols-7 .. ncols-1 (the block's last columns and what lies
-// behind it), rows s = -1 .. 5 of the chain, with five channels per node --
-// inside the grid, qubit, the coset frame's x bit and z bit (qubits), the
-// syndrome bit (checks) -- then one-hot direction, one-hot message length,
-// 10 p and a constant 1.
+// Features of a message: see bbp_warm_features.cuh.
 //
 // Training is FP32 CUDA-core code: a 64 x 64-tile GEMM with bias / GELU
 // epilogues and transposed operands for the backward pass.  Inference runs
@@ -23,6 +17,7 @@
 #include "../../include/blockbp.h"
 #include "bbp_fused.cuh"
 #include "bbp_launch.h"
+#include "bbp_warm_features.cuh"
 #include "bbp_warm_tc.h"
 
 namespace bbp {
@@ -34,83 +29,35 @@ constexpr int O = BBP_WARM_OUT;        // 16
 constexpr int kParams = F * H + H + H * H + H + H * O + O;
 
 // ---------------------------------------------------------------------------
-// Features.
+// Features (bbp_warm_features.cuh), one CTA per (syndrome, coset).
 __global__ void features_kernel(Geo g, int M, double p, const uint8_t* synd, float* feats, int32_t* lens) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int W = g.W, d = g.d, nb = g.nb;
   const int m = 2 * d * (d - 1);
   uint8_t* s = smem;
   uint8_t* frame = smem + align_up(m, 16);
-  int16_t* msg_of = reinterpret_cast<int16_t*>(frame + align_up(W * W, 16));
-  int16_t* meta = msg_of + align_up(nb * nb * 4, 8);
+  int16_t* meta = reinterpret_cast<int16_t*>(frame + align_up(W * W, 16));
   const long long cta = blockIdx.x;
   const long long shot = cta >> 2;
   const int coset = (int)(cta & 3);
   for (int i = threadIdx.x; i < m; i += blockDim.x) s[i] = synd[shot * m + i];
   __syncthreads();
-  const int bx = (coset == 1 || coset == 2), bz = (coset == 2 || coset == 3);
-  for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
-    const int i = e / W, j = e % W;
-    int fx = 0, fz = 0;
-    if ((i & 1) == 0 && (j & 1) == 0) {
-      const int r = i >> 1, cc = j >> 1;
-      for (int c2 = 0; c2 < cc; ++c2) fx ^= s[r * (d - 1) + c2];
-      for (int r2 = 0; r2 < r; ++r2) fz ^= s[d * (d - 1) + r2 * d + cc];
-      if (bx && r == 0) fx ^= 1;
-      if (bz && cc == 0) fz ^= 1;
-    }
-    frame[e] = (uint8_t)(fx | (fz << 1));
-  }
+  for (int e = threadIdx.x; e < W * W; e += blockDim.x) frame[e] = frame_byte(s, d, e / W, e % W, coset);
   if (threadIdx.x == 0) {
     int idx = 0;
     for (int I = 0; I < nb; ++I)
       for (int J = 0; J < nb; ++J)
-        for (int dir = 0; dir < 4; ++dir) {
-          const int key = (I * nb + J) * 4 + dir;
-          if (g.has(I, J, dir)) { msg_of[key] = (int16_t)idx; meta[idx] = (int16_t)key; ++idx; }
-          else msg_of[key] = -1;
-        }
+        for (int dir = 0; dir < 4; ++dir)
+          if (g.has(I, J, dir)) meta[idx++] = (int16_t)((I * nb + J) * 4 + dir);
   }
   __syncthreads();
-  Ctx<float, kFusedK> c;
-  c.g = g; c.msg_of = msg_of;
+  const float p10 = (float)(10.0 * p);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int idx = warp; idx < M; idx += nw) {
     const int key = meta[idx];
-    const int I = key / 4 / nb, J = (key / 4) % nb, dir = key & 3;
-    const Frame f = make_frame(c, I, J, dir);
+    const MsgGeo f = msg_geo(g, key / 4 / nb, (key / 4) % nb, key & 3);
     const long long row = cta * M + idx;
-    for (int q = lane; q < F; q += 32) {
-      float v = 0.f;
-      if (q < 5 * 49) {
-        const int ch = q / 49, pos = q % 49;
-        const int t = f.ncols - 7 + pos / 7, sp = -1 + pos % 7;
-        int i, j;
-        f.node(t, sp, &i, &j);
-        const bool in = i >= 0 && j >= 0 && i < W && j < W;
-        if (in) {
-          const bool qubit = ((i + j) & 1) == 0;
-          if (ch == 0) v = 1.f;
-          else if (ch == 1) v = qubit ? 1.f : 0.f;
-          else if (ch == 2) v = qubit ? (float)(frame[i * W + j] & 1) : 0.f;
-          else if (ch == 3) v = qubit ? (float)((frame[i * W + j] >> 1) & 1) : 0.f;
-          else if (!qubit) {
-            const int bit = (i & 1) == 0 ? (i >> 1) * (d - 1) + (j >> 1)              // A_(r,c)
-                                         : d * (d - 1) + (i >> 1) * d + (j >> 1);     // B_(r,j)
-            v = (float)s[bit];
-          }
-        }
-      } else if (q < 245 + 4) {
-        v = (q - 245 == dir) ? 1.f : 0.f;
-      } else if (q < 249 + 4) {
-        v = (q - 249 == f.h - 1) ? 1.f : 0.f;
-      } else if (q == 253) {
-        v = (float)(10.0 * p);
-      } else if (q == 254) {
-        v = 1.f;
-      }
-      feats[row * F + q] = v;
-    }
+    for (int q = lane; q < F; q += 32) feats[row * F + q] = message_feature(g, f, q, frame, s, p10);
     if (lane == 0 && lens) lens[row] = 1 << f.h;
   }
 }
@@ -297,7 +244,7 @@ int bbp_message_features(const uint8_t* syndromes, int64_t B, const bbp_params* 
   int M = 0, ae = 0;
   count_messages(g, 1, &M, &ae);
   const int m = 2 * g.d * (g.d - 1);
-  const int smem = align_up(m, 16) + align_up(g.W * g.W, 16) + 2 * align_up(g.nb * g.nb * 4, 8) + 2 * M + 64;
+  const int smem = align_up(m, 16) + align_up(g.W * g.W, 16) + align_up(2 * M, 16);
   features_kernel<<<(unsigned)(B * 4), 256, smem, static_cast<cudaStream_t>(stream)>>>(g, M, prm->p, syndromes,
                                                                                       feats, lens);
   return cudaGetLastError() == cudaSuccess ? BBP_OK : BBP_ECUDA;
@@ -317,6 +264,26 @@ int bbp_warm_infer(const float* theta, const float* feats, const int32_t* lens, 
   if (!workspace || workspace_bytes < infer_tc_workspace_bytes()) return BBP_ENOSPACE;
   if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return BBP_EINVAL;
   return infer_tc(theta, feats, lens, N, alpha, msgs, workspace, static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? BBP_OK
+             : BBP_ECUDA;
+}
+
+int bbp_warm_infer_syndromes(const float* theta, const uint8_t* syndromes, int64_t B, const bbp_params* prm,
+                             float alpha, float* msgs, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!theta || !syndromes || !msgs || !prm || B < 0 || prm->d < 2 || prm->d > 64 || prm->k < 1 ||
+      prm->k > kFusedK || !(prm->p > 0.0 && prm->p < 0.75))
+    return BBP_EINVAL;
+  if (!(alpha >= 0.f && alpha <= 1.f)) return BBP_EINVAL;
+  if (B == 0) return BBP_OK;
+  if (!workspace || workspace_bytes < infer_tc_workspace_bytes()) return BBP_ENOSPACE;
+  if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return BBP_EINVAL;
+  const Geo g = make_geo(prm->d, prm->k);
+  int M = 0, ae = 0;
+  count_messages(g, 1, &M, &ae);
+  if (M == 0) return BBP_OK;
+  if (infer_tc_syndromes_smem(g, M) > kMaxSmemBytes) return BBP_EUNSUPPORTED;
+  return infer_tc_syndromes(theta, syndromes, B, g, M, prm->p, alpha, msgs, workspace,
+                            static_cast<cudaStream_t>(stream)) == cudaSuccess
              ? BBP_OK
              : BBP_ECUDA;
 }

@@ -1,0 +1,89 @@
+// Features of one directed block edge for the warm-start network, shared by
+// the features kernel (training data) and the tensor-core inference kernel
+// (which computes them on the fly from the syndrome), so that the network
+// always sees the same inputs.
+//
+// The message from block (I, J) towards direction dir is read in the frame
+// rotated so that dir points right: a 7 x 7 window of grid nodes, columns
+// t = ncols-7 .. ncols-1 (the block's last columns and what lies behind
+// it), rows s = -1 .. 5 of the chain, with five channels per node -- inside
+// the grid, qubit, the coset frame's x bit and z bit (qubits), the syndrome
+// bit (checks) -- then one-hot direction, one-hot message length, 10 p and
+// a constant 1.
+#pragma once
+
+#include <stdint.h>
+
+#include "bbp_geometry.h"
+
+namespace bbp {
+namespace warm {
+
+// Position of a message's block in the grid, rotated so that dir points right.
+struct MsgGeo {
+  int dir, h, ncols, r0, r1, c0, c1;
+  __device__ __forceinline__ void node(int t, int s, int* i, int* j) const {
+    switch (dir) {
+      case kDirR: *i = r0 + s; *j = c0 + t; break;
+      case kDirL: *i = r0 + s; *j = c1 - 1 - t; break;
+      case kDirD: *i = r0 + t; *j = c0 + s; break;
+      default:    *i = r1 - 1 - t; *j = c0 + s; break;
+    }
+  }
+};
+
+__device__ __forceinline__ MsgGeo msg_geo(const Geo& g, int I, int J, int dir) {
+  MsgGeo f;
+  f.dir = dir;
+  f.r0 = g.lo(I); f.r1 = g.hi(I); f.c0 = g.lo(J); f.c1 = g.hi(J);
+  const bool rowwise = dir == kDirR || dir == kDirL;
+  f.h = rowwise ? f.r1 - f.r0 : f.c1 - f.c0;
+  f.ncols = rowwise ? f.c1 - f.c0 : f.r1 - f.r0;
+  return f;
+}
+
+// Frame byte (x bit | z bit << 1) of grid node (i, j) for a coset: the pure
+// error of the syndrome (x: checks A to the node's left in its row; z:
+// checks B above it in its column) times the coset's logical string (X-bar
+// on row 0, Z-bar on column 0).  Zero on checks and on vertical-edge qubits.
+__device__ __forceinline__ uint8_t frame_byte(const uint8_t* synd, int d, int i, int j, int coset) {
+  int fx = 0, fz = 0;
+  if ((i & 1) == 0 && (j & 1) == 0) {
+    const int r = i >> 1, cc = j >> 1;
+    for (int c2 = 0; c2 < cc; ++c2) fx ^= synd[r * (d - 1) + c2];
+    for (int r2 = 0; r2 < r; ++r2) fz ^= synd[d * (d - 1) + r2 * d + cc];
+    if ((coset == 1 || coset == 2) && r == 0) fx ^= 1;
+    if ((coset == 2 || coset == 3) && cc == 0) fz ^= 1;
+  }
+  return (uint8_t)(fx | (fz << 1));
+}
+
+// Feature q (0 .. 255) of the message; frame is the coset's W x W frame.
+__device__ __forceinline__ float message_feature(const Geo& g, const MsgGeo& f, int q, const uint8_t* frame,
+                                                 const uint8_t* synd, float p10) {
+  const int W = g.W, d = g.d;
+  if (q < 5 * 49) {
+    const int ch = q / 49, pos = q % 49;
+    const int t = f.ncols - 7 + pos / 7, sp = -1 + pos % 7;
+    int i, j;
+    f.node(t, sp, &i, &j);
+    if (!(i >= 0 && j >= 0 && i < W && j < W)) return 0.f;
+    const bool qubit = ((i + j) & 1) == 0;
+    if (ch == 0) return 1.f;
+    if (ch == 1) return qubit ? 1.f : 0.f;
+    if (ch == 2) return qubit ? (float)(frame[i * W + j] & 1) : 0.f;
+    if (ch == 3) return qubit ? (float)((frame[i * W + j] >> 1) & 1) : 0.f;
+    if (qubit) return 0.f;
+    const int bit = (i & 1) == 0 ? (i >> 1) * (d - 1) + (j >> 1)              // A_(r,c)
+                                 : d * (d - 1) + (i >> 1) * d + (j >> 1);     // B_(r,j)
+    return (float)synd[bit];
+  }
+  if (q < 245 + 4) return (q - 245 == f.dir) ? 1.f : 0.f;
+  if (q < 249 + 4) return (q - 249 == f.h - 1) ? 1.f : 0.f;
+  if (q == 253) return p10;
+  if (q == 254) return 1.f;
+  return 0.f;
+}
+
+}  // namespace warm
+}  // namespace bbp

@@ -23,6 +23,7 @@
 #include <stdint.h>
 
 #include "../../include/blockbp.h"
+#include "bbp_warm_features.cuh"
 #include "bbp_warm_tc.h"
 
 namespace bbp {
@@ -202,10 +203,31 @@ __device__ __forceinline__ void issue_layer(uint32_t d_tmem, const unsigned char
   mma_commit(mbar);
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
-    mlp_tc_kernel(const float* __restrict__ feats, const int32_t* __restrict__ lens, long long N,
-                  const unsigned char* __restrict__ wt, const float* __restrict__ b1, const float* __restrict__ b2,
-                  const float* __restrict__ b3, float alpha, float* __restrict__ msgs, int32_t* status) {
+struct MlpArgs {
+  const float* feats;        // feature rows [N][256] (from a features tensor), or
+  const int32_t* lens;       //   their message lengths;
+  const uint8_t* synd;       // syndromes [N / (4 M)][m]: features computed here
+  Geo g;
+  int M, max_pairs;
+  float p10;
+  long long N;
+  const unsigned char* wt;
+  const float *b1, *b2, *b3;
+  float alpha;
+  float* msgs;
+  int32_t* status;
+};
+
+// Shared memory of the syndrome-fed kernel beyond the operand tiles: the
+// message table, then per (syndrome, coset) pair of a tile its syndrome and
+// its frame.
+__host__ __device__ inline int synd_extra_bytes(const Geo& g, int M, int max_pairs) {
+  const int m = 2 * g.d * (g.d - 1);
+  return align_up(2 * M, 16) + max_pairs * (align_up(m, 16) + align_up(g.W * g.W, 16));
+}
+
+template <bool kSynd>
+__global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(MlpArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem;                 // operand tile / hidden activations
   unsigned char* sB = smem + kTileA;        // weights of the current layer
@@ -213,8 +235,24 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ uint32_t tmem_slot;
   __shared__ float sb1[NH], sb2[NH], sb3[NO];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int i = tid; i < NH; i += kThreads) { sb1[i] = b1[i]; sb2[i] = b2[i]; }
-  if (tid < NO) sb3[tid] = b3[tid];
+  const long long N = a.N;
+  const float alpha = a.alpha;
+  const unsigned char* wt = a.wt;
+  for (int i = tid; i < NH; i += kThreads) { sb1[i] = a.b1[i]; sb2[i] = a.b2[i]; }
+  if (tid < NO) sb3[tid] = a.b3[tid];
+  // Syndrome-fed: the message table (index -> (I, J, dir)) once per CTA.
+  const Geo g = a.g;
+  const int M = a.M, m = 2 * g.d * (g.d - 1), WW = g.W * g.W;
+  int16_t* meta = reinterpret_cast<int16_t*>(smem + kTileA + kTileB);
+  uint8_t* pair_base = smem + kTileA + kTileB + align_up(2 * M, 16);
+  const int pair_stride = align_up(m, 16) + align_up(WW, 16);
+  if (kSynd && tid == 0) {
+    int idx = 0;
+    for (int I = 0; I < g.nb; ++I)
+      for (int J = 0; J < g.nb; ++J)
+        for (int dir = 0; dir < 4; ++dir)
+          if (g.has(I, J, dir)) meta[idx++] = (int16_t)((I * g.nb + J) * 4 + dir);
+  }
   if (tid == 0) {
     mbar_init(&mbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -232,20 +270,58 @@ __global__ void __launch_bounds__(kThreads, 1)
   const long long ntiles = (N + TM - 1) / TM;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long r0 = tile * TM;
-    // X: rows r0 .. r0 + 127 of the FP32 features, rounded to BF16 (one
-    // 8-element chunk of one row per task; consecutive threads, consecutive rows).
-#pragma unroll 8
-    for (int task = tid; task < TM * (KD / 8); task += kThreads) {
-      const int row = task & (TM - 1), ch = task >> 7;
-      const long long gr = r0 + row;
-      uint4 pk = make_uint4(0u, 0u, 0u, 0u);
-      if (gr < N) {
-        const float4* src = reinterpret_cast<const float4*>(feats + gr * KD + ch * 8);
-        const float4 x0 = src[0], x1 = src[1];
-        pk.x = pack_bf16(x0.x, x0.y); pk.y = pack_bf16(x0.z, x0.w);
-        pk.z = pack_bf16(x1.x, x1.y); pk.w = pack_bf16(x1.z, x1.w);
+    if (kSynd) {
+      // Syndromes and frames of the (syndrome, coset) pairs the tile touches.
+      const long long p0 = r0 / M;
+      const long long plast = ((r0 + TM < N ? r0 + TM : N) - 1) / M;
+      const int np = (int)(plast - p0 + 1);
+      for (int e = tid; e < np * m; e += kThreads) {
+        const int pi = e / m, i = e - pi * m;
+        pair_base[pi * pair_stride + i] = a.synd[((p0 + pi) >> 2) * m + i];
       }
-      *reinterpret_cast<uint4*>(sA + core_off(row, ch * 8)) = pk;
+      __syncthreads();
+      for (int e = tid; e < np * WW; e += kThreads) {
+        const int pi = e / WW, ij = e - pi * WW;
+        uint8_t* pb = pair_base + pi * pair_stride;
+        pb[align_up(m, 16) + ij] = frame_byte(pb, g.d, ij / g.W, ij % g.W, (int)((p0 + pi) & 3));
+      }
+      __syncthreads();
+      // X: the features of rows r0 .. r0 + 127 (bbp_warm_features.cuh), in BF16.
+#pragma unroll 2
+      for (int task = tid; task < TM * (KD / 8); task += kThreads) {
+        const int row = task & (TM - 1), ch = task >> 7;
+        const long long gr = r0 + row;
+        uint4 pk = make_uint4(0u, 0u, 0u, 0u);
+        if (gr < N) {
+          const long long pr = gr / M;
+          const int idx = (int)(gr - pr * M);
+          const uint8_t* pb = pair_base + (int)(pr - p0) * pair_stride;
+          const int key = meta[idx];
+          const MsgGeo f = msg_geo(g, key / 4 / g.nb, (key / 4) % g.nb, key & 3);
+          float v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] = message_feature(g, f, ch * 8 + u, pb + align_up(m, 16), pb, a.p10);
+          pk.x = pack_bf16(v[0], v[1]); pk.y = pack_bf16(v[2], v[3]);
+          pk.z = pack_bf16(v[4], v[5]); pk.w = pack_bf16(v[6], v[7]);
+        }
+        *reinterpret_cast<uint4*>(sA + core_off(row, ch * 8)) = pk;
+      }
+    } else {
+      // X: rows r0 .. r0 + 127 of the FP32 features, rounded to BF16 (one
+      // 8-element chunk of one row per task; consecutive threads, consecutive rows).
+#pragma unroll 8
+      for (int task = tid; task < TM * (KD / 8); task += kThreads) {
+        const int row = task & (TM - 1), ch = task >> 7;
+        const long long gr = r0 + row;
+        uint4 pk = make_uint4(0u, 0u, 0u, 0u);
+        if (gr < N) {
+          const float4* src = reinterpret_cast<const float4*>(a.feats + gr * KD + ch * 8);
+          const float4 x0 = src[0], x1 = src[1];
+          pk.x = pack_bf16(x0.x, x0.y); pk.y = pack_bf16(x0.z, x0.w);
+          pk.z = pack_bf16(x1.x, x1.y); pk.w = pack_bf16(x1.z, x1.w);
+        }
+        *reinterpret_cast<uint4*>(sA + core_off(row, ch * 8)) = pk;
+      }
     }
     copy_tile(sB, wt, kTileB, tid);
     // Three layers: operands written by the threads become visible to the
@@ -274,9 +350,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       // Give up on this tile: NaN proposals make the decoder start uniform.
       for (int e = tid; e < TM * NO; e += kThreads) {
         const long long gr = r0 + e / NO;
-        if (gr < N) msgs[gr * NO + (e % NO)] = __int_as_float(0x7fc00000);
+        if (gr < N) a.msgs[gr * NO + (e % NO)] = __int_as_float(0x7fc00000);
       }
-      if (tid == 0) atomicExch(status, 1);
+      if (tid == 0) atomicExch(a.status, 1);
       break;
     }
     // Output layer: TMEM columns [256, 272) hold the logits of row 32 q + lane.
@@ -286,7 +362,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       tmem_wait_ld();
       const long long gr = r0 + 32 * warp + lane;
       if (gr < N) {
-        const int n = lens[gr];
+        int n;
+        if (kSynd) {
+          const int key = meta[(int)(gr % M)];
+          n = 1 << msg_geo(g, key / 4 / g.nb, (key / 4) % g.nb, key & 3).h;
+        } else {
+          n = a.lens[gr];
+        }
         float o[NO], mm[NO];
         float mx = -INFINITY;
 #pragma unroll
@@ -309,7 +391,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           s2b += b[i] * b[i];
         }
         const float ib = rsqrtf(s2b);
-        float4* dst = reinterpret_cast<float4*>(msgs + gr * NO);
+        float4* dst = reinterpret_cast<float4*>(a.msgs + gr * NO);
 #pragma unroll
         for (int i = 0; i < NO; i += 4) dst[i / 4] = make_float4(b[i] * ib, b[i + 1] * ib, b[i + 2] * ib, b[i + 3] * ib);
       }
@@ -333,28 +415,56 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 size_t infer_tc_workspace_bytes() { return (size_t)kStatusOffset + 256; }
 
-cudaError_t infer_tc(const float* theta, const float* feats, const int32_t* lens, long long N, float alpha,
-                     float* msgs, void* workspace, cudaStream_t st) {
+namespace {
+
+// Weights into the workspace, status cleared, then the persistent kernel.
+template <bool kSynd>
+cudaError_t launch_mlp(const float* theta, MlpArgs a, int extra_smem, void* workspace, cudaStream_t st) {
   unsigned char* wt = static_cast<unsigned char*>(workspace);
-  int32_t* status = reinterpret_cast<int32_t*>(wt + kStatusOffset);
+  a.wt = wt;
+  a.status = reinterpret_cast<int32_t*>(wt + kStatusOffset);
+  a.b1 = theta + KD * NH;
+  a.b2 = a.b1 + NH + NH * NH;
+  a.b3 = a.b2 + NH + NH * NO;
   const int nw = 2 * NH * KD + NO * KD;
   prep_weights_kernel<<<(nw + 255) / 256, 256, 0, st>>>(theta, wt);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(status, 0, sizeof(int32_t), st)) != cudaSuccess) return e;
-  const int smem = kTileA + kTileB;
-  if ((e = cudaFuncSetAttribute(mlp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+  if ((e = cudaMemsetAsync(a.status, 0, sizeof(int32_t), st)) != cudaSuccess) return e;
+  const int smem = kTileA + kTileB + extra_smem;
+  if ((e = cudaFuncSetAttribute(mlp_tc_kernel<kSynd>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
+      cudaSuccess)
     return e;
   int dev = 0, sms = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  const long long ntiles = (N + TM - 1) / TM;
+  const long long ntiles = (a.N + TM - 1) / TM;
   const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
-  const float* b1 = theta + KD * NH;
-  const float* b2 = b1 + NH + NH * NH;
-  const float* b3 = b2 + NH + NH * NO;
-  mlp_tc_kernel<<<grid, kThreads, smem, st>>>(feats, lens, N, wt, b1, b2, b3, alpha, msgs, status);
+  mlp_tc_kernel<kSynd><<<grid, kThreads, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t infer_tc(const float* theta, const float* feats, const int32_t* lens, long long N, float alpha,
+                     float* msgs, void* workspace, cudaStream_t st) {
+  MlpArgs a{};
+  a.feats = feats; a.lens = lens; a.N = N; a.alpha = alpha; a.msgs = msgs;
+  return launch_mlp<false>(theta, a, 0, workspace, st);
+}
+
+int infer_tc_syndromes_smem(const Geo& g, int M) {
+  const int max_pairs = (TM - 1) / M + 2;
+  return kTileA + kTileB + synd_extra_bytes(g, M, max_pairs) + 4096;   // + static shared memory
+}
+
+cudaError_t infer_tc_syndromes(const float* theta, const uint8_t* synd, long long B, const Geo& g, int M, double p,
+                               float alpha, float* msgs, void* workspace, cudaStream_t st) {
+  MlpArgs a{};
+  a.synd = synd; a.g = g; a.M = M; a.max_pairs = (TM - 1) / M + 2;
+  a.p10 = (float)(10.0 * p);
+  a.N = B * 4 * (long long)M; a.alpha = alpha; a.msgs = msgs;
+  return launch_mlp<true>(theta, a, synd_extra_bytes(g, M, a.max_pairs), workspace, st);
 }
 
 }  // namespace warm

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "../../include/blockbp.h"
+#include "bbp_geometry.h"
 
 namespace bbp {
 namespace warm {
@@ -22,6 +23,14 @@ size_t infer_tc_workspace_bytes();
 // msgs[N x 16] = proposals for feats[N x 256] (FP32 row-major), lens = 2^w per row.
 cudaError_t infer_tc(const float* theta, const float* feats, const int32_t* lens, long long N, float alpha,
                      float* msgs, void* workspace, cudaStream_t st);
+
+// Shared memory the syndrome-fed kernel needs at geometry g (bytes).
+int infer_tc_syndromes_smem(const Geo& g, int M);
+
+// msgs[B * 4 * M x 16] = proposals for every message of B syndromes, rows
+// ordered (syndrome, coset, message), the features computed in the kernel.
+cudaError_t infer_tc_syndromes(const float* theta, const uint8_t* synd, long long B, const Geo& g, int M, double p,
+                               float alpha, float* msgs, void* workspace, cudaStream_t st);
 
 }  // namespace warm
 }  // namespace bbp

@@ -101,6 +101,18 @@ class WarmStart:
                                        _ptr(out[a:b]), _ptr(ws), ws.numel(), _stream(stream)))
         return out
 
+    def infer_syndromes(self, syndromes, prm: DecoderParams, out=None, stream=None, alpha=1.0):
+        """Initial messages [B*4*M, 16] for every message of the syndromes
+        [B, m], the features computed inside the tensor-core kernel."""
+        B = syndromes.shape[0]
+        N = B * 4 * message_count(prm)
+        out = out if out is not None else torch.empty(N, WARM_O, dtype=torch.float32, device=syndromes.device)
+        ws = self.infer_ws.get(WARM_INFER_WS_BYTES, self.device)
+        cp = prm.c()
+        check(lib().bbp_warm_infer_syndromes(_ptr(self.theta), _ptr(syndromes.contiguous()), B, ctypes.byref(cp),
+                                             alpha, _ptr(out), _ptr(ws), ws.numel(), _stream(stream)))
+        return out
+
     def status(self) -> int:
         """Status word of the last inference (0 = every device wait completed)."""
         torch.cuda.synchronize(self.device)
@@ -154,9 +166,9 @@ DEFAULT_ALPHA = 0.1     # blend weight of the proposal (measured: larger weights
 
 
 def decode_warm(syndromes, prm: DecoderParams, net: WarmStart, stream=None, out=None, alpha=DEFAULT_ALPHA):
-    """Learned warm start: features -> network -> fused decode."""
-    feats, lens = features(syndromes, prm, stream)
-    init = net.infer(feats, lens, stream=stream, alpha=alpha)
+    """Learned warm start: the network on every message (features computed
+    in its kernel) -> fused decode from its proposals."""
+    init = net.infer_syndromes(syndromes, prm, stream=stream, alpha=alpha)
     return decode_ex(syndromes, prm, init_msgs=init, stream=stream, out=out)
 
 
@@ -253,7 +265,8 @@ def evaluate(net: WarmStart, d=13, p=0.10, shots=10000, k=4, seed=5000, device="
 
 
 def time_inference(syndromes_n=2500, d=11, p=0.10, k=4, seed=5000, reps=3):
-    """Features and tensor-core inference of an untrained network over the
+    """Features, tensor-core inference from them, and inference with the
+    features computed in its kernel, for an untrained network over the
     messages of ``syndromes_n`` seeded syndromes (4 M rows per syndrome);
     returns the rows and the best times in ms."""
     from .decoder import sample
@@ -264,7 +277,8 @@ def time_inference(syndromes_n=2500, d=11, p=0.10, k=4, seed=5000, reps=3):
     feats, lens = features(s, prm)
     out = net.infer(feats, lens)
     res = {"rows": int(feats.shape[0])}
-    for name, fn in (("features_ms", lambda: features(s, prm)), ("infer_ms", lambda: net.infer(feats, lens, out=out))):
+    for name, fn in (("features_ms", lambda: features(s, prm)), ("infer_ms", lambda: net.infer(feats, lens, out=out)),
+                     ("infer_from_syndromes_ms", lambda: net.infer_syndromes(s, prm, out=out))):
         best = float("inf")
         for _ in range(reps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -127,6 +127,23 @@ def test_tensor_core_inference_matches_bf16_model(dev, N):
     assert st == 0
 
 
+@pytest.mark.parametrize("d,k,B", [(11, 4, 40), (3, 4, 30), (7, 3, 20), (5, 2, 9)])
+def test_infer_from_syndromes_equals_features_then_infer(dev, d, k, B):
+    # Features computed inside the tensor-core kernel, tile by tile (a tile
+    # spans up to 17 (syndrome, coset) pairs at d = 3), give the same bits as
+    # the features kernel followed by inference.
+    net = wsm.WarmStart(device=dev, seed=3)
+    _, _, S = synth.sample_syndromes(77, 0, B, d, 0.08)
+    s = torch.from_numpy(S).to(dev)
+    prm = pkg.DecoderParams(d=d, k=k, p=0.08, precision="fp32", algorithm="fused")
+    feats, lens = wsm.features(s, prm)
+    a = net.infer(feats, lens, alpha=0.4)
+    b = net.infer_syndromes(s, prm, alpha=0.4)
+    torch.cuda.synchronize()
+    assert a.shape == b.shape and torch.equal(a, b)
+    assert net.status() == 0
+
+
 def expected_features(d, k, p, s, coset):
     """Direct re-derivation of the feature rows of one (syndrome, coset)."""
     lat = Lattice(d)
