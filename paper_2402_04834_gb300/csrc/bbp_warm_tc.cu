@@ -218,12 +218,20 @@ struct MlpArgs {
   int32_t* status;
 };
 
+// One row of a tile in the syndrome-fed kernel: its (syndrome, coset) pair
+// within the tile and its message's geometry.
+struct RowGeo {
+  int16_t r0, r1, c0, c1;
+  int8_t pair, dir, h, ncols;
+};
+
 // Shared memory of the syndrome-fed kernel beyond the operand tiles: the
-// message table, then per (syndrome, coset) pair of a tile its syndrome and
-// its frame.
+// message table, the tile's row table, then per (syndrome, coset) pair of a
+// tile its syndrome and its frame.
 __host__ __device__ inline int synd_extra_bytes(const Geo& g, int M, int max_pairs) {
   const int m = 2 * g.d * (g.d - 1);
-  return align_up(2 * M, 16) + max_pairs * (align_up(m, 16) + align_up(g.W * g.W, 16));
+  return align_up(2 * M, 16) + align_up(TM * (int)sizeof(RowGeo), 16) +
+         max_pairs * (align_up(m, 16) + align_up(g.W * g.W, 16));
 }
 
 template <bool kSynd>
@@ -244,7 +252,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(MlpArgs a) {
   const Geo g = a.g;
   const int M = a.M, m = 2 * g.d * (g.d - 1), WW = g.W * g.W;
   int16_t* meta = reinterpret_cast<int16_t*>(smem + kTileA + kTileB);
-  uint8_t* pair_base = smem + kTileA + kTileB + align_up(2 * M, 16);
+  RowGeo* rows = reinterpret_cast<RowGeo*>(smem + kTileA + kTileB + align_up(2 * M, 16));
+  uint8_t* pair_base = reinterpret_cast<uint8_t*>(rows) + align_up(TM * (int)sizeof(RowGeo), 16);
   const int pair_stride = align_up(m, 16) + align_up(WW, 16);
   if (kSynd && tid == 0) {
     int idx = 0;
@@ -285,6 +294,17 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(MlpArgs a) {
         uint8_t* pb = pair_base + pi * pair_stride;
         pb[align_up(m, 16) + ij] = frame_byte(pb, g.d, ij / g.W, ij % g.W, (int)((p0 + pi) & 3));
       }
+      // Row table: pair and message geometry of each row, once per tile.
+      if (tid < TM && r0 + tid < N) {
+        const int local = (int)(r0 + tid - p0 * M);
+        const int pi = local / M;
+        const int key = meta[local - pi * M];
+        const MsgGeo f = msg_geo(g, key / 4 / g.nb, (key / 4) % g.nb, key & 3);
+        RowGeo rg;
+        rg.r0 = (int16_t)f.r0; rg.r1 = (int16_t)f.r1; rg.c0 = (int16_t)f.c0; rg.c1 = (int16_t)f.c1;
+        rg.pair = (int8_t)pi; rg.dir = (int8_t)f.dir; rg.h = (int8_t)f.h; rg.ncols = (int8_t)f.ncols;
+        rows[tid] = rg;
+      }
       __syncthreads();
       // X: the features of rows r0 .. r0 + 127 (bbp_warm_features.cuh), in BF16.
 #pragma unroll 2
@@ -293,11 +313,11 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(MlpArgs a) {
         const long long gr = r0 + row;
         uint4 pk = make_uint4(0u, 0u, 0u, 0u);
         if (gr < N) {
-          const long long pr = gr / M;
-          const int idx = (int)(gr - pr * M);
-          const uint8_t* pb = pair_base + (int)(pr - p0) * pair_stride;
-          const int key = meta[idx];
-          const MsgGeo f = msg_geo(g, key / 4 / g.nb, (key / 4) % g.nb, key & 3);
+          const RowGeo rg = rows[row];
+          const uint8_t* pb = pair_base + rg.pair * pair_stride;
+          MsgGeo f;
+          f.r0 = rg.r0; f.r1 = rg.r1; f.c0 = rg.c0; f.c1 = rg.c1;
+          f.dir = rg.dir; f.h = rg.h; f.ncols = rg.ncols;
           float v[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) v[u] = message_feature(g, f, ch * 8 + u, pb + align_up(m, 16), pb, a.p10);
@@ -364,8 +384,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(MlpArgs a) {
       if (gr < N) {
         int n;
         if (kSynd) {
-          const int key = meta[(int)(gr % M)];
-          n = 1 << msg_geo(g, key / 4 / g.nb, (key / 4) % g.nb, key & 3).h;
+          n = 1 << rows[32 * warp + lane].h;
         } else {
           n = a.lens[gr];
         }
