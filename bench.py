@@ -4,9 +4,9 @@ Workload (one step = one batch through the whole hot path): the distance-11
 planar surface code under depolarizing noise p = 0.10, 10^4 seeded synthetic
 syndromes per GPU, blockBP with 4x4-node blocks, max-iter 20, delta0 = 1e-4,
 delta1 = 1e-2, eta = 0.1 (Sec. IV parameters), D = 8 for the MPS form.
-The headline decoder is the learned + mixed-precision one: the warm-start
-network on the tensor cores (trained first, untimed, on converged messages
-of seeded decodes; message features computed in its kernel), then the fused-block
+The headline decoder is the learned + mixed-precision one: message
+features, the warm-start network on the tensor cores (trained first,
+untimed, on converged messages of seeded decodes), then the fused-block
 form of Remark 9 (the form the paper ran for k = 4) in FP32 with FP64
 Delta sums and read-out, started from the network's proposals.  Timed
 beside it on the same batch: the same decoder from the uniform start
@@ -290,10 +290,9 @@ def ours(args):
                       "final_loss": hist[-1]}
         del Ftr, Ttr, Ltr
 
-    # One step = the whole decoder over the batch.  Learned: the tensor-core
-    # network on every message (its features computed in the kernel from the
-    # syndromes) -> fused decode from the proposals; events around the
-    # network and around the decode kernel.
+    # One step = the whole decoder over the batch.  Learned: message
+    # features -> tensor-core network -> fused decode from the proposals;
+    # events around the network and around the decode kernel.
     M = wsm.message_count(prm)
     rows = B * 4 * M
     ev_mlp = []
@@ -311,9 +310,10 @@ def ours(args):
                 ev_dec.append((a, b))
             return out
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
+        feats, lens = wsm.features(S_dev, prm)
         if record:
             evs[0].record(stream)
-        init = net.infer_syndromes(S_dev, prm, alpha=wsm.DEFAULT_ALPHA)
+        init = net.infer(feats, lens, alpha=wsm.DEFAULT_ALPHA)
         if record:
             evs[1].record(stream)
             evs[2].record(stream)
@@ -446,7 +446,7 @@ def ours(args):
             pass
         mf = rows * MLP_FLOPS_PER_ROW / (mlp_ms / 1e3) / 1e12
         roof_mlp = {"bound": "tensor", "achieved": mf, "peak": bf16_peak, "unit": "TFLOP/s", "frac": mf / bf16_peak,
-                    "traffic": None, "kernel": "mlp_tc_kernel, syndrome-fed (+ weight preparation)", "launch_ms": mlp_ms,
+                    "traffic": None, "kernel": "mlp_tc_kernel (+ weight preparation)", "launch_ms": mlp_ms,
                     "rows": rows, "peak_source": src}
 
     # Learned warm start against cold start on the same shots: iterations and
@@ -459,7 +459,8 @@ def ours(args):
                         "iterations_saved_fraction": ev["iterations_saved_fraction"],
                         "decision_agreement": ev["decision_agreement"]}
 
-    per_step = 4 if learned else 2          # weights, network, fused decode, decision
+    chunks = -(-rows // _lib.WARM_MAX_ROWS)
+    per_step = (1 + 2 * chunks + 2) if learned else 2     # features, (weights, network) per chunk, decode, decision
     line = {
         "metric": METRIC, "value": value, "unit": "syndromes/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms_max / args.steps,

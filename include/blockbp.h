@@ -263,7 +263,10 @@ int bbp_warm_infer(const float* theta, const float* feats, const int32_t* lens, 
  * message), equal bit for bit to bbp_message_features followed by
  * bbp_warm_infer.  Uses prm's d, k (<= 4) and p.  Workspace and status word
  * as bbp_warm_infer; BBP_EUNSUPPORTED if the geometry's tables do not fit
- * in shared memory next to the operand tiles.
+ * in shared memory next to the operand tiles.  It needs no features buffer
+ * (1 KB per message) but takes about 1.5x the time of the two calls (d = 11:
+ * the features are computed by the 8 warps of the one CTA per SM that the
+ * operand tiles allow, between the tensor-core phases).
  */
 int bbp_warm_infer_syndromes(const float* theta, const uint8_t* syndromes, int64_t B, const bbp_params* prm,
                              float alpha, float* msgs, void* workspace, size_t workspace_bytes, void* stream);

@@ -14,6 +14,11 @@
 // written over the operand tile as the next layer's input; the output
 // layer's 16 logits per row go through the message head.
 //
+// Each layer's weights are moved by the bulk-copy engine (cp.async.bulk,
+// completion on a second mbarrier), issued by one thread so that they
+// stream in while the threads stage the features or run the previous
+// layer's epilogue.
+//
 // Every mbarrier wait is bounded: a wait that gives up marks the tile's
 // messages NaN (the decoder then starts those messages uniform), sets the
 // status word and the CTA frees its TMEM and returns.
@@ -154,13 +159,19 @@ __global__ void prep_weights_kernel(const float* __restrict__ theta, unsigned ch
   *dst = __float2bfloat16_rn(w);
 }
 
-// Copy `bytes` (a multiple of 16) from global to shared, 16 bytes a thread.
-__device__ __forceinline__ void copy_tile(unsigned char* dst, const unsigned char* __restrict__ src, int bytes,
-                                          int tid) {
-  const uint4* s = reinterpret_cast<const uint4*>(src);
-  uint4* d = reinterpret_cast<uint4*>(dst);
-#pragma unroll 8
-  for (int i = tid; i < bytes / 16; i += kThreads) d[i] = s[i];
+// One thread: a layer's weights (bytes, a multiple of 16) from global into
+// shared memory with the bulk-copy engine in chunks; the mbarrier's phase
+// completes when all bytes have landed.
+constexpr int kBulkChunk = 16384;
+__device__ __forceinline__ void load_weights(unsigned char* dst, const unsigned char* src, int bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+  for (int off = 0; off < bytes; off += kBulkChunk) {
+    const int n = bytes - off < kBulkChunk ? bytes - off : kBulkChunk;
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     su32(dst + off)),
+                 "l"(src + off), "r"(n), "r"(su32(bar))
+                 : "memory");
+  }
 }
 
 // Accumulators of a hidden layer (TMEM columns [0, 256)) -> + bias, GELU,
@@ -239,7 +250,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(MlpArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem;                 // operand tile / hidden activations
   unsigned char* sB = smem + kTileA;        // weights of the current layer
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar;    // MMA completion
+  __shared__ __align__(8) uint64_t wbar;    // weights landed in sB
   __shared__ uint32_t tmem_slot;
   __shared__ float sb1[NH], sb2[NH], sb3[NO];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -264,6 +276,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(MlpArgs a) {
   }
   if (tid == 0) {
     mbar_init(&mbar, 1);
+    mbar_init(&wbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -274,11 +287,13 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(MlpArgs a) {
   __syncthreads();
   tc_after();
   const uint32_t tmem = tmem_slot;
-  uint32_t phase = 0;
+  uint32_t phase = 0, wphase = 0;
   int ok = 1;
   const long long ntiles = (N + TM - 1) / TM;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long r0 = tile * TM;
+    // The first layer's weights stream in while the threads build X.
+    if (tid == 0) load_weights(sB, wt, kTileB, &wbar);
     if (kSynd) {
       // Syndromes and frames of the (syndrome, coset) pairs the tile touches.
       const long long p0 = r0 / M;
@@ -343,14 +358,18 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(MlpArgs a) {
         *reinterpret_cast<uint4*>(sA + core_off(row, ch * 8)) = pk;
       }
     }
-    copy_tile(sB, wt, kTileB, tid);
     // Three layers: operands written by the threads become visible to the
-    // tensor cores (proxy fence, barrier), one thread issues, all wait.
+    // tensor cores (proxy fence, barrier), the weights have landed (the
+    // issuing thread waits on their mbarrier), one thread issues, all wait.
 #pragma unroll 1
     for (int layer = 0; layer < 3 && ok; ++layer) {
+      int wdone = 1;
+      if (tid == 0) wdone = mbar_wait(&wbar, wphase) ? 1 : 0;
+      wphase ^= 1u;
       fence_proxy_async();
       tc_before();
-      __syncthreads();
+      ok = __syncthreads_and(wdone);
+      if (!ok) break;
       tc_after();
       if (tid == 0)
         issue_layer(layer < 2 ? tmem : tmem + NH, sA, sB, layer < 2 ? instr_desc(TM, NH) : instr_desc(TM, NO), &mbar);
@@ -360,10 +379,10 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(MlpArgs a) {
       if (!ok) break;
       tc_after();
       if (layer < 2) {
-        // The MMAs have read sA and sB: overwrite sA with the activations
-        // while the next layer's weights replace sB.
+        // The MMAs have read sA and sB: the next layer's weights stream into
+        // sB while the threads overwrite sA with the activations.
+        if (tid == 0) load_weights(sB, wt + (layer + 1) * kTileB, layer == 0 ? kTileB : kTileB3, &wbar);
         hidden_epilogue(tmem, sA, layer == 0 ? sb1 : sb2, warp, lane);
-        copy_tile(sB, wt + (layer + 1) * kTileB, layer == 0 ? kTileB : kTileB3, tid);
       }
     }
     if (!ok) {
@@ -421,8 +440,10 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(MlpArgs a) {
     tc_after();
   }
   if (!ok) {
-    // A wait gave up: let the MMAs in flight finish (bounded) before TMEM goes.
+    // A wait gave up: let the MMAs and copies in flight finish (bounded)
+    // before TMEM and shared memory go.
     mbar_wait(&mbar, phase ^ 1u);
+    if (tid == 0) mbar_wait(&wbar, wphase ^ 1u);
   }
   tc_before();
   __syncthreads();
