@@ -56,6 +56,12 @@ FP32_FMA_PER_SM_CLK = 128
 FP64_FMA_PER_SM_CLK = 2
 # Warm-start network: 256 -> 256 -> 256 -> 16, two flops per multiply-add.
 MLP_FLOPS_PER_ROW = 2 * (256 * 256 + 256 * 256 + 256 * 16)
+# DRAM bytes read + written, from ncu captures of the current kernels
+# (profiles/fused_kernel_fp32_d11_1024shots.md: 371.2 KB for 1024 syndromes;
+# profiles/mlp_tc_kernel_bf16_1200k_rows.md: 1.234 GB + 74.6 MB for 1.2 M
+# rows), scaled by the units a launch processes.
+FUSED_DRAM_BYTES_PER_SYNDROME = 371.2e3 / 1024
+NETWORK_DRAM_BYTES_PER_ROW = (1.234248e9 + 74.605312e6) / 1.2e6
 
 
 def oracle_one(args):
@@ -432,7 +438,8 @@ def ours(args):
         flops = float(out["iters"].double().sum().item()) * f_it + B * 4 * f_ro
         achieved = flops / (dec_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "fused_kernel",
+                "frac": achieved / peak, "traffic": FUSED_DRAM_BYTES_PER_SYNDROME * B, "kernel": "fused_kernel",
+                "traffic_source": "ncu DRAM bytes of a 1024-syndrome launch, scaled to the batch",
                 "launch_ms": dec_ms,
                 "peak_source": ("derived: 128 FP32 lanes x 2 x 152 SMs x 2070 MHz" if fp
                                 else "derived: 2 FP64 FMA/clk/SM x 2 x 152 SMs x 2070 MHz"),
@@ -446,7 +453,9 @@ def ours(args):
             pass
         mf = rows * MLP_FLOPS_PER_ROW / (mlp_ms / 1e3) / 1e12
         roof_mlp = {"bound": "tensor", "achieved": mf, "peak": bf16_peak, "unit": "TFLOP/s", "frac": mf / bf16_peak,
-                    "traffic": None, "kernel": "mlp_tc_kernel (+ weight preparation)", "launch_ms": mlp_ms,
+                    "traffic": NETWORK_DRAM_BYTES_PER_ROW * rows,
+                    "traffic_source": "ncu DRAM bytes of a 1.2 M-row launch, scaled to the step's rows",
+                    "kernel": "mlp_tc_kernel (+ weight preparation)", "launch_ms": mlp_ms,
                     "rows": rows, "peak_source": src}
 
     # Learned warm start against cold start on the same shots: iterations and
