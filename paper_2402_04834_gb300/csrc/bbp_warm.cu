@@ -56,9 +56,17 @@ __global__ void features_kernel(Geo g, int M, double p, const uint8_t* synd, flo
   for (int idx = warp; idx < M; idx += nw) {
     const int key = meta[idx];
     const MsgGeo f = msg_geo(g, key / 4 / nb, (key / 4) % nb, key & 3);
-    const long long row = cta * M + idx;
-    for (int q = lane; q < F; q += 32) feats[row * F + q] = message_feature(g, f, q, frame, s, p10);
-    if (lane == 0 && lens) lens[row] = 1 << f.h;
+    float* out = feats + (cta * M + idx) * F;
+    // One window node per lane, its five channels at once (each channel's
+    // 49 values are contiguous, so the stores stay coalesced).
+    for (int pos = lane; pos < 49; pos += 32) {
+      float c[5];
+      window_node(g, f, pos, frame, s, c);
+#pragma unroll
+      for (int ch = 0; ch < 5; ++ch) out[ch * 49 + pos] = c[ch];
+    }
+    if (lane < F - 245) out[245 + lane] = tail_feature(f, 245 + lane, p10);
+    if (lane == 0 && lens) lens[cta * M + idx] = 1 << f.h;
   }
 }
 

@@ -58,31 +58,48 @@ __device__ __forceinline__ uint8_t frame_byte(const uint8_t* synd, int d, int i,
   return (uint8_t)(fx | (fz << 1));
 }
 
-// Feature q (0 .. 255) of the message; frame is the coset's W x W frame.
-__device__ __forceinline__ float message_feature(const Geo& g, const MsgGeo& f, int q, const uint8_t* frame,
-                                                 const uint8_t* synd, float p10) {
+// The five channels of window node pos (0 .. 48) of the message: inside the
+// grid, qubit, frame x bit, frame z bit (qubits), syndrome bit (checks).
+__device__ __forceinline__ void window_node(const Geo& g, const MsgGeo& f, int pos, const uint8_t* frame,
+                                            const uint8_t* synd, float c[5]) {
   const int W = g.W, d = g.d;
-  if (q < 5 * 49) {
-    const int ch = q / 49, pos = q % 49;
-    const int t = f.ncols - 7 + pos / 7, sp = -1 + pos % 7;
-    int i, j;
-    f.node(t, sp, &i, &j);
-    if (!(i >= 0 && j >= 0 && i < W && j < W)) return 0.f;
-    const bool qubit = ((i + j) & 1) == 0;
-    if (ch == 0) return 1.f;
-    if (ch == 1) return qubit ? 1.f : 0.f;
-    if (ch == 2) return qubit ? (float)(frame[i * W + j] & 1) : 0.f;
-    if (ch == 3) return qubit ? (float)((frame[i * W + j] >> 1) & 1) : 0.f;
-    if (qubit) return 0.f;
+  const int t = f.ncols - 7 + pos / 7, sp = -1 + pos % 7;
+  int i, j;
+  f.node(t, sp, &i, &j);
+  c[0] = c[1] = c[2] = c[3] = c[4] = 0.f;
+  if (!(i >= 0 && j >= 0 && i < W && j < W)) return;
+  c[0] = 1.f;
+  if (((i + j) & 1) == 0) {
+    const int fr = frame[i * W + j];
+    c[1] = 1.f;
+    c[2] = (float)(fr & 1);
+    c[3] = (float)((fr >> 1) & 1);
+  } else {
     const int bit = (i & 1) == 0 ? (i >> 1) * (d - 1) + (j >> 1)              // A_(r,c)
                                  : d * (d - 1) + (i >> 1) * d + (j >> 1);     // B_(r,j)
-    return (float)synd[bit];
+    c[4] = (float)synd[bit];
   }
+}
+
+// Features 245 .. 255: one-hot direction, one-hot message length, 10 p, 1, 0.
+__device__ __forceinline__ float tail_feature(const MsgGeo& f, int q, float p10) {
   if (q < 245 + 4) return (q - 245 == f.dir) ? 1.f : 0.f;
   if (q < 249 + 4) return (q - 249 == f.h - 1) ? 1.f : 0.f;
   if (q == 253) return p10;
   if (q == 254) return 1.f;
   return 0.f;
+}
+
+// Feature q (0 .. 255) of the message; frame is the coset's W x W frame.
+__device__ __forceinline__ float message_feature(const Geo& g, const MsgGeo& f, int q, const uint8_t* frame,
+                                                 const uint8_t* synd, float p10) {
+  if (q < 5 * 49) {
+    float c[5];
+    window_node(g, f, q % 49, frame, synd, c);
+    const int ch = q / 49;
+    return ch == 0 ? c[0] : ch == 1 ? c[1] : ch == 2 ? c[2] : ch == 3 ? c[3] : c[4];
+  }
+  return tail_feature(f, q, p10);
 }
 
 }  // namespace warm
