@@ -93,3 +93,20 @@ def test_decode_null_pointers_rejected_before_any_cuda_call(L):
 def test_empty_batch_is_a_no_op(L):
     c = pkg.DecoderParams(d=5, k=3, D=4).c()
     assert L.bbp_decode_batch(None, 0, ctypes.byref(c), None, None, None, None, None, None, 0, None) == 0
+
+
+def test_warm_start_arguments_checked_on_the_host(L):
+    # Argument errors of the warm-start entry points are reported before any
+    # CUDA call; an empty batch is a no-op.
+    vp = ctypes.c_void_p
+    c = pkg.DecoderParams(d=11, k=4, precision="fp32", algorithm="fused").c()
+    big = vp(256)                                   # never dereferenced: every call below returns first
+    assert L.bbp_warm_infer_syndromes(None, big, 4, ctypes.byref(c), 0.1, big, big, 1 << 20, None) == -1
+    assert L.bbp_warm_infer_syndromes(big, big, 4, ctypes.byref(c), 1.5, big, big, 1 << 20, None) == -1
+    assert L.bbp_warm_infer_syndromes(big, big, 4, ctypes.byref(c), 0.1, big, big, 1024, None) == -3
+    assert L.bbp_warm_infer_syndromes(big, big, 0, ctypes.byref(c), 0.1, big, None, 0, None) == 0
+    c5 = pkg.DecoderParams(d=11, k=5, precision="fp32", algorithm="fused").c()
+    assert L.bbp_warm_infer_syndromes(big, big, 4, ctypes.byref(c5), 0.1, big, big, 1 << 20, None) == -1
+    assert L.bbp_warm_infer(big, big, big, 10, 0.1, big, big, _lib.WARM_INFER_WS_BYTES - 1, None) == -3
+    assert L.bbp_warm_infer(big, big, big, _lib.WARM_MAX_ROWS + 1, 0.1, big, big, 1 << 20, None) == -1
+    assert L.bbp_warm_infer(big, big, big, 0, 0.1, big, None, 0, None) == 0
