@@ -321,25 +321,34 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(MlpArgs a) {
         rows[tid] = rg;
       }
       __syncthreads();
-      // X: the features of rows r0 .. r0 + 127 (bbp_warm_features.cuh), in BF16.
-#pragma unroll 2
-      for (int task = tid; task < TM * (KD / 8); task += kThreads) {
-        const int row = task & (TM - 1), ch = task >> 7;
-        const long long gr = r0 + row;
-        uint4 pk = make_uint4(0u, 0u, 0u, 0u);
-        if (gr < N) {
+      // X: the features of rows r0 .. r0 + 127 (bbp_warm_features.cuh), in
+      // BF16: one window node of one row per task (its five channels), then
+      // the eleven tail features of each row.
+      __nv_bfloat16* xa = reinterpret_cast<__nv_bfloat16*>(sA);
+      for (int task = tid; task < TM * 49; task += kThreads) {
+        const int row = task & (TM - 1), pos = task >> 7;
+        float c[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        if (r0 + row < N) {
           const RowGeo rg = rows[row];
-          const uint8_t* pb = pair_base + rg.pair * pair_stride;
           MsgGeo f;
           f.r0 = rg.r0; f.r1 = rg.r1; f.c0 = rg.c0; f.c1 = rg.c1;
           f.dir = rg.dir; f.h = rg.h; f.ncols = rg.ncols;
-          float v[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) v[u] = message_feature(g, f, ch * 8 + u, pb + align_up(m, 16), pb, a.p10);
-          pk.x = pack_bf16(v[0], v[1]); pk.y = pack_bf16(v[2], v[3]);
-          pk.z = pack_bf16(v[4], v[5]); pk.w = pack_bf16(v[6], v[7]);
+          const uint8_t* pb = pair_base + rg.pair * pair_stride;
+          window_node(g, f, pos, pb + align_up(m, 16), pb, c);
         }
-        *reinterpret_cast<uint4*>(sA + core_off(row, ch * 8)) = pk;
+#pragma unroll
+        for (int ch = 0; ch < 5; ++ch) xa[core_off(row, ch * 49 + pos) / 2] = __float2bfloat16_rn(c[ch]);
+      }
+      for (int task = tid; task < TM * (KD - 245); task += kThreads) {
+        const int row = task & (TM - 1), q = 245 + (task >> 7);
+        float v = 0.f;
+        if (r0 + row < N) {
+          const RowGeo rg = rows[row];
+          MsgGeo f;
+          f.dir = rg.dir; f.h = rg.h;
+          v = tail_feature(f, q, a.p10);
+        }
+        xa[core_off(row, q) / 2] = __float2bfloat16_rn(v);
       }
     } else {
       // X: rows r0 .. r0 + 127 of the FP32 features, rounded to BF16 (one
