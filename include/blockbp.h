@@ -264,7 +264,7 @@ int bbp_warm_infer(const float* theta, const float* feats, const int32_t* lens, 
  * bbp_warm_infer.  Uses prm's d, k (<= 4) and p.  Workspace and status word
  * as bbp_warm_infer; BBP_EUNSUPPORTED if the geometry's tables do not fit
  * in shared memory next to the operand tiles.  It needs no features buffer
- * (1 KB per message) but takes about 1.5x the time of the two calls (d = 11:
+ * (1 KB per message) and takes about 1.1x the time of the two calls (d = 11:
  * the features are computed by the 8 warps of the one CTA per SM that the
  * operand tiles allow, between the tensor-core phases).
  */

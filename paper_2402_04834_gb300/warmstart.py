@@ -168,7 +168,7 @@ DEFAULT_ALPHA = 0.1     # blend weight of the proposal (measured: larger weights
 def decode_warm(syndromes, prm: DecoderParams, net: WarmStart, stream=None, out=None, alpha=DEFAULT_ALPHA):
     """Learned warm start: message features -> network on the tensor cores
     -> fused decode from its proposals.  (``WarmStart.infer_syndromes``
-    skips the features buffer, 1 KB per message, at about 1.5x the time.)"""
+    skips the features buffer, 1 KB per message, at about 1.1x the time.)"""
     feats, lens = features(syndromes, prm, stream)
     init = net.infer(feats, lens, stream=stream, alpha=alpha)
     return decode_ex(syndromes, prm, init_msgs=init, stream=stream, out=out)
