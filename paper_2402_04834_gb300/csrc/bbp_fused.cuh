@@ -519,79 +519,58 @@ __device__ __forceinline__ T read_dot(const T* x, const T* y, int n, int lane) {
 }
 
 // The per-message term 2 - 2 <x, y>^2 of Delta (Remark 4) for unit vectors
-// x (new) and y (old), summed over a group of lanes that hold one entry
-// each: part() is a lane's share, finish() the term from the group's sum.
+// x (new) and y (old), each held one entry per lane in a group of lanes.
 // FP64 evaluates it as written.  FP32 evaluates the same quantity as
 // s (2 - s / 2) with s = ||x - y||^2 (an identity for unit vectors): no
 // cancellation when a message barely moved, and no FP64 instruction per
 // update (FP64 issues at 1/64 of the FP32 rate here).
 template <typename T> struct DeltaTerm;
 template <> struct DeltaTerm<double> {
-  static __device__ __forceinline__ double part(double x, double y) { return x * y; }
-  static __device__ __forceinline__ double finish(double o) { return 2.0 - 2.0 * o * o; }
+  static __device__ __forceinline__ double eval(double x, double y, int width) {
+    const double o = group_sum(x * y, width);
+    return 2.0 - 2.0 * o * o;
+  }
 };
 template <> struct DeltaTerm<float> {
-  static __device__ __forceinline__ float part(float x, float y) {
+  static __device__ __forceinline__ float eval(float x, float y, int width) {
     const float t = x - y;
-    return t * t;
+    const float s = group_sum(t * t, width);
+    return s * (2.f - 0.5f * s);
   }
-  static __device__ __forceinline__ float finish(float s) { return s * (2.f - 0.5f * s); }
 };
 
-// Remark 3 then Remark 7 for one entry: the new vector x (with |x|^2 = a and
-// <x, y> = b over its group) normalised, damped with the stored unit vector
-// y, normalised again.  The damped vector's norm follows from the unit
-// norms: |(1 - eta) x/|x| + eta y|^2 = (1 - eta)^2 + eta^2 + 2 eta (1 - eta) <x/|x|, y>.
+// Unit L2 norm (Remark 3) of the vector held by a group of lanes.
 template <typename T>
-__device__ __forceinline__ T damp_unit(T x, T y, T a, T b, T eta, T one_m_eta) {
-  const T nx = xsqrt(a);
-  const T inv = nx > T(0) ? T(1) / nx : T(0);
-  const T ny2 = (nx > T(0) ? one_m_eta * one_m_eta : T(0)) + eta * eta + T(2) * eta * one_m_eta * (b * inv);
-  const T invy = ny2 > T(0) ? T(1) / xsqrt(ny2) : T(0);
-  return (one_m_eta * (x * inv) + eta * y) * invy;
+__device__ __forceinline__ T group_normalize(T v, int width) {
+  const T nrm = xsqrt(group_sum(v * v, width));
+  return v * (nrm > T(0) ? T(1) / nrm : T(0));
 }
 
 // After a sweep: normalise the new messages in ws.s0 (Remark 3), damp them
 // with the stored ones (Remark 7), normalise again, record each coset's
 // Delta term in ovl[coset * M + idx] and store the result.  Entry e of the
-// n x 2^h outgoing vectors sits in lane e % 32 (e < 64: G <= 4, h <= 4);
-// the two halves share every reduction step (two rounds in all).
+// n x 2^h outgoing vectors sits in lane e % 32 (e < 64: G <= 4, h <= 4).
 template <typename T>
 __device__ __forceinline__ void fused_update(const FusedWS<T>& ws, T* msgs, int stride, unsigned cos_of, int n,
                                              int idx, int h, T eta, T one_m_eta, double* ovl, int M, int lane) {
   const int width = 1 << h, tot = n << h;
-  const bool two = tot > 32;
-  const int e0 = lane, e1 = lane + 32;
-  const bool on0 = e0 < tot, on1 = two && e1 < tot;
-  const int q0 = on0 ? slot_coset(cos_of, e0 >> h) : 0;
-  const int q1 = on1 ? slot_coset(cos_of, e1 >> h) : 0;
-  T* o0 = msgs + q0 * stride + idx * kFusedVec + (e0 & (width - 1));
-  T* o1 = msgs + q1 * stride + idx * kFusedVec + (e1 & (width - 1));
-  const T x0 = on0 ? ws.s0[e0] : T(0), y0 = on0 ? *o0 : T(0);
-  const T x1 = on1 ? ws.s0[e1] : T(0), y1 = on1 ? *o1 : T(0);
-  T a0 = x0 * x0, b0 = x0 * y0, a1 = x1 * x1, b1 = x1 * y1;
-  for (int off = width >> 1; off > 0; off >>= 1) {
-    a0 += __shfl_xor_sync(kFull, a0, off);
-    b0 += __shfl_xor_sync(kFull, b0, off);
-    if (two) {
-      a1 += __shfl_xor_sync(kFull, a1, off);
-      b1 += __shfl_xor_sync(kFull, b1, off);
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    if (r == 1 && tot <= 32) break;
+    const int e = lane + 32 * r;
+    const bool on = e < tot;
+    const int q = on ? slot_coset(cos_of, e >> h) : 0;
+    T* old = msgs + q * stride + idx * kFusedVec + (e & (width - 1));
+    T x = on ? ws.s0[e] : T(0);
+    const T y = on ? *old : T(0);
+    x = group_normalize(x, width);
+    x = one_m_eta * x + eta * y;
+    x = group_normalize(x, width);
+    const T term = DeltaTerm<T>::eval(x, y, width);
+    if (on) {
+      *old = x;
+      if ((e & (width - 1)) == 0) ovl[q * M + idx] = (double)term;
     }
-  }
-  const T u0 = damp_unit(x0, y0, a0, b0, eta, one_m_eta);
-  const T u1 = damp_unit(x1, y1, a1, b1, eta, one_m_eta);
-  T t0 = DeltaTerm<T>::part(u0, y0), t1 = DeltaTerm<T>::part(u1, y1);
-  for (int off = width >> 1; off > 0; off >>= 1) {
-    t0 += __shfl_xor_sync(kFull, t0, off);
-    if (two) t1 += __shfl_xor_sync(kFull, t1, off);
-  }
-  if (on0) {
-    *o0 = u0;
-    if ((e0 & (width - 1)) == 0) ovl[q0 * M + idx] = (double)DeltaTerm<T>::finish(t0);
-  }
-  if (on1) {
-    *o1 = u1;
-    if ((e1 & (width - 1)) == 0) ovl[q1 * M + idx] = (double)DeltaTerm<T>::finish(t1);
   }
   __syncwarp();
 }
