@@ -91,13 +91,13 @@ extern "C" {
  *             tensors) and resident CTAs per SM of bbp_decode_mixed.  0 picks
  *             the fastest compiled shape whose shared memory fits; compiled
  *             (warps, cosets): FP32 (8,4) (8,2) (4,2) (4,4) (16,1) (8,1)
- *             (4,1), FP64 (4,2) (8,2) (8,1) (4,4); other requests give
- *             BBP_EUNSUPPORTED.
+ *             (4,1), FP64 (4,2) (8,2) (8,1) (4,4); for k = 5, 6: FP32 (4,1)
+ *             (2,1), FP64 (2,1); other requests give BBP_EUNSUPPORTED.
  *   algorithm BBP_ALG_MPS, or BBP_ALG_FUSED: every k x k block fused into one
  *             vertex with dense messages (Remark 9; the form the paper ran for
  *             k = 1, 2, 4).  Nothing is truncated, D and cutoff are unused,
  *             and the result equals BBP_ALG_MPS whenever that truncates
- *             nothing.  Needs k <= 4 and no workspace.
+ *             nothing.  Needs k <= 6 and no workspace.
  */
 typedef struct bbp_params {
   int32_t d;
@@ -111,7 +111,7 @@ typedef struct bbp_params {
   double cutoff;
   int32_t precision;
   int32_t algorithm;
-  int32_t launch_warps;        /* fused path: warps per CTA (4, 8, 16), 0 = default */
+  int32_t launch_warps;        /* fused path: warps per CTA (2, 4, 8, 16), 0 = default */
   int32_t launch_ctas_per_sm;  /* bbp_decode_mixed: resident CTAs per SM, 0 = the occupancy limit */
   int32_t launch_cosets;       /* fused path: cosets per CTA (1, 2, 4), 0 = default */
 } bbp_params;
@@ -288,7 +288,8 @@ int bbp_warm_train_step(float* theta, float* adam_m, float* adam_v, int32_t step
  * optional initial messages init_msgs [B][4][M][16] (renormalised; an
  * all-zero message falls back to uniform) and optional export of the
  * messages after the BP loop into final_msgs [B][4][M][16] (float).
- * Errors as bbp_decode_batch; BBP_EINVAL for the MPS algorithm.
+ * Errors as bbp_decode_batch; BBP_EINVAL for the MPS algorithm, and for
+ * k > 4 when messages are given or asked for.
  */
 int bbp_decode_batch_ex(const uint8_t* syndromes, int64_t B, const bbp_params* prm, const float* init_msgs,
                         float* final_msgs, double* logp, double* delta, int32_t* iters, int32_t* flags,

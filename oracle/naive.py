@@ -23,39 +23,47 @@ from .blockbp import DIRS, OPPOSITE, STEP, ranges
 
 
 def fuse_block(T, rows, cols):
-    """Contract the nodes of one block; returns F[left, right, top, bottom]."""
+    """Contract the nodes of one block; returns F[left, right, top, bottom].
+
+    Contracted one row at a time (each row's chain first, then the row onto
+    the block through its vertical legs), so that no single contraction
+    names more labels than numpy's einsum allows (k = 6 blocks have 84
+    internal bonds)."""
     r0, r1 = rows
     c0, c1 = cols
-    label = {}
-    nxt = [0]
-
-    def lab(key):
-        if key not in label:
-            label[key] = nxt[0]
-            nxt[0] += 1
-        return label[key]
-
-    ops = []
+    w = c1 - c0
+    letters = "abcdefghijklmnopqrstuvwxyzABCDEFGHIJKLMNOPQRSTUVWXYZ"
+    blk = None
+    nL = 0                                  # left / right legs collected so far
     for i in range(r0, r1):
-        for j in range(c0, c1):
-            l = lab(("h", i, j - 1))       # edge between (i, j-1) and (i, j)
-            r = lab(("h", i, j))
-            u = lab(("v", i - 1, j))       # edge between (i-1, j) and (i, j)
-            dn = lab(("v", i, j))
-            ops += [T[i][j], [l, r, u, dn]]
-    out_left = [label[("h", i, c0 - 1)] for i in range(r0, r1)]
-    out_right = [label[("h", i, c1 - 1)] for i in range(r0, r1)]
-    out_top = [label[("v", r0 - 1, j)] for j in range(c0, c1)]
-    out_bot = [label[("v", r1 - 1, j)] for j in range(c0, c1)]
-    out = out_left + out_right + out_top + out_bot
-    F = np.einsum(*ops, out, optimize="greedy")
-    dl = int(np.prod(F.shape[:len(out_left)]))
-    o = len(out_left)
-    dr = int(np.prod(F.shape[o:o + len(out_right)]))
-    o += len(out_right)
-    dt = int(np.prod(F.shape[o:o + len(out_top)]))
-    db = int(np.prod(F.shape[o + len(out_top):]))
-    return F.reshape(dl, dr, dt, db)
+        # The row as one tensor: axes l, r, u_0 .. u_{w-1}, d_0 .. d_{w-1}.
+        row = T[i][c0]
+        for j in range(1, w):
+            u_prev = letters[2:2 + j]
+            d_prev = letters[2 + j:2 + 2 * j]
+            lhs = "a" + "Y" + u_prev + d_prev            # Y: the bond between nodes j-1 and j
+            rhs = "Yb" + "X" + "Z"                          # node (l=Y, r=b, u=X, d=Z)
+            out = "ab" + u_prev + "X" + d_prev + "Z"
+            row = np.einsum(f"{lhs},{rhs}->{out}", row, T[i][c0 + j])
+        if blk is None:
+            blk = row
+            nL = 1
+            continue
+        # blk axes: L_0..L_{nL-1}, R_0..R_{nL-1}, top_0..top_{w-1}, bot_0..bot_{w-1}
+        L = letters[0:nL]
+        R = letters[nL:2 * nL]
+        top = letters[2 * nL:2 * nL + w]
+        bot = letters[2 * nL + w:2 * nL + 2 * w]          # contracted with the row's u legs
+        l2, r2 = letters[2 * nL + 2 * w], letters[2 * nL + 2 * w + 1]
+        d2 = letters[2 * nL + 2 * w + 2:2 * nL + 3 * w + 2]
+        blk = np.einsum(f"{L}{R}{top}{bot},{l2}{r2}{bot}{d2}->{L}{l2}{R}{r2}{top}{d2}", blk, row)
+        nL += 1
+    sh = blk.shape
+    dl = int(np.prod(sh[:nL]))
+    dr = int(np.prod(sh[nL:2 * nL]))
+    dt = int(np.prod(sh[2 * nL:2 * nL + w]))
+    db = int(np.prod(sh[2 * nL + w:]))
+    return blk.reshape(dl, dr, dt, db)
 
 
 def run_naive(tensors, k, max_iter, eta, delta0, k_cols=None, init=None):

@@ -29,6 +29,8 @@ WARM_INFER_WS_BYTES = 270592      # workspace of bbp_warm_infer, for any N
 # Compiled launch shapes (warps per CTA, cosets per CTA) of the fused kernel.
 FUSED_SHAPES = {"fp32": ((8, 4), (8, 2), (4, 2), (4, 4), (16, 1), (8, 1), (4, 1)),
                 "fp64": ((4, 2), (8, 2), (8, 1), (4, 4))}
+# ... and for block sides 5 and 6 (one coset per CTA).
+FUSED_SHAPES_K6 = {"fp32": ((4, 1), (2, 1)), "fp64": ((2, 1),)}
 BBP_ETOOLARGE = -5
 STATIC_WORKSPACE_BYTES = 32 << 20
 
@@ -55,7 +57,7 @@ class DecoderParams:
     delta1: float = 1e-2
     cutoff: float | None = None
     precision: str = "fp64"
-    algorithm: str = "mps"          # "mps" (Sec. III.D) or "fused" (Remark 9, k <= 4)
+    algorithm: str = "mps"          # "mps" (Sec. III.D) or "fused" (Remark 9, k <= 6)
     warps: int = 0                  # fused launch shape (tuning only): warps per CTA
     ctas_per_sm: int = 0            # persistent mixed launch: resident CTAs per SM (0 = occupancy)
     cosets: int = 0                 # fused launch shape (tuning only): cosets per CTA (1, 2, 4)

@@ -13,7 +13,7 @@ import dataclasses
 
 import torch
 
-from ._lib import FUSED_SHAPES, BbpError, DecoderParams
+from ._lib import FUSED_SHAPES, FUSED_SHAPES_K6, BbpError, DecoderParams
 from .decoder import decode, decode_mixed
 
 _cache: dict = {}
@@ -35,7 +35,7 @@ def _time(fn, reps=3):
 
 def tune_uniform(syndromes, prm: DecoderParams, shapes=None):
     """Best (warps, cosets) per CTA for a same-distance batch; returns (params, table)."""
-    shapes = tuple(shapes or FUSED_SHAPES[prm.precision])
+    shapes = tuple(shapes or (FUSED_SHAPES_K6 if prm.k > 4 else FUSED_SHAPES)[prm.precision])
     key = ("uniform", prm.d, prm.k, prm.precision, prm.max_iter, shapes)
     if key in _cache:
         return dataclasses.replace(prm, **_cache[key][0]), _cache[key][1]
@@ -54,7 +54,7 @@ def tune_uniform(syndromes, prm: DecoderParams, shapes=None):
 
 def tune_mixed(packed, offsets, d_of, prm: DecoderParams, shapes=None, ctas=(0, 1, 2, 3, 4)):
     """Best (warps, cosets, resident CTAs per SM) for a mixed batch; returns (params, table)."""
-    shapes = tuple(shapes or FUSED_SHAPES[prm.precision])
+    shapes = tuple(shapes or (FUSED_SHAPES_K6 if prm.k > 4 else FUSED_SHAPES)[prm.precision])
     sig = tuple(sorted(torch.unique(d_of).tolist()))
     key = ("mixed", sig, prm.k, prm.precision, prm.max_iter, shapes, tuple(ctas))
     if key in _cache:

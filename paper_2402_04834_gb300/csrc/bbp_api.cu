@@ -31,7 +31,8 @@ int check_params(const bbp_params* p) {
   if (p->precision != BBP_FP64 && p->precision != BBP_FP32) return BBP_EINVAL;
   if (p->algorithm != BBP_ALG_MPS && p->algorithm != BBP_ALG_FUSED) return BBP_EINVAL;
   if (p->algorithm == BBP_ALG_MPS && (p->k > bbp::kMaxK || p->D > bbp::kMaxD)) return BBP_EUNSUPPORTED;
-  if (p->launch_warps != 0 && p->launch_warps != 4 && p->launch_warps != 8 && p->launch_warps != 16)
+  if (p->launch_warps != 0 && p->launch_warps != 2 && p->launch_warps != 4 && p->launch_warps != 8 &&
+      p->launch_warps != 16)
     return BBP_EINVAL;
   if (p->launch_cosets != 0 && p->launch_cosets != 1 && p->launch_cosets != 2 && p->launch_cosets != 4)
     return BBP_EINVAL;
@@ -115,7 +116,7 @@ int bbp_decode_batch_ex(const uint8_t* syndromes, int64_t B, const bbp_params* p
   a.p = prm->p; a.eta = prm->eta; a.delta0 = prm->delta0; a.delta1 = prm->delta1; a.cutoff = prm->cutoff;
   a.synd = syndromes; a.arena = workspace; a.logp = logp; a.delta = delta; a.iters = iters;
   a.flags = flags; a.decision = decision; a.B = B;
-  if ((init_msgs || final_msgs) && prm->algorithm != BBP_ALG_FUSED) return BBP_EINVAL;
+  if ((init_msgs || final_msgs) && (prm->algorithm != BBP_ALG_FUSED || prm->k > 4)) return BBP_EINVAL;
   a.init_msgs = init_msgs; a.final_msgs = final_msgs;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;

@@ -29,9 +29,9 @@ cudaError_t launch_decode_t(const LaunchArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, int K>
 int fused_smem_for(const Geo& g, int M, int warps, int cosets) {
-  return fused_layout<T>(g, M, warps, cosets).total;
+  return fused_layout<T, K>(g, M, warps, cosets).total;
 }
 
 template <typename T>
@@ -45,11 +45,11 @@ KArgs<T> fused_args(const LaunchArgs& a) {
   return k;
 }
 
-template <typename T, int NW, int G>
+template <typename T, int NW, int G, int K>
 cudaError_t launch_fused_nw(const LaunchArgs& a, cudaStream_t st) {
   const KArgs<T> k = fused_args<T>(a);
-  const int smem = fused_smem_for<T>(a.geo, a.M, NW, G);
-  auto kern = fused_kernel<T, NW, G>;
+  const int smem = fused_smem_for<T, K>(a.geo, a.M, NW, G);
+  auto kern = fused_kernel<T, NW, G, K>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)(a.B * (4 / G));
@@ -57,14 +57,14 @@ cudaError_t launch_fused_nw(const LaunchArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <typename T, int NW, int G>
+template <typename T, int NW, int G, int K>
 cudaError_t launch_fused_mixed_nw(const LaunchArgs& a, const MixedLaunch& m, cudaStream_t st) {
   const KArgs<T> k = fused_args<T>(a);
   const Geo gmax = make_geo(m.d_max, a.geo.k);
   int Mmax = 0, ae = 0;
   count_messages(gmax, 1, &Mmax, &ae);
-  const int smem = fused_smem_for<T>(gmax, Mmax, NW, G);
-  auto kern = fused_mixed_kernel<T, NW, G>;
+  const int smem = fused_smem_for<T, K>(gmax, Mmax, NW, G);
+  auto kern = fused_mixed_kernel<T, NW, G, K>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   int per_sm = m.ctas_per_sm;

@@ -31,38 +31,43 @@
 
 namespace bbp {
 
-constexpr int kFusedK = 4;                 // largest block side of the fused path
-constexpr int kFusedVec = 1 << kFusedK;    // dense message length
-// Largest state of one coset: with k <= 4 the side-message bits a and b
-// together never exceed 3 at a node pass nor 4 at a side step, so
-// a + rows + b + v <= 8 bits.
-constexpr int kFusedSlot = 256;
+constexpr int kFusedK = 4;                 // block side of the learned warm start's messages
+constexpr int kFusedVec = 1 << kFusedK;    // their dense length
 constexpr int kFusedMaxG = 4;              // cosets per CTA
+
+// Sizes of the kernels compiled for block sides up to K (K = 4 or 6): dense
+// messages of 2^K entries and a per-coset state of at most 2^(2K) entries
+// (a block with h rows and nc columns never holds more than h + nc bits:
+// a and b together carry at most nc).
+template <int K> struct FusedDim {
+  static constexpr int vec = 1 << K;
+  static constexpr int slot = 1 << (2 * K);
+};
 
 // Per-warp scratch for G cosets, carved from shared memory.
 template <typename T>
-struct FusedWS {
-  T* s0;   // state, G * kFusedSlot
-  T* s1;   // state, G * kFusedSlot
+struct FusedWS {   // (sizes for block side K: slot = FusedDim<K>::slot, vec = FusedDim<K>::vec)
+  T* s0;   // state, G * slot
+  T* s1;   // state, G * slot
   T* wn;   // node tensors, 16 per coset
-  T* mt;   // side message A in consumption order, kFusedVec per coset
-  T* mb;   // side message B in consumption order, kFusedVec per coset
+  T* mt;   // side message A in consumption order, vec per coset
+  T* mb;   // side message B in consumption order, vec per coset
 };
 
-template <typename T>
+template <typename T, int K>
 BBP_HD int fused_ws_bytes(int G) {
-  return align_up((int)sizeof(T) * G * (2 * kFusedSlot + 16 + 2 * kFusedVec), 16);
+  return align_up((int)sizeof(T) * G * (2 * FusedDim<K>::slot + 16 + 2 * FusedDim<K>::vec), 16);
 }
 
-template <typename T>
+template <typename T, int K>
 __device__ __forceinline__ FusedWS<T> fused_ws_at(unsigned char* base, int G) {
   FusedWS<T> w;
   T* p = reinterpret_cast<T*>(base);
   w.s0 = p;
-  w.s1 = p + G * kFusedSlot;
-  w.wn = p + 2 * G * kFusedSlot;
+  w.s1 = p + G * FusedDim<K>::slot;
+  w.wn = p + 2 * G * FusedDim<K>::slot;
   w.mt = w.wn + 16 * G;
-  w.mb = w.mt + kFusedVec * G;
+  w.mb = w.mt + FusedDim<K>::vec * G;
   return w;
 }
 
@@ -71,7 +76,7 @@ struct FusedLayout {
   int synd, frame, msg_of, meta, work, ovl, rlog, misc, msgs, ws, ws_stride, total;
 };
 
-template <typename T>
+template <typename T, int K>
 BBP_HD FusedLayout fused_layout(const Geo& g, int M, int nwarps, int G) {
   FusedLayout L;
   const int m = 2 * g.d * (g.d - 1);
@@ -84,9 +89,9 @@ BBP_HD FusedLayout fused_layout(const Geo& g, int M, int nwarps, int G) {
   L.ovl = o;    o = align_up(o + 8 * G * M, 16);
   L.rlog = o;   o = align_up(o + 8 * G * (g.nb * g.nb + M), 16);
   L.misc = o;   o = align_up(o + 128, 16);
-  L.msgs = o;   o = align_up(o + (int)sizeof(T) * kFusedVec * G * M, 16);
+  L.msgs = o;   o = align_up(o + (int)sizeof(T) * FusedDim<K>::vec * G * M, 16);
   L.ws = o;
-  L.ws_stride = fused_ws_bytes<T>(G);
+  L.ws_stride = fused_ws_bytes<T, K>(G);
   o = align_up(o + nwarps * L.ws_stride, 16);
   L.total = o;
   return L;
@@ -167,15 +172,15 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
   for (int e = lane; e < (n << h); e += 32) {
     const int H = e & ((1 << h) - 1);
     const T* ms = msgs + slot_coset(cos_of, e >> h) * stride;
-    cur[e] = f.in_idx >= 0 ? ms[f.in_idx * kFusedVec + H] : (H == 0 ? T(1) : T(0));
+    cur[e] = f.in_idx >= 0 ? ms[f.in_idx * FusedDim<K>::vec + H] : (H == 0 ? T(1) : T(0));
   }
   // Side messages in consumption order.
   for (int e = lane; e < (n << nc); e += 32) {
     const int i = e & ((1 << nc) - 1);
     const int j = f.rev ? bitrev(i, nc) : i;
     const T* ms = msgs + slot_coset(cos_of, e >> nc) * stride;
-    ws.mt[e] = f.a_idx >= 0 ? ms[f.a_idx * kFusedVec + j] : T(0);
-    ws.mb[e] = f.b_idx >= 0 ? ms[f.b_idx * kFusedVec + j] : T(0);
+    ws.mt[e] = f.a_idx >= 0 ? ms[f.a_idx * FusedDim<K>::vec + j] : T(0);
+    ws.mb[e] = f.b_idx >= 0 ? ms[f.b_idx * FusedDim<K>::vec + j] : T(0);
   }
   __syncwarp();
   FState st{0, h, 0, 0};
@@ -512,10 +517,12 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
   }
 }
 
-// <x, y> over n <= 32 entries for the read-out, in the working precision.
+// <x, y> over n <= 64 entries for the read-out, in the working precision.
 template <typename T>
 __device__ __forceinline__ T read_dot(const T* x, const T* y, int n, int lane) {
-  return warp_sum(lane < n ? x[lane] * y[lane] : T(0));
+  T acc = lane < n ? x[lane] * y[lane] : T(0);
+  if (n > 32 && lane + 32 < n) acc += x[lane + 32] * y[lane + 32];
+  return warp_sum(acc);
 }
 
 // The per-message term 2 - 2 <x, y>^2 of Delta (Remark 4) for unit vectors
@@ -549,8 +556,9 @@ __device__ __forceinline__ T group_normalize(T v, int width) {
 // After a sweep: normalise the new messages in ws.s0 (Remark 3), damp them
 // with the stored ones (Remark 7), normalise again, record each coset's
 // Delta term in ovl[coset * M + idx] and store the result.  Entry e of the
-// n x 2^h outgoing vectors sits in lane e % 32 (e < 64: G <= 4, h <= 4).
-template <typename T>
+// n x 2^h outgoing vectors sits in lane e % 32 (e < 64: G <= 4, h <= 4 or
+// G = 1, h <= 6).
+template <typename T, int K>
 __device__ __forceinline__ void fused_update(const FusedWS<T>& ws, T* msgs, int stride, unsigned cos_of, int n,
                                              int idx, int h, T eta, T one_m_eta, double* ovl, int M, int lane) {
   const int width = 1 << h, tot = n << h;
@@ -560,7 +568,7 @@ __device__ __forceinline__ void fused_update(const FusedWS<T>& ws, T* msgs, int 
     const int e = lane + 32 * r;
     const bool on = e < tot;
     const int q = on ? slot_coset(cos_of, e >> h) : 0;
-    T* old = msgs + q * stride + idx * kFusedVec + (e & (width - 1));
+    T* old = msgs + q * stride + idx * FusedDim<K>::vec + (e & (width - 1));
     T x = on ? ws.s0[e] : T(0);
     const T y = on ? *old : T(0);
     x = group_normalize(x, width);
@@ -577,20 +585,23 @@ __device__ __forceinline__ void fused_update(const FusedWS<T>& ws, T* msgs, int 
 
 // Resident CTAs per SM the register budget is sized for: with one coset per
 // CTA, 32 warps per SM in FP32 (64 registers a thread) and 16 in FP64; with
-// more cosets per CTA shared memory allows half as many.
-template <typename T, int NW, int G> struct FusedMinBlocks {
-  static constexpr int warps = (sizeof(T) == 4 ? 32 : 16) / (G > 1 ? 2 : 1);
+// more cosets per CTA shared memory allows half as many; with k = 6 states
+// (16 KB a coset) one CTA.
+template <typename T, int NW, int G, int K> struct FusedMinBlocks {
+  static constexpr int warps = K > 4 ? NW : (sizeof(T) == 4 ? 32 : 16) / (G > 1 ? 2 : 1);
   static constexpr int value = warps / NW > 1 ? warps / NW : 1;
 };
 
 // Cosets c0 .. c0 + G - 1 of one syndrome decoded by the whole CTA: syn_src
 // holds the syndrome's m bytes and outputs go to row syn * 4 + coset.
-template <typename T, int NW, int G>
+template <typename T, int NW, int G, int K>
 __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const int M, const uint8_t* syn_src,
                                            const long long syn, const int c0, unsigned char* smem) {
   const int W = g.W, d = g.d, nb = g.nb, WW = W * W;
   const int m = 2 * d * (d - 1);
-  const FusedLayout Lo = fused_layout<T>(g, M, NW, G);
+  static_assert(K <= 4 || G == 1, "k = 6 states hold one coset per CTA");
+  constexpr int VEC = FusedDim<K>::vec;
+  const FusedLayout Lo = fused_layout<T, K>(g, M, NW, G);
   uint8_t* synd = smem + Lo.synd;
   uint8_t* frames = smem + Lo.frame;
   int16_t* msg_of = reinterpret_cast<int16_t*>(smem + Lo.msg_of);
@@ -601,10 +612,10 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
   int* misc = reinterpret_cast<int*>(smem + Lo.misc);      // [0] counter, [2..4] list sizes, [8 + q] flags
   double* dsh = reinterpret_cast<double*>(smem + Lo.misc + 64);
   T* msgs = reinterpret_cast<T*>(smem + Lo.msgs);
-  const int stride = M * kFusedVec;                          // messages of one coset
+  const int stride = M * VEC;                                // messages of one coset
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const FusedWS<T> ws = fused_ws_at<T>(smem + Lo.ws + warp * Lo.ws_stride, G);
+  const FusedWS<T> ws = fused_ws_at<T, K>(smem + Lo.ws + warp * Lo.ws_stride, G);
 
   for (int i = tid; i < m; i += NW * 32) synd[i] = syn_src[i];
   __syncthreads();
@@ -646,7 +657,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
   }
   __syncthreads();
 
-  Ctx<T, kFusedK> c;
+  Ctx<T, K> c;
   c.g = g; c.D = 0; c.cutoff2 = T(0);
   c.pI = (T)(1.0 - a.p); c.pE = (T)(a.p / 3.0);
   c.frame = frames; c.msg_of = msg_of; c.msg_off = nullptr; c.dims = nullptr;
@@ -658,18 +669,18 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
     const int q = qi / M, idx = qi - q * M;
     const int key = meta[idx];
     const int w = g.side_len(key / 4 / nb, (key / 4) % nb, key & 3);
-    T* x = msgs + q * stride + idx * kFusedVec;
+    T* x = msgs + q * stride + idx * VEC;
     bool uniform = true;
-    if (a.init_msgs) {
-      const float* src = a.init_msgs + ((syn * 4 + c0 + q) * M + idx) * kFusedVec;
+    if (K <= 4 && a.init_msgs) {                    // proposals exist for k <= 4
+      const float* src = a.init_msgs + ((syn * 4 + c0 + q) * M + idx) * VEC;
       const T v = lane < (1 << w) ? (T)src[lane] : T(0);
       const T nrm = xsqrt(group_sum(v * v, 32));
       uniform = !(nrm > T(0));
-      if (!uniform && lane < kFusedVec) x[lane] = v * (T(1) / nrm);
+      if (!uniform && lane < VEC) x[lane] = v * (T(1) / nrm);
     }
     if (uniform) {                                   // no (or an unusable) proposal
       const T u = (T)rsqrt((double)(1 << w));
-      if (lane < kFusedVec) x[lane] = lane < (1 << w) ? u : T(0);
+      for (int i = lane; i < VEC; i += 32) x[i] = i < (1 << w) ? u : T(0);
     }
   }
   __syncthreads();
@@ -700,7 +711,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
         const int I = key / 4 / nb, J = (key / 4) % nb, dir = key & 3;
         const Frame f = make_frame(c, I, J, dir);
         fused_sweep(ws, c, msgs, stride, cos_of, n, frames, f, (LogAcc<T>*)nullptr, lane);
-        fused_update(ws, msgs, stride, cos_of, n, idx, f.h, eta, one_m_eta, ovl, M, lane);
+        fused_update<T, K>(ws, msgs, stride, cos_of, n, idx, f.h, eta, one_m_eta, ovl, M, lane);
       }
       __syncthreads();
       if (tid == 0) misc[0] = 0;
@@ -758,7 +769,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
 #pragma unroll
       for (int q = 0; q < G; ++q) {
         const T* mq = msgs + q * stride;
-        const T z = right >= 0 ? read_dot(ws.s0 + (q << f.h), mq + right * kFusedVec, 1 << f.h, lane)
+        const T z = right >= 0 ? read_dot(ws.s0 + (q << f.h), mq + right * VEC, 1 << f.h, lane)
                                : ws.s0[q << f.h];
         if (lane == 0) {
           ls[q].mul(z < T(0) ? -z : z);
@@ -776,7 +787,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
 #pragma unroll
       for (int q = 0; q < G; ++q) {
         const T* mq = msgs + q * stride;
-        const T o = read_dot(mq + idx * kFusedVec, mq + other * kFusedVec, 1 << w, lane);
+        const T o = read_dot(mq + idx * VEC, mq + other * VEC, 1 << w, lane);
         if (lane == 0) {
           rlog[q * per + item] = -log(fabs((double)o));
           if (!(o > T(0))) atomicOr(&misc[8 + q], kFlagOverlap);
@@ -808,14 +819,14 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
 }
 
 // One CTA per (syndrome, group of G cosets).
-template <typename T, int NW, int G>
-__global__ void __launch_bounds__(NW * 32, (FusedMinBlocks<T, NW, G>::value)) fused_kernel(KArgs<T> a) {
+template <typename T, int NW, int G, int K>
+__global__ void __launch_bounds__(NW * 32, (FusedMinBlocks<T, NW, G, K>::value)) fused_kernel(KArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NG = 4 / G;
   const long long syn = blockIdx.x / NG;
   const int c0 = (int)(blockIdx.x % NG) * G;
   const int m = 2 * a.geo.d * (a.geo.d - 1);
-  fused_item<T, NW, G>(a, a.geo, a.M, a.synd + syn * m, syn, c0, smem);
+  fused_item<T, NW, G, K>(a, a.geo, a.M, a.synd + syn * m, syn, c0, smem);
 }
 
 // A batch of syndromes of different distances in one persistent launch: CTAs
@@ -830,8 +841,8 @@ struct MixedArgs {
   int k;
 };
 
-template <typename T, int NW, int G>
-__global__ void __launch_bounds__(NW * 32, (FusedMinBlocks<T, NW, G>::value))
+template <typename T, int NW, int G, int K>
+__global__ void __launch_bounds__(NW * 32, (FusedMinBlocks<T, NW, G, K>::value))
     fused_mixed_kernel(KArgs<T> a, MixedArgs mx) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long item_sh;
@@ -847,7 +858,7 @@ __global__ void __launch_bounds__(NW * 32, (FusedMinBlocks<T, NW, G>::value))
     const Geo g = make_geo(mx.d_of[shot], mx.k);
     int M = 0, ae = 0;
     count_messages(g, 1, &M, &ae);
-    fused_item<T, NW, G>(a, g, M, a.synd + mx.offsets[shot], shot, c0, smem);
+    fused_item<T, NW, G, K>(a, g, M, a.synd + mx.offsets[shot], shot, c0, smem);
     __syncthreads();
   }
 }

@@ -5,28 +5,42 @@
 namespace bbp {
 
 cudaError_t launch_fused_f32(const LaunchArgs& a, int warps, int cosets, cudaStream_t st) {
+  if (a.geo.k > 4) {                       // block sides 5 and 6
+    switch (warps * 10 + cosets) {
+      case 21: return launch_fused_nw<float, 2, 1, 6>(a, st);
+      case 41: return launch_fused_nw<float, 4, 1, 6>(a, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (warps * 10 + cosets) {
-    case 41: return launch_fused_nw<float, 4, 1>(a, st);
-    case 81: return launch_fused_nw<float, 8, 1>(a, st);
-    case 161: return launch_fused_nw<float, 16, 1>(a, st);
-    case 42: return launch_fused_nw<float, 4, 2>(a, st);
-    case 82: return launch_fused_nw<float, 8, 2>(a, st);
-    case 44: return launch_fused_nw<float, 4, 4>(a, st);
-    case 84: return launch_fused_nw<float, 8, 4>(a, st);
+    case 41: return launch_fused_nw<float, 4, 1, 4>(a, st);
+    case 81: return launch_fused_nw<float, 8, 1, 4>(a, st);
+    case 161: return launch_fused_nw<float, 16, 1, 4>(a, st);
+    case 42: return launch_fused_nw<float, 4, 2, 4>(a, st);
+    case 82: return launch_fused_nw<float, 8, 2, 4>(a, st);
+    case 44: return launch_fused_nw<float, 4, 4, 4>(a, st);
+    case 84: return launch_fused_nw<float, 8, 4, 4>(a, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_fused_mixed_f32(const LaunchArgs& a, const MixedLaunch& m, int warps, int cosets,
                                    cudaStream_t st) {
+  if (a.geo.k > 4) {
+    switch (warps * 10 + cosets) {
+      case 21: return launch_fused_mixed_nw<float, 2, 1, 6>(a, m, st);
+      case 41: return launch_fused_mixed_nw<float, 4, 1, 6>(a, m, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (warps * 10 + cosets) {
-    case 41: return launch_fused_mixed_nw<float, 4, 1>(a, m, st);
-    case 81: return launch_fused_mixed_nw<float, 8, 1>(a, m, st);
-    case 161: return launch_fused_mixed_nw<float, 16, 1>(a, m, st);
-    case 42: return launch_fused_mixed_nw<float, 4, 2>(a, m, st);
-    case 82: return launch_fused_mixed_nw<float, 8, 2>(a, m, st);
-    case 44: return launch_fused_mixed_nw<float, 4, 4>(a, m, st);
-    case 84: return launch_fused_mixed_nw<float, 8, 4>(a, m, st);
+    case 41: return launch_fused_mixed_nw<float, 4, 1, 4>(a, m, st);
+    case 81: return launch_fused_mixed_nw<float, 8, 1, 4>(a, m, st);
+    case 161: return launch_fused_mixed_nw<float, 16, 1, 4>(a, m, st);
+    case 42: return launch_fused_mixed_nw<float, 4, 2, 4>(a, m, st);
+    case 82: return launch_fused_mixed_nw<float, 8, 2, 4>(a, m, st);
+    case 44: return launch_fused_mixed_nw<float, 4, 4, 4>(a, m, st);
+    case 84: return launch_fused_mixed_nw<float, 8, 4, 4>(a, m, st);
     default: return cudaErrorInvalidValue;
   }
 }

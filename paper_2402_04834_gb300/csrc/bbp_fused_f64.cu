@@ -5,22 +5,25 @@
 namespace bbp {
 
 cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, int cosets, cudaStream_t st) {
+  if (a.geo.k > 4) return warps * 10 + cosets == 21 ? launch_fused_nw<double, 2, 1, 6>(a, st) : cudaErrorInvalidValue;
   switch (warps * 10 + cosets) {
-    case 81: return launch_fused_nw<double, 8, 1>(a, st);
-    case 42: return launch_fused_nw<double, 4, 2>(a, st);
-    case 82: return launch_fused_nw<double, 8, 2>(a, st);
-    case 44: return launch_fused_nw<double, 4, 4>(a, st);
+    case 81: return launch_fused_nw<double, 8, 1, 4>(a, st);
+    case 42: return launch_fused_nw<double, 4, 2, 4>(a, st);
+    case 82: return launch_fused_nw<double, 8, 2, 4>(a, st);
+    case 44: return launch_fused_nw<double, 4, 4, 4>(a, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_fused_mixed_f64(const LaunchArgs& a, const MixedLaunch& m, int warps, int cosets,
                                    cudaStream_t st) {
+  if (a.geo.k > 4)
+    return warps * 10 + cosets == 21 ? launch_fused_mixed_nw<double, 2, 1, 6>(a, m, st) : cudaErrorInvalidValue;
   switch (warps * 10 + cosets) {
-    case 81: return launch_fused_mixed_nw<double, 8, 1>(a, m, st);
-    case 42: return launch_fused_mixed_nw<double, 4, 2>(a, m, st);
-    case 82: return launch_fused_mixed_nw<double, 8, 2>(a, m, st);
-    case 44: return launch_fused_mixed_nw<double, 4, 4>(a, m, st);
+    case 81: return launch_fused_mixed_nw<double, 8, 1, 4>(a, m, st);
+    case 42: return launch_fused_mixed_nw<double, 4, 2, 4>(a, m, st);
+    case 82: return launch_fused_mixed_nw<double, 8, 2, 4>(a, m, st);
+    case 44: return launch_fused_mixed_nw<double, 4, 4, 4>(a, m, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -39,15 +42,23 @@ struct Shape {
 constexpr Shape kShapesF32[] = {{8, 4}, {8, 2}, {4, 2}, {4, 4}, {16, 1}, {8, 1}, {4, 1}};
 constexpr Shape kShapesF64[] = {{4, 2}, {8, 2}, {8, 1}, {4, 4}};
 
+// Block sides 5 and 6: states of 2^12 entries, one coset per CTA.
+constexpr Shape kShapesF32K6[] = {{4, 1}, {2, 1}};
+constexpr Shape kShapesF64K6[] = {{2, 1}};
+
 }  // namespace
 
 int fused_smem_bytes(int precision, const Geo& g, int M, int warps, int cosets) {
-  return precision == 0 ? fused_smem_for<double>(g, M, warps, cosets) : fused_smem_for<float>(g, M, warps, cosets);
+  if (g.k > 4)
+    return precision == 0 ? fused_smem_for<double, 6>(g, M, warps, cosets) : fused_smem_for<float, 6>(g, M, warps, cosets);
+  return precision == 0 ? fused_smem_for<double, 4>(g, M, warps, cosets) : fused_smem_for<float, 4>(g, M, warps, cosets);
 }
 
 bool fused_shape(int precision, const Geo& g, int M, int* warps, int* cosets) {
-  const Shape* sh = precision == 0 ? kShapesF64 : kShapesF32;
-  const int n = precision == 0 ? (int)(sizeof(kShapesF64) / sizeof(Shape)) : (int)(sizeof(kShapesF32) / sizeof(Shape));
+  const bool k6 = g.k > 4;
+  const Shape* sh = k6 ? (precision == 0 ? kShapesF64K6 : kShapesF32K6) : (precision == 0 ? kShapesF64 : kShapesF32);
+  const int n = k6 ? (precision == 0 ? (int)(sizeof(kShapesF64K6) / sizeof(Shape)) : (int)(sizeof(kShapesF32K6) / sizeof(Shape)))
+                   : (precision == 0 ? (int)(sizeof(kShapesF64) / sizeof(Shape)) : (int)(sizeof(kShapesF32) / sizeof(Shape)));
   for (int i = 0; i < n; ++i) {
     if (*warps != 0 && sh[i].warps != *warps) continue;
     if (*cosets != 0 && sh[i].cosets != *cosets) continue;

@@ -35,8 +35,9 @@ struct LaunchArgs {
 // Shared memory of one CTA in bytes for the given precision (0 = fp64, 1 = fp32).
 int cta_smem_bytes(int precision, const Geo& g, int M);
 
-// Fused-block path (Remark 9): block side k <= kFusedMaxK, messages in shared memory.
-constexpr int kFusedMaxK = 4;
+// Fused-block path (Remark 9): block side k <= kFusedMaxK, messages in shared
+// memory; kernels compiled for k <= 4 and for k = 5, 6.
+constexpr int kFusedMaxK = 6;
 constexpr int kMaxSmemBytes = 227 * 1024;       // opt-in shared memory of one CTA
 int fused_smem_bytes(int precision, const Geo& g, int M, int warps, int cosets);
 // Launch shape of the fused kernel: *warps / *cosets are requests (0 = any);

@@ -88,6 +88,50 @@ def test_fused_matches_dense_oracle(dev, d, k, iters, p, precision, warps, coset
                 assert out["iters"][b][L] == iters
 
 
+SHAPES_K6 = [(prec, w, c) for prec, shapes in pkg.FUSED_SHAPES_K6.items() for (w, c) in shapes]
+
+
+@pytest.mark.parametrize("d,k,iters,p", [
+    (7, 6, 4, 0.08),      # blocks 6, 6, 1: an interior 6 x 6 block with all four side messages
+    (4, 6, 4, 0.10),      # blocks 6, 1
+    (9, 5, 3, 0.10),      # blocks 5, 5, 5, 2
+])
+@pytest.mark.parametrize("precision,warps,cosets", SHAPES_K6, ids=[f"{a}-w{b}-g{c}" for a, b, c in SHAPES_K6])
+def test_fused_k6_matches_dense_oracle(dev, d, k, iters, p, precision, warps, cosets):
+    # Block sides 5 and 6 (dense messages of 32 and 64, states of up to 2^12
+    # entries): FP64 to 1e-9 and FP32 to 1e-3 against the dense oracle.
+    _, _, S = synth.sample_syndromes(515, 0, 2, d, p)
+    prm = pkg.DecoderParams(d=d, k=k, p=p, max_iter=iters, delta0=0.0, precision=precision,
+                            algorithm="fused", warps=warps, cosets=cosets)
+    out = gpu(S, prm, dev)
+    ref = naive_logp(S, d, k, p, iters)
+    tol = 1e-9 if precision == "fp64" else 1e-3
+    for b in range(S.shape[0]):
+        for L in range(4):
+            lp, dl, it = ref[b][L]
+            assert abs(out["logp"][b][L] - lp) <= tol, (b, L, out["logp"][b][L], lp)
+            assert abs(out["delta"][b][L] - dl) <= (1e-7 if precision == "fp64" else 1e-4)
+            assert out["iters"][b][L] == iters
+
+
+def test_fused_k6_large_distances(dev):
+    # d = 13 with 6 x 6 blocks: FP32 against FP64.  d = 31 (the largest
+    # configuration; FP64 messages would not fit in shared memory): finite
+    # log-probabilities below 0, valid decisions, bitwise-repeatable results.
+    _, _, S13 = synth.sample_syndromes(4013, 0, 6, 13, 0.10)
+    r = {prec: gpu(S13, pkg.DecoderParams(d=13, k=6, p=0.10, max_iter=8, delta0=0.0, precision=prec,
+                                           algorithm="fused"), dev) for prec in ("fp32", "fp64")}
+    assert np.max(np.abs(r["fp32"]["logp"] - r["fp64"]["logp"])) < 1e-3
+    assert np.array_equal(r["fp32"]["decision"], r["fp64"]["decision"])
+    _, _, S31 = synth.sample_syndromes(4031, 0, 4, 31, 0.12)
+    prm = pkg.DecoderParams(d=31, k=6, p=0.12, max_iter=6, delta0=0.0, precision="fp32", algorithm="fused")
+    a, b = gpu(S31, prm, dev), gpu(S31, prm, dev)
+    assert np.all(np.isfinite(a["logp"])) and np.all(a["logp"] < 0)
+    assert np.all((a["decision"] >= 0) & (a["decision"] < 4))
+    for key in ("logp", "delta", "iters", "decision"):
+        assert np.array_equal(a[key], b[key]), key
+
+
 def test_fused_equals_mps_golden_at_d11(dev):
     with open(os.path.join(HERE, "golden", "oracle_d11_k4_D8_p010.json")) as f:
         g = json.load(f)

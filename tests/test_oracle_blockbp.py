@@ -122,3 +122,34 @@ def test_dense_and_mps_oracles_agree_at_d11_k4_D8():
     lp, dl, it, _ = run_naive(T, 4, 4, 0.1, 0.0)
     assert stats.truncations == 0
     assert abs(r.logp - lp) < 1e-9
+
+
+def test_k6_single_block_is_the_exact_contraction():
+    # d = 3 (W = 5) with k = 6: one block covers the network, so the fused
+    # block tensor's value is the exact coset probability (no BP at all).
+    d, p = 3, 0.12
+    lat = Lattice(d)
+    _, _, S = synth.sample_syndromes(31, 0, 3, d, p)
+    for s in S:
+        ex = exact_coset_logprobs(lat, s, p)
+        for L in range(4):
+            lp, _, _, _ = run_naive(coset_network(lat, s, L, p), 6, 3, 0.1, 0.0)
+            assert abs(lp - ex[L]) < 1e-10
+
+
+@pytest.mark.parametrize("d,shots", [(4, 2), (7, 1)])
+def test_k6_dense_equals_untruncated_mps(d, shots):
+    # 6 x 6 blocks: the dense fused-block BP (row-by-row block tensors) and
+    # the MPS blockBP with D = 64 (no truncation at k = 6) are independent
+    # implementations of the same rule.
+    p = 0.08
+    lat = Lattice(d)
+    _, _, S = synth.sample_syndromes(515, 0, shots, d, p)
+    P = bb.Params(d=d, k=6, D=64, p=p, max_iter=4, delta0=0.0)
+    for s in S:
+        for L in range(4):
+            T = coset_network(lat, s, L, p)
+            r = bb.run_blockbp(T, P)
+            lp, dl, _, _ = run_naive(T, 6, 4, 0.1, 0.0)
+            assert abs(r.logp - lp) < 1e-9
+            assert abs(r.delta - dl) < 1e-7
