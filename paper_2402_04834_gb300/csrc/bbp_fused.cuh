@@ -537,11 +537,21 @@ template <> struct DeltaTerm<double> {
     const double o = group_sum(x * y, width);
     return 2.0 - 2.0 * o * o;
   }
+  // A 64-entry vector held as entries lane and lane + 32.
+  static __device__ __forceinline__ double eval2(double x0, double y0, double x1, double y1) {
+    const double o = warp_sum(x0 * y0 + x1 * y1);
+    return 2.0 - 2.0 * o * o;
+  }
 };
 template <> struct DeltaTerm<float> {
   static __device__ __forceinline__ float eval(float x, float y, int width) {
     const float t = x - y;
     const float s = group_sum(t * t, width);
+    return s * (2.f - 0.5f * s);
+  }
+  static __device__ __forceinline__ float eval2(float x0, float y0, float x1, float y1) {
+    const float t0 = x0 - y0, t1 = x1 - y1;
+    const float s = warp_sum(t0 * t0 + t1 * t1);
     return s * (2.f - 0.5f * s);
   }
 };
@@ -557,11 +567,34 @@ __device__ __forceinline__ T group_normalize(T v, int width) {
 // with the stored ones (Remark 7), normalise again, record each coset's
 // Delta term in ovl[coset * M + idx] and store the result.  Entry e of the
 // n x 2^h outgoing vectors sits in lane e % 32 (e < 64: G <= 4, h <= 4 or
-// G = 1, h <= 6).
+// G = 1, h <= 6); a vector of 64 entries spans both halves.
 template <typename T, int K>
 __device__ __forceinline__ void fused_update(const FusedWS<T>& ws, T* msgs, int stride, unsigned cos_of, int n,
                                              int idx, int h, T eta, T one_m_eta, double* ovl, int M, int lane) {
   const int width = 1 << h, tot = n << h;
+  if (K > 5 && width > 32) {
+    // One vector of 64 entries (k = 6, one coset): entries lane and lane + 32
+    // are reduced together.
+    const int q = slot_coset(cos_of, 0);
+    T* old0 = msgs + q * stride + idx * FusedDim<K>::vec + lane;
+    T* old1 = old0 + 32;
+    T x0 = ws.s0[lane], x1 = ws.s0[lane + 32];
+    const T y0 = *old0, y1 = *old1;
+    T nrm = xsqrt(warp_sum(x0 * x0 + x1 * x1));
+    T inv = nrm > T(0) ? T(1) / nrm : T(0);
+    x0 = one_m_eta * (x0 * inv) + eta * y0;
+    x1 = one_m_eta * (x1 * inv) + eta * y1;
+    nrm = xsqrt(warp_sum(x0 * x0 + x1 * x1));
+    inv = nrm > T(0) ? T(1) / nrm : T(0);
+    x0 *= inv;
+    x1 *= inv;
+    const T term = DeltaTerm<T>::eval2(x0, y0, x1, y1);
+    *old0 = x0;
+    *old1 = x1;
+    if (lane == 0) ovl[q * M + idx] = (double)term;
+    __syncwarp();
+    return;
+  }
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     if (r == 1 && tot <= 32) break;
