@@ -3,9 +3,15 @@
 Calls only ``oracle/`` (and the seeded workload in ``synth/``).  Each file
 holds, per shot, the oracle's log P, Delta, iterations, flags, decision and
 the smallest relative Schmidt gap at a real truncation (inf = none), for a
-seeded workload named in the file.
+seeded workload named in the file.  The k = 6 workloads (d = 31, 6 x 6
+blocks) run the dense fused-block oracle of Remark 9 (``oracle.naive``),
+which truncates nothing; one coset takes about ten minutes and 11 GB
+there, so they are spread over (shot, coset) pairs.
 
-    python tests/golden/make_golden.py [--which d5|d11|all] [--procs N]
+    python tests/golden/make_golden.py [--which d5|d11|...|all] [--procs N]
+
+``all`` leaves out the d = 31 workloads (about an hour on four cores and
+45 GB): name them, e.g. ``--which d31_k6_p012,d31_k6_p015 --procs 4``.
 """
 
 from __future__ import annotations
@@ -23,6 +29,7 @@ import numpy as np  # noqa: E402
 
 import synth  # noqa: E402
 from oracle import blockbp as bb  # noqa: E402
+from oracle import naive  # noqa: E402
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -39,6 +46,36 @@ for _ip, _p in ((0, 0.05), (1, 0.08), (3, 0.13), (4, 0.15)):
     WORKLOADS[f"d11_p{int(round(_p * 100)):03d}"] = dict(
         file=f"oracle_d11_k4_D8_p{int(round(_p * 100)):03d}.json", d=11, k=4, D=8, p=_p, max_iter=20,
         delta0=0.0, seed=synth.workload_seed(2, _ip), first_shot=0, shots=4)
+
+# Distance 31, k = 6 (dense 64-entry messages), 20 fixed iterations, at the
+# two noise levels of the d = 31 workload (p index 0, 1).
+for _ip, _p in ((0, 0.12), (1, 0.15)):
+    WORKLOADS[f"d31_k6_p{int(round(_p * 100)):03d}"] = dict(
+        file=f"oracle_d31_k6_p{int(round(_p * 100)):03d}.json", d=31, k=6, D=64, p=_p, max_iter=20,
+        delta0=0.0, seed=synth.workload_seed(5, _ip), first_shot=0, shots=3, form="fused")
+
+
+def _one_coset(args):
+    """One coset of one shot through the dense fused-block oracle."""
+    w, b, L, s = args
+    T = bb.coset_network(bb.Lattice(w["d"]), np.asarray(s, dtype=np.uint8), L, w["p"])
+    logp, delta, iters, _ = naive.run_naive(T, w["k"], w["max_iter"], 0.1, w["delta0"])
+    return b, L, float(logp), float(delta), int(iters)
+
+
+def _assemble(w, rows):
+    """Per-shot records from per-coset results (flags: Delta >= delta1 only,
+    since positive tensors and messages keep every Z_v and o_e positive)."""
+    out = []
+    for b in range(w["shots"]):
+        mine = sorted((r for r in rows if r[0] == b), key=lambda r: r[1])
+        logp = [r[2] for r in mine]
+        delta = [r[3] for r in mine]
+        flags = [bb.FLAG_UNTRUSTED if dl >= 1e-2 else 0 for dl in delta]
+        out.append(dict(shot=w["first_shot"] + b, logp=logp, delta=delta, iters=[r[4] for r in mine],
+                        flags=flags, decision=int(bb.decide(logp, delta, flags)), min_gap=None,
+                        truncations=0))
+    return out
 
 
 def _one(args):
@@ -57,9 +94,17 @@ def make(name: str, procs: int):
     w = WORKLOADS[name]
     ex, ez, S = synth.sample_syndromes(w["seed"], w["first_shot"], w["shots"], w["d"], w["p"])
     ctx = mp.get_context("spawn")
-    with ctx.Pool(procs) as pool:
-        rows = pool.map(_one, [(w, b, S[b].tolist()) for b in range(w["shots"])])
-    meta = {k: v for k, v in w.items() if k != "file"}
+    if w.get("form") == "fused":
+        with ctx.Pool(procs) as pool:
+            per = pool.map(_one_coset, [(w, b, L, S[b].tolist()) for b in range(w["shots"]) for L in range(4)],
+                           chunksize=1)
+        rows = _assemble(w, per)
+    else:
+        with ctx.Pool(procs) as pool:
+            rows = pool.map(_one, [(w, b, S[b].tolist()) for b in range(w["shots"])])
+    meta = {k: v for k, v in w.items() if k not in ("file", "form")}
+    if w.get("form") == "fused":
+        meta["oracle"] = "dense fused-block blockBP (Remark 9), no truncation"
     meta["eta"], meta["delta1"], meta["cutoff"] = 0.1, 1e-2, 1e-13
     with open(os.path.join(HERE, w["file"]), "w") as f:
         json.dump({"workload": meta, "shots": rows}, f, indent=0)
@@ -71,5 +116,6 @@ if __name__ == "__main__":
     ap.add_argument("--which", default="all")
     ap.add_argument("--procs", type=int, default=os.cpu_count() or 1)
     a = ap.parse_args()
-    for name in (WORKLOADS if a.which == "all" else [a.which]):
+    names = [n for n in WORKLOADS if not n.startswith("d31")] if a.which == "all" else a.which.split(",")
+    for name in names:
         make(name, a.procs)
