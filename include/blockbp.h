@@ -91,13 +91,15 @@ extern "C" {
  *             tensors) and resident CTAs per SM of bbp_decode_mixed.  0 picks
  *             the fastest compiled shape whose shared memory fits; compiled
  *             (warps, cosets): FP32 (8,4) (8,2) (4,2) (4,4) (16,1) (8,1)
- *             (4,1), FP64 (4,2) (8,2) (8,1) (4,4); for k = 5, 6: FP32 (4,1)
- *             (2,1), FP64 (2,1); other requests give BBP_EUNSUPPORTED.
+ *             (4,1), FP64 (4,2) (8,2) (8,1) (4,4); for k = 5, 6: FP32 (6,1)
+ *             (4,1) (2,1), FP64 (3,1) (2,1); other requests give
+ *             BBP_EUNSUPPORTED.
  *   algorithm BBP_ALG_MPS, or BBP_ALG_FUSED: every k x k block fused into one
  *             vertex with dense messages (Remark 9; the form the paper ran for
  *             k = 1, 2, 4).  Nothing is truncated, D and cutoff are unused,
  *             and the result equals BBP_ALG_MPS whenever that truncates
- *             nothing.  Needs k <= 6 and no workspace.
+ *             nothing.  Needs k <= 6; no workspace for k <= 4 (messages in
+ *             shared memory), a message slot per resident CTA for k = 5, 6.
  */
 typedef struct bbp_params {
   int32_t d;
@@ -111,14 +113,17 @@ typedef struct bbp_params {
   double cutoff;
   int32_t precision;
   int32_t algorithm;
-  int32_t launch_warps;        /* fused path: warps per CTA (2, 4, 8, 16), 0 = default */
+  int32_t launch_warps;        /* fused path: warps per CTA (2, 3, 4, 6, 8, 16), 0 = default */
   int32_t launch_ctas_per_sm;  /* bbp_decode_mixed: resident CTAs per SM, 0 = the occupancy limit */
   int32_t launch_cosets;       /* fused path: cosets per CTA (1, 2, 4), 0 = default */
 } bbp_params;
 
 /*
  * bbp_workspace_bytes -- device scratch needed by bbp_decode_batch for B
- * syndromes (MPS messages of every syndrome x coset, Sec. III.D).  With
+ * syndromes: the MPS messages of every syndrome x coset (Sec. III.D); for
+ * BBP_ALG_FUSED none at k <= 4, and at k = 5, 6 the dense messages of the
+ * resident CTAs, min(4B, 512) slots of 64 M scalars (M directed block
+ * edges; d = 31: 440 x 64 x 4 bytes = 112.6 KB a slot in FP32).  With
  * include_io != 0 it also counts room for device copies of the inputs and
  * outputs, as bbp_decode_batch_host needs.  Writes the size to *bytes.
  * Errors: BBP_EINVAL for invalid parameters or a null pointer.
@@ -289,7 +294,8 @@ int bbp_warm_train_step(float* theta, float* adam_m, float* adam_v, int32_t step
  * all-zero message falls back to uniform) and optional export of the
  * messages after the BP loop into final_msgs [B][4][M][16] (float).
  * Errors as bbp_decode_batch; BBP_EINVAL for the MPS algorithm, and for
- * k > 4 when messages are given or asked for.
+ * k > 4 when messages are given or asked for.  workspace: at least
+ * bbp_workspace_bytes(prm, B, 0) bytes (none for k <= 4).
  */
 int bbp_decode_batch_ex(const uint8_t* syndromes, int64_t B, const bbp_params* prm, const float* init_msgs,
                         float* final_msgs, double* logp, double* delta, int32_t* iters, int32_t* flags,
@@ -305,7 +311,8 @@ int bbp_decode_batch_ex(const uint8_t* syndromes, int64_t B, const bbp_params* p
  *   order      device [B] int32 permutation of 0..B-1, or NULL (natural order)
  *   prm        k, p, eta, delta0, delta1, max_iter, precision; d is ignored;
  *              algorithm must be BBP_ALG_FUSED
- *   workspace  device, at least 256 bytes (the work counter)
+ *   workspace  device, at least 256 bytes (the work counter); for k = 5, 6
+ *              256 + min(4B, 512) x 64 M(d_max) scalars (the message slots)
  * Errors as bbp_decode_batch.
  */
 int bbp_decode_mixed(const uint8_t* syndromes, const int64_t* offsets, const int32_t* d_of, const int32_t* order,

@@ -30,7 +30,7 @@ WARM_INFER_WS_BYTES = 270592      # workspace of bbp_warm_infer, for any N
 FUSED_SHAPES = {"fp32": ((8, 4), (8, 2), (4, 2), (4, 4), (16, 1), (8, 1), (4, 1)),
                 "fp64": ((4, 2), (8, 2), (8, 1), (4, 4))}
 # ... and for block sides 5 and 6 (one coset per CTA).
-FUSED_SHAPES_K6 = {"fp32": ((4, 1), (2, 1)), "fp64": ((2, 1),)}
+FUSED_SHAPES_K6 = {"fp32": ((6, 1), (4, 1), (2, 1)), "fp64": ((3, 1), (2, 1))}
 BBP_ETOOLARGE = -5
 STATIC_WORKSPACE_BYTES = 32 << 20
 

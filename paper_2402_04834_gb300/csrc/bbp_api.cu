@@ -31,8 +31,8 @@ int check_params(const bbp_params* p) {
   if (p->precision != BBP_FP64 && p->precision != BBP_FP32) return BBP_EINVAL;
   if (p->algorithm != BBP_ALG_MPS && p->algorithm != BBP_ALG_FUSED) return BBP_EINVAL;
   if (p->algorithm == BBP_ALG_MPS && (p->k > bbp::kMaxK || p->D > bbp::kMaxD)) return BBP_EUNSUPPORTED;
-  if (p->launch_warps != 0 && p->launch_warps != 2 && p->launch_warps != 4 && p->launch_warps != 8 &&
-      p->launch_warps != 16)
+  if (p->launch_warps != 0 && p->launch_warps != 2 && p->launch_warps != 3 && p->launch_warps != 4 &&
+      p->launch_warps != 6 && p->launch_warps != 8 && p->launch_warps != 16)
     return BBP_EINVAL;
   if (p->launch_cosets != 0 && p->launch_cosets != 1 && p->launch_cosets != 2 && p->launch_cosets != 4)
     return BBP_EINVAL;
@@ -51,7 +51,12 @@ struct Sizes {
   Geo g;
   int M, arena_elems, m;
   size_t elem, arena_bytes, io_bytes;
+  long long slots;        // fused, k = 5, 6: message slots in the arena
 };
+
+// Fused k = 5, 6: one message slot (64 * M scalars) per resident CTA.
+long long fused_slots(int64_t B) { return B * 4 < bbp::kFusedSlots ? (long long)B * 4 : bbp::kFusedSlots; }
+size_t fused_slot_bytes(int M, size_t elem) { return (size_t)M * 64 * elem; }
 
 Sizes sizes_for(const bbp_params* p, int64_t B) {
   Sizes s;
@@ -59,7 +64,15 @@ Sizes sizes_for(const bbp_params* p, int64_t B) {
   bbp::count_messages(s.g, p->D, &s.M, &s.arena_elems);
   s.m = 2 * p->d * (p->d - 1);
   s.elem = p->precision == BBP_FP64 ? sizeof(double) : sizeof(float);
-  s.arena_bytes = p->algorithm == BBP_ALG_FUSED ? 0 : align256((size_t)B * 4 * (size_t)s.arena_elems * s.elem);
+  s.slots = 0;
+  if (p->algorithm != BBP_ALG_FUSED) {
+    s.arena_bytes = align256((size_t)B * 4 * (size_t)s.arena_elems * s.elem);
+  } else if (p->k > 4) {
+    s.slots = fused_slots(B);
+    s.arena_bytes = align256((size_t)s.slots * fused_slot_bytes(s.M, s.elem));
+  } else {
+    s.arena_bytes = 0;
+  }
   s.io_bytes = align256((size_t)B * s.m) + align256((size_t)B * 4 * 8) * 2 +
                align256((size_t)B * 4 * 4) * 2 + align256((size_t)B);
   return s;
@@ -118,6 +131,7 @@ int bbp_decode_batch_ex(const uint8_t* syndromes, int64_t B, const bbp_params* p
   a.flags = flags; a.decision = decision; a.B = B;
   if ((init_msgs || final_msgs) && (prm->algorithm != BBP_ALG_FUSED || prm->k > 4)) return BBP_EINVAL;
   a.init_msgs = init_msgs; a.final_msgs = final_msgs;
+  a.slots = s.slots;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   if (prm->algorithm == BBP_ALG_FUSED) {
@@ -193,6 +207,12 @@ int bbp_decode_mixed(const uint8_t* syndromes, const int64_t* offsets, const int
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int Mmax = 0, ae = 0, w = 0, c = 0;
   bbp::count_messages(a.geo, 1, &Mmax, &ae);
+  if (prm->k > 4) {   // message slots after the counter
+    const size_t elem = prm->precision == BBP_FP64 ? sizeof(double) : sizeof(float);
+    m.slots = fused_slots(B);
+    if (workspace_bytes < 256 + (size_t)m.slots * fused_slot_bytes(Mmax, elem)) return BBP_ENOSPACE;
+    m.slot_base = static_cast<char*>(workspace) + 256;
+  }
   if (!shape_of(prm, a.geo, Mmax, &w, &c)) return BBP_EUNSUPPORTED;
   cudaError_t e = prm->precision == BBP_FP64 ? bbp::launch_fused_mixed_f64(a, m, w, c, st)
                                              : bbp::launch_fused_mixed_f32(a, m, w, c, st);

@@ -20,6 +20,7 @@ cudaError_t launch_decode_t(const LaunchArgs& a, cudaStream_t st) {
   k.synd = a.synd; k.arena = static_cast<T*>(a.arena);
   k.logp = a.logp; k.delta = a.delta; k.iters = a.iters; k.flags = a.flags;
   k.init_msgs = nullptr; k.final_msgs = nullptr;
+  k.n_items = 0; k.slot_elems = 0;
   const int smem = smem_bytes_for<T>(a.geo, a.M);
   auto kern = decode_kernel<T, kMaxK, kMaxD, kWarps>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -42,7 +43,29 @@ KArgs<T> fused_args(const LaunchArgs& a) {
   k.synd = a.synd; k.arena = nullptr;
   k.logp = a.logp; k.delta = a.delta; k.iters = a.iters; k.flags = a.flags;
   k.init_msgs = a.init_msgs; k.final_msgs = a.final_msgs;
+  k.n_items = 0; k.slot_elems = 0;
   return k;
+}
+
+// Persistent grid of a k = 5, 6 launch: resident CTAs, at most one per item
+// and per message slot.
+template <typename Kern>
+cudaError_t persistent_grid(Kern kern, int threads, int smem, int ctas_per_sm, long long items, long long slots,
+                            long long* grid) {
+  cudaError_t e;
+  int per_sm = ctas_per_sm;
+  if (per_sm <= 0) {
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem)) != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+  }
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  long long g = (long long)sms * per_sm;
+  if (g > items) g = items;
+  if (g > slots) g = slots;
+  *grid = g;
+  return g > 0 ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 template <typename T, int NW, int G, int K>
@@ -52,8 +75,18 @@ cudaError_t launch_fused_nw(const LaunchArgs& a, cudaStream_t st) {
   auto kern = fused_kernel<T, NW, G, K>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  const unsigned grid = (unsigned)(a.B * (4 / G));
-  kern<<<grid, NW * 32, smem, st>>>(k);
+  const long long items = a.B * (4 / G);
+  if (K > 4) {
+    KArgs<T> kp = k;
+    kp.arena = static_cast<T*>(a.arena);
+    kp.n_items = items;
+    kp.slot_elems = (long long)G * a.M * FusedDim<K>::vec;
+    long long grid = 0;
+    if ((e = persistent_grid(kern, NW * 32, smem, 0, items, a.slots, &grid)) != cudaSuccess) return e;
+    kern<<<(unsigned)grid, NW * 32, smem, st>>>(kp);
+    return cudaGetLastError();
+  }
+  kern<<<(unsigned)items, NW * 32, smem, st>>>(k);
   return cudaGetLastError();
 }
 
@@ -81,8 +114,15 @@ cudaError_t launch_fused_mixed_nw(const LaunchArgs& a, const MixedLaunch& m, cud
   mx.n_items = a.B * (4 / G); mx.k = a.geo.k;
   long long grid = (long long)sms * per_sm;
   if (grid > mx.n_items) grid = mx.n_items;
+  KArgs<T> kp = k;
+  if (K > 4) {   // messages in the workspace, one slot per CTA
+    kp.arena = static_cast<T*>(m.slot_base);
+    kp.slot_elems = (long long)G * Mmax * FusedDim<K>::vec;
+    if (grid > m.slots) grid = m.slots;
+    if (grid < 1) return cudaErrorInvalidValue;
+  }
   if ((e = cudaMemsetAsync(m.counter, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
-  kern<<<(unsigned)grid, NW * 32, smem, st>>>(k, mx);
+  kern<<<(unsigned)grid, NW * 32, smem, st>>>(kp, mx);
   return cudaGetLastError();
 }
 

@@ -89,7 +89,8 @@ BBP_HD FusedLayout fused_layout(const Geo& g, int M, int nwarps, int G) {
   L.ovl = o;    o = align_up(o + 8 * G * M, 16);
   L.rlog = o;   o = align_up(o + 8 * G * (g.nb * g.nb + M), 16);
   L.misc = o;   o = align_up(o + 128, 16);
-  L.msgs = o;   o = align_up(o + (int)sizeof(T) * FusedDim<K>::vec * G * M, 16);
+  L.msgs = o;   // k <= 4: the messages live here; k = 5, 6: in the workspace
+  if (K <= 4) o = align_up(o + (int)sizeof(T) * FusedDim<K>::vec * G * M, 16);
   L.ws = o;
   L.ws_stride = fused_ws_bytes<T, K>(G);
   o = align_up(o + nwarps * L.ws_stride, 16);
@@ -619,7 +620,7 @@ __device__ __forceinline__ void fused_update(const FusedWS<T>& ws, T* msgs, int 
 // Resident CTAs per SM the register budget is sized for: with one coset per
 // CTA, 32 warps per SM in FP32 (64 registers a thread) and 16 in FP64; with
 // more cosets per CTA shared memory allows half as many; with k = 6 states
-// (16 KB a coset) one CTA.
+// (16 KB a buffer in FP32) the shared memory decides.
 template <typename T, int NW, int G, int K> struct FusedMinBlocks {
   static constexpr int warps = K > 4 ? NW : (sizeof(T) == 4 ? 32 : 16) / (G > 1 ? 2 : 1);
   static constexpr int value = warps / NW > 1 ? warps / NW : 1;
@@ -627,9 +628,11 @@ template <typename T, int NW, int G, int K> struct FusedMinBlocks {
 
 // Cosets c0 .. c0 + G - 1 of one syndrome decoded by the whole CTA: syn_src
 // holds the syndrome's m bytes and outputs go to row syn * 4 + coset.
+// gmsgs: this CTA's message slot in global memory (k = 5, 6; the slot is
+// L2-resident and touched only a few times per block sweep), else null.
 template <typename T, int NW, int G, int K>
 __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const int M, const uint8_t* syn_src,
-                                           const long long syn, const int c0, unsigned char* smem) {
+                                           const long long syn, const int c0, unsigned char* smem, T* gmsgs) {
   const int W = g.W, d = g.d, nb = g.nb, WW = W * W;
   const int m = 2 * d * (d - 1);
   static_assert(K <= 4 || G == 1, "k = 6 states hold one coset per CTA");
@@ -644,7 +647,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
   double* rlog = reinterpret_cast<double*>(smem + Lo.rlog);
   int* misc = reinterpret_cast<int*>(smem + Lo.misc);      // [0] counter, [2..4] list sizes, [8 + q] flags
   double* dsh = reinterpret_cast<double*>(smem + Lo.misc + 64);
-  T* msgs = reinterpret_cast<T*>(smem + Lo.msgs);
+  T* msgs = K > 4 ? gmsgs : reinterpret_cast<T*>(smem + Lo.msgs);
   const int stride = M * VEC;                                // messages of one coset
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -851,15 +854,26 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
   }
 }
 
-// One CTA per (syndrome, group of G cosets).
+// k <= 4: one CTA per (syndrome, group of G cosets).  k = 5, 6: a
+// persistent grid, CTA b taking items b, b + gridDim.x, ... with its
+// messages in workspace slot b.
 template <typename T, int NW, int G, int K>
 __global__ void __launch_bounds__(NW * 32, (FusedMinBlocks<T, NW, G, K>::value)) fused_kernel(KArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NG = 4 / G;
-  const long long syn = blockIdx.x / NG;
-  const int c0 = (int)(blockIdx.x % NG) * G;
   const int m = 2 * a.geo.d * (a.geo.d - 1);
-  fused_item<T, NW, G, K>(a, a.geo, a.M, a.synd + syn * m, syn, c0, smem);
+  if constexpr (K > 4) {
+    T* gm = a.arena + (long long)blockIdx.x * a.slot_elems;
+    for (long long item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+      const long long syn = item / NG;
+      fused_item<T, NW, G, K>(a, a.geo, a.M, a.synd + syn * m, syn, (int)(item % NG) * G, smem, gm);
+      __syncthreads();
+    }
+  } else {
+    const long long syn = blockIdx.x / NG;
+    const int c0 = (int)(blockIdx.x % NG) * G;
+    fused_item<T, NW, G, K>(a, a.geo, a.M, a.synd + syn * m, syn, c0, smem, nullptr);
+  }
 }
 
 // A batch of syndromes of different distances in one persistent launch: CTAs
@@ -891,7 +905,8 @@ __global__ void __launch_bounds__(NW * 32, (FusedMinBlocks<T, NW, G, K>::value))
     const Geo g = make_geo(mx.d_of[shot], mx.k);
     int M = 0, ae = 0;
     count_messages(g, 1, &M, &ae);
-    fused_item<T, NW, G, K>(a, g, M, a.synd + mx.offsets[shot], shot, c0, smem);
+    fused_item<T, NW, G, K>(a, g, M, a.synd + mx.offsets[shot], shot, c0, smem,
+                            K > 4 ? a.arena + (long long)blockIdx.x * a.slot_elems : nullptr);
     __syncthreads();
   }
 }

@@ -9,6 +9,7 @@ cudaError_t launch_fused_f32(const LaunchArgs& a, int warps, int cosets, cudaStr
     switch (warps * 10 + cosets) {
       case 21: return launch_fused_nw<float, 2, 1, 6>(a, st);
       case 41: return launch_fused_nw<float, 4, 1, 6>(a, st);
+      case 61: return launch_fused_nw<float, 6, 1, 6>(a, st);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -30,6 +31,7 @@ cudaError_t launch_fused_mixed_f32(const LaunchArgs& a, const MixedLaunch& m, in
     switch (warps * 10 + cosets) {
       case 21: return launch_fused_mixed_nw<float, 2, 1, 6>(a, m, st);
       case 41: return launch_fused_mixed_nw<float, 4, 1, 6>(a, m, st);
+      case 61: return launch_fused_mixed_nw<float, 6, 1, 6>(a, m, st);
       default: return cudaErrorInvalidValue;
     }
   }

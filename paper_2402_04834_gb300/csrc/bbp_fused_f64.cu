@@ -5,7 +5,13 @@
 namespace bbp {
 
 cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, int cosets, cudaStream_t st) {
-  if (a.geo.k > 4) return warps * 10 + cosets == 21 ? launch_fused_nw<double, 2, 1, 6>(a, st) : cudaErrorInvalidValue;
+  if (a.geo.k > 4) {
+    switch (warps * 10 + cosets) {
+      case 21: return launch_fused_nw<double, 2, 1, 6>(a, st);
+      case 31: return launch_fused_nw<double, 3, 1, 6>(a, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (warps * 10 + cosets) {
     case 81: return launch_fused_nw<double, 8, 1, 4>(a, st);
     case 42: return launch_fused_nw<double, 4, 2, 4>(a, st);
@@ -17,8 +23,13 @@ cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, int cosets, cudaStr
 
 cudaError_t launch_fused_mixed_f64(const LaunchArgs& a, const MixedLaunch& m, int warps, int cosets,
                                    cudaStream_t st) {
-  if (a.geo.k > 4)
-    return warps * 10 + cosets == 21 ? launch_fused_mixed_nw<double, 2, 1, 6>(a, m, st) : cudaErrorInvalidValue;
+  if (a.geo.k > 4) {
+    switch (warps * 10 + cosets) {
+      case 21: return launch_fused_mixed_nw<double, 2, 1, 6>(a, m, st);
+      case 31: return launch_fused_mixed_nw<double, 3, 1, 6>(a, m, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (warps * 10 + cosets) {
     case 81: return launch_fused_mixed_nw<double, 8, 1, 4>(a, m, st);
     case 42: return launch_fused_mixed_nw<double, 4, 2, 4>(a, m, st);
@@ -42,9 +53,10 @@ struct Shape {
 constexpr Shape kShapesF32[] = {{8, 4}, {8, 2}, {4, 2}, {4, 4}, {16, 1}, {8, 1}, {4, 1}};
 constexpr Shape kShapesF64[] = {{4, 2}, {8, 2}, {8, 1}, {4, 4}};
 
-// Block sides 5 and 6: states of 2^12 entries, one coset per CTA.
-constexpr Shape kShapesF32K6[] = {{4, 1}, {2, 1}};
-constexpr Shape kShapesF64K6[] = {{2, 1}};
+// Block sides 5 and 6: states of 2^12 entries, one coset per CTA, messages
+// in the workspace; the most warps whose state buffers fit one SM first.
+constexpr Shape kShapesF32K6[] = {{6, 1}, {4, 1}, {2, 1}};
+constexpr Shape kShapesF64K6[] = {{3, 1}, {2, 1}};
 
 }  // namespace
 

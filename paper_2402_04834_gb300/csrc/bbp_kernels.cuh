@@ -86,6 +86,8 @@ struct KArgs {
   int32_t* flags;
   const float* init_msgs;   // fused path: [cta][M][16] initial messages, or null (uniform)
   float* final_msgs;        // fused path: [cta][M][16] messages after the BP loop, or null
+  long long n_items;        // fused path, k = 5, 6: (syndrome, coset group) items of the launch
+  long long slot_elems;     // fused path, k = 5, 6: scalars of one CTA's message slot in arena
 };
 
 // Everything a warp needs to reach the CTA's shared tables.

@@ -30,14 +30,17 @@ struct LaunchArgs {
   long long B;
   const float* init_msgs = nullptr;
   float* final_msgs = nullptr;
+  long long slots = 0;            // fused, k = 5, 6: message slots of 64 * M scalars in arena
 };
 
 // Shared memory of one CTA in bytes for the given precision (0 = fp64, 1 = fp32).
 int cta_smem_bytes(int precision, const Geo& g, int M);
 
-// Fused-block path (Remark 9): block side k <= kFusedMaxK, messages in shared
-// memory; kernels compiled for k <= 4 and for k = 5, 6.
+// Fused-block path (Remark 9): block side k <= kFusedMaxK; kernels compiled
+// for k <= 4 (messages in shared memory) and for k = 5, 6 (messages in a
+// workspace slot per resident CTA, at most kFusedSlots slots).
 constexpr int kFusedMaxK = 6;
+constexpr long long kFusedSlots = 512;
 constexpr int kMaxSmemBytes = 227 * 1024;       // opt-in shared memory of one CTA
 int fused_smem_bytes(int precision, const Geo& g, int M, int warps, int cosets);
 // Launch shape of the fused kernel: *warps / *cosets are requests (0 = any);
@@ -52,6 +55,8 @@ struct MixedLaunch {
   unsigned long long* counter;
   int d_max;
   int ctas_per_sm;
+  void* slot_base = nullptr;      // k = 5, 6: message slots (kernel scalars), 64 * M(d_max) each
+  long long slots = 0;
 };
 
 cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, int cosets, cudaStream_t st);

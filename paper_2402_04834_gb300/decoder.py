@@ -10,6 +10,7 @@ depolarizing errors and syndromes on the device.
 from __future__ import annotations
 
 import ctypes
+import dataclasses
 
 import numpy as np
 import torch
@@ -138,7 +139,11 @@ def decode_mixed(packed, offsets, d_of, prm: DecoderParams, largest_first=True, 
         order = torch.argsort(d_of, descending=True, stable=True).to(torch.int32)
     if d_max is None:
         d_max = int(d_of.max().item())
-    counter = counter if counter is not None else torch.empty(256, dtype=torch.uint8, device=dev)
+    need = 256
+    if prm.k > 4:   # message slots after the work counter
+        need += workspace_bytes(dataclasses.replace(prm, d=d_max), B)
+    if counter is None or counter.numel() < need:
+        counter = torch.empty(need, dtype=torch.uint8, device=dev)
     cp = prm.c()
     check(lib().bbp_decode_mixed(_ptr(packed), _ptr(offsets), _ptr(d_of), _ptr(order) if order is not None else None,
                                  B, d_max, ctypes.byref(cp), _ptr(out["logp"]), _ptr(out["delta"]),

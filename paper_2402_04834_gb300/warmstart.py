@@ -16,7 +16,7 @@ import numpy as np
 import torch
 
 from ._lib import (WARM_F, WARM_H, WARM_INFER_WS_BYTES, WARM_MAX_ROWS, WARM_O, WARM_STATUS_OFFSET as STATUS_OFFSET,
-                   DecoderParams, check, lib)
+                   DecoderParams, check, lib, workspace_bytes)
 from .decoder import Workspace, _ptr, _stream, decode
 
 
@@ -153,7 +153,7 @@ def decode_ex(syndromes, prm: DecoderParams, init_msgs=None, final_msgs=None, wo
             "decision": torch.empty(B, dtype=torch.int8, device=dev),
         }
     cp = prm.c()
-    ws = (workspace or Workspace()).get(256, dev)
+    ws = (workspace or Workspace()).get(max(256, workspace_bytes(prm, B)), dev)
     check(lib().bbp_decode_batch_ex(_ptr(syndromes), B, ctypes.byref(cp),
                                     _ptr(init_msgs) if init_msgs is not None else None,
                                     _ptr(final_msgs) if final_msgs is not None else None,

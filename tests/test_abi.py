@@ -79,6 +79,22 @@ def test_fused_launch_shapes_checked_on_the_host(L):
     assert L.bbp_workspace_bytes(ctypes.byref(c), 10, 0, ctypes.byref(out)) == -4
     c = pkg.DecoderParams(d=31, k=4, precision="fp64", algorithm="fused").c()
     assert L.bbp_workspace_bytes(ctypes.byref(c), 10, 0, ctypes.byref(out)) == 0
+    for prec, shapes in pkg.FUSED_SHAPES_K6.items():
+        for w, g in shapes:
+            c = pkg.DecoderParams(d=31, k=6, precision=prec, algorithm="fused", warps=w, cosets=g).c()
+            assert L.bbp_workspace_bytes(ctypes.byref(c), 10, 0, ctypes.byref(out)) == 0, (prec, w, g)
+    c = pkg.DecoderParams(d=31, k=6, precision="fp64", algorithm="fused", warps=4, cosets=1).c()
+    assert L.bbp_workspace_bytes(ctypes.byref(c), 10, 0, ctypes.byref(out)) == -4
+
+
+def test_fused_k6_workspace_holds_one_message_slot_per_resident_cta(L):
+    # k <= 4 keeps the messages in shared memory; k = 5, 6 keep them in
+    # min(4B, 512) slots of 64 M scalars (d = 31: M = 440 directed edges).
+    assert pkg.workspace_bytes(pkg.DecoderParams(d=31, k=4, precision="fp32", algorithm="fused"), 1000) == 0
+    for B, prec, size in ((10, "fp32", 4), (10, "fp64", 8), (1000, "fp32", 4)):
+        slots = min(4 * B, 512)
+        want = -(-slots * 440 * 64 * size // 256) * 256
+        assert pkg.workspace_bytes(pkg.DecoderParams(d=31, k=6, precision=prec, algorithm="fused"), B) == want
 
 
 def test_decode_null_pointers_rejected_before_any_cuda_call(L):
