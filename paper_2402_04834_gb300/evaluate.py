@@ -4,11 +4,14 @@ P_L is estimated as in Sec. IV: errors are drawn on the device
 (``decoder.sample``, which also returns each error's true logical class), the
 decoder picks a coset, and a shot fails when the pick is not the true
 class; the 95 % interval is Wilson's.  Throughput is timed with CUDA events
-around one decode of the whole batch.  The paper observes that BP converges
-faster at low noise, so max-iter can be lowered there (Sec. IV, last
-paragraph); ``sweep`` measures that trade-off.
+around the decode calls of the whole batch.  The paper observes that BP
+converges faster at low noise, so max-iter can be lowered there (Sec. IV,
+last paragraph); ``sweep`` measures that trade-off.
 
     python -m paper_2402_04834_gb300.evaluate --d 11 --p 0.05 0.10 --max-iter 5 10 20 --shots 10000
+    # d = 31 with 6 x 6 blocks, 10^5 shots per noise level (seeds 5000, 5001)
+    python -m paper_2402_04834_gb300.evaluate --d 31 --k 6 --p 0.12 0.15 --max-iter 20 --shots 100000 \
+        --seed-base 5000 --seed-per-d 0
 """
 
 from __future__ import annotations
@@ -23,32 +26,39 @@ from .decoder import decode, sample
 from .warmstart import wilson
 
 
-def logical_error_rate(d: int, p: float, shots: int, seed: int, **params) -> dict:
-    """Decode ``shots`` seeded syndromes; P_L with its Wilson 95 % interval,
-    mean iterations over cosets and syndromes per second."""
+def logical_error_rate(d: int, p: float, shots: int, seed: int, chunk: int = 16384, **params) -> dict:
+    """Decode ``shots`` seeded syndromes, ``chunk`` per call after one
+    untimed warm-up call; P_L with its Wilson 95 % interval, mean iterations
+    over cosets and syndromes per second (device time of the decode calls)."""
     _, _, s, tc = sample(seed, 0, shots, d, p, with_errors=False)
     prm = DecoderParams(d=d, p=p, **params)
-    out = decode(s, prm)
+    decode(s[:min(shots, 64)], prm)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dec, its = [], []
     a.record()
-    out = decode(s, prm, out=out)
+    for c0 in range(0, shots, chunk):
+        out = decode(s[c0:c0 + chunk], prm)
+        dec.append(out["decision"])
+        its.append(out["iters"])
     b.record()
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
-    fails = int((out["decision"].to(torch.int64) != tc.to(torch.int64)).sum().item())
+    fails = int((torch.cat(dec).to(torch.int64) != tc.to(torch.int64)).sum().item())
     lo, hi = wilson(fails, shots)
     return {"d": d, "p": p, "shots": shots, **params, "failures": fails, "P_L": fails / shots,
-            "P_L_wilson95": [lo, hi], "mean_iters": float(out["iters"].double().mean().item()),
+            "P_L_wilson95": [lo, hi], "mean_iters": float(torch.cat(its).double().mean().item()),
             "syndromes_per_s": shots / ms * 1e3}
 
 
-def sweep(d_list, p_list, max_iters, shots, k=4, precision="fp32", algorithm="fused", seed_base=7000):
+def sweep(d_list, p_list, max_iters, shots, k=4, precision="fp32", algorithm="fused", seed_base=7000,
+          seed_per_d=100):
+    """Seeds: seed_base + seed_per_d * d + (index of p in p_list)."""
     rows = []
     for d in d_list:
         for ip, p in enumerate(p_list):
             for mi in max_iters:
-                rows.append(logical_error_rate(d, p, shots, seed_base + 100 * d + ip, k=k, max_iter=mi,
+                rows.append(logical_error_rate(d, p, shots, seed_base + seed_per_d * d + ip, k=k, max_iter=mi,
                                                precision=precision, algorithm=algorithm))
     return rows
 
@@ -61,8 +71,12 @@ def main():
     ap.add_argument("--shots", type=int, default=10000)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--algorithm", default="fused", choices=["fused", "mps"])
+    ap.add_argument("--k", type=int, default=4, help="block side (6: the d = 31 scheme of Sec. IV)")
+    ap.add_argument("--seed-base", type=int, default=7000)
+    ap.add_argument("--seed-per-d", type=int, default=100)
     args = ap.parse_args()
-    for r in sweep(args.d, args.p, args.max_iter, args.shots, precision=args.precision, algorithm=args.algorithm):
+    for r in sweep(args.d, args.p, args.max_iter, args.shots, k=args.k, precision=args.precision,
+                   algorithm=args.algorithm, seed_base=args.seed_base, seed_per_d=args.seed_per_d):
         print(json.dumps(r), flush=True)
 
 
