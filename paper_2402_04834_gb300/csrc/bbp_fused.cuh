@@ -102,6 +102,64 @@ template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
 
+// The data column of side message A with SD recorded legs and NF legs still
+// to come (k = 5, 6: NF = 2), one coset, the message in registers: each
+// lane takes groups hbv of (rows, b), reads in[a, hbv] for the 2^SD values
+// of a once and writes out[a2, hbv, v] = sum_a m[a, v, a2] in[a, hbv].
+template <typename T, int SD, int NF>
+__device__ __forceinline__ void data_column_a(const T* mt, const T* cur, T* nxt, int ib, int ob, int hb,
+                                              int lane) {
+  using V2 = typename Vec2<T>::type;
+  constexpr int NA = 1 << SD, NO = 1 << NF, NM = 1 << (SD + 1 + NF);
+  T mr[NM];
+#pragma unroll
+  for (int i = 0; i < NM; ++i) mr[i] = mt[i];
+  const int low = (1 << hb) - 1;
+  for (int hbv = lane; hbv <= low; hbv += 32) {
+    T x[NA];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) x[a] = cur[ib | (a << hb) | hbv];
+#pragma unroll
+    for (int a2 = 0; a2 < NO; ++a2) {
+      T s0 = T(0), s1 = T(0);
+#pragma unroll
+      for (int a = 0; a < NA; ++a) {
+        s0 += mr[((a << 1) << NF) | a2] * x[a];
+        s1 += mr[(((a << 1) | 1) << NF) | a2] * x[a];
+      }
+      V2 o;
+      o.x = s0; o.y = s1;
+      *reinterpret_cast<V2*>(nxt + 2 * (ob | (a2 << hb) | hbv)) = o;
+    }
+  }
+}
+
+// The data column of side message B (SD recorded legs, NF to come), one
+// coset: each lane takes groups al of (a, rows), reads the 2^SD pairs
+// in[al, b, v] once and writes out[al, b2] = sum_{b,v} m[b, v, b2] in[al, b, v].
+template <typename T, int SD, int NF>
+__device__ __forceinline__ void data_column_b(const T* mb, const T* cur, T* nxt, int ab0, int hah, int lane) {
+  using V2 = typename Vec2<T>::type;
+  constexpr int NB = 1 << SD, NO = 1 << NF, NM = 1 << (SD + 1 + NF);
+  T mr[NM];
+#pragma unroll
+  for (int i = 0; i < NM; ++i) mr[i] = mb[i];
+  for (int al = lane; al < (1 << hah); al += 32) {
+    const int ah = ab0 | al;
+    V2 x[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) x[b] = *reinterpret_cast<const V2*>(cur + (((ah << SD) | b) << 1));
+#pragma unroll
+    for (int b2 = 0; b2 < NO; ++b2) {
+      T val = T(0);
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+        val += mr[((b << 1) << NF) | b2] * x[b].x + mr[(((b << 1) | 1) << NF) | b2] * x[b].y;
+      nxt[(ah << NF) | b2] = val;
+    }
+  }
+}
+
 __device__ __forceinline__ int bitrev(int x, int w) {
   return (int)(__brev((unsigned)x) >> (32 - w));
 }
@@ -202,7 +260,13 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
       const int np = n << (ns.bits() - 1);
       const int hb = h + st.bb;                        // bits of (rows, b)
       const int low = (1 << hb) - 1;
-      if (t == sd && f.a_idx >= 0 && hb >= 5 && nf <= 1) {
+      if (K > 4 && t == sd && f.a_idx >= 0 && hb >= 5 && nf == 2 && (sd == 2 || sd == 3)) {
+        for (int s = 0; s < n; ++s) {
+          const int ib = s << (st.ab + hb), ob = s << (nf + hb);
+          if (sd == 3) data_column_a<T, 3, 2>(ws.mt + (s << nc), cur, nxt, ib, ob, hb, lane);
+          else data_column_a<T, 2, 2>(ws.mt + (s << nc), cur, nxt, ib, ob, hb, lane);
+        }
+      } else if (t == sd && f.a_idx >= 0 && hb >= 5 && nf <= 1) {
         // The data column, one coset at a time with its side message in
         // registers: each lane reads the 2^ab values in[a, rows, b] of its
         // (rows, b) once and writes all outputs (a2, v) of that group.
@@ -242,6 +306,20 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
             }
           }
         }
+      } else if (f.a_idx >= 0 && t < sd) {
+        // Record v as a's new low bit: out[(slot, a, a'), hbv, v] = [a' = v]
+        // in[(slot, a), hbv]; each input entry is read once and written to
+        // both of its output pairs.
+        const int nin = n << st.bits();
+        for (int e = lane; e < nin; e += 32) {
+          const T x = cur[e];
+          const int e0 = (((e >> hb) << 1) << hb) | (e & low);   // a' = 0
+          V2 o0, o1;
+          o0.x = x; o0.y = T(0);
+          o1.x = T(0); o1.y = x;
+          *reinterpret_cast<V2*>(nxt + 2 * e0) = o0;
+          *reinterpret_cast<V2*>(nxt + 2 * (e0 | (1 << hb))) = o1;
+        }
       } else
       for (int e2 = lane; e2 < np; e2 += 32) {
         const int a2f = e2 >> hb, hbv = e2 & low;      // a2f = (slot, a); (rows, b) is shared by in and out
@@ -279,6 +357,10 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
     // read and written as two pairs of adjacent entries.
     const int lnq = st.bits() - 2;                    // quads per coset, log2
     const int nq = n << lnq;
+    // k = 5, 6 (few warps per SM): each lane loads U quads before it stores
+    // any; a lane past the end repeats the last quad (same values, same
+    // addresses).
+    constexpr int U = K > 4 ? 2 : 1;
     for (int s = 0; s < h; ++s) {
       const int P = (h - 1 - s) + st.bb + 1;          // bit of the node's row in the index
       const int bitP = 1 << P;
@@ -299,40 +381,62 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
           if (check_first) {
             // out[c, r, d] = sum_l in[c, l, v=c] g[l^r][c^d]; rows bits P (c) and P-1 (qubit).
             const int Q = P - 1, bitQ = 1 << Q, lowq = (1 << (Q - 1)) - 1;
-            for (int g = lane; g < nq; g += 32) {
-              const int base = ((g >> (Q - 1)) << (Q + 1)) | ((g & lowq) << 1);
-              const int cb = (base >> P) & 1;
-              const T x0 = cur[base | cb];
-              const T x1 = cur[base | bitQ | cb];
-              // g[a][c ^ d] by selects (a dynamic index would put gt in local memory)
-              const T g00 = cb ? gt[1] : gt[0], g01 = cb ? gt[0] : gt[1];
-              const T g10 = cb ? gt[3] : gt[2], g11 = cb ? gt[2] : gt[3];
-              V2 o0, o1;
-              o0.x = x0 * g00 + x1 * g10;   // r = 0, d = 0
-              o0.y = x0 * g01 + x1 * g11;   // r = 0, d = 1
-              o1.x = x0 * g10 + x1 * g00;   // r = 1, d = 0
-              o1.y = x0 * g11 + x1 * g01;   // r = 1, d = 1
-              *reinterpret_cast<V2*>(nxt + base) = o0;
-              *reinterpret_cast<V2*>(nxt + (base | bitQ)) = o1;
+            for (int g0 = lane; g0 < nq; g0 += 32 * U) {
+              int bs[U], cbs[U];
+              T x0s[U], x1s[U];
+#pragma unroll
+              for (int u = 0; u < U; ++u) {
+                const int g = U == 1 ? g0 : min(g0 + 32 * u, nq - 1);
+                bs[u] = ((g >> (Q - 1)) << (Q + 1)) | ((g & lowq) << 1);
+                cbs[u] = (bs[u] >> P) & 1;
+                x0s[u] = cur[bs[u] | cbs[u]];
+                x1s[u] = cur[bs[u] | bitQ | cbs[u]];
+              }
+#pragma unroll
+              for (int u = 0; u < U; ++u) {
+                const int base = bs[u], cb = cbs[u];
+                const T x0 = x0s[u], x1 = x1s[u];
+                // g[a][c ^ d] by selects (a dynamic index would put gt in local memory)
+                const T g00 = cb ? gt[1] : gt[0], g01 = cb ? gt[0] : gt[1];
+                const T g10 = cb ? gt[3] : gt[2], g11 = cb ? gt[2] : gt[3];
+                V2 o0, o1;
+                o0.x = x0 * g00 + x1 * g10;   // r = 0, d = 0
+                o0.y = x0 * g01 + x1 * g11;   // r = 0, d = 1
+                o1.x = x0 * g10 + x1 * g00;   // r = 1, d = 0
+                o1.y = x0 * g11 + x1 * g01;   // r = 1, d = 1
+                *reinterpret_cast<V2*>(nxt + base) = o0;
+                *reinterpret_cast<V2*>(nxt + (base | bitQ)) = o1;
+              }
             }
           } else {
             // out[r, c, v] = [v = c] sum_{l,u} in[l, c, u] g[l^r][u^c]; qubit bit P, check bit P-1.
             const int cpos = P - 1;
-            for (int g = lane; g < nq; g += 32) {
-              const int base = ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
-              const int cb = (base >> cpos) & 1;
-              const V2 i0 = *reinterpret_cast<const V2*>(cur + base);          // in[0][u=0,1]
-              const V2 i1 = *reinterpret_cast<const V2*>(cur + (base | bitP)); // in[1][u=0,1]
-              // g[l ^ r][u ^ c]
-              const T g00 = cb ? gt[1] : gt[0], g01 = cb ? gt[0] : gt[1];
-              const T g10 = cb ? gt[3] : gt[2], g11 = cb ? gt[2] : gt[3];
-              const T r0 = i0.x * g00 + i0.y * g01 + i1.x * g10 + i1.y * g11;
-              const T r1 = i0.x * g10 + i0.y * g11 + i1.x * g00 + i1.y * g01;
-              V2 o0, o1;
-              o0.x = cb ? T(0) : r0; o0.y = cb ? r0 : T(0);
-              o1.x = cb ? T(0) : r1; o1.y = cb ? r1 : T(0);
-              *reinterpret_cast<V2*>(nxt + base) = o0;
-              *reinterpret_cast<V2*>(nxt + (base | bitP)) = o1;
+            for (int g0 = lane; g0 < nq; g0 += 32 * U) {
+              int bs[U];
+              V2 i0s[U], i1s[U];
+#pragma unroll
+              for (int u = 0; u < U; ++u) {
+                const int g = U == 1 ? g0 : min(g0 + 32 * u, nq - 1);
+                bs[u] = ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
+                i0s[u] = *reinterpret_cast<const V2*>(cur + bs[u]);          // in[0][u=0,1]
+                i1s[u] = *reinterpret_cast<const V2*>(cur + (bs[u] | bitP)); // in[1][u=0,1]
+              }
+#pragma unroll
+              for (int u = 0; u < U; ++u) {
+                const int base = bs[u];
+                const int cb = (base >> cpos) & 1;
+                const V2 i0 = i0s[u], i1 = i1s[u];
+                // g[l ^ r][u ^ c]
+                const T g00 = cb ? gt[1] : gt[0], g01 = cb ? gt[0] : gt[1];
+                const T g10 = cb ? gt[3] : gt[2], g11 = cb ? gt[2] : gt[3];
+                const T r0 = i0.x * g00 + i0.y * g01 + i1.x * g10 + i1.y * g11;
+                const T r1 = i0.x * g10 + i0.y * g11 + i1.x * g00 + i1.y * g01;
+                V2 o0, o1;
+                o0.x = cb ? T(0) : r0; o0.y = cb ? r0 : T(0);
+                o1.x = cb ? T(0) : r1; o1.y = cb ? r1 : T(0);
+                *reinterpret_cast<V2*>(nxt + base) = o0;
+                *reinterpret_cast<V2*>(nxt + (base | bitP)) = o1;
+              }
             }
           }
           __syncwarp();
@@ -346,17 +450,27 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
         // convolution with the 2 x 2 table g[alpha][beta].
         T gt[4];
         qubit_table(c, ni, nj, rowwise, gt);
-        for (int g = lane; g < nq; g += 32) {
-          const int base = ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
-          const V2 i0 = *reinterpret_cast<const V2*>(cur + base);          // in[0][0], in[0][1]
-          const V2 i1 = *reinterpret_cast<const V2*>(cur + (base | bitP)); // in[1][0], in[1][1]
-          V2 o0, o1;
-          o0.x = i0.x * gt[0] + i0.y * gt[1] + i1.x * gt[2] + i1.y * gt[3];
-          o0.y = i0.x * gt[1] + i0.y * gt[0] + i1.x * gt[3] + i1.y * gt[2];
-          o1.x = i0.x * gt[2] + i0.y * gt[3] + i1.x * gt[0] + i1.y * gt[1];
-          o1.y = i0.x * gt[3] + i0.y * gt[2] + i1.x * gt[1] + i1.y * gt[0];
-          *reinterpret_cast<V2*>(nxt + base) = o0;
-          *reinterpret_cast<V2*>(nxt + (base | bitP)) = o1;
+        for (int g0 = lane; g0 < nq; g0 += 32 * U) {
+          int bs[U];
+          V2 i0s[U], i1s[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int g = U == 1 ? g0 : min(g0 + 32 * u, nq - 1);
+            bs[u] = ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
+            i0s[u] = *reinterpret_cast<const V2*>(cur + bs[u]);          // in[0][0], in[0][1]
+            i1s[u] = *reinterpret_cast<const V2*>(cur + (bs[u] | bitP)); // in[1][0], in[1][1]
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const V2 i0 = i0s[u], i1 = i1s[u];
+            V2 o0, o1;
+            o0.x = i0.x * gt[0] + i0.y * gt[1] + i1.x * gt[2] + i1.y * gt[3];
+            o0.y = i0.x * gt[1] + i0.y * gt[0] + i1.x * gt[3] + i1.y * gt[2];
+            o1.x = i0.x * gt[2] + i0.y * gt[3] + i1.x * gt[0] + i1.y * gt[1];
+            o1.y = i0.x * gt[3] + i0.y * gt[2] + i1.x * gt[1] + i1.y * gt[0];
+            *reinterpret_cast<V2*>(nxt + bs[u]) = o0;
+            *reinterpret_cast<V2*>(nxt + (bs[u] | bitP)) = o1;
+          }
         }
         __syncwarp();
         T* tmp = cur; cur = nxt; nxt = tmp;
@@ -364,15 +478,24 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
       }
       if (interior) {
         // Interior check: a copy tensor over four legs, out[r][d] = [r = d] in[r][r].
-        for (int g = lane; g < nq; g += 32) {
-          const int base = ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
-          const V2 i0 = *reinterpret_cast<const V2*>(cur + base);
-          const V2 i1 = *reinterpret_cast<const V2*>(cur + (base | bitP));
-          V2 o0, o1;
-          o0.x = i0.x; o0.y = T(0);
-          o1.x = T(0); o1.y = i1.y;
-          *reinterpret_cast<V2*>(nxt + base) = o0;
-          *reinterpret_cast<V2*>(nxt + (base | bitP)) = o1;
+        for (int g0 = lane; g0 < nq; g0 += 32 * U) {
+          int bs[U];
+          T i0x[U], i1y[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int g = U == 1 ? g0 : min(g0 + 32 * u, nq - 1);
+            bs[u] = ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
+            i0x[u] = reinterpret_cast<const V2*>(cur + bs[u])->x;
+            i1y[u] = reinterpret_cast<const V2*>(cur + (bs[u] | bitP))->y;
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            V2 o0, o1;
+            o0.x = i0x[u]; o0.y = T(0);
+            o1.x = T(0); o1.y = i1y[u];
+            *reinterpret_cast<V2*>(nxt + bs[u]) = o0;
+            *reinterpret_cast<V2*>(nxt + (bs[u] | bitP)) = o1;
+          }
         }
         __syncwarp();
         T* tmp = cur; cur = nxt; nxt = tmp;
@@ -425,7 +548,14 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
       else ns.bb = st.bb - 1;
       const int nt = n << ns.bits();
       const int hah = st.ab + h;                       // bits of (a, rows)
-      if (t == sd && f.b_idx >= 0 && hah >= 5 && nf <= 1) {
+      if (K > 4 && t == sd && f.b_idx >= 0 && hah >= 5 && nf == 2 && (sd == 2 || sd == 3)) {
+        for (int s = 0; s < n; ++s) {
+          if (sd == 3) data_column_b<T, 3, 2>(ws.mb + (s << nc), cur, nxt, s << hah, hah, lane);
+          else data_column_b<T, 2, 2>(ws.mb + (s << nc), cur, nxt, s << hah, hah, lane);
+        }
+        __syncwarp();
+        T* tmp = cur; cur = nxt; nxt = tmp;
+      } else if (t == sd && f.b_idx >= 0 && hah >= 5 && nf <= 1) {
         // The data column, one coset at a time with its side message in
         // registers: each lane reads the 2^bb pairs in[a, rows, b, v] of its
         // (a, rows) once and writes all outputs b2 of that group.
