@@ -666,24 +666,24 @@ template <typename T> struct DeltaTerm;
 template <> struct DeltaTerm<double> {
   static __device__ __forceinline__ double eval(double x, double y, int width) {
     const double o = group_sum(x * y, width);
-    return 2.0 - 2.0 * o * o;
+    return fma(-2.0 * o, o, 2.0);
   }
   // A 64-entry vector held as entries lane and lane + 32.
   static __device__ __forceinline__ double eval2(double x0, double y0, double x1, double y1) {
     const double o = warp_sum(x0 * y0 + x1 * y1);
-    return 2.0 - 2.0 * o * o;
+    return fma(-2.0 * o, o, 2.0);
   }
 };
 template <> struct DeltaTerm<float> {
   static __device__ __forceinline__ float eval(float x, float y, int width) {
     const float t = x - y;
     const float s = group_sum(t * t, width);
-    return s * (2.f - 0.5f * s);
+    return s * fmaf(-0.5f, s, 2.f);
   }
   static __device__ __forceinline__ float eval2(float x0, float y0, float x1, float y1) {
     const float t0 = x0 - y0, t1 = x1 - y1;
     const float s = warp_sum(t0 * t0 + t1 * t1);
-    return s * (2.f - 0.5f * s);
+    return s * fmaf(-0.5f, s, 2.f);
   }
 };
 
@@ -713,8 +713,8 @@ __device__ __forceinline__ void fused_update(const FusedWS<T>& ws, T* msgs, int 
     const T y0 = *old0, y1 = *old1;
     T nrm = xsqrt(warp_sum(x0 * x0 + x1 * x1));
     T inv = nrm > T(0) ? T(1) / nrm : T(0);
-    x0 = one_m_eta * (x0 * inv) + eta * y0;
-    x1 = one_m_eta * (x1 * inv) + eta * y1;
+    x0 = fma(one_m_eta, x0 * inv, eta * y0);
+    x1 = fma(one_m_eta, x1 * inv, eta * y1);
     nrm = xsqrt(warp_sum(x0 * x0 + x1 * x1));
     inv = nrm > T(0) ? T(1) / nrm : T(0);
     x0 *= inv;
@@ -736,7 +736,7 @@ __device__ __forceinline__ void fused_update(const FusedWS<T>& ws, T* msgs, int 
     T x = on ? ws.s0[e] : T(0);
     const T y = on ? *old : T(0);
     x = group_normalize(x, width);
-    x = one_m_eta * x + eta * y;
+    x = fma(one_m_eta, x, eta * y);
     x = group_normalize(x, width);
     const T term = DeltaTerm<T>::eval(x, y, width);
     if (on) {
