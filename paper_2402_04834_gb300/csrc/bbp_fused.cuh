@@ -311,14 +311,44 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
         // in[(slot, a), hbv]; each input entry is read once and written to
         // both of its output pairs.
         const int nin = n << st.bits();
-        for (int e = lane; e < nin; e += 32) {
-          const T x = cur[e];
-          const int e0 = (((e >> hb) << 1) << hb) | (e & low);   // a' = 0
-          V2 o0, o1;
-          o0.x = x; o0.y = T(0);
-          o1.x = T(0); o1.y = x;
-          *reinterpret_cast<V2*>(nxt + 2 * e0) = o0;
-          *reinterpret_cast<V2*>(nxt + 2 * (e0 | (1 << hb))) = o1;
+        constexpr int U = K > 4 ? 2 : 1;               // entries per lane and step (loads first)
+        for (int e00 = lane; e00 < nin; e00 += 32 * U) {
+          T xs[U];
+          int es[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            es[u] = U == 1 ? e00 : min(e00 + 32 * u, nin - 1);
+            xs[u] = cur[es[u]];
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int e = es[u];
+            const int e0 = (((e >> hb) << 1) << hb) | (e & low);   // a' = 0
+            V2 o0, o1;
+            o0.x = xs[u]; o0.y = T(0);
+            o1.x = T(0); o1.y = xs[u];
+            *reinterpret_cast<V2*>(nxt + 2 * e0) = o0;
+            *reinterpret_cast<V2*>(nxt + 2 * (e0 | (1 << hb))) = o1;
+          }
+        }
+      } else if (K > 4 && f.a_idx >= 0 && t > sd) {
+        // Move a's top bit into v: out[(slot, a), hbv, v] = in[(slot, v, a), hbv]
+        // (two entries per lane and step, loads first).
+        const int top = 1 << (st.ab - 1);
+        for (int e20 = lane; e20 < np; e20 += 64) {
+          V2 os[2];
+          int es[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int e2 = min(e20 + 32 * u, np - 1);
+            const int a2f = e2 >> hb, hbv = e2 & low;
+            const int ai = ((a2f >> ns.ab) << st.ab) | (a2f & ((1 << ns.ab) - 1));
+            os[u].x = cur[(ai << hb) | hbv];
+            os[u].y = cur[((ai | top) << hb) | hbv];
+            es[u] = e2;
+          }
+#pragma unroll
+          for (int u = 0; u < 2; ++u) *reinterpret_cast<V2*>(nxt + 2 * es[u]) = os[u];
         }
       } else
       for (int e2 = lane; e2 < np; e2 += 32) {
@@ -360,7 +390,7 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
     // k = 5, 6 (few warps per SM): each lane loads U quads before it stores
     // any; a lane past the end repeats the last quad (same values, same
     // addresses).
-    constexpr int U = K > 4 ? 2 : 1;
+    constexpr int U = K > 4 ? 4 : 1;
     for (int s = 0; s < h; ++s) {
       const int P = (h - 1 - s) + st.bb + 1;          // bit of the node's row in the index
       const int bitP = 1 << P;
@@ -593,6 +623,25 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
               nxt[ah] = val;
             }
           }
+        }
+        __syncwarp();
+        T* tmp = cur; cur = nxt; nxt = tmp;
+      } else if (K > 4 && f.b_idx >= 0 && t > sd) {
+        // Close v against b's top bit: out[(slot, a, rows), b] = in[.., (0, b), v = 0]
+        // + in[.., (1, b), v = 1] (two outputs per lane and step, loads first).
+        const int top = 1 << (st.bb - 1);
+        for (int e0 = lane; e0 < nt; e0 += 64) {
+          T vs[2];
+          int es[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int e = min(e0 + 32 * u, nt - 1);
+            const int b2 = e & ((1 << ns.bb) - 1), ah = e >> ns.bb;
+            vs[u] = cur[((ah << st.bb) | b2) << 1] + cur[(((ah << st.bb) | top | b2) << 1) | 1];
+            es[u] = e;
+          }
+#pragma unroll
+          for (int u = 0; u < 2; ++u) nxt[es[u]] = vs[u];
         }
         __syncwarp();
         T* tmp = cur; cur = nxt; nxt = tmp;
