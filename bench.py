@@ -214,6 +214,96 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+MIXED_DISTANCES = (7, 9, 13, 17, 21)
+
+
+def mixed_batch_leg(args, dev, pkg):
+    """Batching: ``args.mixed_batch`` syndromes of distances drawn uniformly
+    from MIXED_DISTANCES (p = 0.10, k = 4) in one persistent launch, launch
+    shape from the autotuner, captured in a CUDA graph and replayed; against
+    one launch per distance on the same syndromes.  Group j (distance
+    MIXED_DISTANCES[j]) holds consecutive shots of seed workload_seed(3, j);
+    the batch is packed in a seeded random order."""
+    import torch
+
+    from paper_2402_04834_gb300 import autotune
+    from paper_2402_04834_gb300.decoder import decode_mixed, pack_mixed
+    n = args.mixed_batch
+    rng = np.random.default_rng(synth.workload_seed(3, 9))
+    counts = np.bincount(rng.integers(0, len(MIXED_DISTANCES), size=n), minlength=len(MIXED_DISTANCES))
+    shots, ds = [], []
+    for j, (d, c) in enumerate(zip(MIXED_DISTANCES, counts)):
+        if c:
+            _, _, S = synth.sample_syndromes(synth.workload_seed(3, j), 0, int(c), d, P_NOISE)
+            shots += list(S)
+            ds += [d] * int(c)
+    perm = rng.permutation(n)
+    shots = [shots[i] for i in perm]
+    ds = np.asarray(ds)[perm]
+    packed, offsets, d_of = pack_mixed(shots, device=dev)
+    prm = pkg.DecoderParams(d=0, k=K_BLOCK, p=P_NOISE, max_iter=MAX_ITER, eta=ETA, delta0=DELTA0, delta1=DELTA1,
+                            precision="fp32", algorithm="fused")
+    prm, table = autotune.tune_mixed(packed, offsets, d_of, prm, shapes=((8, 4), (8, 2), (4, 2), (4, 4)),
+                                     ctas=(0, 1, 2))
+    order = torch.argsort(d_of, descending=True, stable=True).to(torch.int32)
+    d_max = int(max(MIXED_DISTANCES))
+    counter = torch.empty(256, dtype=torch.uint8, device=dev)
+    out = decode_mixed(packed, offsets, d_of, prm, counter=counter, order=order, d_max=d_max)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            decode_mixed(packed, offsets, d_of, prm, counter=counter, order=order, d_max=d_max, out=out,
+                         stream=side)
+    torch.cuda.current_stream(dev).wait_stream(side)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    reps, ms = 3, 0.0
+    for i in range(reps):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.replay()
+        b.record()
+        torch.cuda.synchronize()
+        ms += a.elapsed_time(b)
+    mixed_val = reps * n / (ms / 1e3)
+    # One launch per distance (default shapes), the same syndromes.
+    groups = [(d, np.nonzero(ds == d)[0]) for d in MIXED_DISTANCES]
+    dev_groups = [(d, idx, torch.from_numpy(np.stack([shots[i] for i in idx])).to(dev)) for d, idx in groups
+                  if len(idx)]
+    outs = {}
+    for d, idx, S in dev_groups:
+        outs[d] = pkg.decode(S, pkg.DecoderParams(**{**prm.__dict__, "d": d, "warps": 0, "cosets": 0,
+                                                     "ctas_per_sm": 0}))
+    torch.cuda.synchronize()
+    ms2 = 0.0
+    for i in range(reps):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for d, idx, S in dev_groups:
+            pkg.decode(S, pkg.DecoderParams(**{**prm.__dict__, "d": d, "warps": 0, "cosets": 0, "ctas_per_sm": 0}),
+                       out=outs[d])
+        b.record()
+        torch.cuda.synchronize()
+        ms2 += a.elapsed_time(b)
+    per_d_val = reps * n / (ms2 / 1e3)
+    dec = out["decision"].cpu().numpy()
+    agree = float(np.mean(np.concatenate([dec[idx] == outs[d]["decision"].cpu().numpy()
+                                          for d, idx, _ in dev_groups])))
+    return {"value": mixed_val, "unit": "syndromes/s", "batch": n, "distances": list(MIXED_DISTANCES),
+            "counts": [int(c) for c in counts], "p": P_NOISE, "precision": "fp32", "algorithm": "fused",
+            "launch": "one persistent launch, largest distance first, replayed from a CUDA graph",
+            "shape": {"warps": prm.warps, "cosets": prm.cosets, "ctas_per_sm": prm.ctas_per_sm},
+            "autotune_candidates": len(table),
+            "mean_iters": float(out["iters"].double().mean().item()),
+            "per_distance_launches": {"value": per_d_val, "unit": "syndromes/s", "launches": len(dev_groups)},
+            "speedup_vs_per_distance": mixed_val / per_d_val, "decision_agreement_with_per_distance": agree}
+
+
 def reference_arm(args):
     """CPU FP64 oracle timed on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -407,6 +497,7 @@ def ours(args):
                 "decision_agreement_with_headline": agree, "headline_speedup": value / world / val}
 
     cold = leg("fused", args.precision, B) if learned else None
+    mixed = mixed_batch_leg(args, dev, pkg) if args.mixed_batch > 0 and args.algorithm == "fused" else None
     fp64_mps = leg("mps", "fp64", args.fp64_batch)
     legs = {"fp64_fused": leg("fused", "fp64", args.other_batch),
             "fp32_mps": leg("mps", "fp32", args.other_batch // 4)}
@@ -487,7 +578,8 @@ def ours(args):
                 "d2h_bytes_per_step": int(B * (1 + 32))},
         "gpu_launches": per_step * args.steps,
         "roofline": roof, "roofline_network": roof_mlp, "cpu_baseline": cpu,
-        "cold_start": cold, "plain_fp64_gpu": fp64_mps, "other_paths": legs, "learned_warm_start": learned_info,
+        "cold_start": cold, "plain_fp64_gpu": fp64_mps, "other_paths": legs, "mixed_batch": mixed,
+        "learned_warm_start": learned_info,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -505,6 +597,8 @@ def main():
     ap.add_argument("--algorithm", default="fused", choices=["fused", "mps"])
     ap.add_argument("--fp64-batch", type=int, default=512)
     ap.add_argument("--other-batch", type=int, default=4096)
+    ap.add_argument("--mixed-batch", type=int, default=4096,
+                    help="syndromes of the mixed-distance batching leg (0 skips it)")
     ap.add_argument("--cpu-procs", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-warm", dest="warm", action="store_false")

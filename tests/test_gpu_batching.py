@@ -93,6 +93,37 @@ def test_cuda_graph_capture_replays_the_decode(dev):
             assert torch.equal(out[key], ref[key]), key
 
 
+def test_cuda_graph_capture_replays_the_mixed_decode(dev):
+    # The persistent mixed-distance launch (counter reset, kernel, decision)
+    # captured once and replayed on new syndromes of the same shapes.
+    p = 0.1
+    ds, shots1 = mixed_batch(64, [5, 7, 9, 11], p, 61)
+    shots2 = [synth.sample_syndromes(62, b, 1, int(d), p)[2][0] for b, d in enumerate(ds)]
+    packed, offsets, d_of = pack_mixed(shots1, device=dev)
+    packed2, _, _ = pack_mixed(shots2, device=dev)
+    prm = pkg.DecoderParams(d=0, k=4, p=p, max_iter=12, delta0=1e-4, precision="fp32", algorithm="fused")
+    order = torch.argsort(d_of, descending=True, stable=True).to(torch.int32)
+    counter = torch.empty(256, dtype=torch.uint8, device=dev)
+    out = decode_mixed(packed, offsets, d_of, prm, counter=counter, order=order, d_max=11)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(g, stream=stream):
+            decode_mixed(packed, offsets, d_of, prm, counter=counter, order=order, d_max=11, out=out, stream=stream)
+    torch.cuda.current_stream().wait_stream(stream)
+    src = packed.clone()
+    for new in (packed2, src):
+        packed.copy_(new)
+        g.replay()
+        torch.cuda.synchronize()
+        ref = decode_mixed(new, offsets, d_of, prm)
+        torch.cuda.synchronize()
+        for key in ("logp", "delta", "iters", "flags", "decision"):
+            assert torch.equal(out[key], ref[key]), key
+
+
 def test_autotuned_shapes_give_identical_results(dev):
     d, p = 9, 0.1
     _, _, S = synth.sample_syndromes(41, 0, 256, d, p)
