@@ -180,6 +180,22 @@ int bbp_sample(uint64_t seed, int64_t first_shot, int64_t B, int32_t d, double p
                void* stream);
 
 /*
+ * bbp_pure_error -- the pure error f_s of each syndrome (Algorithm 1, first
+ * step: "a Pauli string that produces the syndrome"; the construction is
+ * this library's reading): for every flagged site check A_(r,c) an X string
+ * on the horizontal edges of row r right of it, for every flagged plaquette
+ * B_(r,j) a Z string on the horizontal edges of column j below it.  f_s
+ * vanishes on the supports of both logicals; s(f_s) = s.
+ *   d           distance, 2 <= d <= 64
+ *   syndromes   device [B][m] bytes 0/1 (order above)
+ *   fx, fz      device [B][n] bytes, caller-owned: X and Z bit planes, qubits
+ *               in the order of bbp_sample (grid row-major over i + j even)
+ * Asynchronous on ``stream``.  Errors: BBP_EINVAL for a bad d or B or a null
+ * pointer (B = 0 is a no-op), BBP_ECUDA.
+ */
+int bbp_pure_error(int32_t d, const uint8_t* syndromes, int64_t B, uint8_t* fx, uint8_t* fz, void* stream);
+
+/*
  * bbp_decode_batch_static -- the decode of bbp_decode_batch without any
  * allocation, for callers that cannot allocate device memory: real-time
  * loops that must not take the allocator's locks or fail for lack of memory

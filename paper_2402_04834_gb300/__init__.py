@@ -6,7 +6,7 @@ device memory and streams through PyTorch.
 """
 
 from ._lib import FP32, FP64, FUSED_SHAPES, FUSED_SHAPES_K6, BbpError, DecoderParams, lib, workspace_bytes  # noqa: F401
-from .decoder import Workspace, decode, decode_host, sample  # noqa: F401
+from .decoder import Workspace, decode, decode_host, pure_error, sample  # noqa: F401
 
-__all__ = ["DecoderParams", "decode", "decode_host", "sample", "workspace_bytes", "Workspace",
+__all__ = ["DecoderParams", "decode", "decode_host", "pure_error", "sample", "workspace_bytes", "Workspace",
            "lib", "BbpError", "FP32", "FP64"]

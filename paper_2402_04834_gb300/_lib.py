@@ -22,7 +22,8 @@ FLAG_UNTRUSTED, FLAG_OVERLAP, FLAG_BLOCK, FLAG_NONFINITE = 1, 2, 4, 8
 SYMBOLS = ("bbp_workspace_bytes", "bbp_decode_batch", "bbp_decode_batch_host", "bbp_sample",
            "bbp_strerror", "bbp_version", "bbp_decode_batch_static", "bbp_message_count",
            "bbp_message_features", "bbp_warm_param_count", "bbp_warm_workspace_bytes", "bbp_warm_infer",
-           "bbp_warm_train_step", "bbp_decode_batch_ex", "bbp_decode_mixed", "bbp_warm_infer_syndromes")
+           "bbp_warm_train_step", "bbp_decode_batch_ex", "bbp_decode_mixed", "bbp_warm_infer_syndromes",
+           "bbp_pure_error")
 WARM_F, WARM_H, WARM_O, WARM_MAX_ROWS = 256, 256, 16, 4194240
 WARM_STATUS_OFFSET = 270336       # int32 status word of bbp_warm_infer in its workspace
 WARM_INFER_WS_BYTES = 270592      # workspace of bbp_warm_infer, for any N
@@ -119,6 +120,8 @@ def lib():
         L.bbp_decode_batch_static.restype = ctypes.c_int
         L.bbp_sample.argtypes = [ctypes.c_uint64, i64, i64, i32, ctypes.c_double, vp, vp, vp, vp, vp]
         L.bbp_sample.restype = ctypes.c_int
+        L.bbp_pure_error.argtypes = [i32, vp, i64, vp, vp, vp]
+        L.bbp_pure_error.restype = ctypes.c_int
         L.bbp_strerror.argtypes = [ctypes.c_int]
         L.bbp_strerror.restype = ctypes.c_char_p
         L.bbp_version.argtypes = []

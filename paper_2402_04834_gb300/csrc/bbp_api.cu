@@ -232,4 +232,12 @@ int bbp_sample(uint64_t seed, int64_t first_shot, int64_t B, int32_t d, double p
   return e == cudaSuccess ? BBP_OK : BBP_ECUDA;
 }
 
+int bbp_pure_error(int32_t d, const uint8_t* syndromes, int64_t B, uint8_t* fx, uint8_t* fz, void* stream) {
+  if (d < 2 || d > 64 || B < 0 || B > (int64_t(1) << 31) - 1) return BBP_EINVAL;
+  if (B == 0) return BBP_OK;
+  if (!syndromes || !fx || !fz) return BBP_EINVAL;
+  const cudaError_t e = bbp::launch_pure_error(d, syndromes, B, fx, fz, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? BBP_OK : BBP_ECUDA;
+}
+
 }  // extern "C"

@@ -68,6 +68,7 @@ cudaError_t launch_fused_mixed_f32(const LaunchArgs& a, const MixedLaunch& mx, i
 cudaError_t launch_decode_f64(const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_decode_f32(const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_decide(const LaunchArgs& a, cudaStream_t st);
+cudaError_t launch_pure_error(int d, const uint8_t* synd, long long B, uint8_t* fx, uint8_t* fz, cudaStream_t st);
 cudaError_t launch_sample(uint64_t seed, long long first_shot, long long B, int d,
                           unsigned long long id_threshold, uint8_t* ex, uint8_t* ez,
                           uint8_t* synd, int8_t* true_class, cudaStream_t st);

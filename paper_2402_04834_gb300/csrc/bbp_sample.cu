@@ -1,5 +1,6 @@
 // Seeded depolarizing sampler on the device (Sec. IV workload): errors,
-// syndromes and the coset index of each error relative to the pure error.
+// syndromes and the coset index of each error relative to the pure error;
+// and the pure error f_s of given syndromes (Algorithm 1, first step).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -76,6 +77,40 @@ cudaError_t launch_sample(uint64_t seed, long long first_shot, long long B, int 
     if (e != cudaSuccess) return e;
   }
   sample_kernel<<<(unsigned)B, 128, smem, st>>>(seed, first_shot, d, id_threshold, ex, ez, synd, true_class);
+  return cudaGetLastError();
+}
+
+// Pure error f_s (Algorithm 1 asks for any Pauli with syndrome s; the
+// choice here): for every flagged site check A_(r,c) an X string on the
+// horizontal edges h(r, c+1 .. d-1) to the right boundary, for every flagged
+// plaquette B_(r,j) a Z string on h(r+1 .. d-1, j) down to the bottom.
+// Horizontal-edge qubit h(r, cc) therefore carries x = XOR of A_(r,c) over
+// c < cc and z = XOR of B_(r2,cc) over r2 < r; vertical-edge qubits carry
+// nothing.  One thread per (syndrome, qubit), qubits in sampler order.
+__global__ void pure_error_kernel(int d, const uint8_t* synd, long long B, uint8_t* fx, uint8_t* fz) {
+  const int n = d * d + (d - 1) * (d - 1), m = 2 * d * (d - 1);
+  const long long total = B * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long b = t / n;
+    const int q = (int)(t - b * n);
+    const int pair = q / (2 * d - 1), rem = q % (2 * d - 1);
+    uint8_t x = 0, z = 0;
+    if (rem < d) {                                   // horizontal edge h(pair, rem)
+      const uint8_t* s = synd + b * m;
+      for (int c = 0; c < rem; ++c) x ^= s[pair * (d - 1) + c];
+      for (int r2 = 0; r2 < pair; ++r2) z ^= s[d * (d - 1) + r2 * d + rem];
+    }
+    fx[t] = x;
+    fz[t] = z;
+  }
+}
+
+cudaError_t launch_pure_error(int d, const uint8_t* synd, long long B, uint8_t* fx, uint8_t* fz, cudaStream_t st) {
+  const long long total = B * (long long)(d * d + (d - 1) * (d - 1));
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;          // grid-stride beyond 64 blocks per SM
+  pure_error_kernel<<<(unsigned)blocks, 256, 0, st>>>(d, synd, B, fx, fz);
   return cudaGetLastError();
 }
 

@@ -89,6 +89,16 @@ def decode_host(syndromes: np.ndarray, prm: DecoderParams, workspace: Workspace 
     return out
 
 
+def pure_error(syndromes: torch.Tensor, d: int, stream=None):
+    """Pure error f_s of each syndrome on the device (Algorithm 1): (fx, fz), [B][n] uint8."""
+    B = syndromes.shape[0]
+    n = d * d + (d - 1) ** 2
+    fx = torch.empty(B, n, dtype=torch.uint8, device=syndromes.device)
+    fz = torch.empty(B, n, dtype=torch.uint8, device=syndromes.device)
+    check(lib().bbp_pure_error(d, _ptr(syndromes), B, _ptr(fx), _ptr(fz), _stream(stream)))
+    return fx, fz
+
+
 def sample(seed: int, first_shot: int, B: int, d: int, p: float, device="cuda", with_errors=True,
            stream=None):
     """Seeded depolarizing errors and syndromes on the device (Sec. IV workload)."""

@@ -106,6 +106,16 @@ def test_decode_null_pointers_rejected_before_any_cuda_call(L):
     assert L.bbp_sample(1, 0, 4, 1, 0.1, None, None, None, None, None) == -1
 
 
+def test_pure_error_arguments_checked_on_the_host(L):
+    big = ctypes.c_void_p(256)                      # never dereferenced: every call below returns first
+    assert L.bbp_pure_error(1, big, 4, big, big, None) == -1
+    assert L.bbp_pure_error(65, big, 4, big, big, None) == -1
+    assert L.bbp_pure_error(5, None, 4, big, big, None) == -1
+    assert L.bbp_pure_error(5, big, 4, None, big, None) == -1
+    assert L.bbp_pure_error(5, big, -1, big, big, None) == -1
+    assert L.bbp_pure_error(5, None, 0, None, None, None) == 0
+
+
 def test_empty_batch_is_a_no_op(L):
     c = pkg.DecoderParams(d=5, k=3, D=4).c()
     assert L.bbp_decode_batch(None, 0, ctypes.byref(c), None, None, None, None, None, None, 0, None) == 0
