@@ -105,12 +105,16 @@ def run_oracle_sample(first_shot: int, n: int, procs: int, algorithm: str):
 
 
 def fused_flops(d: int, k: int):
-    """Arithmetic of the fused kernel (multiply-adds count 2), per coset.
+    """Algorithmic arithmetic of the fused-block update (multiply-adds count 2), per coset.
 
     Returns (per BP iteration, read-out): the node-by-node contraction of
-    every block towards each neighbour (side-message data columns, four-term
-    node updates, copy-out sums), normalisation, damping and overlaps, then
-    the Lemma 1 read-out.  Mirrors the loop structure of the kernel."""
+    every block towards each neighbour in the order the kernel takes it
+    (side-message data columns, node updates, copy-out sums), normalisation,
+    damping and overlaps, then the Lemma 1 read-out.  Every node, qubit or
+    check, counts as a dense 2x2x2x2 tensor (four multiply-adds per output
+    entry): the count of the contraction, not of the kernel's instructions,
+    which skip the zeros of the check nodes' copy tensors (moves and merged
+    check/qubit pairs), so the kernel executes fewer flops than this."""
     W = 2 * d - 1
     rng = [(a, min(a + k, W)) for a in range(0, W, k)]
     nb = len(rng)
