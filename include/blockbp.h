@@ -254,6 +254,38 @@ int bbp_message_count(const bbp_params* prm, int32_t* M);
 int bbp_message_features(const uint8_t* syndromes, int64_t B, const bbp_params* prm, float* feats,
                          int32_t* lens, void* stream);
 
+/*
+ * bbp_message_classes -- which feature rows of a syndrome are distinct.  The
+ * four coset frames differ only on the horizontal edges of grid row 0 and
+ * column 0 (the logical strings), so a message whose 7 x 7 window holds
+ * none of them has the same features, hence the same proposal, in all four
+ * cosets.  Host only, no CUDA call.
+ *   uniq_of  host [4][M] int32: distinct row of (coset, message)
+ *   row_key  host [4*M] int32 (capacity): row u stands for (coset, message)
+ *            = (row_key[u] / M, row_key[u] % M); coset 0 for shared rows
+ *   n_rows   the number U of distinct rows (d = 11, k = 4: 210 of 480)
+ * Requires k <= 4.  Errors: BBP_EINVAL.
+ */
+int bbp_message_classes(const bbp_params* prm, int32_t* uniq_of, int32_t* row_key, int32_t* n_rows);
+
+/*
+ * bbp_message_features_rows -- bbp_message_features for the U listed rows of
+ * every syndrome only: feats [B*U][BBP_WARM_FEATURES] (row b*U + u is
+ * (coset, message) = row_key[u] of syndrome b, bit for bit the row that
+ * bbp_message_features writes for it), lens [B*U] or NULL.  row_key is
+ * device memory (from bbp_message_classes).  Asynchronous on ``stream``.
+ */
+int bbp_message_features_rows(const uint8_t* syndromes, int64_t B, const bbp_params* prm, const int32_t* row_key,
+                              int32_t U, float* feats, int32_t* lens, void* stream);
+
+/*
+ * bbp_expand_rows -- messages [B][4][M][16] from distinct rows [B*U][16]:
+ * msgs[b][c][i] = rows[b*U + uniq_of[c*M + i]] (uniq_of device, from
+ * bbp_message_classes).  Asynchronous on ``stream``.
+ */
+int bbp_expand_rows(const float* rows, int64_t B, int32_t U, const int32_t* uniq_of, int32_t M, float* msgs,
+                    void* stream);
+
 /* Parameters of the network: W1 (F x H), b1, W2 (H x H), b2, W3 (H x O), b3, row-major. */
 int bbp_warm_param_count(void);
 

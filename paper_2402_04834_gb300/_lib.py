@@ -23,7 +23,7 @@ SYMBOLS = ("bbp_workspace_bytes", "bbp_decode_batch", "bbp_decode_batch_host", "
            "bbp_strerror", "bbp_version", "bbp_decode_batch_static", "bbp_message_count",
            "bbp_message_features", "bbp_warm_param_count", "bbp_warm_workspace_bytes", "bbp_warm_infer",
            "bbp_warm_train_step", "bbp_decode_batch_ex", "bbp_decode_mixed", "bbp_warm_infer_syndromes",
-           "bbp_pure_error")
+           "bbp_pure_error", "bbp_message_classes", "bbp_message_features_rows", "bbp_expand_rows")
 WARM_F, WARM_H, WARM_O, WARM_MAX_ROWS = 256, 256, 16, 4194240
 WARM_STATUS_OFFSET = 270336       # int32 status word of bbp_warm_infer in its workspace
 WARM_INFER_WS_BYTES = 270592      # workspace of bbp_warm_infer, for any N
@@ -122,6 +122,12 @@ def lib():
         L.bbp_sample.restype = ctypes.c_int
         L.bbp_pure_error.argtypes = [i32, vp, i64, vp, vp, vp]
         L.bbp_pure_error.restype = ctypes.c_int
+        L.bbp_message_classes.argtypes = [P, vp, vp, ctypes.POINTER(i32)]
+        L.bbp_message_classes.restype = ctypes.c_int
+        L.bbp_message_features_rows.argtypes = [vp, i64, P, vp, i32, vp, vp, vp]
+        L.bbp_message_features_rows.restype = ctypes.c_int
+        L.bbp_expand_rows.argtypes = [vp, i64, i32, vp, i32, vp, vp]
+        L.bbp_expand_rows.restype = ctypes.c_int
         L.bbp_strerror.argtypes = [ctypes.c_int]
         L.bbp_strerror.restype = ctypes.c_char_p
         L.bbp_version.argtypes = []

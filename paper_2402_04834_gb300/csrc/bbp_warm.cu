@@ -70,6 +70,67 @@ __global__ void features_kernel(Geo g, int M, double p, const uint8_t* synd, flo
   }
 }
 
+// Features of listed rows: row u of syndrome b is (coset, message) =
+// row_key[u] = coset * M + message; one CTA per syndrome holding the four
+// coset frames.  Row (b, u) is written at b * U + u.
+__global__ void features_rows_kernel(Geo g, int M, double p, const uint8_t* synd, const int32_t* row_key, int U,
+                                     float* feats, int32_t* lens) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int W = g.W, WW = W * W, d = g.d, nb = g.nb;
+  const int m = 2 * d * (d - 1);
+  uint8_t* s = smem;
+  uint8_t* frames = smem + align_up(m, 16);
+  int16_t* meta = reinterpret_cast<int16_t*>(frames + align_up(4 * WW, 16));
+  const long long shot = blockIdx.x;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) s[i] = synd[shot * m + i];
+  __syncthreads();
+  for (int e = threadIdx.x; e < 4 * WW; e += blockDim.x) {
+    const int c = e / WW, ij = e - c * WW;
+    frames[e] = frame_byte(s, d, ij / W, ij % W, c);
+  }
+  if (threadIdx.x == 0) {
+    int idx = 0;
+    for (int I = 0; I < nb; ++I)
+      for (int J = 0; J < nb; ++J)
+        for (int dir = 0; dir < 4; ++dir)
+          if (g.has(I, J, dir)) meta[idx++] = (int16_t)((I * nb + J) * 4 + dir);
+  }
+  __syncthreads();
+  const float p10 = (float)(10.0 * p);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int u = warp; u < U; u += nw) {
+    const int key = row_key[u];
+    const int coset = key / M, idx = key - coset * M;
+    const int mk = meta[idx];
+    const MsgGeo f = msg_geo(g, mk / 4 / nb, (mk / 4) % nb, mk & 3);
+    const uint8_t* frame = frames + coset * WW;
+    float* out = feats + (shot * U + u) * F;
+    for (int pos = lane; pos < 49; pos += 32) {
+      float c[5];
+      window_node(g, f, pos, frame, s, c);
+#pragma unroll
+      for (int ch = 0; ch < 5; ++ch) out[ch * 49 + pos] = c[ch];
+    }
+    if (lane < F - 245) out[245 + lane] = tail_feature(f, 245 + lane, p10);
+    if (lane == 0 && lens) lens[shot * U + u] = 1 << f.h;
+  }
+}
+
+// msgs[b][c][idx] = rows[b][uniq_of[c * M + idx]], 16 floats each (four
+// float4 per message, one per thread).
+__global__ void expand_rows_kernel(const float4* rows, long long B, int U, const int32_t* uniq_of, int M,
+                                   float4* msgs) {
+  const long long total = B * 4 * M * 4;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(t & 3);
+    const long long r = t >> 2;                       // (b, c, idx)
+    const long long b = r / (4 * M);
+    const int cm = (int)(r - b * 4 * M);
+    msgs[t] = rows[(b * U + uniq_of[cm]) * 4 + q];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // GEMM: C[M x N] = op(A) op(B) (+ bias) with optional GELU, FP32.
 // op(A) is A (M x K, row-major, lda) or A^T with A stored K x M; op(B) is B
@@ -255,6 +316,64 @@ int bbp_message_features(const uint8_t* syndromes, int64_t B, const bbp_params* 
   const int smem = align_up(m, 16) + align_up(g.W * g.W, 16) + align_up(2 * M, 16);
   features_kernel<<<(unsigned)(B * 4), 256, smem, static_cast<cudaStream_t>(stream)>>>(g, M, prm->p, syndromes,
                                                                                       feats, lens);
+  return cudaGetLastError() == cudaSuccess ? BBP_OK : BBP_ECUDA;
+}
+
+int bbp_message_classes(const bbp_params* prm, int32_t* uniq_of, int32_t* row_key, int32_t* n_rows) {
+  if (!prm || !uniq_of || !row_key || !n_rows || prm->d < 2 || prm->d > 64 || prm->k < 1 || prm->k > kFusedK)
+    return BBP_EINVAL;
+  const Geo g = make_geo(prm->d, prm->k);
+  int M = 0, ae = 0;
+  count_messages(g, 1, &M, &ae);
+  int idx = 0, u = 0;
+  for (int I = 0; I < g.nb; ++I)
+    for (int J = 0; J < g.nb; ++J)
+      for (int dir = 0; dir < 4; ++dir) {
+        if (!g.has(I, J, dir)) continue;
+        if (window_sees_logicals(g, msg_geo(g, I, J, dir))) {
+          for (int c = 0; c < 4; ++c) {
+            uniq_of[c * M + idx] = u;
+            row_key[u++] = c * M + idx;
+          }
+        } else {
+          for (int c = 0; c < 4; ++c) uniq_of[c * M + idx] = u;
+          row_key[u++] = idx;                          // coset 0 stands for all four
+        }
+        ++idx;
+      }
+  *n_rows = u;
+  return BBP_OK;
+}
+
+int bbp_message_features_rows(const uint8_t* syndromes, int64_t B, const bbp_params* prm, const int32_t* row_key,
+                              int32_t U, float* feats, int32_t* lens, void* stream) {
+  if (!prm || !syndromes || !row_key || !feats || B < 0 || prm->d < 2 || prm->d > 64 || prm->k < 1 ||
+      prm->k > kFusedK || U < 0)
+    return BBP_EINVAL;
+  if (B == 0 || U == 0) return BBP_OK;
+  const Geo g = make_geo(prm->d, prm->k);
+  int M = 0, ae = 0;
+  count_messages(g, 1, &M, &ae);
+  if (U > 4 * M) return BBP_EINVAL;
+  const int m = 2 * g.d * (g.d - 1);
+  const int smem = align_up(m, 16) + align_up(4 * g.W * g.W, 16) + align_up(2 * M, 16);
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(features_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return BBP_ECUDA;
+  features_rows_kernel<<<(unsigned)B, 256, smem, static_cast<cudaStream_t>(stream)>>>(g, M, prm->p, syndromes,
+                                                                                     row_key, U, feats, lens);
+  return cudaGetLastError() == cudaSuccess ? BBP_OK : BBP_ECUDA;
+}
+
+int bbp_expand_rows(const float* rows, int64_t B, int32_t U, const int32_t* uniq_of, int32_t M, float* msgs,
+                    void* stream) {
+  if (!rows || !uniq_of || !msgs || B < 0 || U < 1 || M < 1) return BBP_EINVAL;
+  if (B == 0) return BBP_OK;
+  const long long total = B * 4 * (long long)M * 4;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  expand_rows_kernel<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      reinterpret_cast<const float4*>(rows), B, U, uniq_of, M, reinterpret_cast<float4*>(msgs));
   return cudaGetLastError() == cudaSuccess ? BBP_OK : BBP_ECUDA;
 }
 

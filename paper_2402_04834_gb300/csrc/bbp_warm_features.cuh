@@ -22,7 +22,7 @@ namespace warm {
 // Position of a message's block in the grid, rotated so that dir points right.
 struct MsgGeo {
   int dir, h, ncols, r0, r1, c0, c1;
-  __device__ __forceinline__ void node(int t, int s, int* i, int* j) const {
+  BBP_HD void node(int t, int s, int* i, int* j) const {
     switch (dir) {
       case kDirR: *i = r0 + s; *j = c0 + t; break;
       case kDirL: *i = r0 + s; *j = c1 - 1 - t; break;
@@ -32,7 +32,7 @@ struct MsgGeo {
   }
 };
 
-__device__ __forceinline__ MsgGeo msg_geo(const Geo& g, int I, int J, int dir) {
+BBP_HD MsgGeo msg_geo(const Geo& g, int I, int J, int dir) {
   MsgGeo f;
   f.dir = dir;
   f.r0 = g.lo(I); f.r1 = g.hi(I); f.c0 = g.lo(J); f.c1 = g.hi(J);
@@ -40,6 +40,20 @@ __device__ __forceinline__ MsgGeo msg_geo(const Geo& g, int I, int J, int dir) {
   f.h = rowwise ? f.r1 - f.r0 : f.c1 - f.c0;
   f.ncols = rowwise ? f.c1 - f.c0 : f.r1 - f.r0;
   return f;
+}
+
+// Whether the message's window holds a horizontal-edge qubit of grid row 0
+// or grid column 0, the only places where the four coset frames differ (the
+// logical strings X-bar and Z-bar); every other window has the same features
+// in all four cosets.
+BBP_HD bool window_sees_logicals(const Geo& g, const MsgGeo& f) {
+  for (int pos = 0; pos < 49; ++pos) {
+    const int t = f.ncols - 7 + pos / 7, sp = -1 + pos % 7;
+    int i, j;
+    f.node(t, sp, &i, &j);
+    if (i >= 0 && j >= 0 && i < g.W && j < g.W && (i == 0 || j == 0) && (i & 1) == 0 && (j & 1) == 0) return true;
+  }
+  return false;
 }
 
 // Frame byte (x bit | z bit << 1) of grid node (i, j) for a coset: the pure

@@ -40,6 +40,51 @@ def features(syndromes: torch.Tensor, prm: DecoderParams, stream=None):
     return feats, lens
 
 
+_classes: dict = {}
+
+
+def message_classes(prm: DecoderParams, device=None):
+    """Distinct feature rows of a syndrome (bbp_message_classes): (uniq_of
+    [4*M], row_key [U]) int32, on ``device`` if given; cached per geometry.
+    Messages whose window misses grid row 0 and column 0 share one row
+    across the four cosets (d = 11, k = 4: 210 of 480 rows)."""
+    key = (prm.d, prm.k, str(device))
+    if key not in _classes:
+        M = message_count(prm)
+        uniq = np.empty(4 * M, dtype=np.int32)
+        rk = np.empty(4 * M, dtype=np.int32)
+        U = ctypes.c_int32(0)
+        cp = prm.c()
+        check(lib().bbp_message_classes(ctypes.byref(cp), uniq.ctypes.data, rk.ctypes.data, ctypes.byref(U)))
+        uq, rk = torch.from_numpy(uniq), torch.from_numpy(rk[:U.value].copy())
+        _classes[key] = (uq.to(device), rk.to(device)) if device is not None else (uq, rk)
+    return _classes[key]
+
+
+def features_rows(syndromes: torch.Tensor, prm: DecoderParams, stream=None):
+    """Features [B*U, 256] and lengths [B*U] of the distinct rows only
+    (``message_classes``); row b*U + u is (coset, message) = row_key[u]."""
+    B = syndromes.shape[0]
+    _, rk = message_classes(prm, syndromes.device)
+    U = rk.numel()
+    feats = torch.empty(B * U, WARM_F, dtype=torch.float32, device=syndromes.device)
+    lens = torch.empty(B * U, dtype=torch.int32, device=syndromes.device)
+    cp = prm.c()
+    check(lib().bbp_message_features_rows(_ptr(syndromes.contiguous()), B, ctypes.byref(cp), _ptr(rk), U,
+                                          _ptr(feats), _ptr(lens), _stream(stream)))
+    return feats, lens
+
+
+def expand_rows(rows: torch.Tensor, B: int, prm: DecoderParams, out=None, stream=None):
+    """Messages [B*4*M, 16] (rows ordered syndrome, coset, message) from the
+    distinct rows [B*U, 16]."""
+    uq, rk = message_classes(prm, rows.device)
+    M = message_count(prm)
+    out = out if out is not None else torch.empty(B * 4 * M, WARM_O, dtype=torch.float32, device=rows.device)
+    check(lib().bbp_expand_rows(_ptr(rows), B, rk.numel(), _ptr(uq), M, _ptr(out), _stream(stream)))
+    return out
+
+
 def _ws_bytes(N: int) -> int:
     out = ctypes.c_size_t(0)
     check(lib().bbp_warm_workspace_bytes(N, ctypes.byref(out)))
@@ -165,12 +210,21 @@ def decode_ex(syndromes, prm: DecoderParams, init_msgs=None, final_msgs=None, wo
 DEFAULT_ALPHA = 0.1     # blend weight of the proposal (measured: larger weights raise P_L)
 
 
+def propose(syndromes, prm: DecoderParams, net: WarmStart, stream=None, alpha=DEFAULT_ALPHA):
+    """Initial messages [B*4*M, 16] from the network: features of the
+    distinct rows, the network on the tensor cores over those rows, and the
+    expansion to every (coset, message); equal bit for bit to the network
+    over every row."""
+    feats, lens = features_rows(syndromes, prm, stream)
+    rows = net.infer(feats, lens, stream=stream, alpha=alpha)
+    return expand_rows(rows, syndromes.shape[0], prm, stream=stream)
+
+
 def decode_warm(syndromes, prm: DecoderParams, net: WarmStart, stream=None, out=None, alpha=DEFAULT_ALPHA):
-    """Learned warm start: message features -> network on the tensor cores
-    -> fused decode from its proposals.  (``WarmStart.infer_syndromes``
-    skips the features buffer, 1 KB per message, at about 1.1x the time.)"""
-    feats, lens = features(syndromes, prm, stream)
-    init = net.infer(feats, lens, stream=stream, alpha=alpha)
+    """Learned warm start: proposals from the network (``propose``) -> fused
+    decode from them.  (``WarmStart.infer_syndromes`` runs the network over
+    every row with the features computed in its kernel.)"""
+    init = propose(syndromes, prm, net, stream=stream, alpha=alpha)
     return decode_ex(syndromes, prm, init_msgs=init, stream=stream, out=out)
 
 

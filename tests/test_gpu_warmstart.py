@@ -144,6 +144,40 @@ def test_infer_from_syndromes_equals_features_then_infer(dev, d, k, B):
     assert net.status() == 0
 
 
+@pytest.mark.parametrize("d,k,B", [(11, 4, 24), (13, 4, 8), (3, 4, 10), (7, 3, 6), (5, 2, 5)])
+def test_distinct_rows_reproduce_every_row(dev, d, k, B):
+    # The premise (rows of messages whose window misses grid row 0 and
+    # column 0 are equal in all four cosets) on the features themselves;
+    # the listed rows equal the full rows bit for bit; the network over the
+    # distinct rows, expanded, equals the network over every row.
+    _, _, S = synth.sample_syndromes(88, 0, B, d, 0.1)
+    s = torch.from_numpy(S).to(dev)
+    prm = pkg.DecoderParams(d=d, k=k, p=0.1, precision="fp32", algorithm="fused")
+    M = wsm.message_count(prm)
+    uq, rk = wsm.message_classes(prm)
+    U = rk.numel()
+    full, flens = wsm.features(s, prm)
+    rows, rlens = wsm.features_rows(s, prm)
+    torch.cuda.synchronize()
+    full = full.view(B, 4, M, 256).cpu()
+    flens = flens.view(B, 4, M).cpu()
+    rows = rows.view(B, U, 256).cpu()
+    rlens = rlens.view(B, U).cpu()
+    for c in range(4):
+        for i in range(M):
+            u = int(uq[c * M + i])
+            assert torch.equal(full[:, c, i], rows[:, u]), (c, i)
+            assert torch.equal(flens[:, c, i], rlens[:, u])
+    for u in range(U):
+        key = int(rk[u])
+        assert torch.equal(rows[:, u], full[:, key // M, key % M])
+    net = wsm.WarmStart(device=dev, seed=4)
+    a = net.infer(wsm.features(s, prm)[0], flens.view(-1).to(dev), alpha=0.3)
+    b = wsm.propose(s, prm, net, alpha=0.3)
+    torch.cuda.synchronize()
+    assert a.shape == b.shape and torch.equal(a, b)
+
+
 def expected_features(d, k, p, s, coset):
     """Direct re-derivation of the feature rows of one (syndrome, coset)."""
     lat = Lattice(d)
