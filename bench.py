@@ -391,8 +391,8 @@ def ours(args):
         del Ftr, Ttr, Ltr
 
     # One step = the whole decoder over the batch.  Learned: features of the
-    # distinct message rows (a message whose window misses grid row 0 and
-    # column 0 has one row for its four cosets) -> tensor-core network ->
+    # distinct message rows (cosets that agree on the logical strings a
+    # message's window sees share its row) -> tensor-core network ->
     # expansion to every (coset, message) -> fused decode from the
     # proposals; events around the network and around the decode kernel.
     M = wsm.message_count(prm)

@@ -256,14 +256,17 @@ int bbp_message_features(const uint8_t* syndromes, int64_t B, const bbp_params* 
 
 /*
  * bbp_message_classes -- which feature rows of a syndrome are distinct.  The
- * four coset frames differ only on the horizontal edges of grid row 0 and
- * column 0 (the logical strings), so a message whose 7 x 7 window holds
- * none of them has the same features, hence the same proposal, in all four
- * cosets.  Host only, no CUDA call.
+ * four coset frames differ only on the horizontal edges of grid row 0 (the
+ * X-bar string, flipped in cosets X and Y) and of grid column 0 (Z-bar,
+ * flipped in Y and Z), so cosets that agree on the strings a message's 7 x 7
+ * window sees have the same features, hence the same proposal: one row for
+ * a window that sees neither, two for one string, four for both.  Host
+ * only, no CUDA call.
  *   uniq_of  host [4][M] int32: distinct row of (coset, message)
  *   row_key  host [4*M] int32 (capacity): row u stands for (coset, message)
- *            = (row_key[u] / M, row_key[u] % M); coset 0 for shared rows
- *   n_rows   the number U of distinct rows (d = 11, k = 4: 210 of 480)
+ *            = (row_key[u] / M, row_key[u] % M), the coset being the first
+ *            of the cosets it stands for (order I, X, Y, Z)
+ *   n_rows   the number U of distinct rows (d = 11, k = 4: 154 of 480)
  * Requires k <= 4.  Errors: BBP_EINVAL.
  */
 int bbp_message_classes(const bbp_params* prm, int32_t* uniq_of, int32_t* row_key, int32_t* n_rows);

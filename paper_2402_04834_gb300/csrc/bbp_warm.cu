@@ -330,14 +330,18 @@ int bbp_message_classes(const bbp_params* prm, int32_t* uniq_of, int32_t* row_ke
     for (int J = 0; J < g.nb; ++J)
       for (int dir = 0; dir < 4; ++dir) {
         if (!g.has(I, J, dir)) continue;
-        if (window_sees_logicals(g, msg_geo(g, I, J, dir))) {
-          for (int c = 0; c < 4; ++c) {
-            uniq_of[c * M + idx] = u;
-            row_key[u++] = c * M + idx;
+        // Coset c = (bx, bz) is represented by (bx if the window sees X-bar,
+        // bz if it sees Z-bar); representatives in coset order I, X, Y, Z.
+        const int seen = window_logicals(g, msg_geo(g, I, J, dir));
+        int row_of_rep[4] = {-1, -1, -1, -1};
+        for (int c = 0; c < 4; ++c) {
+          const int bx = (c == 1 || c == 2) && (seen & 1), bz = (c == 2 || c == 3) && (seen & 2);
+          const int rep = bx ? (bz ? 2 : 1) : (bz ? 3 : 0);
+          if (row_of_rep[rep] < 0) {
+            row_of_rep[rep] = u;
+            row_key[u++] = rep * M + idx;
           }
-        } else {
-          for (int c = 0; c < 4; ++c) uniq_of[c * M + idx] = u;
-          row_key[u++] = idx;                          // coset 0 stands for all four
+          uniq_of[c * M + idx] = row_of_rep[rep];
         }
         ++idx;
       }

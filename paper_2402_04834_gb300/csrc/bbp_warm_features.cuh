@@ -42,18 +42,23 @@ BBP_HD MsgGeo msg_geo(const Geo& g, int I, int J, int dir) {
   return f;
 }
 
-// Whether the message's window holds a horizontal-edge qubit of grid row 0
-// or grid column 0, the only places where the four coset frames differ (the
-// logical strings X-bar and Z-bar); every other window has the same features
-// in all four cosets.
-BBP_HD bool window_sees_logicals(const Geo& g, const MsgGeo& f) {
+// Which logical strings the message's window sees: bit 0 if it holds a
+// horizontal-edge qubit of grid row 0 (X-bar, flipped in cosets X and Y),
+// bit 1 if one of grid column 0 (Z-bar, flipped in cosets Y and Z).  The
+// coset frames differ nowhere else, so cosets that agree on the strings a
+// window sees have the same features there.
+BBP_HD int window_logicals(const Geo& g, const MsgGeo& f) {
+  int seen = 0;
   for (int pos = 0; pos < 49; ++pos) {
     const int t = f.ncols - 7 + pos / 7, sp = -1 + pos % 7;
     int i, j;
     f.node(t, sp, &i, &j);
-    if (i >= 0 && j >= 0 && i < g.W && j < g.W && (i == 0 || j == 0) && (i & 1) == 0 && (j & 1) == 0) return true;
+    if (i >= 0 && j >= 0 && i < g.W && j < g.W && (i & 1) == 0 && (j & 1) == 0) {
+      if (i == 0) seen |= 1;
+      if (j == 0) seen |= 2;
+    }
   }
-  return false;
+  return seen;
 }
 
 // Frame byte (x bit | z bit << 1) of grid node (i, j) for a coset: the pure

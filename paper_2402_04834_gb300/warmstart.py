@@ -46,8 +46,8 @@ _classes: dict = {}
 def message_classes(prm: DecoderParams, device=None):
     """Distinct feature rows of a syndrome (bbp_message_classes): (uniq_of
     [4*M], row_key [U]) int32, on ``device`` if given; cached per geometry.
-    Messages whose window misses grid row 0 and column 0 share one row
-    across the four cosets (d = 11, k = 4: 210 of 480 rows)."""
+    Cosets that agree on the logical strings a message's window sees share
+    one row (d = 11, k = 4: 154 of 480 rows)."""
     key = (prm.d, prm.k, str(device))
     if key not in _classes:
         M = message_count(prm)

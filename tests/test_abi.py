@@ -138,28 +138,31 @@ def test_warm_start_arguments_checked_on_the_host(L):
     assert L.bbp_warm_infer(big, big, big, 0, 0.1, big, None, 0, None) == 0
 
 
-def _window_sees_logicals(d, k, I, J, dr):
-    """Independent restatement: the 7 x 7 window of message (I, J, dr) in
-    its rotated frame (chain rows -1 .. 5, the last 7 columns) holds a
-    horizontal-edge qubit (even, even) of grid row 0 or column 0."""
+def _window_logicals(d, k, I, J, dr):
+    """Independent restatement: which logical strings the 7 x 7 window of
+    message (I, J, dr) in its rotated frame (chain rows -1 .. 5, the last 7
+    columns) sees: bit 0 for a horizontal-edge qubit (even, even) of grid
+    row 0 (X-bar), bit 1 for one of grid column 0 (Z-bar)."""
     W = 2 * d - 1
     rg = [(a, min(a + k, W)) for a in range(0, W, k)]
     r0, r1 = rg[I]
     c0, c1 = rg[J]
     ncols = (c1 - c0) if dr in (0, 1) else (r1 - r0)
+    seen = 0
     for t in range(ncols - 7, ncols):
         for sp in range(-1, 6):
             i, j = {0: (r0 + sp, c0 + t), 1: (r0 + sp, c1 - 1 - t), 2: (r0 + t, c0 + sp),
                     3: (r1 - 1 - t, c0 + sp)}[dr]
-            if 0 <= i < W and 0 <= j < W and (i == 0 or j == 0) and i % 2 == 0 and j % 2 == 0:
-                return True
-    return False
+            if 0 <= i < W and 0 <= j < W and i % 2 == 0 and j % 2 == 0:
+                seen |= (1 if i == 0 else 0) | (2 if j == 0 else 0)
+    return seen
 
 
 @pytest.mark.parametrize("d,k", [(11, 4), (13, 4), (3, 4), (7, 3), (5, 2)])
 def test_message_classes_on_the_host(L, d, k):
-    # Near messages (window on row 0 or column 0) keep one row per coset,
-    # the others one row for all four; d = 11, k = 4: 30 near, 90 far.
+    # Cosets (bx, bz) that agree on the logical strings a window sees share
+    # a row: one row when it sees neither, two for one string, four for
+    # both; d = 11, k = 4: 90 / 14 / 14 / 2 messages, 154 rows.
     c = pkg.DecoderParams(d=d, k=k, precision="fp32", algorithm="fused").c()
     M = ctypes.c_int32(0)
     assert L.bbp_message_count(ctypes.byref(c), ctypes.byref(M)) == 0
@@ -172,15 +175,17 @@ def test_message_classes_on_the_host(L, d, k):
     msgs = [(I, J, dr) for I in range(nb) for J in range(nb) for dr, (di, dj) in
             enumerate(((0, 1), (0, -1), (1, 0), (-1, 0))) if 0 <= I + di < nb and 0 <= J + dj < nb]
     assert len(msgs) == M
-    near = [_window_sees_logicals(d, k, *m) for m in msgs]
-    assert U.value == sum(4 if n else 1 for n in near)
+    seen = [_window_logicals(d, k, *m) for m in msgs]
+    assert U.value == sum({0: 1, 1: 2, 2: 2, 3: 4}[x] for x in seen)
     if (d, k) == (11, 4):
-        assert sum(near) == 30 and U.value == 210
-    for i, n in enumerate(near):
-        us = {uq[c2 * M + i] for c2 in range(4)}
-        assert len(us) == (4 if n else 1)
+        assert [seen.count(x) for x in range(4)] == [90, 14, 14, 2] and U.value == 154
+    for i, x in enumerate(seen):
+        assert len({uq[c2 * M + i] for c2 in range(4)}) == {0: 1, 1: 2, 2: 2, 3: 4}[x]
         for c2 in range(4):
+            bx = c2 in (1, 2) and bool(x & 1)
+            bz = c2 in (2, 3) and bool(x & 2)
+            rep = (2 if bz else 1) if bx else (3 if bz else 0)
             key = rk[uq[c2 * M + i]]
-            assert key % M == i and key // M == (c2 if n else 0)
+            assert key % M == i and key // M == rep
     bad = pkg.DecoderParams(d=d, k=5, precision="fp32", algorithm="fused").c()
     assert L.bbp_message_classes(ctypes.byref(bad), uq, rk, ctypes.byref(U)) == -1
