@@ -34,6 +34,45 @@ def test_strips_are_a_chain_and_blockbp_is_exact(d, kc, D):
         np.testing.assert_allclose(got, ex, rtol=0, atol=1e-9)
 
 
+def _random_positive_grid(W, seed):
+    """A W x W grid of random positive (l, r, u, d) tensors, border legs of dimension 1."""
+    rng = np.random.default_rng(seed)
+    T = []
+    for i in range(W):
+        row = []
+        for j in range(W):
+            dims = (1 if j == 0 else 2, 1 if j == W - 1 else 2, 1 if i == 0 else 2, 1 if i == W - 1 else 2)
+            row.append(rng.uniform(0.2, 1.8, size=dims))
+        T.append(row)
+    return T
+
+
+@pytest.mark.parametrize("W,k,kc,seed", [(5, 5, 1, 1), (5, 1, 5, 2), (7, 7, 2, 3), (6, 2, 6, 4)])
+def test_lemma1_on_random_positive_tree_networks(W, k, kc, seed):
+    # Lemma 1 beyond the coset networks: on random positive tensors, strips
+    # (k x kc blocks spanning the grid one way) form a chain of blocks, where
+    # converged BP with the Bethe read-out gives the exact contraction; the
+    # MPS form with an untruncating bond agrees with the dense form.
+    from oracle.exact import exact_contract_log
+    T = _random_positive_grid(W, seed)
+    ref = exact_contract_log(T)
+    lp, dl, it, _ = run_naive(T, k, 200, 0.1, 1e-15, k_cols=kc)
+    assert dl < 1e-12 and abs(lp - ref) < 1e-9 * max(1.0, abs(ref))
+    P = bb.Params(d=(W + 1) // 2, k=k, k_cols=kc, D=1 << W, p=0.1, max_iter=200, delta0=1e-15, cutoff=1e-15)
+    r = bb.run_blockbp(T, P)
+    assert abs(r.logp - ref) < 1e-9 * max(1.0, abs(ref))
+
+
+def test_bethe_readout_is_not_exact_on_a_loop():
+    # Sanity of the pin above: with 2 x 2 blocks of a 4 x 4 random grid the
+    # block graph has a loop and the Bethe value differs from the exact one.
+    from oracle.exact import exact_contract_log
+    T = _random_positive_grid(4, 9)
+    ref = exact_contract_log(T)
+    lp, dl, it, _ = run_naive(T, 2, 200, 0.1, 1e-15)
+    assert abs(lp - ref) > 1e-6
+
+
 def test_mps_blockbp_equals_dense_naive_blockbp_when_nothing_truncates():
     # d = 5, k = 3, D = 4: messages have bond <= 2 and the in-block cuts <= 4,
     # so MPS blockBP equals the fused-block dense BP of Remark 9.
