@@ -29,26 +29,32 @@ from .warmstart import wilson
 def logical_error_rate(d: int, p: float, shots: int, seed: int, chunk: int = 16384, **params) -> dict:
     """Decode ``shots`` seeded syndromes, ``chunk`` per call after one
     untimed warm-up call; P_L with its Wilson 95 % interval, mean iterations
-    over cosets and syndromes per second (device time of the decode calls)."""
+    over cosets, syndromes per second (device time of the decode calls) and
+    a histogram of the final Delta of every coset by decade."""
     _, _, s, tc = sample(seed, 0, shots, d, p, with_errors=False)
     prm = DecoderParams(d=d, p=p, **params)
     decode(s[:min(shots, 64)], prm)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    dec, its = [], []
+    dec, its, dls = [], [], []
     a.record()
     for c0 in range(0, shots, chunk):
         out = decode(s[c0:c0 + chunk], prm)
         dec.append(out["decision"])
         its.append(out["iters"])
+        dls.append(out["delta"])
     b.record()
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
     fails = int((torch.cat(dec).to(torch.int64) != tc.to(torch.int64)).sum().item())
     lo, hi = wilson(fails, shots)
+    # Final Delta of every coset in decades: [0, 1e-8), [1e-8, 1e-7), ..., [1e-1, inf).
+    dl = torch.cat(dls).double().clamp_min(1e-300).log10().floor().clamp(-9, -1).cpu()
+    hist = [int((dl == e).sum().item()) for e in range(-9, 0)]
     return {"d": d, "p": p, "shots": shots, **params, "failures": fails, "P_L": fails / shots,
             "P_L_wilson95": [lo, hi], "mean_iters": float(torch.cat(its).double().mean().item()),
-            "syndromes_per_s": shots / ms * 1e3}
+            "syndromes_per_s": shots / ms * 1e3,
+            "delta_decades": {"edges": [0.0] + [10.0 ** e for e in range(-8, 0)] + ["inf"], "counts": hist}}
 
 
 def sweep(d_list, p_list, max_iters, shots, k=4, precision="fp32", algorithm="fused", seed_base=7000,
