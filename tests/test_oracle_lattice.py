@@ -107,3 +107,47 @@ def test_d2_pauli_group_partition():
         count[(s, c)] = count.get((s, c), 0) + 1
     assert len(count) == 2 ** lat.m * 4
     assert set(count.values()) == {2 ** lat.m}
+
+
+def test_d3_all_4_13_paulis_split_evenly_into_cosets():
+    # All 4^13 Paulis of d = 3: every (syndrome, coset) class, the coset
+    # taken relative to the pure error (f_s vanishes on both logicals'
+    # supports, so the class is read off the Pauli itself), holds exactly
+    # |G| = 2^12 Paulis.  The checks are of one type each (A sees x, B sees
+    # z) and so are the class bits (X-bar part from x, Z-bar part from z),
+    # so the count over (x, z) is the outer product of two exact counts over
+    # the 2^13 x-parts and the 2^13 z-parts.
+    lat = Lattice(3)
+    n, d = lat.n, lat.d
+    nA = d * (d - 1)
+    xb, zb = lat.logical_bits()
+    bits = ((np.arange(1 << n)[:, None] >> np.arange(n)[None, :]) & 1).astype(np.int64)   # [2^n, n]
+    supA = np.zeros((nA, n), dtype=np.int64)
+    supB = np.zeros((lat.m - nA, n), dtype=np.int64)
+    for ci, (kind, _) in enumerate(lat.checks):
+        for q in lat.support[ci]:
+            if kind == "A":
+                supA[ci, q] = 1
+            else:
+                supB[ci - nA, q] = 1
+    sA = (bits @ supA.T) & 1                        # syndrome bits seen by x parts
+    sB = (bits @ supB.T) & 1                        # ... by z parts
+    cx = (bits @ zb.astype(np.int64)) & 1           # X-bar component: anticommutes with Z-bar
+    cz = (bits @ xb.astype(np.int64)) & 1           # Z-bar component: anticommutes with X-bar
+    kx = (sA * (1 << np.arange(nA))).sum(1) * 2 + cx
+    kz = (sB * (1 << np.arange(lat.m - nA))).sum(1) * 2 + cz
+    hx = np.bincount(kx, minlength=1 << (nA + 1))
+    hz = np.bincount(kz, minlength=1 << (lat.m - nA + 1))
+    joint = np.outer(hx, hz)                        # [(sA, cx), (sB, cz)] over all 4^13 Paulis
+    assert joint.sum() == 4 ** n
+    assert np.all(joint == 1 << lat.m)
+    # The same classes from the library's own maps on a sample of Paulis.
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        fx, fz = rng.integers(0, 2, n).astype(np.uint8), rng.integers(0, 2, n).astype(np.uint8)
+        s = lat.syndrome(fx, fz)
+        ix = int((fx.astype(np.int64) * (1 << np.arange(n))).sum())
+        iz = int((fz.astype(np.int64) * (1 << np.arange(n))).sum())
+        assert np.array_equal(s, np.concatenate([sA[ix], sB[iz]]).astype(np.uint8))
+        c = lat.true_class(fx, fz, s)
+        assert c == ((2 if cz[iz] else 1) if cx[ix] else (3 if cz[iz] else 0))
