@@ -389,7 +389,10 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
     const int nq = n << lnq;
     // k = 5, 6 (few warps per SM): each lane loads U quads before it stores
     // any; a lane past the end repeats the last quad (same values, same
-    // addresses).
+    // addresses).  Quad g sits at base 4g - 2 (g & low); for k <= 4 the row
+    // bit P is at most h + b <= 4 + 2 (b holds at most nc / 2 legs), so
+    // 2^(P-1) divides 32, g & low stays lane & low and a lane's base grows by
+    // exactly 128 per step.
     constexpr int U = K > 4 ? 4 : 1;
     for (int s = 0; s < h; ++s) {
       const int P = (h - 1 - s) + st.bb + 1;          // bit of the node's row in the index
@@ -411,13 +414,14 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
           if (check_first) {
             // out[c, r, d] = sum_l in[c, l, v=c] g[l^r][c^d]; rows bits P (c) and P-1 (qubit).
             const int Q = P - 1, bitQ = 1 << Q, lowq = (1 << (Q - 1)) - 1;
-            for (int g0 = lane; g0 < nq; g0 += 32 * U) {
+            int bq = 4 * lane - 2 * (lane & lowq);   // k <= 4: base of quad g0, +128 per step
+            for (int g0 = lane; g0 < nq; g0 += 32 * U, bq += 128) {
               int bs[U], cbs[U];
               T x0s[U], x1s[U];
 #pragma unroll
               for (int u = 0; u < U; ++u) {
                 const int g = U == 1 ? g0 : min(g0 + 32 * u, nq - 1);
-                bs[u] = ((g >> (Q - 1)) << (Q + 1)) | ((g & lowq) << 1);
+                bs[u] = K <= 4 ? bq : ((g >> (Q - 1)) << (Q + 1)) | ((g & lowq) << 1);
                 cbs[u] = (bs[u] >> P) & 1;
                 x0s[u] = cur[bs[u] | cbs[u]];
                 x1s[u] = cur[bs[u] | bitQ | cbs[u]];
@@ -441,13 +445,13 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
           } else {
             // out[r, c, v] = [v = c] sum_{l,u} in[l, c, u] g[l^r][u^c]; qubit bit P, check bit P-1.
             const int cpos = P - 1;
-            for (int g0 = lane; g0 < nq; g0 += 32 * U) {
+            for (int g0 = lane, bq = 4 * lane - 2 * (lane & lowmask); g0 < nq; g0 += 32 * U, bq += 128) {
               int bs[U];
               V2 i0s[U], i1s[U];
 #pragma unroll
               for (int u = 0; u < U; ++u) {
                 const int g = U == 1 ? g0 : min(g0 + 32 * u, nq - 1);
-                bs[u] = ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
+                bs[u] = K <= 4 ? bq : ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
                 i0s[u] = *reinterpret_cast<const V2*>(cur + bs[u]);          // in[0][u=0,1]
                 i1s[u] = *reinterpret_cast<const V2*>(cur + (bs[u] | bitP)); // in[1][u=0,1]
               }
@@ -480,13 +484,13 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
         // convolution with the 2 x 2 table g[alpha][beta].
         T gt[4];
         qubit_table(c, ni, nj, rowwise, gt);
-        for (int g0 = lane; g0 < nq; g0 += 32 * U) {
+        for (int g0 = lane, bq = 4 * lane - 2 * (lane & lowmask); g0 < nq; g0 += 32 * U, bq += 128) {
           int bs[U];
           V2 i0s[U], i1s[U];
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             const int g = U == 1 ? g0 : min(g0 + 32 * u, nq - 1);
-            bs[u] = ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
+            bs[u] = K <= 4 ? bq : ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
             i0s[u] = *reinterpret_cast<const V2*>(cur + bs[u]);          // in[0][0], in[0][1]
             i1s[u] = *reinterpret_cast<const V2*>(cur + (bs[u] | bitP)); // in[1][0], in[1][1]
           }
@@ -508,13 +512,13 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
       }
       if (interior) {
         // Interior check: a copy tensor over four legs, out[r][d] = [r = d] in[r][r].
-        for (int g0 = lane; g0 < nq; g0 += 32 * U) {
+        for (int g0 = lane, bq = 4 * lane - 2 * (lane & lowmask); g0 < nq; g0 += 32 * U, bq += 128) {
           int bs[U];
           T i0x[U], i1y[U];
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             const int g = U == 1 ? g0 : min(g0 + 32 * u, nq - 1);
-            bs[u] = ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
+            bs[u] = K <= 4 ? bq : ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
             i0x[u] = reinterpret_cast<const V2*>(cur + bs[u])->x;
             i1y[u] = reinterpret_cast<const V2*>(cur + (bs[u] | bitP))->y;
           }
