@@ -415,6 +415,11 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
             // out[c, r, d] = sum_l in[c, l, v=c] g[l^r][c^d]; rows bits P (c) and P-1 (qubit).
             const int Q = P - 1, bitQ = 1 << Q, lowq = (1 << (Q - 1)) - 1;
             int bq = 4 * lane - 2 * (lane & lowq);   // k <= 4: base of quad g0, +128 per step
+            // k <= 4: bit P <= 6 of the base does not change in steps of 128,
+            // so the check bit and its table entries are fixed per lane.
+            const int cbl = (bq >> P) & 1;
+            const T l00 = cbl ? gt[1] : gt[0], l01 = cbl ? gt[0] : gt[1];
+            const T l10 = cbl ? gt[3] : gt[2], l11 = cbl ? gt[2] : gt[3];
             for (int g0 = lane; g0 < nq; g0 += 32 * U, bq += 128) {
               int bs[U], cbs[U];
               T x0s[U], x1s[U];
@@ -422,7 +427,7 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
               for (int u = 0; u < U; ++u) {
                 const int g = U == 1 ? g0 : min(g0 + 32 * u, nq - 1);
                 bs[u] = K <= 4 ? bq : ((g >> (Q - 1)) << (Q + 1)) | ((g & lowq) << 1);
-                cbs[u] = (bs[u] >> P) & 1;
+                cbs[u] = K <= 4 ? cbl : (bs[u] >> P) & 1;
                 x0s[u] = cur[bs[u] | cbs[u]];
                 x1s[u] = cur[bs[u] | bitQ | cbs[u]];
               }
@@ -431,8 +436,8 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
                 const int base = bs[u], cb = cbs[u];
                 const T x0 = x0s[u], x1 = x1s[u];
                 // g[a][c ^ d] by selects (a dynamic index would put gt in local memory)
-                const T g00 = cb ? gt[1] : gt[0], g01 = cb ? gt[0] : gt[1];
-                const T g10 = cb ? gt[3] : gt[2], g11 = cb ? gt[2] : gt[3];
+                const T g00 = K <= 4 ? l00 : (cb ? gt[1] : gt[0]), g01 = K <= 4 ? l01 : (cb ? gt[0] : gt[1]);
+                const T g10 = K <= 4 ? l10 : (cb ? gt[3] : gt[2]), g11 = K <= 4 ? l11 : (cb ? gt[2] : gt[3]);
                 V2 o0, o1;
                 o0.x = x0 * g00 + x1 * g10;   // r = 0, d = 0
                 o0.y = x0 * g01 + x1 * g11;   // r = 0, d = 1
@@ -445,6 +450,10 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
           } else {
             // out[r, c, v] = [v = c] sum_{l,u} in[l, c, u] g[l^r][u^c]; qubit bit P, check bit P-1.
             const int cpos = P - 1;
+            // k <= 4: bit P - 1 <= 5 of the base is fixed per lane (see above).
+            const int cbl = ((4 * lane - 2 * (lane & lowmask)) >> cpos) & 1;
+            const T l00 = cbl ? gt[1] : gt[0], l01 = cbl ? gt[0] : gt[1];
+            const T l10 = cbl ? gt[3] : gt[2], l11 = cbl ? gt[2] : gt[3];
             for (int g0 = lane, bq = 4 * lane - 2 * (lane & lowmask); g0 < nq; g0 += 32 * U, bq += 128) {
               int bs[U];
               V2 i0s[U], i1s[U];
@@ -458,11 +467,11 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
 #pragma unroll
               for (int u = 0; u < U; ++u) {
                 const int base = bs[u];
-                const int cb = (base >> cpos) & 1;
+                const int cb = K <= 4 ? cbl : (base >> cpos) & 1;
                 const V2 i0 = i0s[u], i1 = i1s[u];
                 // g[l ^ r][u ^ c]
-                const T g00 = cb ? gt[1] : gt[0], g01 = cb ? gt[0] : gt[1];
-                const T g10 = cb ? gt[3] : gt[2], g11 = cb ? gt[2] : gt[3];
+                const T g00 = K <= 4 ? l00 : (cb ? gt[1] : gt[0]), g01 = K <= 4 ? l01 : (cb ? gt[0] : gt[1]);
+                const T g10 = K <= 4 ? l10 : (cb ? gt[3] : gt[2]), g11 = K <= 4 ? l11 : (cb ? gt[2] : gt[3]);
                 const T r0 = i0.x * g00 + i0.y * g01 + i1.x * g10 + i1.y * g11;
                 const T r1 = i0.x * g10 + i0.y * g11 + i1.x * g00 + i1.y * g01;
                 V2 o0, o1;
