@@ -177,17 +177,17 @@ __device__ __forceinline__ int slot_coset(unsigned cos_of, int s) { return (int)
 // one of x, z is the parity of its in/out legs (alpha), the other the
 // parity of its chain legs (beta); alpha is z for horizontal-edge qubits
 // swept along rows and for vertical-edge qubits swept along columns.
+// Exactly one entry is pi(I): the one whose (x, z) equals the frame's
+// (fx, fz), at index q = (alpha, beta) = (fz, fx) = the frame byte itself
+// when alpha is z, and (fx, fz) = the byte with its two bits swapped when
+// alpha is x.
 template <typename T, int K>
 __device__ __forceinline__ void qubit_table(const Ctx<T, K>& c, int qi, int qj, bool rowwise, T gt[4]) {
   const int fr = c.frame[qi * c.g.W + qj];
-  const int fx = fr & 1, fz = (fr >> 1) & 1;
   const bool alpha_is_z = ((qi & 1) == 0) == rowwise;
+  const int qi_id = alpha_is_z ? fr : (((fr & 1) << 1) | (fr >> 1));
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int al = q >> 1, be = q & 1;
-    const int xb = alpha_is_z ? be : al, zb = alpha_is_z ? al : be;
-    gt[q] = ((fx ^ xb) | (fz ^ zb)) ? c.pE : c.pI;
-  }
+  for (int q = 0; q < 4; ++q) gt[q] = q == qi_id ? c.pI : c.pE;
 }
 
 // Log of a product of positive factors, for the read-out (Lemma 1).  FP64
