@@ -102,6 +102,9 @@ template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
 
+// (Index fields below occupy disjoint bits; they are added rather than or-ed
+// so that the compiler can advance the addresses instead of rebuilding them.)
+//
 // The data column of side message A with SD recorded legs and NF legs still
 // to come (k = 5, 6: NF = 2), one coset, the message in registers: each
 // lane takes groups hbv of (rows, b), reads in[a, hbv] for the 2^SD values
@@ -118,7 +121,7 @@ __device__ __forceinline__ void data_column_a(const T* mt, const T* cur, T* nxt,
   for (int hbv = lane; hbv <= low; hbv += 32) {
     T x[NA];
 #pragma unroll
-    for (int a = 0; a < NA; ++a) x[a] = cur[ib | (a << hb) | hbv];
+    for (int a = 0; a < NA; ++a) x[a] = cur[ib + (a << hb) + hbv];
 #pragma unroll
     for (int a2 = 0; a2 < NO; ++a2) {
       T s0 = T(0), s1 = T(0);
@@ -129,7 +132,7 @@ __device__ __forceinline__ void data_column_a(const T* mt, const T* cur, T* nxt,
       }
       V2 o;
       o.x = s0; o.y = s1;
-      *reinterpret_cast<V2*>(nxt + 2 * (ob | (a2 << hb) | hbv)) = o;
+      *reinterpret_cast<V2*>(nxt + 2 * (ob + (a2 << hb) + hbv)) = o;
     }
   }
 }
@@ -145,10 +148,10 @@ __device__ __forceinline__ void data_column_b(const T* mb, const T* cur, T* nxt,
 #pragma unroll
   for (int i = 0; i < NM; ++i) mr[i] = mb[i];
   for (int al = lane; al < (1 << hah); al += 32) {
-    const int ah = ab0 | al;
+    const int ah = ab0 + al;
     V2 x[NB];
 #pragma unroll
-    for (int b = 0; b < NB; ++b) x[b] = *reinterpret_cast<const V2*>(cur + (((ah << SD) | b) << 1));
+    for (int b = 0; b < NB; ++b) x[b] = *reinterpret_cast<const V2*>(cur + (((ah << SD) + b) << 1));
 #pragma unroll
     for (int b2 = 0; b2 < NO; ++b2) {
       T val = T(0);
@@ -279,7 +282,7 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
           for (int hbv = lane; hbv <= low; hbv += 32) {
             T x[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) x[a] = a < na ? cur[ib | (a << hb) | hbv] : T(0);
+            for (int a = 0; a < 4; ++a) x[a] = a < na ? cur[ib + (a << hb) + hbv] : T(0);
             if (nf == 1) {
 #pragma unroll
               for (int a2 = 0; a2 < 2; ++a2) {
@@ -291,7 +294,7 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
                 }
                 V2 o;
                 o.x = s0; o.y = s1;
-                *reinterpret_cast<V2*>(nxt + 2 * (ob | (a2 << hb) | hbv)) = o;
+                *reinterpret_cast<V2*>(nxt + 2 * (ob + (a2 << hb) + hbv)) = o;
               }
             } else {
               T s0 = T(0), s1 = T(0);
@@ -302,7 +305,7 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
               }
               V2 o;
               o.x = s0; o.y = s1;
-              *reinterpret_cast<V2*>(nxt + 2 * (ob | hbv)) = o;
+              *reinterpret_cast<V2*>(nxt + 2 * (ob + hbv)) = o;
             }
           }
         }
@@ -608,12 +611,12 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
 #pragma unroll
           for (int i = 0; i < 16; ++i) mr[i] = i < (1 << nc) ? ws.mb[(s << nc) + i] : T(0);
           for (int al = lane; al < (1 << hah); al += 32) {
-            const int ah = (s << hah) | al;
+            const int ah = (s << hah) + al;
             V2 x[4];
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
               if (b < nbb) {
-                x[b] = *reinterpret_cast<const V2*>(cur + (((ah << st.bb) | b) << 1));
+                x[b] = *reinterpret_cast<const V2*>(cur + (((ah << st.bb) + b) << 1));
               } else {
                 x[b].x = T(0); x[b].y = T(0);
               }
