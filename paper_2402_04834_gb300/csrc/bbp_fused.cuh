@@ -390,6 +390,8 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
     // read and written as two pairs of adjacent entries.
     const int lnq = st.bits() - 2;                    // quads per coset, log2
     const int nq = n << lnq;
+    // The base of a quad has the row bit P and bit 0 (v) clear, so the other
+    // entries of the quad are at base + bitP, base + 1, base + bitP + 1.
     // k = 5, 6 (few warps per SM): each lane loads U quads before it stores
     // any; a lane past the end repeats the last quad (same values, same
     // addresses).  Quad g sits at base 4g - 2 (g & low); for k <= 4 the row
@@ -431,8 +433,8 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
                 const int g = U == 1 ? g0 : min(g0 + 32 * u, nq - 1);
                 bs[u] = K <= 4 ? bq : ((g >> (Q - 1)) << (Q + 1)) | ((g & lowq) << 1);
                 cbs[u] = K <= 4 ? cbl : (bs[u] >> P) & 1;
-                x0s[u] = cur[bs[u] | cbs[u]];
-                x1s[u] = cur[bs[u] | bitQ | cbs[u]];
+                x0s[u] = cur[bs[u] + cbs[u]];
+                x1s[u] = cur[bs[u] + bitQ + cbs[u]];
               }
 #pragma unroll
               for (int u = 0; u < U; ++u) {
@@ -447,7 +449,7 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
                 o1.x = x0 * g10 + x1 * g00;   // r = 1, d = 0
                 o1.y = x0 * g11 + x1 * g01;   // r = 1, d = 1
                 *reinterpret_cast<V2*>(nxt + base) = o0;
-                *reinterpret_cast<V2*>(nxt + (base | bitQ)) = o1;
+                *reinterpret_cast<V2*>(nxt + (base + bitQ)) = o1;
               }
             }
           } else {
@@ -465,7 +467,7 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
                 const int g = U == 1 ? g0 : min(g0 + 32 * u, nq - 1);
                 bs[u] = K <= 4 ? bq : ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
                 i0s[u] = *reinterpret_cast<const V2*>(cur + bs[u]);          // in[0][u=0,1]
-                i1s[u] = *reinterpret_cast<const V2*>(cur + (bs[u] | bitP)); // in[1][u=0,1]
+                i1s[u] = *reinterpret_cast<const V2*>(cur + (bs[u] + bitP)); // in[1][u=0,1]
               }
 #pragma unroll
               for (int u = 0; u < U; ++u) {
@@ -481,7 +483,7 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
                 o0.x = cb ? T(0) : r0; o0.y = cb ? r0 : T(0);
                 o1.x = cb ? T(0) : r1; o1.y = cb ? r1 : T(0);
                 *reinterpret_cast<V2*>(nxt + base) = o0;
-                *reinterpret_cast<V2*>(nxt + (base | bitP)) = o1;
+                *reinterpret_cast<V2*>(nxt + (base + bitP)) = o1;
               }
             }
           }
@@ -504,7 +506,7 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
             const int g = U == 1 ? g0 : min(g0 + 32 * u, nq - 1);
             bs[u] = K <= 4 ? bq : ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
             i0s[u] = *reinterpret_cast<const V2*>(cur + bs[u]);          // in[0][0], in[0][1]
-            i1s[u] = *reinterpret_cast<const V2*>(cur + (bs[u] | bitP)); // in[1][0], in[1][1]
+            i1s[u] = *reinterpret_cast<const V2*>(cur + (bs[u] + bitP)); // in[1][0], in[1][1]
           }
 #pragma unroll
           for (int u = 0; u < U; ++u) {
@@ -515,7 +517,7 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
             o1.x = i0.x * gt[2] + i0.y * gt[3] + i1.x * gt[0] + i1.y * gt[1];
             o1.y = i0.x * gt[3] + i0.y * gt[2] + i1.x * gt[1] + i1.y * gt[0];
             *reinterpret_cast<V2*>(nxt + bs[u]) = o0;
-            *reinterpret_cast<V2*>(nxt + (bs[u] | bitP)) = o1;
+            *reinterpret_cast<V2*>(nxt + (bs[u] + bitP)) = o1;
           }
         }
         __syncwarp();
@@ -532,7 +534,7 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
             const int g = U == 1 ? g0 : min(g0 + 32 * u, nq - 1);
             bs[u] = K <= 4 ? bq : ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
             i0x[u] = reinterpret_cast<const V2*>(cur + bs[u])->x;
-            i1y[u] = reinterpret_cast<const V2*>(cur + (bs[u] | bitP))->y;
+            i1y[u] = reinterpret_cast<const V2*>(cur + (bs[u] + bitP))->y;
           }
 #pragma unroll
           for (int u = 0; u < U; ++u) {
@@ -540,7 +542,7 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
             o0.x = i0x[u]; o0.y = T(0);
             o1.x = T(0); o1.y = i1y[u];
             *reinterpret_cast<V2*>(nxt + bs[u]) = o0;
-            *reinterpret_cast<V2*>(nxt + (bs[u] | bitP)) = o1;
+            *reinterpret_cast<V2*>(nxt + (bs[u] + bitP)) = o1;
           }
         }
         __syncwarp();
@@ -571,7 +573,7 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
         }
         const int base = ((g >> (P - 1)) << (P + 1)) | ((g & lowmask) << 1);
         const V2 i0 = *reinterpret_cast<const V2*>(cur + base);          // (l=0,u=0), (l=0,u=1)
-        const V2 i1 = *reinterpret_cast<const V2*>(cur + (base | bitP)); // (l=1,u=0), (l=1,u=1)
+        const V2 i1 = *reinterpret_cast<const V2*>(cur + (base + bitP)); // (l=1,u=0), (l=1,u=1)
         V2 o0, o1;
         // w index: ((l*2 + r)*2 + u)*2 + d
         o0.x = i0.x * w[0] + i0.y * w[2] + i1.x * w[8] + i1.y * w[10];     // r=0, d=0
@@ -579,7 +581,7 @@ __device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K
         o1.x = i0.x * w[4] + i0.y * w[6] + i1.x * w[12] + i1.y * w[14];    // r=1, d=0
         o1.y = i0.x * w[5] + i0.y * w[7] + i1.x * w[13] + i1.y * w[15];    // r=1, d=1
         *reinterpret_cast<V2*>(nxt + base) = o0;
-        *reinterpret_cast<V2*>(nxt + (base | bitP)) = o1;
+        *reinterpret_cast<V2*>(nxt + (base + bitP)) = o1;
       }
       __syncwarp();
       T* tmp = cur; cur = nxt; nxt = tmp;
