@@ -57,10 +57,10 @@ FP64_FMA_PER_SM_CLK = 2
 # Warm-start network: 256 -> 256 -> 256 -> 16, two flops per multiply-add.
 MLP_FLOPS_PER_ROW = 2 * (256 * 256 + 256 * 256 + 256 * 16)
 # DRAM bytes read + written, from ncu captures of the current kernels
-# (profiles/fused_kernel_fp32_d11_1024shots.md: 487.2 KB for 1024 syndromes;
+# (profiles/fused_kernel_fp32_d11_1024shots.md: 369.4 KB for 1024 syndromes;
 # profiles/mlp_tc_kernel_bf16_1200k_rows.md: 1.234 GB + 74.6 MB for 1.2 M
 # rows), scaled by the units a launch processes.
-FUSED_DRAM_BYTES_PER_SYNDROME = 487.168e3 / 1024
+FUSED_DRAM_BYTES_PER_SYNDROME = 369.408e3 / 1024
 NETWORK_DRAM_BYTES_PER_ROW = (1.234248e9 + 74.605312e6) / 1.2e6
 
 
