@@ -61,7 +61,7 @@ extern "C" {
 
 /* Algorithms. */
 #define BBP_ALG_MPS 0          /* blockBP with boundary-MPS messages of bond D (Sec. III.D) */
-#define BBP_ALG_FUSED 1        /* fused-block BP with dense messages of 2^k (Remark 9), k <= 4 */
+#define BBP_ALG_FUSED 1        /* fused-block BP with dense messages of 2^k (Remark 9), k <= 6 */
 
 /* Precisions. */
 #define BBP_FP64 0             /* all arithmetic in double */
@@ -181,8 +181,8 @@ int bbp_sample(uint64_t seed, int64_t first_shot, int64_t B, int32_t d, double p
 
 /*
  * bbp_pure_error -- the pure error f_s of each syndrome (Algorithm 1, first
- * step: "a Pauli string that produces the syndrome"; the construction is
- * this library's reading): for every flagged site check A_(r,c) an X string
+ * step, which asks for any Pauli with syndrome s; this construction is the
+ * library's choice): for every flagged site check A_(r,c) an X string
  * on the horizontal edges of row r right of it, for every flagged plaquette
  * B_(r,j) a Z string on the horizontal edges of column j below it.  f_s
  * vanishes on the supports of both logicals; s(f_s) = s.
