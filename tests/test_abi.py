@@ -189,3 +189,19 @@ def test_message_classes_on_the_host(L, d, k):
             assert key % M == i and key // M == rep
     bad = pkg.DecoderParams(d=d, k=5, precision="fp32", algorithm="fused").c()
     assert L.bbp_message_classes(ctypes.byref(bad), uq, rk, ctypes.byref(U)) == -1
+
+
+@pytest.mark.parametrize("alg,prec,k,d_max", [("fused", "fp32", 4, 48), ("fused", "fp64", 4, 36),
+                                              ("fused", "fp32", 2, 25), ("fused", "fp32", 1, 13),
+                                              ("fused", "fp32", 6, 64), ("fused", "fp64", 6, 64),
+                                              ("mps", "fp64", 4, 64), ("mps", "fp32", 4, 64)])
+def test_largest_supported_distance(L, alg, prec, k, d_max):
+    # Fused k <= 4 keeps every message in shared memory, which bounds d (the
+    # messages of k < 4 are padded to 16 entries); k = 6 and the MPS form keep
+    # them in the workspace and take the API's d <= 64.  Past the bound the
+    # call is refused on the host.
+    out = ctypes.c_size_t(0)
+    c = pkg.DecoderParams(d=d_max, k=k, D=8, precision=prec, algorithm=alg).c()
+    assert L.bbp_workspace_bytes(ctypes.byref(c), 4, 0, ctypes.byref(out)) == 0
+    c = pkg.DecoderParams(d=d_max + 1, k=k, D=8, precision=prec, algorithm=alg).c()
+    assert L.bbp_workspace_bytes(ctypes.byref(c), 4, 0, ctypes.byref(out)) == (-4 if d_max < 64 else -1)

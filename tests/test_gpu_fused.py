@@ -235,3 +235,16 @@ def test_fused_early_exit_and_decision(dev, precision, warps, cosets):
 def test_fused_needs_no_workspace(dev):
     prm = pkg.DecoderParams(d=11, k=4, algorithm="fused")
     assert pkg.workspace_bytes(prm, 1000) == 0
+
+
+@pytest.mark.parametrize("d,precision", [(48, "fp32"), (36, "fp64")])
+def test_fused_k4_at_the_largest_distance(dev, d, precision):
+    # The largest distances whose messages fit in shared memory: finite
+    # log-probabilities below 0, valid decisions, repeatable bit for bit.
+    _, _, S = synth.sample_syndromes(4800 + d, 0, 2, d, 0.1)
+    prm = pkg.DecoderParams(d=d, k=4, p=0.1, max_iter=3, delta0=0.0, precision=precision, algorithm="fused")
+    a, b = gpu(S, prm, dev), gpu(S, prm, dev)
+    assert np.all(np.isfinite(a["logp"])) and np.all(a["logp"] < 0)
+    assert np.all((a["decision"] >= 0) & (a["decision"] < 4))
+    for key in ("logp", "delta", "iters", "decision"):
+        assert np.array_equal(a[key], b[key]), key
