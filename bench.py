@@ -247,11 +247,13 @@ def mixed_batch_leg(args, dev, pkg):
     packed, offsets, d_of = pack_mixed(shots, device=dev)
     prm = pkg.DecoderParams(d=0, k=K_BLOCK, p=P_NOISE, max_iter=MAX_ITER, eta=ETA, delta0=DELTA0, delta1=DELTA1,
                             precision="fp32", algorithm="fused")
-    prm, table = autotune.tune_mixed(packed, offsets, d_of, prm, shapes=((8, 4), (8, 2), (4, 2), (4, 4)),
+    prm, table = autotune.tune_mixed(packed, offsets, d_of, prm,
+                                     shapes=((8, 4, 1), (8, 4, 2), (8, 2, 1), (8, 2, 2), (4, 2, 1), (4, 4, 1)),
                                      ctas=(0, 1, 2))
     order = torch.argsort(d_of, descending=True, stable=True).to(torch.int32)
     d_max = int(max(MIXED_DISTANCES))
-    counter = torch.empty(256, dtype=torch.uint8, device=dev)
+    counter = torch.empty(256 + pkg.workspace_bytes(pkg.DecoderParams(**{**prm.__dict__, "d": d_max}), n),
+                          dtype=torch.uint8, device=dev)
     out = decode_mixed(packed, offsets, d_of, prm, counter=counter, order=order, d_max=d_max)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
@@ -281,7 +283,7 @@ def mixed_batch_leg(args, dev, pkg):
     outs = {}
     for d, idx, S in dev_groups:
         outs[d] = pkg.decode(S, pkg.DecoderParams(**{**prm.__dict__, "d": d, "warps": 0, "cosets": 0,
-                                                     "ctas_per_sm": 0}))
+                                                     "ctas_per_sm": 0, "messages": 0}))
     torch.cuda.synchronize()
     ms2 = 0.0
     for i in range(reps):
@@ -289,8 +291,8 @@ def mixed_batch_leg(args, dev, pkg):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         for d, idx, S in dev_groups:
-            pkg.decode(S, pkg.DecoderParams(**{**prm.__dict__, "d": d, "warps": 0, "cosets": 0, "ctas_per_sm": 0}),
-                       out=outs[d])
+            pkg.decode(S, pkg.DecoderParams(**{**prm.__dict__, "d": d, "warps": 0, "cosets": 0, "ctas_per_sm": 0,
+                                               "messages": 0}), out=outs[d])
         b.record()
         torch.cuda.synchronize()
         ms2 += a.elapsed_time(b)
@@ -301,7 +303,8 @@ def mixed_batch_leg(args, dev, pkg):
     return {"value": mixed_val, "unit": "syndromes/s", "batch": n, "distances": list(MIXED_DISTANCES),
             "counts": [int(c) for c in counts], "p": P_NOISE, "precision": "fp32", "algorithm": "fused",
             "launch": "one persistent launch, largest distance first, replayed from a CUDA graph",
-            "shape": {"warps": prm.warps, "cosets": prm.cosets, "ctas_per_sm": prm.ctas_per_sm},
+            "shape": {"warps": prm.warps, "cosets": prm.cosets, "messages": "shared" if prm.messages == 1 else "workspace",
+                      "ctas_per_sm": prm.ctas_per_sm},
             "autotune_candidates": len(table),
             "mean_iters": float(out["iters"].double().mean().item()),
             "per_distance_launches": {"value": per_d_val, "unit": "syndromes/s", "launches": len(dev_groups)},

@@ -84,22 +84,27 @@ extern "C" {
  *             singular values below cutoff * sigma_1 are dropped as numerical
  *             zeros (the paper is silent; 1e-13 for BBP_FP64, 1e-7 for BBP_FP32)
  *   precision BBP_FP64 or BBP_FP32
- *   launch_warps, launch_cosets, launch_ctas_per_sm  launch shape of the
- *             fused path (tuning only; results do not depend on them): warps
- *             per CTA, cosets decoded together by one CTA (1, 2 or 4; they
- *             share the block geometry and, off row 0 and column 0, the node
- *             tensors) and resident CTAs per SM of bbp_decode_mixed.  0 picks
- *             the fastest compiled shape whose shared memory fits; compiled
- *             (warps, cosets): FP32 (8,4) (8,2) (4,2) (4,4) (16,1) (8,1)
- *             (4,1), FP64 (4,2) (8,2) (8,1) (4,4); for k = 5, 6: FP32 (6,1)
- *             (4,1) (2,1), FP64 (3,1) (2,1); other requests give
- *             BBP_EUNSUPPORTED.
+ *   launch_warps, launch_cosets, launch_ctas_per_sm, launch_messages
+ *             launch shape of the fused path (tuning only; results do not
+ *             depend on them): warps per CTA, cosets decoded together by one
+ *             CTA (1, 2 or 4; they share the block geometry and, off row 0
+ *             and column 0, the node tensors), resident CTAs per SM of
+ *             bbp_decode_mixed, and where the messages live (1 shared memory,
+ *             2 a workspace slot per resident CTA with a persistent grid).
+ *             0 picks the first compiled shape, in order of measured speed,
+ *             whose shared memory allows the CTAs per SM its registers are
+ *             sized for, else the first that fits; compiled (warps, cosets):
+ *             FP32 (8,4) (8,2) (4,2) (4,4) (16,1) (8,1) (4,1), of which (8,4)
+ *             and (8,2) also with workspace messages; FP64 (4,2) (8,2) (8,1)
+ *             (4,4), (4,2) also with workspace messages; for k = 5, 6
+ *             (workspace messages only): FP32 (6,1) (4,1) (2,1), FP64 (3,1)
+ *             (2,1); other requests give BBP_EUNSUPPORTED.
  *   algorithm BBP_ALG_MPS, or BBP_ALG_FUSED: every k x k block fused into one
  *             vertex with dense messages (Remark 9; the form the paper ran for
  *             k = 1, 2, 4).  Nothing is truncated, D and cutoff are unused,
  *             and the result equals BBP_ALG_MPS whenever that truncates
- *             nothing.  Needs k <= 6; no workspace for k <= 4 (messages in
- *             shared memory), a message slot per resident CTA for k = 5, 6.
+ *             nothing.  Needs k <= 6; a workspace when the messages live in
+ *             workspace slots (always for k = 5, 6).
  */
 typedef struct bbp_params {
   int32_t d;
@@ -116,14 +121,17 @@ typedef struct bbp_params {
   int32_t launch_warps;        /* fused path: warps per CTA (2, 3, 4, 6, 8, 16), 0 = default */
   int32_t launch_ctas_per_sm;  /* bbp_decode_mixed: resident CTAs per SM, 0 = the occupancy limit */
   int32_t launch_cosets;       /* fused path: cosets per CTA (1, 2, 4), 0 = default */
+  int32_t launch_messages;     /* fused path: 1 shared memory, 2 workspace slots, 0 = default */
 } bbp_params;
 
 /*
  * bbp_workspace_bytes -- device scratch needed by bbp_decode_batch for B
  * syndromes: the MPS messages of every syndrome x coset (Sec. III.D); for
- * BBP_ALG_FUSED none at k <= 4, and at k = 5, 6 the dense messages of the
- * resident CTAs, min(4B, 512) slots of 64 M scalars (M directed block
- * edges; d = 31: 440 x 64 x 4 bytes = 112.6 KB a slot in FP32).  With
+ * BBP_ALG_FUSED none when the launch shape keeps the messages in shared
+ * memory, else the dense messages of the resident CTAs, min(4B / G, 512)
+ * slots of G x M x V scalars (G cosets per CTA, M directed block edges,
+ * V = 16 for k <= 4 and 64 for k = 5, 6; d = 31, k = 6: 440 x 64 x 4 bytes
+ * = 112.6 KB a slot in FP32).  With
  * include_io != 0 it also counts room for device copies of the inputs and
  * outputs, as bbp_decode_batch_host needs.  Writes the size to *bytes.
  * Errors: BBP_EINVAL for invalid parameters or a null pointer.
@@ -362,8 +370,9 @@ int bbp_decode_batch_ex(const uint8_t* syndromes, int64_t B, const bbp_params* p
  *   order      device [B] int32 permutation of 0..B-1, or NULL (natural order)
  *   prm        k, p, eta, delta0, delta1, max_iter, precision; d is ignored;
  *              algorithm must be BBP_ALG_FUSED
- *   workspace  device, at least 256 bytes (the work counter); for k = 5, 6
- *              256 + min(4B, 512) x 64 M(d_max) scalars (the message slots)
+ *   workspace  device, at least 256 bytes (the work counter); when the launch
+ *              shape keeps its messages in the workspace (always for k = 5,
+ *              6), 256 + bbp_workspace_bytes of d_max and B (the slots)
  * Errors as bbp_decode_batch.
  */
 int bbp_decode_mixed(const uint8_t* syndromes, const int64_t* offsets, const int32_t* d_of, const int32_t* order,

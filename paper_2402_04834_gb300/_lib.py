@@ -30,7 +30,9 @@ WARM_INFER_WS_BYTES = 270592      # workspace of bbp_warm_infer, for any N
 # Compiled launch shapes (warps per CTA, cosets per CTA) of the fused kernel.
 FUSED_SHAPES = {"fp32": ((8, 4), (8, 2), (4, 2), (4, 4), (16, 1), (8, 1), (4, 1)),
                 "fp64": ((4, 2), (8, 2), (8, 1), (4, 4))}
-# ... and for block sides 5 and 6 (one coset per CTA).
+# ... of which these also with their messages in workspace slots (messages=2)
+FUSED_SHAPES_WS = {"fp32": ((8, 4), (8, 2)), "fp64": ((4, 2),)}
+# ... and for block sides 5 and 6 (one coset per CTA, messages in the workspace).
 FUSED_SHAPES_K6 = {"fp32": ((6, 1), (4, 1), (2, 1)), "fp64": ((3, 1), (2, 1))}
 BBP_ETOOLARGE = -5
 STATIC_WORKSPACE_BYTES = 32 << 20
@@ -42,7 +44,7 @@ class BbpParams(ctypes.Structure):
                 ("delta0", ctypes.c_double), ("delta1", ctypes.c_double), ("cutoff", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("algorithm", ctypes.c_int32),
                 ("launch_warps", ctypes.c_int32), ("launch_ctas_per_sm", ctypes.c_int32),
-                ("launch_cosets", ctypes.c_int32)]
+                ("launch_cosets", ctypes.c_int32), ("launch_messages", ctypes.c_int32)]
 
 
 @dataclass
@@ -62,13 +64,14 @@ class DecoderParams:
     warps: int = 0                  # fused launch shape (tuning only): warps per CTA
     ctas_per_sm: int = 0            # persistent mixed launch: resident CTAs per SM (0 = occupancy)
     cosets: int = 0                 # fused launch shape (tuning only): cosets per CTA (1, 2, 4)
+    messages: int = 0               # fused (tuning only): 1 shared memory, 2 workspace slots, 0 = default
 
     def c(self) -> BbpParams:
         prec = FP64 if self.precision == "fp64" else FP32
         cut = self.cutoff if self.cutoff is not None else (1e-13 if prec == FP64 else 1e-7)
         alg = ALG_MPS if self.algorithm == "mps" else ALG_FUSED
         return BbpParams(self.d, self.k, self.D, self.max_iter, self.p, self.eta, self.delta0,
-                         self.delta1, cut, prec, alg, self.warps, self.ctas_per_sm, self.cosets)
+                         self.delta1, cut, prec, alg, self.warps, self.ctas_per_sm, self.cosets, self.messages)
 
     @property
     def m(self) -> int:

@@ -14,11 +14,15 @@ using bbp::Geo;
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-// Launch shape of the fused kernel for this request at geometry g.
-bool shape_of(const bbp_params* p, const Geo& g, int M, int* warps, int* cosets) {
+// Launch shape of the fused kernel for this request at geometry g; *gm is
+// set when its messages live in the workspace.
+bool shape_of(const bbp_params* p, const Geo& g, int M, int* warps, int* cosets, bool* gm) {
   *warps = p->launch_warps;
   *cosets = p->launch_cosets;
-  return bbp::fused_shape(p->precision, g, M, warps, cosets);
+  int messages = p->launch_messages;
+  const bool ok = bbp::fused_shape(p->precision, g, M, warps, cosets, &messages);
+  *gm = messages == 2;
+  return ok;
 }
 
 int check_params(const bbp_params* p) {
@@ -37,12 +41,14 @@ int check_params(const bbp_params* p) {
   if (p->launch_cosets != 0 && p->launch_cosets != 1 && p->launch_cosets != 2 && p->launch_cosets != 4)
     return BBP_EINVAL;
   if (p->launch_ctas_per_sm < 0 || p->launch_ctas_per_sm > 32) return BBP_EINVAL;
+  if (p->launch_messages < 0 || p->launch_messages > 2) return BBP_EINVAL;
   if (p->algorithm == BBP_ALG_FUSED) {
     if (p->k > bbp::kFusedMaxK) return BBP_EUNSUPPORTED;
     const bbp::Geo g = bbp::make_geo(p->d, p->k);
     int M = 0, ae = 0, w = 0, c = 0;
+    bool gm = false;
     bbp::count_messages(g, 1, &M, &ae);
-    if (!shape_of(p, g, M, &w, &c)) return BBP_EUNSUPPORTED;
+    if (!shape_of(p, g, M, &w, &c, &gm)) return BBP_EUNSUPPORTED;
   }
   return BBP_OK;
 }
@@ -51,12 +57,18 @@ struct Sizes {
   Geo g;
   int M, arena_elems, m;
   size_t elem, arena_bytes, io_bytes;
-  long long slots;        // fused, k = 5, 6: message slots in the arena
+  int warps, cosets;      // fused: launch shape
+  bool gm;                // fused: messages in the workspace
+  long long slots;        // fused with gm: message slots in the arena
 };
 
-// Fused k = 5, 6: one message slot (64 * M scalars) per resident CTA.
-long long fused_slots(int64_t B) { return B * 4 < bbp::kFusedSlots ? (long long)B * 4 : bbp::kFusedSlots; }
-size_t fused_slot_bytes(int M, size_t elem) { return (size_t)M * 64 * elem; }
+// Fused path with its messages in the workspace: one slot of G cosets x M
+// messages x (16 or 64) scalars per resident CTA, at most one per item.
+long long fused_slots(int64_t B, int G) {
+  const long long items = (long long)B * (4 / G);
+  return items < bbp::kFusedSlots ? items : bbp::kFusedSlots;
+}
+size_t fused_slot_bytes(int k, int G, int M, size_t elem) { return (size_t)G * M * (k > 4 ? 64 : 16) * elem; }
 
 Sizes sizes_for(const bbp_params* p, int64_t B) {
   Sizes s;
@@ -65,13 +77,18 @@ Sizes sizes_for(const bbp_params* p, int64_t B) {
   s.m = 2 * p->d * (p->d - 1);
   s.elem = p->precision == BBP_FP64 ? sizeof(double) : sizeof(float);
   s.slots = 0;
+  s.warps = s.cosets = 0;
+  s.gm = false;
   if (p->algorithm != BBP_ALG_FUSED) {
     s.arena_bytes = align256((size_t)B * 4 * (size_t)s.arena_elems * s.elem);
-  } else if (p->k > 4) {
-    s.slots = fused_slots(B);
-    s.arena_bytes = align256((size_t)s.slots * fused_slot_bytes(s.M, s.elem));
   } else {
+    int M1 = 0, ae = 0;
+    bbp::count_messages(s.g, 1, &M1, &ae);
     s.arena_bytes = 0;
+    if (shape_of(p, s.g, M1, &s.warps, &s.cosets, &s.gm) && s.gm) {
+      s.slots = fused_slots(B, s.cosets);
+      s.arena_bytes = align256((size_t)s.slots * fused_slot_bytes(p->k, s.cosets, M1, s.elem));
+    }
   }
   s.io_bytes = align256((size_t)B * s.m) + align256((size_t)B * 4 * 8) * 2 +
                align256((size_t)B * 4 * 4) * 2 + align256((size_t)B);
@@ -135,9 +152,9 @@ int bbp_decode_batch_ex(const uint8_t* syndromes, int64_t B, const bbp_params* p
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   if (prm->algorithm == BBP_ALG_FUSED) {
-    int w = 0, c = 0;
-    if (!shape_of(prm, s.g, s.M, &w, &c)) return BBP_EUNSUPPORTED;
-    e = prm->precision == BBP_FP64 ? bbp::launch_fused_f64(a, w, c, st) : bbp::launch_fused_f32(a, w, c, st);
+    if (s.warps == 0) return BBP_EUNSUPPORTED;
+    e = prm->precision == BBP_FP64 ? bbp::launch_fused_f64(a, s.warps, s.cosets, s.gm, st)
+                                   : bbp::launch_fused_f32(a, s.warps, s.cosets, s.gm, st);
   } else
     e = prm->precision == BBP_FP64 ? bbp::launch_decode_f64(a, st) : bbp::launch_decode_f32(a, st);
   if (e != cudaSuccess) return BBP_ECUDA;
@@ -206,16 +223,17 @@ int bbp_decode_mixed(const uint8_t* syndromes, const int64_t* offsets, const int
   m.d_max = d_max; m.ctas_per_sm = prm->launch_ctas_per_sm;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int Mmax = 0, ae = 0, w = 0, c = 0;
+  bool gm = false;
   bbp::count_messages(a.geo, 1, &Mmax, &ae);
-  if (prm->k > 4) {   // message slots after the counter
+  if (!shape_of(prm, a.geo, Mmax, &w, &c, &gm)) return BBP_EUNSUPPORTED;
+  if (gm) {   // message slots after the counter
     const size_t elem = prm->precision == BBP_FP64 ? sizeof(double) : sizeof(float);
-    m.slots = fused_slots(B);
-    if (workspace_bytes < 256 + (size_t)m.slots * fused_slot_bytes(Mmax, elem)) return BBP_ENOSPACE;
+    m.slots = fused_slots(B, c);
+    if (workspace_bytes < 256 + (size_t)m.slots * fused_slot_bytes(prm->k, c, Mmax, elem)) return BBP_ENOSPACE;
     m.slot_base = static_cast<char*>(workspace) + 256;
   }
-  if (!shape_of(prm, a.geo, Mmax, &w, &c)) return BBP_EUNSUPPORTED;
-  cudaError_t e = prm->precision == BBP_FP64 ? bbp::launch_fused_mixed_f64(a, m, w, c, st)
-                                             : bbp::launch_fused_mixed_f32(a, m, w, c, st);
+  cudaError_t e = prm->precision == BBP_FP64 ? bbp::launch_fused_mixed_f64(a, m, w, c, gm, st)
+                                             : bbp::launch_fused_mixed_f32(a, m, w, c, gm, st);
   if (e != cudaSuccess) return BBP_ECUDA;
   e = bbp::launch_decide(a, st);
   return e == cudaSuccess ? BBP_OK : BBP_ECUDA;

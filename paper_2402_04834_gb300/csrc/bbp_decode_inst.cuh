@@ -31,8 +31,8 @@ cudaError_t launch_decode_t(const LaunchArgs& a, cudaStream_t st) {
 }
 
 template <typename T, int K>
-int fused_smem_for(const Geo& g, int M, int warps, int cosets) {
-  return fused_layout<T, K>(g, M, warps, cosets).total;
+int fused_smem_for(const Geo& g, int M, int warps, int cosets, bool gm = (K > 4)) {
+  return fused_layout<T, K>(g, M, warps, cosets, gm).total;
 }
 
 template <typename T>
@@ -68,15 +68,17 @@ cudaError_t persistent_grid(Kern kern, int threads, int smem, int ctas_per_sm, l
   return g > 0 ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <typename T, int NW, int G, int K>
+// GM: messages in the workspace (a.arena, a.slots slots of G * M * vec
+// scalars), a persistent grid; always for k = 5, 6.
+template <typename T, int NW, int G, int K, bool GM = (K > 4)>
 cudaError_t launch_fused_nw(const LaunchArgs& a, cudaStream_t st) {
   const KArgs<T> k = fused_args<T>(a);
-  const int smem = fused_smem_for<T, K>(a.geo, a.M, NW, G);
-  auto kern = fused_kernel<T, NW, G, K>;
+  const int smem = fused_smem_for<T, K>(a.geo, a.M, NW, G, GM);
+  auto kern = fused_kernel<T, NW, G, K, GM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const long long items = a.B * (4 / G);
-  if (K > 4) {
+  if (GM) {
     KArgs<T> kp = k;
     kp.arena = static_cast<T*>(a.arena);
     kp.n_items = items;
@@ -90,14 +92,14 @@ cudaError_t launch_fused_nw(const LaunchArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <typename T, int NW, int G, int K>
+template <typename T, int NW, int G, int K, bool GM = (K > 4)>
 cudaError_t launch_fused_mixed_nw(const LaunchArgs& a, const MixedLaunch& m, cudaStream_t st) {
   const KArgs<T> k = fused_args<T>(a);
   const Geo gmax = make_geo(m.d_max, a.geo.k);
   int Mmax = 0, ae = 0;
   count_messages(gmax, 1, &Mmax, &ae);
-  const int smem = fused_smem_for<T, K>(gmax, Mmax, NW, G);
-  auto kern = fused_mixed_kernel<T, NW, G, K>;
+  const int smem = fused_smem_for<T, K>(gmax, Mmax, NW, G, GM);
+  auto kern = fused_mixed_kernel<T, NW, G, K, GM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   int per_sm = m.ctas_per_sm;
@@ -115,7 +117,7 @@ cudaError_t launch_fused_mixed_nw(const LaunchArgs& a, const MixedLaunch& m, cud
   long long grid = (long long)sms * per_sm;
   if (grid > mx.n_items) grid = mx.n_items;
   KArgs<T> kp = k;
-  if (K > 4) {   // messages in the workspace, one slot per CTA
+  if (GM) {      // messages in the workspace, one slot per CTA
     kp.arena = static_cast<T*>(m.slot_base);
     kp.slot_elems = (long long)G * Mmax * FusedDim<K>::vec;
     if (grid > m.slots) grid = m.slots;

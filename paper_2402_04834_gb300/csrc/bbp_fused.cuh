@@ -76,8 +76,10 @@ struct FusedLayout {
   int synd, frame, msg_of, meta, work, ovl, rlog, misc, msgs, ws, ws_stride, total;
 };
 
+// gm: the messages live in a workspace slot of the CTA (always for k = 5,
+// 6; on request for k <= 4), not in shared memory.
 template <typename T, int K>
-BBP_HD FusedLayout fused_layout(const Geo& g, int M, int nwarps, int G) {
+BBP_HD FusedLayout fused_layout(const Geo& g, int M, int nwarps, int G, bool gm = (K > 4)) {
   FusedLayout L;
   const int m = 2 * g.d * (g.d - 1);
   int o = 0;
@@ -89,8 +91,8 @@ BBP_HD FusedLayout fused_layout(const Geo& g, int M, int nwarps, int G) {
   L.ovl = o;    o = align_up(o + 8 * G * M, 16);
   L.rlog = o;   o = align_up(o + 8 * G * (g.nb * g.nb + M), 16);
   L.misc = o;   o = align_up(o + 128, 16);
-  L.msgs = o;   // k <= 4: the messages live here; k = 5, 6: in the workspace
-  if (K <= 4) o = align_up(o + (int)sizeof(T) * FusedDim<K>::vec * G * M, 16);
+  L.msgs = o;   // the messages, unless they live in the workspace
+  if (!gm) o = align_up(o + (int)sizeof(T) * FusedDim<K>::vec * G * M, 16);
   L.ws = o;
   L.ws_stride = fused_ws_bytes<T, K>(G);
   o = align_up(o + nwarps * L.ws_stride, 16);
@@ -825,16 +827,17 @@ template <typename T, int NW, int G, int K> struct FusedMinBlocks {
 
 // Cosets c0 .. c0 + G - 1 of one syndrome decoded by the whole CTA: syn_src
 // holds the syndrome's m bytes and outputs go to row syn * 4 + coset.
-// gmsgs: this CTA's message slot in global memory (k = 5, 6; the slot is
-// L2-resident and touched only a few times per block sweep), else null.
-template <typename T, int NW, int G, int K>
+// GM: the messages live in gmsgs, this CTA's slot in global memory (the slot
+// is L2-resident and touched only a few times per block sweep); always for
+// k = 5, 6.  Otherwise they live in shared memory and gmsgs is null.
+template <typename T, int NW, int G, int K, bool GM>
 __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const int M, const uint8_t* syn_src,
                                            const long long syn, const int c0, unsigned char* smem, T* gmsgs) {
   const int W = g.W, d = g.d, nb = g.nb, WW = W * W;
   const int m = 2 * d * (d - 1);
   static_assert(K <= 4 || G == 1, "k = 6 states hold one coset per CTA");
   constexpr int VEC = FusedDim<K>::vec;
-  const FusedLayout Lo = fused_layout<T, K>(g, M, NW, G);
+  const FusedLayout Lo = fused_layout<T, K>(g, M, NW, G, GM);
   uint8_t* synd = smem + Lo.synd;
   uint8_t* frames = smem + Lo.frame;
   int16_t* msg_of = reinterpret_cast<int16_t*>(smem + Lo.msg_of);
@@ -844,7 +847,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
   double* rlog = reinterpret_cast<double*>(smem + Lo.rlog);
   int* misc = reinterpret_cast<int*>(smem + Lo.misc);      // [0] counter, [2..4] list sizes, [8 + q] flags
   double* dsh = reinterpret_cast<double*>(smem + Lo.misc + 64);
-  T* msgs = K > 4 ? gmsgs : reinterpret_cast<T*>(smem + Lo.msgs);
+  T* msgs = GM ? gmsgs : reinterpret_cast<T*>(smem + Lo.msgs);
   const int stride = M * VEC;                                // messages of one coset
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1051,25 +1054,25 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
   }
 }
 
-// k <= 4: one CTA per (syndrome, group of G cosets).  k = 5, 6: a
-// persistent grid, CTA b taking items b, b + gridDim.x, ... with its
-// messages in workspace slot b.
-template <typename T, int NW, int G, int K>
+// Messages in shared memory: one CTA per (syndrome, group of G cosets).
+// Messages in the workspace (GM; always for k = 5, 6): a persistent grid,
+// CTA b taking items b, b + gridDim.x, ... with its messages in slot b.
+template <typename T, int NW, int G, int K, bool GM = (K > 4)>
 __global__ void __launch_bounds__(NW * 32, (FusedMinBlocks<T, NW, G, K>::value)) fused_kernel(KArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NG = 4 / G;
   const int m = 2 * a.geo.d * (a.geo.d - 1);
-  if constexpr (K > 4) {
+  if constexpr (GM) {
     T* gm = a.arena + (long long)blockIdx.x * a.slot_elems;
     for (long long item = blockIdx.x; item < a.n_items; item += gridDim.x) {
       const long long syn = item / NG;
-      fused_item<T, NW, G, K>(a, a.geo, a.M, a.synd + syn * m, syn, (int)(item % NG) * G, smem, gm);
+      fused_item<T, NW, G, K, true>(a, a.geo, a.M, a.synd + syn * m, syn, (int)(item % NG) * G, smem, gm);
       __syncthreads();
     }
   } else {
     const long long syn = blockIdx.x / NG;
     const int c0 = (int)(blockIdx.x % NG) * G;
-    fused_item<T, NW, G, K>(a, a.geo, a.M, a.synd + syn * m, syn, c0, smem, nullptr);
+    fused_item<T, NW, G, K, false>(a, a.geo, a.M, a.synd + syn * m, syn, c0, smem, nullptr);
   }
 }
 
@@ -1085,7 +1088,7 @@ struct MixedArgs {
   int k;
 };
 
-template <typename T, int NW, int G, int K>
+template <typename T, int NW, int G, int K, bool GM = (K > 4)>
 __global__ void __launch_bounds__(NW * 32, (FusedMinBlocks<T, NW, G, K>::value))
     fused_mixed_kernel(KArgs<T> a, MixedArgs mx) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1102,8 +1105,8 @@ __global__ void __launch_bounds__(NW * 32, (FusedMinBlocks<T, NW, G, K>::value))
     const Geo g = make_geo(mx.d_of[shot], mx.k);
     int M = 0, ae = 0;
     count_messages(g, 1, &M, &ae);
-    fused_item<T, NW, G, K>(a, g, M, a.synd + mx.offsets[shot], shot, c0, smem,
-                            K > 4 ? a.arena + (long long)blockIdx.x * a.slot_elems : nullptr);
+    fused_item<T, NW, G, K, GM>(a, g, M, a.synd + mx.offsets[shot], shot, c0, smem,
+                                GM ? a.arena + (long long)blockIdx.x * a.slot_elems : nullptr);
     __syncthreads();
   }
 }

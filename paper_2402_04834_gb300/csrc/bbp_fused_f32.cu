@@ -4,12 +4,19 @@
 
 namespace bbp {
 
-cudaError_t launch_fused_f32(const LaunchArgs& a, int warps, int cosets, cudaStream_t st) {
+cudaError_t launch_fused_f32(const LaunchArgs& a, int warps, int cosets, bool gm, cudaStream_t st) {
   if (a.geo.k > 4) {                       // block sides 5 and 6
     switch (warps * 10 + cosets) {
       case 21: return launch_fused_nw<float, 2, 1, 6>(a, st);
       case 41: return launch_fused_nw<float, 4, 1, 6>(a, st);
       case 61: return launch_fused_nw<float, 6, 1, 6>(a, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (gm) {                                // k <= 4, messages in the workspace
+    switch (warps * 10 + cosets) {
+      case 84: return launch_fused_nw<float, 8, 4, 4, true>(a, st);
+      case 82: return launch_fused_nw<float, 8, 2, 4, true>(a, st);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -25,13 +32,20 @@ cudaError_t launch_fused_f32(const LaunchArgs& a, int warps, int cosets, cudaStr
   }
 }
 
-cudaError_t launch_fused_mixed_f32(const LaunchArgs& a, const MixedLaunch& m, int warps, int cosets,
+cudaError_t launch_fused_mixed_f32(const LaunchArgs& a, const MixedLaunch& m, int warps, int cosets, bool gm,
                                    cudaStream_t st) {
   if (a.geo.k > 4) {
     switch (warps * 10 + cosets) {
       case 21: return launch_fused_mixed_nw<float, 2, 1, 6>(a, m, st);
       case 41: return launch_fused_mixed_nw<float, 4, 1, 6>(a, m, st);
       case 61: return launch_fused_mixed_nw<float, 6, 1, 6>(a, m, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (gm) {
+    switch (warps * 10 + cosets) {
+      case 84: return launch_fused_mixed_nw<float, 8, 4, 4, true>(a, m, st);
+      case 82: return launch_fused_mixed_nw<float, 8, 2, 4, true>(a, m, st);
       default: return cudaErrorInvalidValue;
     }
   }

@@ -4,7 +4,7 @@
 
 namespace bbp {
 
-cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, int cosets, cudaStream_t st) {
+cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, int cosets, bool gm, cudaStream_t st) {
   if (a.geo.k > 4) {
     switch (warps * 10 + cosets) {
       case 21: return launch_fused_nw<double, 2, 1, 6>(a, st);
@@ -12,6 +12,7 @@ cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, int cosets, cudaStr
       default: return cudaErrorInvalidValue;
     }
   }
+  if (gm) return warps * 10 + cosets == 42 ? launch_fused_nw<double, 4, 2, 4, true>(a, st) : cudaErrorInvalidValue;
   switch (warps * 10 + cosets) {
     case 81: return launch_fused_nw<double, 8, 1, 4>(a, st);
     case 42: return launch_fused_nw<double, 4, 2, 4>(a, st);
@@ -21,7 +22,7 @@ cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, int cosets, cudaStr
   }
 }
 
-cudaError_t launch_fused_mixed_f64(const LaunchArgs& a, const MixedLaunch& m, int warps, int cosets,
+cudaError_t launch_fused_mixed_f64(const LaunchArgs& a, const MixedLaunch& m, int warps, int cosets, bool gm,
                                    cudaStream_t st) {
   if (a.geo.k > 4) {
     switch (warps * 10 + cosets) {
@@ -30,6 +31,8 @@ cudaError_t launch_fused_mixed_f64(const LaunchArgs& a, const MixedLaunch& m, in
       default: return cudaErrorInvalidValue;
     }
   }
+  if (gm)
+    return warps * 10 + cosets == 42 ? launch_fused_mixed_nw<double, 4, 2, 4, true>(a, m, st) : cudaErrorInvalidValue;
   switch (warps * 10 + cosets) {
     case 81: return launch_fused_mixed_nw<double, 8, 1, 4>(a, m, st);
     case 42: return launch_fused_mixed_nw<double, 4, 2, 4>(a, m, st);
@@ -43,41 +46,61 @@ namespace {
 
 struct Shape {
   int warps, cosets;
+  bool gm;        // messages in a workspace slot of the CTA instead of shared memory
 };
 
-// Compiled shapes, in the order the default launch tries them: fastest
-// first on the d = 11, p = 0.10 workload (GB300, syndromes/s: FP32 (8,4)
-// 85.4k, (8,2) 69.9k, (4,2) 66.3k, (4,4) 56.7k, (16,1) 54.5k, (8,1) 53.2k,
-// (4,1) 51.3k; FP64 (4,2) 16.8k, (8,1) 12.9k, (4,4) 11.9k), then by the
-// shared memory they need, so that larger distances still find a shape.
-constexpr Shape kShapesF32[] = {{8, 4}, {8, 2}, {4, 2}, {4, 4}, {16, 1}, {8, 1}, {4, 1}};
-constexpr Shape kShapesF64[] = {{4, 2}, {8, 2}, {8, 1}, {4, 4}};
+// Compiled shapes in the order the default launch tries them.  Shared-memory
+// messages first where they leave room for the CTAs per SM the register
+// budget is sized for (FusedMinBlocks), then the same shape with its
+// messages in the workspace.  Speeds on the d = 11, p = 0.10 workload
+// (GB300, syndromes/s): FP32 (8,4) 85.4k, (8,2) 69.9k, (4,2) 66.3k, (4,4)
+// 56.7k, (16,1) 54.5k, (8,1) 53.2k, (4,1) 51.3k; FP64 (4,2) 16.8k, (8,1)
+// 12.9k, (4,4) 11.9k.
+constexpr Shape kShapesF32[] = {{8, 4, false}, {8, 4, true}, {8, 2, false}, {8, 2, true}, {4, 2, false},
+                                {4, 4, false}, {16, 1, false}, {8, 1, false}, {4, 1, false}};
+constexpr Shape kShapesF64[] = {{4, 2, false}, {4, 2, true}, {8, 2, false}, {8, 1, false}, {4, 4, false}};
 
 // Block sides 5 and 6: states of 2^12 entries, one coset per CTA, messages
 // in the workspace; the most warps whose state buffers fit one SM first.
-constexpr Shape kShapesF32K6[] = {{6, 1}, {4, 1}, {2, 1}};
-constexpr Shape kShapesF64K6[] = {{3, 1}, {2, 1}};
+constexpr Shape kShapesF32K6[] = {{6, 1, true}, {4, 1, true}, {2, 1, true}};
+constexpr Shape kShapesF64K6[] = {{3, 1, true}, {2, 1, true}};
+
+// Resident CTAs per SM that the register budget of a shape is sized for
+// (the host-side value of FusedMinBlocks).
+int target_blocks(int precision, int k, const Shape& s) {
+  const int warps = k > 4 ? s.warps : (precision == 0 ? 16 : 32) / (s.cosets > 1 ? 2 : 1);
+  return warps / s.warps > 1 ? warps / s.warps : 1;
+}
 
 }  // namespace
 
-int fused_smem_bytes(int precision, const Geo& g, int M, int warps, int cosets) {
+int fused_smem_bytes(int precision, const Geo& g, int M, int warps, int cosets, bool gm) {
   if (g.k > 4)
     return precision == 0 ? fused_smem_for<double, 6>(g, M, warps, cosets) : fused_smem_for<float, 6>(g, M, warps, cosets);
-  return precision == 0 ? fused_smem_for<double, 4>(g, M, warps, cosets) : fused_smem_for<float, 4>(g, M, warps, cosets);
+  return precision == 0 ? fused_smem_for<double, 4>(g, M, warps, cosets, gm)
+                        : fused_smem_for<float, 4>(g, M, warps, cosets, gm);
 }
 
-bool fused_shape(int precision, const Geo& g, int M, int* warps, int* cosets) {
+bool fused_shape(int precision, const Geo& g, int M, int* warps, int* cosets, int* messages) {
   const bool k6 = g.k > 4;
   const Shape* sh = k6 ? (precision == 0 ? kShapesF64K6 : kShapesF32K6) : (precision == 0 ? kShapesF64 : kShapesF32);
   const int n = k6 ? (precision == 0 ? (int)(sizeof(kShapesF64K6) / sizeof(Shape)) : (int)(sizeof(kShapesF32K6) / sizeof(Shape)))
                    : (precision == 0 ? (int)(sizeof(kShapesF64) / sizeof(Shape)) : (int)(sizeof(kShapesF32) / sizeof(Shape)));
-  for (int i = 0; i < n; ++i) {
-    if (*warps != 0 && sh[i].warps != *warps) continue;
-    if (*cosets != 0 && sh[i].cosets != *cosets) continue;
-    if (fused_smem_bytes(precision, g, M, sh[i].warps, sh[i].cosets) > kMaxSmemBytes) continue;
-    *warps = sh[i].warps;
-    *cosets = sh[i].cosets;
-    return true;
+  // Pass 0 keeps only shapes whose shared memory allows their target CTAs
+  // per SM; pass 1 any shape that fits.
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int i = 0; i < n; ++i) {
+      if (*warps != 0 && sh[i].warps != *warps) continue;
+      if (*cosets != 0 && sh[i].cosets != *cosets) continue;
+      if (*messages != 0 && (*messages == 2) != sh[i].gm) continue;
+      const int smem = fused_smem_bytes(precision, g, M, sh[i].warps, sh[i].cosets, sh[i].gm);
+      if (smem > kMaxSmemBytes) continue;
+      if (pass == 0 && kSmemPerSm / (smem + kSmemReservedPerCta) < target_blocks(precision, g.k, sh[i])) continue;
+      *warps = sh[i].warps;
+      *cosets = sh[i].cosets;
+      *messages = sh[i].gm ? 2 : 1;
+      return true;
+    }
   }
   return false;
 }

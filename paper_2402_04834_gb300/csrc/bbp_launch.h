@@ -37,16 +37,20 @@ struct LaunchArgs {
 int cta_smem_bytes(int precision, const Geo& g, int M);
 
 // Fused-block path (Remark 9): block side k <= kFusedMaxK; kernels compiled
-// for k <= 4 (messages in shared memory) and for k = 5, 6 (messages in a
-// workspace slot per resident CTA, at most kFusedSlots slots).
+// for k <= 4 (messages in shared memory, or for some shapes in a workspace
+// slot per resident CTA) and for k = 5, 6 (always in a workspace slot); at
+// most kFusedSlots slots.
 constexpr int kFusedMaxK = 6;
 constexpr long long kFusedSlots = 512;
 constexpr int kMaxSmemBytes = 227 * 1024;       // opt-in shared memory of one CTA
-int fused_smem_bytes(int precision, const Geo& g, int M, int warps, int cosets);
-// Launch shape of the fused kernel: *warps / *cosets are requests (0 = any);
-// on success they hold the first compiled shape that matches them and
-// whose shared memory fits, in the order of measured speed.
-bool fused_shape(int precision, const Geo& g, int M, int* warps, int* cosets);
+constexpr int kSmemPerSm = 228 * 1024;          // shared memory of one SM
+constexpr int kSmemReservedPerCta = 1024;       // reserved by the runtime per resident CTA
+int fused_smem_bytes(int precision, const Geo& g, int M, int warps, int cosets, bool gm);
+// Launch shape of the fused kernel: *warps / *cosets / *messages (1 shared
+// memory, 2 workspace slots) are requests (0 = any); on success they hold
+// the first compiled shape that matches them, preferring shapes whose
+// shared memory allows the CTAs per SM their registers are sized for.
+bool fused_shape(int precision, const Geo& g, int M, int* warps, int* cosets, int* messages);
 
 struct MixedLaunch {
   const int32_t* d_of;
@@ -59,11 +63,11 @@ struct MixedLaunch {
   long long slots = 0;
 };
 
-cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, int cosets, cudaStream_t st);
-cudaError_t launch_fused_f32(const LaunchArgs& a, int warps, int cosets, cudaStream_t st);
-cudaError_t launch_fused_mixed_f64(const LaunchArgs& a, const MixedLaunch& mx, int warps, int cosets,
+cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, int cosets, bool gm, cudaStream_t st);
+cudaError_t launch_fused_f32(const LaunchArgs& a, int warps, int cosets, bool gm, cudaStream_t st);
+cudaError_t launch_fused_mixed_f64(const LaunchArgs& a, const MixedLaunch& mx, int warps, int cosets, bool gm,
                                    cudaStream_t st);
-cudaError_t launch_fused_mixed_f32(const LaunchArgs& a, const MixedLaunch& mx, int warps, int cosets,
+cudaError_t launch_fused_mixed_f32(const LaunchArgs& a, const MixedLaunch& mx, int warps, int cosets, bool gm,
                                    cudaStream_t st);
 cudaError_t launch_decode_f64(const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_decode_f32(const LaunchArgs& a, cudaStream_t st);

@@ -44,6 +44,18 @@ extern "C" int bbp_decode_batch_static(const uint8_t* syndromes, int64_t B, cons
   size_t need = 0;
   int rc = bbp_workspace_bytes(prm, B, 0, &need);
   if (rc != BBP_OK) return rc;
+  bbp_params shared = {};
+  if (need > (size_t)BBP_STATIC_WORKSPACE_BYTES && prm->algorithm == BBP_ALG_FUSED && prm->launch_messages == 0) {
+    // The default shape keeps its messages in the workspace; a shape that
+    // keeps them in shared memory needs none.
+    shared = *prm;
+    shared.launch_messages = 1;
+    size_t need_shared = 0;
+    if (bbp_workspace_bytes(&shared, B, 0, &need_shared) == BBP_OK) {
+      prm = &shared;
+      need = need_shared;
+    }
+  }
   if (need > (size_t)BBP_STATIC_WORKSPACE_BYTES) return BBP_ETOOLARGE;
   if (B == 0) return BBP_OK;
   if (!syndromes || !logp || !delta || !iters || !flags || !decision) return BBP_EINVAL;

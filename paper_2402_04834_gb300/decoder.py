@@ -149,9 +149,9 @@ def decode_mixed(packed, offsets, d_of, prm: DecoderParams, largest_first=True, 
         order = torch.argsort(d_of, descending=True, stable=True).to(torch.int32)
     if d_max is None:
         d_max = int(d_of.max().item())
-    need = 256
-    if prm.k > 4:   # message slots after the work counter
-        need += workspace_bytes(dataclasses.replace(prm, d=d_max), B)
+    # The work counter, then the message slots when the launch shape keeps
+    # its messages in the workspace (none otherwise).
+    need = 256 + workspace_bytes(dataclasses.replace(prm, d=d_max), B)
     if counter is None or counter.numel() < need:
         counter = torch.empty(need, dtype=torch.uint8, device=dev)
     cp = prm.c()

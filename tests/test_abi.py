@@ -51,7 +51,7 @@ def test_workspace_sizes_scale_with_batch(L):
 
 @pytest.mark.parametrize("field,val", [("d", 1), ("k", 0), ("D", 0), ("p", 0.0), ("p", 0.8),
                                        ("eta", 1.0), ("precision", 7), ("max_iter", -1),
-                                       ("launch_warps", 5), ("launch_cosets", 3)])
+                                       ("launch_warps", 5), ("launch_cosets", 3), ("launch_messages", 3)])
 def test_invalid_parameters_rejected(L, field, val):
     c = pkg.DecoderParams(d=5, k=3, D=4).c()
     setattr(c, field, val)
@@ -85,12 +85,26 @@ def test_fused_launch_shapes_checked_on_the_host(L):
             assert L.bbp_workspace_bytes(ctypes.byref(c), 10, 0, ctypes.byref(out)) == 0, (prec, w, g)
     c = pkg.DecoderParams(d=31, k=6, precision="fp64", algorithm="fused", warps=4, cosets=1).c()
     assert L.bbp_workspace_bytes(ctypes.byref(c), 10, 0, ctypes.byref(out)) == -4
+    for prec, shapes in pkg.FUSED_SHAPES_WS.items():
+        for w, g in shapes:
+            c = pkg.DecoderParams(d=13, k=4, precision=prec, algorithm="fused", warps=w, cosets=g, messages=2).c()
+            assert L.bbp_workspace_bytes(ctypes.byref(c), 10, 0, ctypes.byref(out)) == 0 and out.value > 0
+    c = pkg.DecoderParams(d=13, k=4, precision="fp32", algorithm="fused", warps=4, cosets=4, messages=2).c()
+    assert L.bbp_workspace_bytes(ctypes.byref(c), 10, 0, ctypes.byref(out)) == -4   # not compiled
+    c = pkg.DecoderParams(d=13, k=6, precision="fp32", algorithm="fused", messages=1).c()
+    assert L.bbp_workspace_bytes(ctypes.byref(c), 10, 0, ctypes.byref(out)) == -4   # k = 6: workspace only
 
 
 def test_fused_k6_workspace_holds_one_message_slot_per_resident_cta(L):
     # k <= 4 keeps the messages in shared memory; k = 5, 6 keep them in
     # min(4B, 512) slots of 64 M scalars (d = 31: M = 440 directed edges).
-    assert pkg.workspace_bytes(pkg.DecoderParams(d=31, k=4, precision="fp32", algorithm="fused"), 1000) == 0
+    assert pkg.workspace_bytes(pkg.DecoderParams(d=31, k=4, precision="fp32", algorithm="fused", messages=1),
+                               1000) == 0
+    # k = 4 at d = 31: the default shape (8 warps, 2 cosets; with 4 cosets the
+    # per-message tables alone leave room for one CTA per SM) keeps its
+    # messages in min(2B, 512) slots of 2 x M x 16 scalars (M = 4 * 16 * 15).
+    assert pkg.workspace_bytes(pkg.DecoderParams(d=31, k=4, precision="fp32", algorithm="fused"), 1000) == \
+        512 * 2 * 960 * 16 * 4
     for B, prec, size in ((10, "fp32", 4), (10, "fp64", 8), (1000, "fp32", 4)):
         slots = min(4 * B, 512)
         want = -(-slots * 440 * 64 * size // 256) * 256
@@ -191,17 +205,18 @@ def test_message_classes_on_the_host(L, d, k):
     assert L.bbp_message_classes(ctypes.byref(bad), uq, rk, ctypes.byref(U)) == -1
 
 
-@pytest.mark.parametrize("alg,prec,k,d_max", [("fused", "fp32", 4, 48), ("fused", "fp64", 4, 36),
-                                              ("fused", "fp32", 2, 25), ("fused", "fp32", 1, 13),
-                                              ("fused", "fp32", 6, 64), ("fused", "fp64", 6, 64),
-                                              ("mps", "fp64", 4, 64), ("mps", "fp32", 4, 64)])
-def test_largest_supported_distance(L, alg, prec, k, d_max):
-    # Fused k <= 4 keeps every message in shared memory, which bounds d (the
-    # messages of k < 4 are padded to 16 entries); k = 6 and the MPS form keep
-    # them in the workspace and take the API's d <= 64.  Past the bound the
-    # call is refused on the host.
+@pytest.mark.parametrize("alg,prec,k,messages,d_max", [
+    ("fused", "fp32", 4, 1, 48), ("fused", "fp64", 4, 1, 36), ("fused", "fp32", 4, 0, 60), ("fused", "fp64", 4, 0, 60),
+    ("fused", "fp32", 2, 0, 32), ("fused", "fp32", 1, 0, 17), ("fused", "fp32", 2, 1, 25), ("fused", "fp32", 1, 1, 13),
+    ("fused", "fp32", 6, 0, 64), ("fused", "fp64", 6, 0, 64), ("mps", "fp64", 4, 0, 64), ("mps", "fp32", 4, 0, 64)])
+def test_largest_supported_distance(L, alg, prec, k, messages, d_max):
+    # Fused k <= 4 with its messages in shared memory is bounded by them (the
+    # messages of k < 4 are padded to 16 entries); with the messages in
+    # workspace slots by the per-message tables that stay in shared memory;
+    # k = 6 and the MPS form take the API's d <= 64.  Past the bound the call
+    # is refused on the host.
     out = ctypes.c_size_t(0)
-    c = pkg.DecoderParams(d=d_max, k=k, D=8, precision=prec, algorithm=alg).c()
+    c = pkg.DecoderParams(d=d_max, k=k, D=8, precision=prec, algorithm=alg, messages=messages).c()
     assert L.bbp_workspace_bytes(ctypes.byref(c), 4, 0, ctypes.byref(out)) == 0
-    c = pkg.DecoderParams(d=d_max + 1, k=k, D=8, precision=prec, algorithm=alg).c()
+    c = pkg.DecoderParams(d=d_max + 1, k=k, D=8, precision=prec, algorithm=alg, messages=messages).c()
     assert L.bbp_workspace_bytes(ctypes.byref(c), 4, 0, ctypes.byref(out)) == (-4 if d_max < 64 else -1)

@@ -130,17 +130,19 @@ def test_autotuned_shapes_give_identical_results(dev):
     s = torch.from_numpy(S).to(dev)
     prm = pkg.DecoderParams(d=d, k=4, p=p, max_iter=10, precision="fp32", algorithm="fused")
     best, table = autotune.tune_uniform(s, prm)
-    assert len(table) == len(pkg.FUSED_SHAPES["fp32"]) and (best.warps, best.cosets) in pkg.FUSED_SHAPES["fp32"]
+    cands = autotune.candidates(prm)
+    assert len(table) == len(cands) and (best.warps, best.cosets, best.messages) in cands
     ref = pkg.decode(s, prm)
-    for w, c in pkg.FUSED_SHAPES["fp32"]:
-        got = pkg.decode(s, pkg.DecoderParams(**{**prm.__dict__, "warps": w, "cosets": c}))
+    for w, c, mem in cands:
+        got = pkg.decode(s, pkg.DecoderParams(**{**prm.__dict__, "warps": w, "cosets": c, "messages": mem}))
         torch.cuda.synchronize()
         for key in ("logp", "delta", "iters", "flags"):
-            assert torch.equal(got[key], ref[key]), (w, c, key)
+            assert torch.equal(got[key], ref[key]), (w, c, mem, key)
     ds, shots = mixed_batch(128, [7, 9, 13], p, 5)
     packed, offsets, d_of = pack_mixed(shots, device=dev)
     mp = pkg.DecoderParams(d=0, k=4, p=p, max_iter=10, precision="fp32", algorithm="fused")
-    best, table = autotune.tune_mixed(packed, offsets, d_of, mp, shapes=((8, 4), (8, 2), (8, 1)), ctas=(0, 2))
+    best, table = autotune.tune_mixed(packed, offsets, d_of, mp, shapes=((8, 4, 1), (8, 4, 2), (8, 2, 1), (8, 1, 1)),
+                                      ctas=(0, 2))
     assert len(table) >= 2
     a = decode_mixed(packed, offsets, d_of, best)
     b = decode_mixed(packed, offsets, d_of, mp)
@@ -155,10 +157,12 @@ def test_mixed_workload_4096_over_five_distances(dev):
     ds, shots = mixed_batch(4096, [7, 9, 13, 17, 21], p, 3000)
     packed, offsets, d_of = pack_mixed(shots, device=dev)
     prm = pkg.DecoderParams(d=0, k=4, p=p, max_iter=20, delta0=1e-4, precision="fp32", algorithm="fused")
-    best, table = autotune.tune_mixed(packed, offsets, d_of, prm, shapes=((8, 4), (8, 2), (8, 1)), ctas=(0, 2))
+    best, table = autotune.tune_mixed(packed, offsets, d_of, prm, shapes=((8, 4, 1), (8, 4, 2), (8, 2, 1), (8, 1, 1)),
+                                      ctas=(0, 2))
     out = decode_mixed(packed, offsets, d_of, best)
     torch.cuda.synchronize()
-    counter = torch.empty(256, dtype=torch.uint8, device=dev)
+    counter = torch.empty(256 + pkg.workspace_bytes(pkg.DecoderParams(**{**best.__dict__, "d": 21}), len(shots)),
+                          dtype=torch.uint8, device=dev)
     g = torch.cuda.CUDAGraph()
     stream = torch.cuda.Stream()
     stream.wait_stream(torch.cuda.current_stream())

@@ -60,7 +60,9 @@ def naive_logp(S, d, k, p, iters, delta0=0.0):
 
 
 # Every compiled launch shape (warps per CTA, cosets per CTA) of each precision.
-SHAPES = [(prec, w, c) for prec, shapes in pkg.FUSED_SHAPES.items() for (w, c) in shapes]
+# ... with the messages in shared memory (1) and, where compiled, in workspace slots (2).
+SHAPES = ([(prec, w, c, 1) for prec, shapes in pkg.FUSED_SHAPES.items() for (w, c) in shapes] +
+          [(prec, w, c, 2) for prec, shapes in pkg.FUSED_SHAPES_WS.items() for (w, c) in shapes])
 
 
 @pytest.mark.parametrize("d,k,iters,p", [
@@ -71,11 +73,12 @@ SHAPES = [(prec, w, c) for prec, shapes in pkg.FUSED_SHAPES.items() for (w, c) i
     (4, 1, 4, 0.10),      # one node per block (plain BP on the network)
     (2, 3, 3, 0.20),      # one block, no messages
 ])
-@pytest.mark.parametrize("precision,warps,cosets", SHAPES, ids=[f"{a}-w{b}-g{c}" for a, b, c in SHAPES])
-def test_fused_matches_dense_oracle(dev, d, k, iters, p, precision, warps, cosets):
+@pytest.mark.parametrize("precision,warps,cosets,messages", SHAPES,
+                         ids=[f"{a}-w{b}-g{c}-m{m}" for a, b, c, m in SHAPES])
+def test_fused_matches_dense_oracle(dev, d, k, iters, p, precision, warps, cosets, messages):
     _, _, S = synth.sample_syndromes(515, 0, 3, d, p)
     prm = pkg.DecoderParams(d=d, k=k, p=p, max_iter=iters, delta0=0.0, precision=precision,
-                            algorithm="fused", warps=warps, cosets=cosets)
+                            algorithm="fused", warps=warps, cosets=cosets, messages=messages)
     out = gpu(S, prm, dev)
     ref = naive_logp(S, d, k, p, iters)
     tol = 1e-9 if precision == "fp64" else 1e-3
@@ -203,16 +206,17 @@ def test_fused_equals_mps_golden_at_d11(dev):
         assert int(out["decision"][b]) == r["decision"]
 
 
-@pytest.mark.parametrize("precision,warps,cosets", [("fp64", 8, 1), ("fp64", 4, 2), ("fp64", 8, 2), ("fp64", 4, 4),
-                                                    ("fp32", 8, 4), ("fp32", 8, 2)])
-def test_fused_early_exit_and_decision(dev, precision, warps, cosets):
+@pytest.mark.parametrize("precision,warps,cosets,messages", [
+    ("fp64", 8, 1, 1), ("fp64", 4, 2, 1), ("fp64", 8, 2, 1), ("fp64", 4, 4, 1), ("fp64", 4, 2, 2),
+    ("fp32", 8, 4, 1), ("fp32", 8, 2, 1), ("fp32", 8, 4, 2), ("fp32", 8, 2, 2)])
+def test_fused_early_exit_and_decision(dev, precision, warps, cosets, messages):
     # delta0 = 1e-4: the cosets of one syndrome stop at different
     # iterations; a CTA that decodes several of them freezes each one when
     # it converges, so iterations and log P match a coset decoded alone.
     d, k, p = 7, 4, 0.06
     _, _, S = synth.sample_syndromes(77, 0, 4, d, p)
     prm = pkg.DecoderParams(d=d, k=k, p=p, max_iter=40, delta0=1e-4, algorithm="fused", precision=precision,
-                            warps=warps, cosets=cosets)
+                            warps=warps, cosets=cosets, messages=messages)
     out = gpu(S, prm, dev)
     lat = Lattice(d)
     margin, tol = (1e-6, 1e-9) if precision == "fp64" else (1e-5, 1e-3)
@@ -233,16 +237,45 @@ def test_fused_early_exit_and_decision(dev, precision, warps, cosets):
 
 
 def test_fused_needs_no_workspace(dev):
-    prm = pkg.DecoderParams(d=11, k=4, algorithm="fused")
+    # The benchmark's shape keeps its messages in shared memory.
+    prm = pkg.DecoderParams(d=11, k=4, algorithm="fused", precision="fp32")
     assert pkg.workspace_bytes(prm, 1000) == 0
+    assert pkg.workspace_bytes(pkg.DecoderParams(d=11, k=4, algorithm="fused", messages=2, precision="fp32"),
+                               1000) > 0
 
 
-@pytest.mark.parametrize("d,precision", [(48, "fp32"), (36, "fp64")])
-def test_fused_k4_at_the_largest_distance(dev, d, precision):
-    # The largest distances whose messages fit in shared memory: finite
-    # log-probabilities below 0, valid decisions, repeatable bit for bit.
+@pytest.mark.parametrize("d,precision,warps,cosets", [(11, "fp32", 8, 4), (13, "fp32", 8, 2), (21, "fp32", 8, 4),
+                                                      (11, "fp64", 4, 2), (13, "fp64", 4, 2)])
+def test_messages_in_workspace_or_shared_memory_give_the_same_bits(dev, d, precision, warps, cosets):
+    # Where the messages live (shared memory, or a workspace slot of a
+    # persistent CTA reused by several items) changes no bit of any output,
+    # early exit, initial messages and exported messages included.
+    from paper_2402_04834_gb300 import warmstart as wsm
+    _, _, S = synth.sample_syndromes(1300 + d, 0, 400, d, 0.1)
+    s = torch.from_numpy(S).to(dev)
+    M = wsm.message_count(pkg.DecoderParams(d=d, k=4, algorithm="fused"))
+    init = torch.rand((400 * 4 * M, 16), generator=torch.Generator().manual_seed(d)).to(dev) + 0.01
+    res = {}
+    for mem in (1, 2):
+        prm = pkg.DecoderParams(d=d, k=4, p=0.1, max_iter=15, delta0=1e-4, precision=precision, algorithm="fused",
+                                warps=warps, cosets=cosets, messages=mem)
+        final = torch.empty_like(init)
+        res[mem] = (wsm.decode_ex(s, prm), wsm.decode_ex(s, prm, init_msgs=init, final_msgs=final), final)
+    torch.cuda.synchronize()
+    for i in range(2):
+        for key in ("logp", "delta", "iters", "flags", "decision"):
+            assert torch.equal(res[1][i][key], res[2][i][key]), (i, key)
+    assert torch.equal(res[1][2], res[2][2])
+
+
+@pytest.mark.parametrize("d,precision,messages", [(48, "fp32", 1), (36, "fp64", 1), (60, "fp32", 0), (60, "fp64", 0)])
+def test_fused_k4_at_the_largest_distance(dev, d, precision, messages):
+    # The largest distances with the messages in shared memory (48 / 36) and
+    # in the workspace (60): finite log-probabilities below 0, valid
+    # decisions, repeatable bit for bit.
     _, _, S = synth.sample_syndromes(4800 + d, 0, 2, d, 0.1)
-    prm = pkg.DecoderParams(d=d, k=4, p=0.1, max_iter=3, delta0=0.0, precision=precision, algorithm="fused")
+    prm = pkg.DecoderParams(d=d, k=4, p=0.1, max_iter=3, delta0=0.0, precision=precision, algorithm="fused",
+                            messages=messages)
     a, b = gpu(S, prm, dev), gpu(S, prm, dev)
     assert np.all(np.isfinite(a["logp"])) and np.all(a["logp"] < 0)
     assert np.all((a["decision"] >= 0) & (a["decision"] < 4))
