@@ -26,12 +26,15 @@ from .decoder import decode, sample
 from .warmstart import wilson
 
 
-def logical_error_rate(d: int, p: float, shots: int, seed: int, chunk: int = 16384, **params) -> dict:
+def logical_error_rate(d: int, p: float, shots: int, seed: int, chunk: int = 16384, first_shot: int = 0,
+                       **params) -> dict:
     """Decode ``shots`` seeded syndromes, ``chunk`` per call after one
     untimed warm-up call; P_L with its Wilson 95 % interval, mean iterations
     over cosets, syndromes per second (device time of the decode calls) and
     a histogram of the final Delta of every coset by decade."""
-    _, _, s, tc = sample(seed, 0, shots, d, p, with_errors=False)
+    # Shots first_shot .. first_shot + shots - 1 of the seed's counter-based
+    # stream: a run resumes, or splits into parts, by shot index.
+    _, _, s, tc = sample(seed, first_shot, shots, d, p, with_errors=False)
     prm = DecoderParams(d=d, p=p, **params)
     decode(s[:min(shots, 64)], prm)
     torch.cuda.synchronize()
@@ -51,21 +54,22 @@ def logical_error_rate(d: int, p: float, shots: int, seed: int, chunk: int = 163
     # Final Delta of every coset in decades: [0, 1e-8), [1e-8, 1e-7), ..., [1e-1, inf).
     dl = torch.cat(dls).double().clamp_min(1e-300).log10().floor().clamp(-9, -1).cpu()
     hist = [int((dl == e).sum().item()) for e in range(-9, 0)]
-    return {"d": d, "p": p, "shots": shots, **params, "failures": fails, "P_L": fails / shots,
+    return {"d": d, "p": p, "shots": shots, "first_shot": first_shot, **params, "failures": fails,
+            "P_L": fails / shots,
             "P_L_wilson95": [lo, hi], "mean_iters": float(torch.cat(its).double().mean().item()),
             "syndromes_per_s": shots / ms * 1e3,
             "delta_decades": {"edges": [0.0] + [10.0 ** e for e in range(-8, 0)] + ["inf"], "counts": hist}}
 
 
 def sweep(d_list, p_list, max_iters, shots, k=4, precision="fp32", algorithm="fused", seed_base=7000,
-          seed_per_d=100):
+          seed_per_d=100, first_shot=0):
     """Seeds: seed_base + seed_per_d * d + (index of p in p_list)."""
     rows = []
     for d in d_list:
         for ip, p in enumerate(p_list):
             for mi in max_iters:
                 rows.append(logical_error_rate(d, p, shots, seed_base + seed_per_d * d + ip, k=k, max_iter=mi,
-                                               precision=precision, algorithm=algorithm))
+                                               precision=precision, algorithm=algorithm, first_shot=first_shot))
     return rows
 
 
@@ -80,9 +84,11 @@ def main():
     ap.add_argument("--k", type=int, default=4, help="block side (6: the d = 31 scheme of Sec. IV)")
     ap.add_argument("--seed-base", type=int, default=7000)
     ap.add_argument("--seed-per-d", type=int, default=100)
+    ap.add_argument("--first-shot", type=int, default=0, help="resume or split a run by shot index")
     args = ap.parse_args()
     for r in sweep(args.d, args.p, args.max_iter, args.shots, k=args.k, precision=args.precision,
-                   algorithm=args.algorithm, seed_base=args.seed_base, seed_per_d=args.seed_per_d):
+                   algorithm=args.algorithm, seed_base=args.seed_base, seed_per_d=args.seed_per_d,
+                   first_shot=args.first_shot):
         print(json.dumps(r), flush=True)
 
 

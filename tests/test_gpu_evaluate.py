@@ -29,3 +29,15 @@ def test_failure_count_matches_oracle_true_class():
     assert r["failures"] == fails
     lo, hi = r["P_L_wilson95"]
     assert lo <= r["P_L"] <= hi and r["mean_iters"] <= 10
+
+
+def test_runs_split_by_shot_index_add_up():
+    # The sampler is counter-based: shots 0 .. 399 decoded in two parts give
+    # the failures and iterations of one run over all of them.
+    build()
+    kw = dict(k=4, max_iter=10, precision="fp32", algorithm="fused")
+    whole = evaluate.logical_error_rate(7, 0.12, 400, 77, **kw)
+    a = evaluate.logical_error_rate(7, 0.12, 150, 77, first_shot=0, **kw)
+    b = evaluate.logical_error_rate(7, 0.12, 250, 77, first_shot=150, **kw)
+    assert a["failures"] + b["failures"] == whole["failures"]
+    assert abs(a["mean_iters"] * 150 + b["mean_iters"] * 250 - whole["mean_iters"] * 400) < 1e-6
