@@ -86,8 +86,8 @@ struct KArgs {
   int32_t* flags;
   const float* init_msgs;   // fused path: [cta][M][16] initial messages, or null (uniform)
   float* final_msgs;        // fused path: [cta][M][16] messages after the BP loop, or null
-  long long n_items;        // fused path, k = 5, 6: (syndrome, coset group) items of the launch
-  long long slot_elems;     // fused path, k = 5, 6: scalars of one CTA's message slot in arena
+  long long n_items;        // fused path, messages in the workspace: (syndrome, coset group) items
+  long long slot_elems;     // fused path, messages in the workspace: scalars of one CTA's slot in arena
 };
 
 // Everything a warp needs to reach the CTA's shared tables.

@@ -30,7 +30,7 @@ struct LaunchArgs {
   long long B;
   const float* init_msgs = nullptr;
   float* final_msgs = nullptr;
-  long long slots = 0;            // fused, k = 5, 6: message slots of 64 * M scalars in arena
+  long long slots = 0;            // fused, messages in the workspace: slots of G * M * vec scalars in arena
 };
 
 // Shared memory of one CTA in bytes for the given precision (0 = fp64, 1 = fp32).
@@ -59,7 +59,7 @@ struct MixedLaunch {
   unsigned long long* counter;
   int d_max;
   int ctas_per_sm;
-  void* slot_base = nullptr;      // k = 5, 6: message slots (kernel scalars), 64 * M(d_max) each
+  void* slot_base = nullptr;      // messages in the workspace: slots of G * M(d_max) * vec scalars
   long long slots = 0;
 };
 
