@@ -47,8 +47,8 @@ KArgs<T> fused_args(const LaunchArgs& a) {
   return k;
 }
 
-// Persistent grid of a launch with its messages in workspace slots: resident CTAs, at most one per item
-// and per message slot.
+// Persistent grid of a launch with its messages in workspace slots:
+// resident CTAs, at most one per item and per message slot.
 template <typename Kern>
 cudaError_t persistent_grid(Kern kern, int threads, int smem, int ctas_per_sm, long long items, long long slots,
                             long long* grid) {
