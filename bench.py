@@ -4,15 +4,18 @@ Workload (one step = one batch through the whole hot path): the distance-11
 planar surface code under depolarizing noise p = 0.10, 10^4 seeded synthetic
 syndromes per GPU, blockBP with 4x4-node blocks, max-iter 20, delta0 = 1e-4,
 delta1 = 1e-2, eta = 0.1 (Sec. IV parameters), D = 8 for the MPS form.
-The headline decoder is the learned + mixed-precision one: message
-features, the warm-start network on the tensor cores (trained first,
-untimed, on converged messages of seeded decodes), then the fused-block
-form of Remark 9 (the form the paper ran for k = 4) in FP32 with FP64
-Delta sums and read-out, started from the network's proposals.  Timed
-beside it on the same batch: the same decoder from the uniform start
-(cold), the plain FP64 blockBP with MPS messages (the denominator of the
-metric), the FP64 fused form and the FP32 MPS form.  ``--no-warm`` makes
-the cold decoder the headline.
+The headline decoder is the learned + mixed-precision one: features of
+the distinct message rows, the warm-start network on the tensor cores
+(trained first, untimed, on converged messages of seeded decodes) and the
+expansion of its proposals to every coset, then the fused-block form of
+Remark 9 (the form the paper ran for k = 4) in FP32 with FP64 Delta sums
+and read-out, started from the proposals.  Timed beside it on the same
+batch: the same decoder from the uniform start (cold), the plain FP64
+blockBP with MPS messages (the denominator of the metric), the FP64 fused
+form and the FP32 MPS form; then a mixed-distance batch (4096 syndromes,
+d in {7, 9, 13, 17, 21}) in one autotuned persistent launch replayed from
+a CUDA graph, against one launch per distance.  ``--no-warm`` makes the
+cold decoder the headline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
