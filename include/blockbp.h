@@ -219,7 +219,12 @@ int bbp_pure_error(int32_t d, const uint8_t* syndromes, int64_t B, uint8_t* fx, 
  *   syndromes in FP32, 256 in FP64).
  *   The first call on a device looks up the array's device address (once per
  *   device, with that device current); make that first call before any
- *   stream capture begins.  No call allocates or frees memory.
+ *   stream capture begins.  With CUDA's lazy module loading (the default)
+ *   that first look-up is also when the device reserves the 32 MiB, so it
+ *   can fail with BBP_ECUDA when the device is out of memory: make it at
+ *   start-up.  The address is cached per device ordinal for the life of the
+ *   process; resetting the device (cudaDeviceReset) after a call leaves the
+ *   cache stale and is not supported.  No call allocates or frees memory.
  *   Every call shares the one array, and the kernel initialises each message
  *   before it reads it, so nothing must start at zero and the last call's
  *   contents are simply overwritten.  Calls whose kernels overlap on the GPU

@@ -10,9 +10,10 @@
 //
 // A warp owns a shared-memory workspace holding the running boundary MPS of
 // one block contraction.  The linear algebra is warp-cooperative on that
-// workspace: Householder QR (right-to-left canonicalisation sweep) and
-// one-sided Jacobi SVD with truncation (left-to-right sweep), the textbook
-// MPS compression of Sec. III.A.  Every loop is bounded; nothing spins.
+// workspace: an LQ step by two passes of modified Gram-Schmidt in registers
+// (right-to-left canonicalisation sweep) and one-sided Jacobi SVD with
+// truncation (left-to-right sweep), the textbook MPS compression of
+// Sec. III.A.  Every loop is bounded; nothing spins.
 #pragma once
 
 #include <cuda_runtime.h>

@@ -109,7 +109,11 @@ __global__ void pure_error_kernel(int d, const uint8_t* synd, long long B, uint8
 cudaError_t launch_pure_error(int d, const uint8_t* synd, long long B, uint8_t* fx, uint8_t* fz, cudaStream_t st) {
   const long long total = B * (long long)(d * d + (d - 1) * (d - 1));
   long long blocks = (total + 255) / 256;
-  if (blocks > 152 * 64) blocks = 152 * 64;          // grid-stride beyond 64 blocks per SM
+  int dev = 0, sms = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if (blocks > (long long)sms * 64) blocks = (long long)sms * 64;   // grid-stride beyond 64 blocks per SM
   pure_error_kernel<<<(unsigned)blocks, 256, 0, st>>>(d, synd, B, fx, fz);
   return cudaGetLastError();
 }

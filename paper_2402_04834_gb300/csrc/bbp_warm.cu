@@ -375,7 +375,11 @@ int bbp_expand_rows(const float* rows, int64_t B, int32_t U, const int32_t* uniq
   if (B == 0) return BBP_OK;
   const long long total = B * 4 * (long long)M * 4;
   long long blocks = (total + 255) / 256;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return BBP_ECUDA;
+  if (blocks > (long long)sms * 32) blocks = (long long)sms * 32;   // grid-stride beyond 32 blocks per SM
   expand_rows_kernel<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
       reinterpret_cast<const float4*>(rows), B, U, uniq_of, M, reinterpret_cast<float4*>(msgs));
   return cudaGetLastError() == cudaSuccess ? BBP_OK : BBP_ECUDA;

@@ -39,13 +39,23 @@ WORKLOADS = {
                seed=synth.workload_seed(1, 0), first_shot=0, shots=200),
     # Distance 11, p = 0.10, k = 4, D = 8, 20 fixed iterations.
     "d11": dict(file="oracle_d11_k4_D8_p010.json", d=11, k=4, D=8, p=0.10, max_iter=20, delta0=0.0,
-                seed=synth.workload_seed(2, 2), first_shot=0, shots=12),
+                seed=synth.workload_seed(2, 2), first_shot=0, shots=200),
 }
 # The other noise levels of the d = 11 workload (p index 0, 1, 3, 4).
 for _ip, _p in ((0, 0.05), (1, 0.08), (3, 0.13), (4, 0.15)):
     WORKLOADS[f"d11_p{int(round(_p * 100)):03d}"] = dict(
         file=f"oracle_d11_k4_D8_p{int(round(_p * 100)):03d}.json", d=11, k=4, D=8, p=_p, max_iter=20,
-        delta0=0.0, seed=synth.workload_seed(2, _ip), first_shot=0, shots=4)
+        delta0=0.0, seed=synth.workload_seed(2, _ip), first_shot=0, shots=50)
+
+# Truncating MPS workloads: k = 4 with D = 2 and 4 at d = 9 and 11 (p = 0.10,
+# 20 fixed iterations).  The in-block boundary MPS of a 4 x 4 block needs a
+# bond of up to 16, so both bonds truncate inside every block, and D = 2
+# also truncates the messages (exact bond up to 4).
+for _d in (9, 11):
+    for _D in (2, 4):
+        WORKLOADS[f"d{_d}_D{_D}"] = dict(
+            file=f"oracle_d{_d}_k4_D{_D}_p010.json", d=_d, k=4, D=_D, p=0.10, max_iter=20, delta0=0.0,
+            seed=synth.workload_seed(6, 10 * _d + _D), first_shot=0, shots=24)
 
 # Distance 31, k = 6 (dense 64-entry messages), 20 fixed iterations, at the
 # two noise levels of the d = 31 workload (p index 0, 1).
