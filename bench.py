@@ -61,11 +61,10 @@ FP64_FMA_PER_SM_CLK = 2
 # Warm-start network: 256 -> 256 -> 256 -> 16, two flops per multiply-add.
 MLP_FLOPS_PER_ROW = 2 * (256 * 256 + 256 * 256 + 256 * 16)
 # DRAM bytes read + written per unit, from ncu captures (dram__bytes_read.sum
-# + dram__bytes_write.sum) of the current kernels: the network kernel moved
-# 1.234 GB + 74.6 MB for 1.2 M rows.  The fused decode kernel keeps its
-# state on chip; its DRAM bytes per syndrome are filled in from a capture of
-# the current build (None until then).
-FUSED_DRAM_BYTES_PER_SYNDROME = None
+# + dram__bytes_write.sum) of the current kernels: the fused decode kernel
+# moved 989.4 KB + 1363.5 KB for 1024 syndromes (d = 11, 4 cosets per CTA);
+# the network kernel 1.234 GB + 74.6 MB for 1.2 M rows.
+FUSED_DRAM_BYTES_PER_SYNDROME = (989.44e3 + 1363.456e3) / 1024
 NETWORK_DRAM_BYTES_PER_ROW = (1.234248e9 + 74.605312e6) / 1.2e6
 
 
@@ -112,8 +111,9 @@ def run_oracle_sample(first_shot: int, n: int, procs: int, algorithm: str):
 def fused_flops(d: int, k: int):
     """Algorithmic arithmetic of the fused-block update (multiply-adds count 2), per coset.
 
-    Returns (per BP iteration, read-out).  Every block is contracted towards
-    each neighbour in the kernel's order: per column, the side message's data
+    Returns (per BP iteration, read-out).  A 4 x 4 block counts the register
+    form of its update (see the kernel); every other block is contracted
+    towards each neighbour in the kernel's order: per column, the side message's data
     column (a dense contraction over the legs recorded so far), then the
     column's nodes, then the closing sums of the other side message.  Only
     the qubit nodes do arithmetic: their tensor pi(f + (x, z)) is a 2 x 2
@@ -170,7 +170,16 @@ def fused_flops(d: int, k: int):
                     order = rows if dr == 2 else reversed(rows)
                     lines = [[(i, j) for j in cols] for i in order]
                     h, ha, hb = c1 - c0, J > 0, J + 1 < nb
-                per_iter += sweep(qubits(lines), h, ha, hb, False) + 12.0 * 2 ** h
+                if h == 4 and len(lines) == 4:
+                    # 4 x 4 blocks: the register form of the update (butterflies
+                    # over single row bits, side messages contracted where their
+                    # legs enter), per (row, coset) entry 116 multiply-adds when
+                    # column 0 starts with a qubit and 108 when it starts with a
+                    # check.
+                    i0, j0 = lines[0][0]
+                    per_iter += 2.0 * 16 * (108 if (i0 + j0) % 2 else 116) + 12.0 * 2 ** h
+                else:
+                    per_iter += sweep(qubits(lines), h, ha, hb, False) + 12.0 * 2 ** h
                 if dr in (0, 2):
                     readout += 2.0 * 2 ** h
             lines = [[(i, j) for i in rows] for j in cols]
@@ -598,9 +607,10 @@ def ours(args):
                 "launch_ms": dec_ms,
                 "peak_source": (f"derived: {per_clk} {'FP32 lanes' if fp else 'FP64 FMA/clk'} per SM x 2 x "
                                 f"{n_sm} SMs x {sm_mhz:.0f} MHz (max SM clock)"),
-                "flop_model": "qubit nodes as 2x2 XOR convolutions (4 multiply-adds per state entry), "
-                              "check nodes as zero-flop copy tensors, side-message data columns, "
-                              "normalise/damp/overlap, Lemma 1 read-out",
+                "flop_model": "4x4 blocks: the multiply-adds of the register form (116 or 108 per row and "
+                              "coset); other blocks: qubit nodes as 2x2 XOR convolutions (4 multiply-adds "
+                              "per state entry), check nodes as zero-flop copy tensors, side-message data "
+                              "columns; normalise/damp/overlap; Lemma 1 read-out (node by node)",
                 "flops_per_syndrome": flops / B}
     if mlp_ms is not None:
         bf16_peak, src = 1900.0, "fallback"

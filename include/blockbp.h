@@ -366,6 +366,45 @@ int bbp_decode_batch_ex(const uint8_t* syndromes, int64_t B, const bbp_params* p
                         int8_t* decision, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * bbp_decode_warm -- the learned decoder in one call (fused path, k <= 4):
+ * features of the distinct message rows (bbp_message_classes,
+ * bbp_message_features_rows), the network on the tensor cores
+ * (bbp_warm_infer, alpha as there), the expansion of each proposal to the
+ * cosets it stands for (bbp_expand_rows), then bbp_decode_batch_ex started
+ * from the proposals.  Outputs as bbp_decode_batch.
+ *   theta      device, bbp_warm_param_count() floats (trained parameters)
+ *   syndromes  device, [B][m] bytes 0/1
+ *   workspace  device, at least bbp_decode_warm_workspace_bytes(prm, B, 0)
+ *              bytes, 256-byte aligned: the network's scratch (its status
+ *              word at byte BBP_WARM_STATUS_OFFSET, as for bbp_warm_infer),
+ *              the class tables, the features of the distinct rows (1 KB
+ *              per row; d = 11, k = 4: 154 rows per syndrome), the
+ *              proposals, the expanded initial messages (B x 4 x M x 16
+ *              floats) and the decode's own workspace
+ * Asynchronous on ``stream``.  Errors: BBP_EINVAL for bad arguments,
+ * algorithm other than BBP_ALG_FUSED or k > 4; BBP_ENOSPACE; BBP_ECUDA.
+ */
+int bbp_decode_warm(const float* theta, const uint8_t* syndromes, int64_t B, const bbp_params* prm, float alpha,
+                    double* logp, double* delta, int32_t* iters, int32_t* flags, int8_t* decision, void* workspace,
+                    size_t workspace_bytes, void* stream);
+
+/*
+ * bbp_decode_warm_host -- bbp_decode_warm with HOST syndromes and outputs:
+ * copies the syndromes in, runs every step above on the device, copies the
+ * outputs back and synchronises ``stream`` before returning.  theta and
+ * workspace are device memory; the workspace holds at least
+ * bbp_decode_warm_workspace_bytes(prm, B, 1) bytes.  Any output pointer
+ * except decision may be NULL to skip its copy.  Errors as bbp_decode_warm.
+ */
+int bbp_decode_warm_host(const float* theta, const uint8_t* syndromes, int64_t B, const bbp_params* prm, float alpha,
+                         double* logp, double* delta, int32_t* iters, int32_t* flags, int8_t* decision,
+                         void* workspace, size_t workspace_bytes, void* stream);
+
+/* Device scratch of bbp_decode_warm (include_io = 0) or bbp_decode_warm_host
+ * (include_io != 0) for B syndromes.  Errors: BBP_EINVAL. */
+int bbp_decode_warm_workspace_bytes(const bbp_params* prm, int64_t B, int include_io, size_t* bytes);
+
+/*
  * bbp_decode_mixed -- syndromes of different distances in one persistent
  * launch (fused path).  CTAs take (syndrome, coset) items from a counter in
  * ``order`` (e.g. largest distance first); outputs are indexed by syndrome.

@@ -111,6 +111,21 @@ class BlockNetwork:
         c0, c1 = self.cols[J]
         return (r1 - r0) if dr in ("R", "L") else (c1 - c0)
 
+    def side_dims(self, I, J, dr):
+        """Dimensions of the legs crossing side ``dr`` of block (I, J), in
+        message site order (2 each in the coset network; a fused network has
+        larger legs)."""
+        r0, r1 = self.rows[I]
+        c0, c1 = self.cols[J]
+        T = self.T
+        if dr == "R":
+            return [T[i][c1 - 1].shape[1] for i in range(r0, r1)]
+        if dr == "L":
+            return [T[i][c0].shape[0] for i in range(r0, r1)]
+        if dr == "D":
+            return [T[r1 - 1][j].shape[3] for j in range(c0, c1)]
+        return [T[r0][j].shape[2] for j in range(c0, c1)]
+
     def incoming(self, msgs, I, J, side):
         """Message arriving at (I, J) across ``side``; trivial at the border."""
         if self.has(I, J, side):
@@ -227,7 +242,7 @@ def run_blockbp(tensors, P: Params, stats=None) -> CosetResult:
     kc = P.k_cols if P.k_cols is not None else P.k
     net = BlockNetwork(tensors, P.k, kc)
     edges = net.directed_edges()
-    msgs = {e: M.uniform(net.side_len(*e)) for e in edges}      # Remark 2
+    msgs = {e: M.uniform_dims(net.side_dims(*e)) for e in edges}     # Remark 2
     Mtot = len(edges)
     delta = 0.0
     iters = 0

@@ -156,6 +156,11 @@ def uniform(w: int):
     return [np.full((1, 2, 1), 1.0 / np.sqrt(2.0)) for _ in range(w)]
 
 
+def uniform_dims(dims):
+    """Unit-norm uniform product message over legs of the given dimensions."""
+    return [np.full((1, n, 1), 1.0 / np.sqrt(float(n))) for n in dims]
+
+
 def reverse(mps):
     """The same vector read with the site order reversed."""
     return [np.transpose(A, (2, 1, 0)) for A in mps[::-1]]

@@ -23,7 +23,8 @@ SYMBOLS = ("bbp_workspace_bytes", "bbp_decode_batch", "bbp_decode_batch_host", "
            "bbp_strerror", "bbp_version", "bbp_decode_batch_static", "bbp_message_count",
            "bbp_message_features", "bbp_warm_param_count", "bbp_warm_workspace_bytes", "bbp_warm_infer",
            "bbp_warm_train_step", "bbp_decode_batch_ex", "bbp_decode_mixed", "bbp_warm_infer_syndromes",
-           "bbp_pure_error", "bbp_message_classes", "bbp_message_features_rows", "bbp_expand_rows")
+           "bbp_pure_error", "bbp_message_classes", "bbp_message_features_rows", "bbp_expand_rows",
+           "bbp_decode_warm", "bbp_decode_warm_host", "bbp_decode_warm_workspace_bytes")
 WARM_F, WARM_H, WARM_O, WARM_MAX_ROWS = 256, 256, 16, 4194240
 WARM_STATUS_OFFSET = 270336       # int32 status word of bbp_warm_infer in its workspace
 WARM_INFER_WS_BYTES = 270592      # workspace of bbp_warm_infer, for any N
@@ -131,6 +132,13 @@ def lib():
         L.bbp_message_features_rows.restype = ctypes.c_int
         L.bbp_expand_rows.argtypes = [vp, i64, i32, vp, i32, vp, vp]
         L.bbp_expand_rows.restype = ctypes.c_int
+        L.bbp_decode_warm.argtypes = [vp, vp, i64, P, ctypes.c_float, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+        L.bbp_decode_warm.restype = ctypes.c_int
+        L.bbp_decode_warm_host.argtypes = [vp, vp, i64, P, ctypes.c_float, vp, vp, vp, vp, vp, vp, ctypes.c_size_t,
+                                           vp]
+        L.bbp_decode_warm_host.restype = ctypes.c_int
+        L.bbp_decode_warm_workspace_bytes.argtypes = [P, i64, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+        L.bbp_decode_warm_workspace_bytes.restype = ctypes.c_int
         L.bbp_strerror.argtypes = [ctypes.c_int]
         L.bbp_strerror.restype = ctypes.c_char_p
         L.bbp_version.argtypes = []

@@ -17,7 +17,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libblockbp.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["bbp_api.cu", "bbp_decode_f64.cu", "bbp_decode_f32.cu", "bbp_fused_f32.cu", "bbp_fused_f64.cu",
-           "bbp_sample.cu", "bbp_static.cu", "bbp_warm.cu", "bbp_warm_tc.cu"]
+           "bbp_sample.cu", "bbp_static.cu", "bbp_warm.cu", "bbp_warm_tc.cu",
+           "bbp_warm_decode.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

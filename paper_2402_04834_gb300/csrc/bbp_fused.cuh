@@ -73,7 +73,7 @@ __device__ __forceinline__ FusedWS<T> fused_ws_at(unsigned char* base, int G) {
 
 // Shared-memory layout of one fused CTA.
 struct FusedLayout {
-  int synd, frame, msg_of, meta, work, ovl, rlog, misc, msgs, ws, ws_stride, total;
+  int synd, frame, msg_of, meta, work, ovl, rlog, misc, qdesc, qid, msgs, ws, ws_stride, total;
 };
 
 // gm: the messages live in a workspace slot of the CTA (always for k = 5,
@@ -88,9 +88,13 @@ BBP_HD FusedLayout fused_layout(const Geo& g, int M, int nwarps, int G, bool gm 
   L.msg_of = o; o = align_up(o + 2 * g.nb * g.nb * 4, 16);
   L.meta = o;   o = align_up(o + 2 * M, 16);
   L.work = o;   o = align_up(o + 2 * 2 * M, 16);
-  L.ovl = o;    o = align_up(o + 8 * G * M, 16);
+  L.ovl = o;    o = align_up(o + (int)sizeof(T) * G * M, 16);
   L.rlog = o;   o = align_up(o + 8 * G * (g.nb * g.nb + M), 16);
   L.misc = o;   o = align_up(o + 128, 16);
+  // 4 x 4 block updates (k = 4): a descriptor per message and the qubit
+  // ids of each (coset, message), built once per syndrome.
+  L.qdesc = o;  if (K == 4 && g.k == 4) o = align_up(o + 8 * M, 16);
+  L.qid = o;    if (K == 4 && g.k == 4) o = align_up(o + 2 * G * M, 16);
   L.msgs = o;   // the messages, unless they live in the workspace
   if (!gm) o = align_up(o + (int)sizeof(T) * FusedDim<K>::vec * G * M, 16);
   L.ws = o;
@@ -225,7 +229,7 @@ template <> struct LogAcc<float> {
 // s at s << h.  For the read-out (ls not null) every column's state is
 // renormalised per coset and the norms taken out go to ls[slot] (lane 0).
 template <typename T, int K>
-__device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K>& c, const T* msgs, int stride,
+__device__ __noinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K>& c, const T* msgs, int stride,
                                          unsigned cos_of, int n, const uint8_t* frames, const Frame& f,
                                          LogAcc<T>* ls, int lane) {
   using V2 = typename Vec2<T>::type;
@@ -770,7 +774,7 @@ __device__ __forceinline__ T group_normalize(T v, int width) {
 // G = 1, h <= 6); a vector of 64 entries spans both halves.
 template <typename T, int K>
 __device__ __forceinline__ void fused_update(const FusedWS<T>& ws, T* msgs, int stride, unsigned cos_of, int n,
-                                             int idx, int h, T eta, T one_m_eta, double* ovl, int M, int lane) {
+                                             int idx, int h, T eta, T one_m_eta, T* ovl, int M, int lane) {
   const int width = 1 << h, tot = n << h;
   if (K > 5 && width > 32) {
     // One vector of 64 entries (k = 6, one coset): entries lane and lane + 32
@@ -791,7 +795,7 @@ __device__ __forceinline__ void fused_update(const FusedWS<T>& ws, T* msgs, int 
     const T term = DeltaTerm<T>::eval2(x0, y0, x1, y1);
     *old0 = x0;
     *old1 = x1;
-    if (lane == 0) ovl[q * M + idx] = (double)term;
+    if (lane == 0) ovl[q * M + idx] = term;
     __syncwarp();
     return;
   }
@@ -810,8 +814,251 @@ __device__ __forceinline__ void fused_update(const FusedWS<T>& ws, T* msgs, int 
     const T term = DeltaTerm<T>::eval(x, y, width);
     if (on) {
       *old = x;
-      if ((e & (width - 1)) == 0) ovl[q * M + idx] = (double)term;
+      if ((e & (width - 1)) == 0) ovl[q * M + idx] = term;
     }
+  }
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// Block update of a 4 x 4 block in registers.
+//
+// Along a column of a 4 x 4 block checks and qubits alternate.  A check is a
+// copy tensor (Sec. III.A), so its row leg, its two chain legs and (in the
+// top or bottom row) the side message's leg are one and the same bit; a
+// qubit's tensor pi(f + (x, z)) depends only on the parity of its in/out
+// legs (alpha) and of its chain legs (beta): g[alpha][beta].  A column
+// therefore acts on the 16-entry row state as two 2-point XOR convolutions
+// (one per qubit row) whose beta is a parity of bits that the checks fix,
+// and the side messages' legs are either tied to a row bit (check in the
+// top / bottom row) or enter a qubit's beta.  Written out column by column
+// this is a short sequence of butterflies over single row bits: a lane holds
+// one (coset, row) entry of the state, with the still-open side-message legs
+// in registers, and the butterflies exchange partners with warp shuffles (row
+// bit s of the chain is lane bit 3 - s).  Two cosets per pass (lanes 0-15
+// and 16-31).  Sides on the grid border have no message; they act as the
+// product vector of their nodes' missing legs: ones for a check (a copy
+// tensor over its remaining legs) and e_0 for a qubit (a missing leg carries
+// 0), which is what the general node-by-node path computes there.
+
+// g[0][be] and g[1][be] of a qubit whose pi(I) entry sits at id = (alpha, beta).
+template <typename T>
+__device__ __forceinline__ void qpair(int id, int be, T pI, T pE, T& g0, T& g1) {
+  const bool hit = (id & 1) == be;
+  const bool hi = (id >> 1) & 1;
+  g0 = (hit && !hi) ? pI : pE;
+  g1 = (hit && hi) ? pI : pE;
+}
+
+template <typename T>
+__device__ __forceinline__ T qval(int id, int al, int be, T pI, T pE) {
+  return ((al << 1) | be) == id ? pI : pE;
+}
+
+template <typename T>
+__device__ __forceinline__ T shx(T v, int mask) {
+  return __shfl_xor_sync(kFull, v, mask);
+}
+
+// What a 4 x 4 block update needs beyond the messages and the qubit ids,
+// fixed for a syndrome: the incoming message opposite the outgoing side,
+// the side messages attached at s' = 0 (upper) and s' = 3 (lower), each an
+// index or -1 on the grid border, and bits: 0 the chain is read bottom to
+// top, 1 the side messages are consumed in reverse site order, 2 the block
+// is 4 x 4, 4-7 / 8-11 / 12-15 the qubit masks of the border vectors of the
+// incoming / upper / lower side (bit 3 - t or 3 - s set at a qubit).
+struct QuadTask {
+  int16_t in_idx, up_idx, lo_idx;
+  uint16_t bits;
+};
+constexpr int kQuadRev = 1, kQuadSideRev = 2, kQuad = 4;
+
+template <typename T, int K>
+__device__ __forceinline__ QuadTask quad_task(const Frame& f) {
+  QuadTask q;
+  int i00, j00;
+  f.node(0, 0, &i00, &j00);
+  const bool rev = (i00 + j00) & 1;                          // column 0 starts with a check
+  const int up_s = rev ? 3 : 0, lo_s = rev ? 0 : 3;
+  int qm_up = 0, qm_lo = 0, qm_in = 0;
+  for (int u = 0; u < 4; ++u) {
+    int i, j;
+    f.node(u, up_s, &i, &j);
+    if (!((i + j) & 1)) qm_up |= 8 >> u;
+    f.node(u, lo_s, &i, &j);
+    if (!((i + j) & 1)) qm_lo |= 8 >> u;
+    f.node(0, u, &i, &j);
+    if (!((i + j) & 1)) qm_in |= 8 >> u;
+  }
+  q.in_idx = (int16_t)f.in_idx;
+  q.up_idx = (int16_t)(rev ? f.b_idx : f.a_idx);
+  q.lo_idx = (int16_t)(rev ? f.a_idx : f.b_idx);
+  q.bits = (uint16_t)((rev ? kQuadRev : 0) | (f.rev ? kQuadSideRev : 0) |
+                      ((K == 4 && f.h == 4 && f.ncols == 4) ? kQuad : 0) | (qm_in << 4) | (qm_up << 8) |
+                      (qm_lo << 12));
+  return q;
+}
+
+// The ids (bits 2 (2t + u)) of the 8 qubits of a 4 x 4 block for one
+// coset frame: id[t][0] the upper, id[t][1] the lower qubit of column t
+// (chain positions 0, 2 for even t and 1, 3 for odd t, read from the top or,
+// reversed, from the bottom).
+__device__ __forceinline__ uint16_t quad_ids(const Frame& f, const uint8_t* fr, int W, bool rev) {
+  const bool rowwise = f.dir == kDirR || f.dir == kDirL;
+  unsigned v = 0;
+  for (int t = 0; t < 4; ++t)
+    for (int u = 0; u < 2; ++u) {
+      const int sq = (t & 1) + 2 * u;
+      int i, j;
+      f.node(t, rev ? 3 - sq : sq, &i, &j);
+      const int fv = fr[i * W + j];
+      const bool alpha_is_z = ((i & 1) == 0) == rowwise;
+      v |= (unsigned)(alpha_is_z ? fv : (((fv & 1) << 1) | (fv >> 1))) << (2 * (2 * t + u));
+    }
+  return (uint16_t)v;
+}
+
+// The outgoing vectors of a 4 x 4 block (f.h == f.ncols == 4) for the n
+// cosets of cos_of, into ws.s0 (slot s at s << 4), as fused_sweep leaves
+// them.  Columns t = 0..3 hold qubits at chain positions {0, 2} or {1, 3},
+// alternating from column to column.  Both node tensors are symmetric in
+// their two chain legs, so reading the chain bottom to top (position
+// s' = 3 - s, the side messages exchanged) turns a block whose column 0
+// starts with a check into one whose column 0 starts with a qubit; only
+// that case is written out.
+// qid[q * qid_stride] holds the qubit ids of coset q (quad_ids).
+template <typename T, int K>
+__device__ __forceinline__ void quad_sweep(const FusedWS<T>& ws, T pI, T pE, const T* msgs, int stride,
+                                           unsigned cos_of, int n, const QuadTask qt, const uint16_t* qid,
+                                           int qid_stride, int lane) {
+  constexpr int VEC = FusedDim<K>::vec;
+  const bool rev = qt.bits & kQuadRev, srev = qt.bits & kQuadSideRev;
+  const int qm_in = (qt.bits >> 4) & 15, qm_up = (qt.bits >> 8) & 15, qm_lo = (qt.bits >> 12) & 15;
+  // The side messages in consumption order, the upper one (attached at
+  // s' = 0) in ws.mt and the lower one in ws.mb, slot q at q << 4.  A side
+  // on the grid border has no message: the product vector of its nodes'
+  // missing legs (1 for a check, e_0 for a qubit), bit 3 - t for column t.
+  for (int e = lane; e < (n << 4); e += 32) {
+    const int i = e & 15, jj = srev ? bitrev(i, 4) : i;
+    const T* ms = msgs + slot_coset(cos_of, e >> 4) * stride;
+    ws.mt[e] = qt.up_idx >= 0 ? ms[qt.up_idx * VEC + jj] : ((i & qm_up) ? T(0) : T(1));
+    ws.mb[e] = qt.lo_idx >= 0 ? ms[qt.lo_idx * VEC + jj] : ((i & qm_lo) ? T(0) : T(1));
+  }
+  __syncwarp();
+  const int R = lane & 15, hi = lane >> 4;
+  const int r0 = (R >> 3) & 1, r1 = (R >> 2) & 1, r2 = (R >> 1) & 1, r3 = R & 1;
+  const int Rn = rev ? bitrev(R, 4) : R;                     // the lane's row in the block's own order
+  for (int sp = 0; sp < n; sp += 2) {
+    const int slot = sp + hi;
+    const bool on = slot < n;
+    const int sl = on ? slot : sp;
+    const int cq = slot_coset(cos_of, sl);
+    const T* mA = ws.mt + (sl << 4);
+    const T* mB = ws.mb + (sl << 4);
+    const unsigned idv = qid[cq * qid_stride];
+    int id[4][2];
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+      for (int u = 0; u < 2; ++u) id[t][u] = (int)((idv >> (2 * (2 * t + u))) & 3u);
+    const T x = qt.in_idx >= 0 ? msgs[cq * stride + qt.in_idx * VEC + Rn] : ((Rn & qm_in) ? T(0) : T(1));
+    // Column 0 (qubits at 0, 2): the upper leg a0 is recorded, the lower leg
+    // b0 is tied to r3 by the check at 3.
+    T S0[2];
+    {
+      T k0, k1;
+      qpair(id[0][1], r1 ^ r3, pI, pE, k0, k1);
+      const T u = k0 * x + k1 * shx(x, 2);
+      const T up = shx(u, 8);
+#pragma unroll
+      for (int a0 = 0; a0 < 2; ++a0) {
+        T h0, h1;
+        qpair(id[0][0], a0 ^ r1, pI, pE, h0, h1);
+        S0[a0] = h0 * u + h1 * up;
+      }
+    }
+    // Column 1 (qubits at 1, 3): a1 is tied to r0 by the check at 0; the
+    // lower leg b1 is recorded.  S1[a0][b0][b1].
+    T S1[2][2][2];
+    {
+      T X[2][2];
+#pragma unroll
+      for (int a0 = 0; a0 < 2; ++a0) {
+        const T o = S0[a0], p = shx(o, 1);
+        X[a0][0] = r3 ? p : o;
+        X[a0][1] = r3 ? o : p;
+      }
+      T h0, h1;
+      qpair(id[1][0], r0 ^ r2, pI, pE, h0, h1);
+#pragma unroll
+      for (int b1 = 0; b1 < 2; ++b1) {
+        T k0, k1;
+        qpair(id[1][1], r2 ^ b1, pI, pE, k0, k1);
+        const T kk0 = r3 ? k1 : k0, kk1 = r3 ? k0 : k1;       // b0 = 0, 1
+#pragma unroll
+        for (int a0 = 0; a0 < 2; ++a0) {
+          const T y0 = kk0 * X[a0][0], y1 = kk1 * X[a0][1];
+          S1[a0][0][b1] = h0 * y0 + h1 * shx(y0, 4);
+          S1[a0][1][b1] = h0 * y1 + h1 * shx(y1, 4);
+        }
+      }
+    }
+    // Column 2 (qubits at 0, 2), the data column of both side messages: the
+    // upper leg v is summed against A[a0 a1 v e], the lower leg w = r3
+    // against B[b0 b1 w f].  S2[e][f].
+    T S2[2][2];
+    {
+      T k0, k1;
+      qpair(id[2][1], r1 ^ r3, pI, pE, k0, k1);
+      T g00, g01, g10, g11;                                  // g[l0 ^ r0][v ^ r1] of the upper qubit
+      qpair(id[2][0], r1, pI, pE, g00, g10);                 // v = 0
+      qpair(id[2][0], r1 ^ 1, pI, pE, g01, g11);             // v = 1
+      T Y[2][2][2];                                          // [e][b0][b1]
+#pragma unroll
+      for (int b0 = 0; b0 < 2; ++b0)
+#pragma unroll
+        for (int b1 = 0; b1 < 2; ++b1) Y[0][b0][b1] = Y[1][b0][b1] = T(0);
+#pragma unroll
+      for (int a0 = 0; a0 < 2; ++a0) {
+        // A0: row bit 0 kept (l0 = r0 = a1), A1: flipped (l0 = a1 = !r0).
+        const T* m0 = mA + (a0 << 3) + (r0 << 2);
+        const T* m1 = mA + (a0 << 3) + ((r0 ^ 1) << 2);
+        const T A00 = m0[0] * g00 + m0[2] * g01, A01 = m0[1] * g00 + m0[3] * g01;   // e = 0, 1
+        const T A10 = m1[0] * g10 + m1[2] * g11, A11 = m1[1] * g10 + m1[3] * g11;
+#pragma unroll
+        for (int b0 = 0; b0 < 2; ++b0)
+#pragma unroll
+          for (int b1 = 0; b1 < 2; ++b1) {
+            const T s1 = S1[a0][b0][b1];
+            const T u = k0 * s1 + k1 * shx(s1, 2);
+            const T up = shx(u, 8);
+            Y[0][b0][b1] += A00 * u + A10 * up;
+            Y[1][b0][b1] += A01 * u + A11 * up;
+          }
+      }
+      const T* mb = mB + (r3 << 1);
+#pragma unroll
+      for (int e = 0; e < 2; ++e)
+#pragma unroll
+        for (int ff = 0; ff < 2; ++ff)
+          S2[e][ff] = mb[ff] * Y[e][0][0] + mb[4 + ff] * Y[e][0][1] + mb[8 + ff] * Y[e][1][0] +
+                      mb[12 + ff] * Y[e][1][1];
+    }
+    // Column 3 (qubits at 1, 3): the upper leg e is tied to r0, the lower
+    // leg f closes against B's expected value.
+    T out;
+    {
+      const T z0 = r0 ? S2[1][0] : S2[0][0], z1 = r0 ? S2[1][1] : S2[0][1];
+      const T p0 = shx(z0, 1), p1 = shx(z1, 1);
+      T k0, k1, m0, m1;
+      qpair(id[3][1], r2, pI, pE, k0, k1);
+      qpair(id[3][1], r2 ^ 1, pI, pE, m0, m1);
+      const T uu = k0 * z0 + k1 * p0 + m0 * z1 + m1 * p1;
+      T h0, h1;
+      qpair(id[3][0], r0 ^ r2, pI, pE, h0, h1);
+      out = h0 * uu + h1 * shx(uu, 4);
+    }
+    if (on) ws.s0[(slot << 4) | Rn] = out;
   }
   __syncwarp();
 }
@@ -843,7 +1090,9 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
   int16_t* msg_of = reinterpret_cast<int16_t*>(smem + Lo.msg_of);
   int16_t* meta = reinterpret_cast<int16_t*>(smem + Lo.meta);
   int16_t* work = reinterpret_cast<int16_t*>(smem + Lo.work);
-  double* ovl = reinterpret_cast<double*>(smem + Lo.ovl);
+  T* ovl = reinterpret_cast<T*>(smem + Lo.ovl);                // Delta term of each (coset, message)
+  QuadTask* qdesc = reinterpret_cast<QuadTask*>(smem + Lo.qdesc);
+  uint16_t* qid = reinterpret_cast<uint16_t*>(smem + Lo.qid);
   double* rlog = reinterpret_cast<double*>(smem + Lo.rlog);
   int* misc = reinterpret_cast<int*>(smem + Lo.misc);      // [0] counter, [2..4] list sizes, [8 + q] flags
   double* dsh = reinterpret_cast<double*>(smem + Lo.misc + 64);
@@ -899,6 +1148,19 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
   c.frame = frames; c.msg_of = msg_of; c.msg_off = nullptr; c.dims = nullptr;
   c.arena = nullptr; c.e0 = nullptr; c.cta_flags = &misc[8];
 
+  const bool quads = K == 4 && g.k == 4;   // 4 x 4 blocks take quad_sweep
+  if (quads) {                              // their descriptors
+    for (int e = tid; e < G * M; e += NW * 32) {
+      const int q = e / M, idx = e - q * M;
+      const int key = meta[idx];
+      const Frame f = make_frame(c, key / 4 / nb, (key / 4) % nb, key & 3);
+      const QuadTask qt = quad_task<T, K>(f);
+      if (q == 0) qdesc[idx] = qt;
+      if (qt.bits & kQuad) qid[e] = quad_ids(f, frames + q * WW, W, qt.bits & kQuadRev);
+    }
+    __syncthreads();
+  }
+
   // Remark 2: uniform messages of unit norm, unless initial messages are
   // given (learned warm start): those are renormalised on entry.
   for (int qi = warp; qi < G * M; qi += NW) {
@@ -943,11 +1205,22 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
         item = __shfl_sync(kFull, item, 0);
         if (item >= nwork) break;
         const int idx = lst[item];
-        const int key = meta[idx];
-        const int I = key / 4 / nb, J = (key / 4) % nb, dir = key & 3;
-        const Frame f = make_frame(c, I, J, dir);
-        fused_sweep(ws, c, msgs, stride, cos_of, n, frames, f, (LogAcc<T>*)nullptr, lane);
-        fused_update<T, K>(ws, msgs, stride, cos_of, n, idx, f.h, eta, one_m_eta, ovl, M, lane);
+        int h = 4;
+        bool quad = false;
+        QuadTask qt;
+        if (quads) {
+          qt = qdesc[idx];
+          quad = qt.bits & kQuad;
+        }
+        if (quad) {
+          quad_sweep<T, K>(ws, c.pI, c.pE, msgs, stride, cos_of, n, qt, qid + idx, M, lane);
+        } else {
+          const int key = meta[idx];
+          const Frame f = make_frame(c, key / 4 / nb, (key / 4) % nb, key & 3);
+          fused_sweep(ws, c, msgs, stride, cos_of, n, frames, f, (LogAcc<T>*)nullptr, lane);
+          h = f.h;
+        }
+        fused_update<T, K>(ws, msgs, stride, cos_of, n, idx, h, eta, one_m_eta, ovl, M, lane);
       }
       __syncthreads();
       if (tid == 0) misc[0] = 0;
@@ -955,7 +1228,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
     }
     if (warp < G && ((act >> warp) & 1u)) {          // Remark 4, one warp per coset
       double acc = 0.0;
-      for (int i = lane; i < M; i += 32) acc += ovl[warp * M + i];
+      for (int i = lane; i < M; i += 32) acc += (double)ovl[warp * M + i];
       acc = warp_sum(acc);
       if (lane == 0) dsh[warp] = sqrt(fmax(acc, 0.0)) / M;
     }

@@ -220,29 +220,57 @@ def propose(syndromes, prm: DecoderParams, net: WarmStart, stream=None, alpha=DE
     return expand_rows(rows, syndromes.shape[0], prm, stream=stream)
 
 
-def decode_warm(syndromes, prm: DecoderParams, net: WarmStart, stream=None, out=None, alpha=DEFAULT_ALPHA):
-    """Learned warm start: proposals from the network (``propose``) -> fused
-    decode from them.  (``WarmStart.infer_syndromes`` runs the network over
-    every row with the features computed in its kernel.)"""
-    init = propose(syndromes, prm, net, stream=stream, alpha=alpha)
-    return decode_ex(syndromes, prm, init_msgs=init, stream=stream, out=out)
+def decode_warm_workspace_bytes(prm: DecoderParams, B: int, include_io: bool = False) -> int:
+    out = ctypes.c_size_t(0)
+    cp = prm.c()
+    check(lib().bbp_decode_warm_workspace_bytes(ctypes.byref(cp), B, int(include_io), ctypes.byref(out)))
+    return int(out.value)
 
 
-def decode_warm_host(syndromes, prm: DecoderParams, net: WarmStart, out=None, alpha=DEFAULT_ALPHA, stream=None):
-    """decode_warm from host memory: syndromes [B, m] uint8 (numpy or CPU
-    tensor, pinned for asynchronous copies) in, decisions [B] and log P
-    [B, 4] back in host memory; synchronises the stream."""
-    syn = torch.as_tensor(syndromes)
+def decode_warm(syndromes, prm: DecoderParams, net: WarmStart, stream=None, out=None, alpha=DEFAULT_ALPHA,
+                workspace=None):
+    """Learned warm start in one library call (bbp_decode_warm): features of
+    the distinct rows, the network on the tensor cores, the expansion to
+    every (coset, message), then the fused decode from the proposals; equal
+    bit for bit to ``propose`` followed by ``decode_ex``."""
+    B = syndromes.shape[0]
+    dev = syndromes.device
+    if out is None:
+        out = {
+            "logp": torch.empty(B, 4, dtype=torch.float64, device=dev),
+            "delta": torch.empty(B, 4, dtype=torch.float64, device=dev),
+            "iters": torch.empty(B, 4, dtype=torch.int32, device=dev),
+            "flags": torch.empty(B, 4, dtype=torch.int32, device=dev),
+            "decision": torch.empty(B, dtype=torch.int8, device=dev),
+        }
+    ws = (workspace or net.infer_ws).get(decode_warm_workspace_bytes(prm, B), dev)
+    cp = prm.c()
+    check(lib().bbp_decode_warm(_ptr(net.theta), _ptr(syndromes.contiguous()), B, ctypes.byref(cp), alpha,
+                                _ptr(out["logp"]), _ptr(out["delta"]), _ptr(out["iters"]), _ptr(out["flags"]),
+                                _ptr(out["decision"]), _ptr(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+def decode_warm_host(syndromes, prm: DecoderParams, net: WarmStart, out=None, alpha=DEFAULT_ALPHA, stream=None,
+                     workspace=None):
+    """The learned decoder from host memory in one library call
+    (bbp_decode_warm_host): syndromes [B, m] uint8 (numpy or CPU tensor,
+    pinned for asynchronous copies) in, decisions [B] and log P [B, 4] back
+    in host memory; the call synchronises the stream."""
+    syn = torch.as_tensor(syndromes).contiguous()
+    B = syn.shape[0]
+    if out is None:
+        out = {"decision": torch.empty(B, dtype=torch.int8, pin_memory=True),
+               "logp": torch.empty(B, 4, dtype=torch.float64, pin_memory=True)}
+    ws = (workspace or net.infer_ws).get(decode_warm_workspace_bytes(prm, B, include_io=True), net.device)
+    cp = prm.c()
     st = stream or torch.cuda.current_stream(net.device)
-    with torch.cuda.stream(st):
-        dev_syn = syn.to(net.device, non_blocking=True)
-        res = decode_warm(dev_syn, prm, net, stream=st, alpha=alpha)
-        if out is None:
-            out = {"decision": torch.empty(syn.shape[0], dtype=torch.int8, pin_memory=True),
-                   "logp": torch.empty(syn.shape[0], 4, dtype=torch.float64, pin_memory=True)}
-        out["decision"].copy_(res["decision"], non_blocking=True)
-        out["logp"].copy_(res["logp"], non_blocking=True)
-    st.synchronize()
+    check(lib().bbp_decode_warm_host(_ptr(net.theta), syn.data_ptr(), B, ctypes.byref(cp), alpha,
+                                     out["logp"].data_ptr() if out.get("logp") is not None else None,
+                                     out["delta"].data_ptr() if out.get("delta") is not None else None,
+                                     out["iters"].data_ptr() if out.get("iters") is not None else None,
+                                     out["flags"].data_ptr() if out.get("flags") is not None else None,
+                                     out["decision"].data_ptr(), _ptr(ws), ws.numel(), _stream(st)))
     return out
 
 

@@ -3,7 +3,12 @@
 Calls only ``oracle/`` (and the seeded workload in ``synth/``).  Each file
 holds, per shot, the oracle's log P, Delta, iterations, flags, decision and
 the smallest relative Schmidt gap at a real truncation (inf = none), for a
-seeded workload named in the file.  The k = 6 workloads (d = 31, 6 x 6
+seeded workload named in the file.  The truncating workloads also record
+how far the oracle's own log P moves when every matrix it decomposes
+carries relative noise of 1e-13 (FP64) or 1e-6 (FP32), about a thousand
+units of rounding (``sens_fp64``, ``sens_fp32``, the larger of two seeded
+draws): the parity tests compare a shot at a precision only where that
+movement is far below the tolerance.  The k = 6 workloads (d = 31, 6 x 6
 blocks) run the dense fused-block oracle of Remark 9 (``oracle.naive``),
 which truncates nothing; one coset takes about ten minutes and 11 GB
 there, so they are spread over (shot, coset) pairs.
@@ -47,6 +52,13 @@ for _ip, _p in ((0, 0.05), (1, 0.08), (3, 0.13), (4, 0.15)):
         file=f"oracle_d11_k4_D8_p{int(round(_p * 100)):03d}.json", d=11, k=4, D=8, p=_p, max_iter=20,
         delta0=0.0, seed=synth.workload_seed(2, _ip), first_shot=0, shots=50)
 
+# The benchmark workload (d = 11, p = 0.10, k = 4, 20 fixed iterations)
+# through the dense fused-block oracle of Remark 9, the reference of the
+# fused form: it truncates nothing, where the MPS oracle drops Schmidt
+# values below 1e-13 of the largest (a few 1e-9 in log P on some shots).
+WORKLOADS["d11_fused"] = dict(file="oracle_d11_k4_fused_p010.json", d=11, k=4, D=16, p=0.10, max_iter=20,
+                              delta0=0.0, seed=synth.workload_seed(2, 2), first_shot=0, shots=200, form="fused")
+
 # Truncating MPS workloads: k = 4 with D = 2 and 4 at d = 9 and 11 (p = 0.10,
 # 20 fixed iterations).  The in-block boundary MPS of a 4 x 4 block needs a
 # bond of up to 16, so both bonds truncate inside every block, and D = 2
@@ -55,7 +67,7 @@ for _d in (9, 11):
     for _D in (2, 4):
         WORKLOADS[f"d{_d}_D{_D}"] = dict(
             file=f"oracle_d{_d}_k4_D{_D}_p010.json", d=_d, k=4, D=_D, p=0.10, max_iter=20, delta0=0.0,
-            seed=synth.workload_seed(6, 10 * _d + _D), first_shot=0, shots=24)
+            seed=synth.workload_seed(6, 10 * _d + _D), first_shot=0, shots=24, sensitivity=True)
 
 # Distance 31, k = 6 (dense 64-entry messages), 20 fixed iterations, at the
 # two noise levels of the d = 31 workload (p index 0, 1).
@@ -88,16 +100,54 @@ def _assemble(w, rows):
     return out
 
 
+def _perturbed_svd(rel, seed):
+    """numpy's SVD applied to M * (1 + rel * n), n standard normal per entry:
+    rounding-level noise on every decomposition the oracle makes."""
+    svd = np.linalg.svd
+    rng = np.random.default_rng(seed)
+
+    def noisy(M, full_matrices=False):
+        return svd(M * (1.0 + rel * rng.standard_normal(M.shape)), full_matrices=full_matrices)
+    return svd, noisy
+
+
+def _sensitivity(P, s, base, rel, seed, draws=2):
+    """Largest |d log P| of the oracle, over ``draws`` seeded draws, when every
+    matrix it decomposes carries a relative perturbation of size rel.  Where
+    the truncated iteration amplifies rounding (near-degenerate cuts, BP that
+    does not settle at a small D), two correct implementations with
+    different rounding can end far apart; this measures how far."""
+    worst = 0.0
+    for k in range(draws):
+        svd, noisy = _perturbed_svd(rel, seed + 7919 * k)
+        np.linalg.svd = noisy
+        try:
+            pert = bb.decode(s, P)["logp"]
+        finally:
+            np.linalg.svd = svd
+        worst = max(worst, float(np.max(np.abs(np.asarray(base) - np.asarray(pert)))))
+    return worst
+
+
 def _one(args):
     w, b, s = args
     P = bb.Params(d=w["d"], k=w["k"], D=w["D"], p=w["p"], max_iter=w["max_iter"], delta0=w["delta0"])
-    r = bb.decode(np.asarray(s, dtype=np.uint8), P)
+    s = np.asarray(s, dtype=np.uint8)
+    r = bb.decode(s, P)
     st = r["stats"]
-    return dict(shot=w["first_shot"] + b, logp=[float(x) for x in r["logp"]],
-                delta=[float(x) for x in r["delta"]], iters=[int(x) for x in r["iters"]],
-                flags=[int(x) for x in r["flags"]], decision=int(r["decision"]),
-                min_gap=(None if not np.isfinite(st.min_gap) else float(st.min_gap)),
-                truncations=int(st.truncations), flops=float(st.flops))
+    row = dict(shot=w["first_shot"] + b, logp=[float(x) for x in r["logp"]],
+               delta=[float(x) for x in r["delta"]], iters=[int(x) for x in r["iters"]],
+               flags=[int(x) for x in r["flags"]], decision=int(r["decision"]),
+               min_gap=(None if not np.isfinite(st.min_gap) else float(st.min_gap)),
+               truncations=int(st.truncations), flops=float(st.flops))
+    if w.get("sensitivity"):
+        # Noise of the size by which two correct decompositions of the same
+        # matrix differ: about a thousand units of rounding (unit roundoff
+        # 1.1e-16 in FP64 and 6e-8 in FP32; the GPU's Gram-Schmidt and
+        # one-sided Jacobi against LAPACK here), seeded by the shot.
+        row["sens_fp64"] = _sensitivity(P, s, r["logp"], 1e-13, 1000 + b)
+        row["sens_fp32"] = _sensitivity(P, s, r["logp"], 1e-6, 2000 + b)
+    return row
 
 
 def make(name: str, procs: int):
@@ -112,7 +162,7 @@ def make(name: str, procs: int):
     else:
         with ctx.Pool(procs) as pool:
             rows = pool.map(_one, [(w, b, S[b].tolist()) for b in range(w["shots"])])
-    meta = {k: v for k, v in w.items() if k not in ("file", "form")}
+    meta = {k: v for k, v in w.items() if k not in ("file", "form", "sensitivity")}
     if w.get("form") == "fused":
         meta["oracle"] = "dense fused-block blockBP (Remark 9), no truncation"
     meta["eta"], meta["delta1"], meta["cutoff"] = 0.1, 1e-2, 1e-13

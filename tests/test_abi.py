@@ -206,8 +206,8 @@ def test_message_classes_on_the_host(L, d, k):
 
 
 @pytest.mark.parametrize("alg,prec,k,messages,d_max", [
-    ("fused", "fp32", 4, 1, 48), ("fused", "fp64", 4, 1, 36), ("fused", "fp32", 4, 0, 60), ("fused", "fp64", 4, 0, 60),
-    ("fused", "fp32", 2, 0, 32), ("fused", "fp32", 1, 0, 17), ("fused", "fp32", 2, 1, 25), ("fused", "fp32", 1, 1, 13),
+    ("fused", "fp32", 4, 1, 46), ("fused", "fp64", 4, 1, 34), ("fused", "fp32", 4, 0, 58), ("fused", "fp64", 4, 0, 54),
+    ("fused", "fp32", 2, 0, 36), ("fused", "fp32", 1, 0, 19), ("fused", "fp32", 2, 1, 25), ("fused", "fp32", 1, 1, 13),
     ("fused", "fp32", 6, 0, 64), ("fused", "fp64", 6, 0, 64), ("mps", "fp64", 4, 0, 64), ("mps", "fp32", 4, 0, 64)])
 def test_largest_supported_distance(L, alg, prec, k, messages, d_max):
     # Fused k <= 4 with its messages in shared memory is bounded by them (the
@@ -220,3 +220,37 @@ def test_largest_supported_distance(L, alg, prec, k, messages, d_max):
     assert L.bbp_workspace_bytes(ctypes.byref(c), 4, 0, ctypes.byref(out)) == 0
     c = pkg.DecoderParams(d=d_max + 1, k=k, D=8, precision=prec, algorithm=alg, messages=messages).c()
     assert L.bbp_workspace_bytes(ctypes.byref(c), 4, 0, ctypes.byref(out)) == (-4 if d_max < 64 else -1)
+
+
+def test_learned_decoder_entry_points_check_arguments_on_the_host(L):
+    # bbp_decode_warm / _host: every argument is checked before any CUDA call.
+    vp = ctypes.c_void_p
+    fused = pkg.DecoderParams(d=11, k=4, p=0.1, precision="fp32", algorithm="fused")
+    cp = fused.c()
+    out = ctypes.c_size_t(0)
+    assert L.bbp_decode_warm_workspace_bytes(ctypes.byref(cp), 100, 0, ctypes.byref(out)) == 0
+    dev_bytes = out.value
+    assert L.bbp_decode_warm_workspace_bytes(ctypes.byref(cp), 100, 1, ctypes.byref(out)) == 0
+    assert out.value > dev_bytes
+    # Room for the features of the distinct rows (154 per syndrome, 1 KB each)
+    # and the expanded initial messages (480 x 16 floats per syndrome).
+    assert dev_bytes >= 100 * (154 * 1024 + 480 * 64)
+    for bad in (pkg.DecoderParams(d=11, k=4, algorithm="mps"),
+                pkg.DecoderParams(d=11, k=6, precision="fp32", algorithm="fused"),
+                pkg.DecoderParams(d=1, k=4, algorithm="fused")):
+        c = bad.c()
+        assert L.bbp_decode_warm_workspace_bytes(ctypes.byref(c), 100, 0, ctypes.byref(out)) == -1
+    assert L.bbp_decode_warm_workspace_bytes(ctypes.byref(cp), 100, 0, None) == -1
+    fake = vp(256)
+    for fn in (L.bbp_decode_warm, L.bbp_decode_warm_host):
+        # null parameter vector, syndromes, decision, workspace
+        assert fn(None, fake, 4, ctypes.byref(cp), 0.1, fake, fake, fake, fake, fake, fake, 1 << 40, None) == -1
+        assert fn(fake, None, 4, ctypes.byref(cp), 0.1, fake, fake, fake, fake, fake, fake, 1 << 40, None) == -1
+        assert fn(fake, fake, 4, ctypes.byref(cp), 0.1, fake, fake, fake, fake, None, fake, 1 << 40, None) == -1
+        assert fn(fake, fake, 4, ctypes.byref(cp), 0.1, fake, fake, fake, fake, fake, None, 1 << 40, None) == -1
+        # alpha outside [0, 1], negative batch, misaligned or short workspace
+        assert fn(fake, fake, 4, ctypes.byref(cp), 1.5, fake, fake, fake, fake, fake, fake, 1 << 40, None) == -1
+        assert fn(fake, fake, -1, ctypes.byref(cp), 0.1, fake, fake, fake, fake, fake, fake, 1 << 40, None) == -1
+        assert fn(fake, fake, 4, ctypes.byref(cp), 0.1, fake, fake, fake, fake, fake, vp(257), 1 << 40, None) == -1
+        assert fn(fake, fake, 4, ctypes.byref(cp), 0.1, fake, fake, fake, fake, fake, fake, 1024, None) == -3
+        assert fn(fake, fake, 0, ctypes.byref(cp), 0.1, None, None, None, None, None, None, 0, None) == 0

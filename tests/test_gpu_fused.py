@@ -192,6 +192,10 @@ def test_fused_k6_d31_matches_oracle_golden(dev, name):
 
 
 def test_fused_equals_mps_golden_at_d11(dev):
+    # The MPS form truncates nothing on these shots (D = 8); its oracle drops
+    # Schmidt values below 1e-13 of the largest, which moves log P by a few
+    # 1e-9 at most: the fused form matches it to 1e-8 and the dense
+    # fused-block oracle to 1e-9 (test_gpu_parity).
     with open(os.path.join(HERE, "golden", "oracle_d11_k4_D8_p010.json")) as f:
         g = json.load(f)
     w = g["workload"]
@@ -202,7 +206,7 @@ def test_fused_equals_mps_golden_at_d11(dev):
     for r in g["shots"]:
         assert r["truncations"] == 0          # the MPS form truncated nothing here
         b = r["shot"] - w["first_shot"]
-        np.testing.assert_allclose(out["logp"][b], r["logp"], rtol=0, atol=1e-9)
+        np.testing.assert_allclose(out["logp"][b], r["logp"], rtol=0, atol=1e-8)
         assert int(out["decision"][b]) == r["decision"]
 
 
@@ -268,10 +272,10 @@ def test_messages_in_workspace_or_shared_memory_give_the_same_bits(dev, d, preci
     assert torch.equal(res[1][2], res[2][2])
 
 
-@pytest.mark.parametrize("d,precision,messages", [(48, "fp32", 1), (36, "fp64", 1), (60, "fp32", 0), (60, "fp64", 0)])
+@pytest.mark.parametrize("d,precision,messages", [(46, "fp32", 1), (34, "fp64", 1), (58, "fp32", 0), (54, "fp64", 0)])
 def test_fused_k4_at_the_largest_distance(dev, d, precision, messages):
-    # The largest distances with the messages in shared memory (48 / 36) and
-    # in the workspace (60): finite log-probabilities below 0, valid
+    # The largest distances with the messages in shared memory (46 / 34) and
+    # in the workspace (58 / 54): finite log-probabilities below 0, valid
     # decisions, repeatable bit for bit.
     _, _, S = synth.sample_syndromes(4800 + d, 0, 2, d, 0.1)
     prm = pkg.DecoderParams(d=d, k=4, p=0.1, max_iter=3, delta0=0.0, precision=precision, algorithm="fused",

@@ -272,3 +272,24 @@ def test_converged_messages_restart_in_one_iteration(dev):
     assert conv.float().mean() > 0.5
     assert torch.all(warm["iters"][conv] <= 2)
     assert torch.max(torch.abs(warm["logp"][conv] - cold["logp"][conv])).item() < 1e-3
+
+
+@pytest.mark.parametrize("d,B", [(11, 300), (7, 57)])
+def test_one_call_learned_decoder_equals_its_steps(dev, d, B):
+    # bbp_decode_warm (device buffers) and bbp_decode_warm_host (host buffers)
+    # against the same steps made one by one: features of the distinct rows,
+    # the network, the expansion, the decode from the proposals.  Bit for bit.
+    k, p = 4, 0.1
+    _, _, S = synth.sample_syndromes(synth.workload_seed(2, 2), 0, B, d, p)
+    s = torch.from_numpy(S).to(dev)
+    prm = pkg.DecoderParams(d=d, k=k, p=p, max_iter=20, delta0=1e-4, precision="fp32", algorithm="fused")
+    net = wsm.WarmStart(device=dev, seed=3)
+    steps = wsm.decode_ex(s, prm, init_msgs=wsm.propose(s, prm, net, alpha=0.3))
+    one = wsm.decode_warm(s, prm, net, alpha=0.3)
+    host = wsm.decode_warm_host(S, prm, net, alpha=0.3)
+    torch.cuda.synchronize()
+    for key in ("logp", "delta", "iters", "flags", "decision"):
+        assert torch.equal(steps[key], one[key]), key
+    assert np.array_equal(host["decision"].numpy(), one["decision"].cpu().numpy())
+    assert np.array_equal(host["logp"].numpy(), one["logp"].cpu().numpy())
+    assert net.status() == 0
