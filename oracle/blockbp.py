@@ -237,12 +237,17 @@ def block_log_z(net: BlockNetwork, msgs, I, J, P: Params, stats):
 
 
 def run_blockbp(tensors, P: Params, stats=None) -> CosetResult:
-    """Algorithm 1 for one coset network: BP loop, Delta, Lemma 1 read-out."""
+    """Algorithm 1 for one coset network: BP loop, Delta, Lemma 1 read-out.
+
+    The arithmetic runs in the tensors' dtype (float64 for the oracle's
+    values; float32 only to measure what the method gives in single
+    precision); logs and sums of the read-out are Python floats."""
     stats = stats if stats is not None else M.Stats()
     kc = P.k_cols if P.k_cols is not None else P.k
     net = BlockNetwork(tensors, P.k, kc)
     edges = net.directed_edges()
-    msgs = {e: M.uniform_dims(net.side_dims(*e)) for e in edges}     # Remark 2
+    dt = tensors[0][0].dtype
+    msgs = {e: [A.astype(dt) for A in M.uniform_dims(net.side_dims(*e))] for e in edges}   # Remark 2
     Mtot = len(edges)
     delta = 0.0
     iters = 0
@@ -309,13 +314,20 @@ def decide(logp, delta, flags) -> int:
     return best
 
 
-def decode(s, P: Params, keep_messages=False):
-    """Decode one syndrome: returns a dict of per-coset results and the decision."""
+def decode(s, P: Params, keep_messages=False, dtype=np.float64):
+    """Decode one syndrome: returns a dict of per-coset results and the decision.
+
+    ``dtype`` other than float64 runs the same steps in that precision (the
+    network's tensors and every message), to measure the method's own
+    rounding error; the oracle's values are float64."""
     lat = Lattice(P.d)
     stats = M.Stats()
     res = []
     for L in range(4):
-        r = run_blockbp(coset_network(lat, s, L, P.p), P, stats)
+        T = coset_network(lat, s, L, P.p)
+        if dtype is not np.float64:
+            T = [[t.astype(dtype) for t in row] for row in T]
+        r = run_blockbp(T, P, stats)
         if not keep_messages:
             r.messages = {}
         res.append(r)

@@ -71,6 +71,23 @@ __device__ __forceinline__ FusedWS<T> fused_ws_at(unsigned char* base, int G) {
   return w;
 }
 
+// What a register-form block update needs beyond the messages and the qubit
+// ids, fixed for a syndrome: the incoming message opposite the outgoing
+// side, the side messages attached at the upper (s' = 0) and lower end of
+// the chain, each an index or -1 on the grid border; the block's shape;
+// flags (bit 0: the chain is read bottom to top, or for a one-node chain
+// column 0 holds a check; bit 1: the side messages are consumed in reverse
+// site order); and the qubit masks of the border vectors of the incoming /
+// upper / lower side (bits 0-3 / 4-7 / 8-11, bit n - 1 - k set where leg k
+// meets a qubit).
+constexpr int kShapeNone = 0, kShapeQuad = 1, kShapeCol = 2, kShapeRow = 3, kShapeDot = 4;
+constexpr int kQuadRev = 1, kQuadSideRev = 2;
+struct QuadTask {
+  int16_t in_idx, up_idx, lo_idx;
+  uint16_t masks;
+  uint8_t shape, flags;
+};
+
 // Shared-memory layout of one fused CTA.
 struct FusedLayout {
   int synd, frame, msg_of, meta, work, ovl, rlog, misc, qdesc, qid, msgs, ws, ws_stride, total;
@@ -93,7 +110,7 @@ BBP_HD FusedLayout fused_layout(const Geo& g, int M, int nwarps, int G, bool gm 
   L.misc = o;   o = align_up(o + 128, 16);
   // 4 x 4 block updates (k = 4): a descriptor per message and the qubit
   // ids of each (coset, message), built once per syndrome.
-  L.qdesc = o;  if (K == 4 && g.k == 4) o = align_up(o + 8 * M, 16);
+  L.qdesc = o;  if (K == 4 && g.k == 4) o = align_up(o + (int)sizeof(QuadTask) * M, 16);
   L.qid = o;    if (K == 4 && g.k == 4) o = align_up(o + 2 * G * M, 16);
   L.msgs = o;   // the messages, unless they live in the workspace
   if (!gm) o = align_up(o + (int)sizeof(T) * FusedDim<K>::vec * G * M, 16);
@@ -218,6 +235,11 @@ template <> struct LogAcc<float> {
     e += ex;
     m = frexpf(m, &ex);
     e += ex;
+  }
+  __device__ __forceinline__ void mul(const LogAcc<float>& o) {
+    int ex;
+    m = frexpf(m * o.m, &ex);
+    e += o.e + ex;
   }
   __device__ __forceinline__ double value() const { return log((double)m) + (double)e * 0.6931471805599453; }
 };
@@ -860,62 +882,220 @@ __device__ __forceinline__ T shx(T v, int mask) {
   return __shfl_xor_sync(kFull, v, mask);
 }
 
-// What a 4 x 4 block update needs beyond the messages and the qubit ids,
-// fixed for a syndrome: the incoming message opposite the outgoing side,
-// the side messages attached at s' = 0 (upper) and s' = 3 (lower), each an
-// index or -1 on the grid border, and bits: 0 the chain is read bottom to
-// top, 1 the side messages are consumed in reverse site order, 2 the block
-// is 4 x 4, 4-7 / 8-11 / 12-15 the qubit masks of the border vectors of the
-// incoming / upper / lower side (bit 3 - t or 3 - s set at a qubit).
-struct QuadTask {
-  int16_t in_idx, up_idx, lo_idx;
-  uint16_t bits;
-};
-constexpr int kQuadRev = 1, kQuadSideRev = 2, kQuad = 4;
+// Shapes with a register form (k = 4): 4 x 4 blocks, and the blocks of one
+// row or one column of nodes that the last block row / column leaves at odd
+// d (4 x 1, 1 x 4, 1 x 1).
+template <int K>
+__device__ __forceinline__ int block_shape(const Frame& f) {
+  if (K != 4) return kShapeNone;
+  if (f.h == 4 && f.ncols == 4) return kShapeQuad;
+  if (f.h == 4 && f.ncols == 1) return kShapeCol;
+  if (f.h == 1 && f.ncols == 4) return kShapeRow;
+  if (f.h == 1 && f.ncols == 1) return kShapeDot;
+  return kShapeNone;
+}
 
 template <typename T, int K>
 __device__ __forceinline__ QuadTask quad_task(const Frame& f) {
   QuadTask q;
+  const int shape = block_shape<K>(f);
+  const int h = f.h, nc = f.ncols;
   int i00, j00;
   f.node(0, 0, &i00, &j00);
-  const bool rev = (i00 + j00) & 1;                          // column 0 starts with a check
-  const int up_s = rev ? 3 : 0, lo_s = rev ? 0 : 3;
+  const bool chk0 = (i00 + j00) & 1;                         // column 0 starts with a check
+  const bool rev = chk0 && h > 1;                            // chain read bottom to top
+  const int up_s = rev ? h - 1 : 0, lo_s = rev ? 0 : h - 1;
   int qm_up = 0, qm_lo = 0, qm_in = 0;
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < nc; ++u) {
     int i, j;
     f.node(u, up_s, &i, &j);
-    if (!((i + j) & 1)) qm_up |= 8 >> u;
+    if (!((i + j) & 1)) qm_up |= 1 << (nc - 1 - u);
     f.node(u, lo_s, &i, &j);
-    if (!((i + j) & 1)) qm_lo |= 8 >> u;
+    if (!((i + j) & 1)) qm_lo |= 1 << (nc - 1 - u);
+  }
+  for (int u = 0; u < h; ++u) {
+    int i, j;
     f.node(0, u, &i, &j);
-    if (!((i + j) & 1)) qm_in |= 8 >> u;
+    if (!((i + j) & 1)) qm_in |= 1 << (h - 1 - u);
   }
   q.in_idx = (int16_t)f.in_idx;
   q.up_idx = (int16_t)(rev ? f.b_idx : f.a_idx);
   q.lo_idx = (int16_t)(rev ? f.a_idx : f.b_idx);
-  q.bits = (uint16_t)((rev ? kQuadRev : 0) | (f.rev ? kQuadSideRev : 0) |
-                      ((K == 4 && f.h == 4 && f.ncols == 4) ? kQuad : 0) | (qm_in << 4) | (qm_up << 8) |
-                      (qm_lo << 12));
+  q.masks = (uint16_t)(qm_in | (qm_up << 4) | (qm_lo << 8));
+  q.shape = (uint8_t)shape;
+  q.flags = (uint8_t)((chk0 ? kQuadRev : 0) | (f.rev ? kQuadSideRev : 0));
   return q;
 }
 
-// The ids (bits 2 (2t + u)) of the 8 qubits of a 4 x 4 block for one
-// coset frame: id[t][0] the upper, id[t][1] the lower qubit of column t
-// (chain positions 0, 2 for even t and 1, 3 for odd t, read from the top or,
-// reversed, from the bottom).
-__device__ __forceinline__ uint16_t quad_ids(const Frame& f, const uint8_t* fr, int W, bool rev) {
+// The ids (2 bits each, pi(I) at (alpha, beta)) of the qubits of a block in
+// register form, for one coset frame.  4 x 4: id[t][0] the upper, id[t][1]
+// the lower qubit of column t (chain positions 0, 2 for even t and 1, 3 for
+// odd t, read from the top or, reversed, from the bottom) at bits
+// 2 (2t + u); 4 x 1: the qubits at s' = 0 and 2; 1 x 4: the qubits of
+// columns 0 and 2, or 1 and 3; 1 x 1: the node (a qubit, or a check).
+__device__ __forceinline__ int node_id(const Frame& f, const uint8_t* fr, int W, int t, int s) {
   const bool rowwise = f.dir == kDirR || f.dir == kDirL;
+  int i, j;
+  f.node(t, s, &i, &j);
+  const int fv = fr[i * W + j];
+  const bool alpha_is_z = ((i & 1) == 0) == rowwise;
+  return alpha_is_z ? fv : (((fv & 1) << 1) | (fv >> 1));
+}
+
+__device__ __forceinline__ uint16_t quad_ids(const Frame& f, const uint8_t* fr, int W, const QuadTask& q) {
+  const bool rev = (q.flags & kQuadRev) != 0;
   unsigned v = 0;
-  for (int t = 0; t < 4; ++t)
-    for (int u = 0; u < 2; ++u) {
-      const int sq = (t & 1) + 2 * u;
-      int i, j;
-      f.node(t, rev ? 3 - sq : sq, &i, &j);
-      const int fv = fr[i * W + j];
-      const bool alpha_is_z = ((i & 1) == 0) == rowwise;
-      v |= (unsigned)(alpha_is_z ? fv : (((fv & 1) << 1) | (fv >> 1))) << (2 * (2 * t + u));
-    }
+  if (q.shape == kShapeQuad) {
+    for (int t = 0; t < 4; ++t)
+      for (int u = 0; u < 2; ++u) {
+        const int sq = (t & 1) + 2 * u;
+        v |= (unsigned)node_id(f, fr, W, t, rev ? 3 - sq : sq) << (2 * (2 * t + u));
+      }
+  } else if (q.shape == kShapeCol) {
+    v = (unsigned)node_id(f, fr, W, 0, rev ? 3 : 0) | ((unsigned)node_id(f, fr, W, 0, rev ? 1 : 2) << 2);
+  } else if (q.shape == kShapeRow) {
+    const int t0 = rev ? 1 : 0;
+    v = (unsigned)node_id(f, fr, W, t0, 0) | ((unsigned)node_id(f, fr, W, t0 + 2, 0) << 2);
+  } else if (q.shape == kShapeDot) {
+    v = (unsigned)node_id(f, fr, W, 0, 0);
+  }
   return (uint16_t)v;
+}
+
+// Register form of a block of one column of 4 nodes (4 x 1 rotated): the
+// column acts as in quad_sweep's column 0, both side messages have one leg.
+template <typename T, int K>
+__device__ __forceinline__ void col_sweep(const FusedWS<T>& ws, T pI, T pE, const T* msgs, int stride,
+                                          unsigned cos_of, int n, const QuadTask qt, const uint16_t* qid,
+                                          int qid_stride, int lane) {
+  constexpr int VEC = FusedDim<K>::vec;
+  const bool rev = qt.flags & kQuadRev;
+  const int qm_in = qt.masks & 15, qm_up = (qt.masks >> 4) & 15, qm_lo = (qt.masks >> 8) & 15;
+  const int R = lane & 15, hi = lane >> 4;
+  const int r1 = (R >> 2) & 1, r3 = R & 1;
+  const int Rn = rev ? bitrev(R, 4) : R;
+  for (int sp = 0; sp < n; sp += 2) {
+    const int slot = sp + hi;
+    const bool on = slot < n;
+    const int cq = slot_coset(cos_of, on ? slot : sp);
+    const T* mq = msgs + cq * stride;
+    const unsigned idv = qid[cq * qid_stride];
+    const int id_up = (int)(idv & 3u), id_lo = (int)((idv >> 2) & 3u);
+    const T x = qt.in_idx >= 0 ? mq[qt.in_idx * VEC + Rn] : ((Rn & qm_in) ? T(0) : T(1));
+    const T a0 = qt.up_idx >= 0 ? mq[qt.up_idx * VEC] : T(1);
+    const T a1 = qt.up_idx >= 0 ? mq[qt.up_idx * VEC + 1] : (qm_up ? T(0) : T(1));
+    const T bb = qt.lo_idx >= 0 ? mq[qt.lo_idx * VEC + r3] : ((r3 && qm_lo) ? T(0) : T(1));
+    T k0, k1, h0, h1, m0, m1;
+    qpair(id_lo, r1 ^ r3, pI, pE, k0, k1);
+    const T u = k0 * x + k1 * shx(x, 2);
+    const T up = shx(u, 8);
+    qpair(id_up, r1, pI, pE, h0, h1);          // top leg 0
+    qpair(id_up, r1 ^ 1, pI, pE, m0, m1);      // top leg 1
+    const T out = bb * (a0 * (h0 * u + h1 * up) + a1 * (m0 * u + m1 * up));
+    if (on) ws.s0[(slot << 4) | Rn] = out;
+  }
+  __syncwarp();
+}
+
+// Register form of a block of one row of 4 nodes (1 x 4 rotated): a lane
+// takes one assignment of the four side legs that the two qubits see (the
+// legs at the checks are tied to the row leg), the 16 lanes of a coset sum.
+template <typename T, int K>
+__device__ __forceinline__ void row_sweep(const FusedWS<T>& ws, T pI, T pE, const T* msgs, int stride,
+                                          unsigned cos_of, int n, const QuadTask qt, const uint16_t* qid,
+                                          int qid_stride, int lane) {
+  constexpr int VEC = FusedDim<K>::vec;
+  const bool chk0 = qt.flags & kQuadRev, srev = qt.flags & kQuadSideRev;
+  const int qm_in = qt.masks & 15, qm_up = (qt.masks >> 4) & 15, qm_lo = (qt.masks >> 8) & 15;
+  for (int e = lane; e < (n << 4); e += 32) {
+    const int i = e & 15, jj = srev ? bitrev(i, 4) : i;
+    const T* ms = msgs + slot_coset(cos_of, e >> 4) * stride;
+    ws.mt[e] = qt.up_idx >= 0 ? ms[qt.up_idx * VEC + jj] : ((i & qm_up) ? T(0) : T(1));
+    ws.mb[e] = qt.lo_idx >= 0 ? ms[qt.lo_idx * VEC + jj] : ((i & qm_lo) ? T(0) : T(1));
+  }
+  __syncwarp();
+  const int j = lane & 15, hi = lane >> 4;
+  const int x0 = (j >> 3) & 1, x2 = (j >> 2) & 1, y0 = (j >> 1) & 1, y2 = j & 1;
+  for (int sp = 0; sp < n; sp += 2) {
+    const int slot = sp + hi;
+    const bool on = slot < n;
+    const int sl = on ? slot : sp;
+    const int cq = slot_coset(cos_of, sl);
+    const T* mq = msgs + cq * stride;
+    const T* mA = ws.mt + (sl << 4);
+    const T* mB = ws.mb + (sl << 4);
+    const unsigned idv = qid[cq * qid_stride];
+    const int ia = (int)(idv & 3u), ib = (int)((idv >> 2) & 3u);
+    const T in0 = qt.in_idx >= 0 ? mq[qt.in_idx * VEC] : T(1);
+    const T in1 = qt.in_idx >= 0 ? mq[qt.in_idx * VEC + 1] : (qm_in ? T(0) : T(1));
+    T part[2];
+    if (!chk0) {
+      // qubit, check, qubit, check: the lane's legs are (a0, a2, b0, b2);
+      // the checks tie a1 = b1 to the row leg l1 and a3 = b3 to r.
+#pragma unroll
+      for (int r = 0; r < 2; ++r) part[r] = T(0);
+#pragma unroll
+      for (int l1 = 0; l1 < 2; ++l1) {
+        T g0, g1;
+        qpair(ia, x0 ^ y0, pI, pE, g0, g1);
+        const T hh = l1 ? in0 * g1 + in1 * g0 : in0 * g0 + in1 * g1;
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+          part[r] += hh * mA[(x0 << 3) | (l1 << 2) | (x2 << 1) | r] * mB[(y0 << 3) | (l1 << 2) | (y2 << 1) | r] *
+                     qval(ib, l1 ^ r, x2 ^ y2, pI, pE);
+      }
+    } else {
+      // check, qubit, check, qubit: the lane's legs are (a1, a3, b1, b3); the
+      // checks tie a0 = b0 = l0 and a2 = b2 = l2.
+      part[0] = part[1] = T(0);
+#pragma unroll
+      for (int l0 = 0; l0 < 2; ++l0)
+#pragma unroll
+        for (int l2 = 0; l2 < 2; ++l2) {
+          const T w = (l0 ? in1 : in0) * mA[(l0 << 3) | (x0 << 2) | (l2 << 1) | x2] *
+                      mB[(l0 << 3) | (y0 << 2) | (l2 << 1) | y2] * qval(ia, l0 ^ l2, x0 ^ y0, pI, pE);
+          part[0] += w * qval(ib, l2, x2 ^ y2, pI, pE);
+          part[1] += w * qval(ib, l2 ^ 1, x2 ^ y2, pI, pE);
+        }
+    }
+#pragma unroll
+    for (int m = 8; m >= 1; m >>= 1) {
+      part[0] += shx(part[0], m);
+      part[1] += shx(part[1], m);
+    }
+    if (on && j < 2) ws.s0[(slot << 1) | j] = j ? part[1] : part[0];
+  }
+  __syncwarp();
+}
+
+// Register form of a single node (1 x 1): lane (l, a, b, r) of the node's
+// legs, summed over l, a, b.
+template <typename T, int K>
+__device__ __forceinline__ void dot_sweep(const FusedWS<T>& ws, T pI, T pE, const T* msgs, int stride,
+                                          unsigned cos_of, int n, const QuadTask qt, const uint16_t* qid,
+                                          int qid_stride, int lane) {
+  constexpr int VEC = FusedDim<K>::vec;
+  const bool chk = qt.flags & kQuadRev;
+  const int qm_in = qt.masks & 15, qm_up = (qt.masks >> 4) & 15, qm_lo = (qt.masks >> 8) & 15;
+  const int j = lane & 15, hi = lane >> 4;
+  const int l = (j >> 3) & 1, a = (j >> 2) & 1, b = (j >> 1) & 1, r = j & 1;
+  for (int sp = 0; sp < n; sp += 2) {
+    const int slot = sp + hi;
+    const bool on = slot < n;
+    const int cq = slot_coset(cos_of, on ? slot : sp);
+    const T* mq = msgs + cq * stride;
+    const int id = (int)(qid[cq * qid_stride] & 3u);
+    const T mi = qt.in_idx >= 0 ? mq[qt.in_idx * VEC + l] : ((l && qm_in) ? T(0) : T(1));
+    const T ma = qt.up_idx >= 0 ? mq[qt.up_idx * VEC + a] : ((a && qm_up) ? T(0) : T(1));
+    const T mb = qt.lo_idx >= 0 ? mq[qt.lo_idx * VEC + b] : ((b && qm_lo) ? T(0) : T(1));
+    const T nv = chk ? ((l == r && a == r && b == r) ? T(1) : T(0)) : qval(id, l ^ r, a ^ b, pI, pE);
+    T v = mi * ma * mb * nv;
+    v += shx(v, 8);
+    v += shx(v, 4);
+    v += shx(v, 2);
+    if (on && j < 2) ws.s0[(slot << 1) | j] = v;
+  }
+  __syncwarp();
 }
 
 // The outgoing vectors of a 4 x 4 block (f.h == f.ncols == 4) for the n
@@ -932,8 +1112,8 @@ __device__ __forceinline__ void quad_sweep(const FusedWS<T>& ws, T pI, T pE, con
                                            unsigned cos_of, int n, const QuadTask qt, const uint16_t* qid,
                                            int qid_stride, int lane) {
   constexpr int VEC = FusedDim<K>::vec;
-  const bool rev = qt.bits & kQuadRev, srev = qt.bits & kQuadSideRev;
-  const int qm_in = (qt.bits >> 4) & 15, qm_up = (qt.bits >> 8) & 15, qm_lo = (qt.bits >> 12) & 15;
+  const bool rev = qt.flags & kQuadRev, srev = qt.flags & kQuadSideRev;
+  const int qm_in = qt.masks & 15, qm_up = (qt.masks >> 4) & 15, qm_lo = (qt.masks >> 8) & 15;
   // The side messages in consumption order, the upper one (attached at
   // s' = 0) in ws.mt and the lower one in ws.mb, slot q at q << 4.  A side
   // on the grid border has no message: the product vector of its nodes'
@@ -1156,7 +1336,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
       const Frame f = make_frame(c, key / 4 / nb, (key / 4) % nb, key & 3);
       const QuadTask qt = quad_task<T, K>(f);
       if (q == 0) qdesc[idx] = qt;
-      if (qt.bits & kQuad) qid[e] = quad_ids(f, frames + q * WW, W, qt.bits & kQuadRev);
+      qid[e] = quad_ids(f, frames + q * WW, W, qt);
     }
     __syncthreads();
   }
@@ -1184,6 +1364,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
   __syncthreads();
 
   const T eta = (T)a.eta, one_m_eta = T(1) - eta;
+  const double d0sq = (a.delta0 * M) * (a.delta0 * M);
   unsigned act = (1u << G) - 1;                      // cosets still iterating
   double delta[G];
   int it_done[G];
@@ -1206,14 +1387,22 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
         if (item >= nwork) break;
         const int idx = lst[item];
         int h = 4;
-        bool quad = false;
+        int shape = kShapeNone;
         QuadTask qt;
         if (quads) {
           qt = qdesc[idx];
-          quad = qt.bits & kQuad;
+          shape = qt.shape;
         }
-        if (quad) {
+        if (shape == kShapeQuad) {
           quad_sweep<T, K>(ws, c.pI, c.pE, msgs, stride, cos_of, n, qt, qid + idx, M, lane);
+        } else if (shape == kShapeCol) {
+          col_sweep<T, K>(ws, c.pI, c.pE, msgs, stride, cos_of, n, qt, qid + idx, M, lane);
+        } else if (shape == kShapeRow) {
+          row_sweep<T, K>(ws, c.pI, c.pE, msgs, stride, cos_of, n, qt, qid + idx, M, lane);
+          h = 1;
+        } else if (shape == kShapeDot) {
+          dot_sweep<T, K>(ws, c.pI, c.pE, msgs, stride, cos_of, n, qt, qid + idx, M, lane);
+          h = 1;
         } else {
           const int key = meta[idx];
           const Frame f = make_frame(c, key / 4 / nb, (key / 4) % nb, key & 3);
@@ -1230,17 +1419,21 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
       double acc = 0.0;
       for (int i = lane; i < M; i += 32) acc += (double)ovl[warp * M + i];
       acc = warp_sum(acc);
-      if (lane == 0) dsh[warp] = sqrt(fmax(acc, 0.0)) / M;
+      if (lane == 0) dsh[warp] = fmax(acc, 0.0);
     }
     __syncthreads();
+    // Delta = sqrt(sum) / M < delta0 compared as sum < (delta0 M)^2; the
+    // square root is taken once, after the loop.
 #pragma unroll
     for (int q = 0; q < G; ++q)
       if ((act >> q) & 1u) {
         delta[q] = dsh[q];
         it_done[q] = it;
-        if (delta[q] < a.delta0) act &= ~(1u << q);
+        if (delta[q] < d0sq) act &= ~(1u << q);
       }
   }
+#pragma unroll
+  for (int q = 0; q < G; ++q) delta[q] = M > 0 ? sqrt(delta[q]) / M : 0.0;
 
   if (a.final_msgs)
     for (int e = tid; e < G * stride; e += NW * 32) {
@@ -1270,19 +1463,59 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
     item = __shfl_sync(kFull, item, 0);
     if (item >= per) break;
     if (item < nblk) {
+      // Z_v: the block's outgoing vector to the right, with every other
+      // incoming message, closed against the message from the right.  Blocks
+      // with a register form need no per-column rescaling (entries are sums
+      // of products of node values and message entries, all at most 1).
       const int I = item / nb, J = item % nb;
       const Frame f = make_frame(c, I, J, kDirR);
       LogAcc<T> ls[kFusedMaxG];
-      fused_sweep(ws, c, msgs, stride, all, G, frames, f, ls, lane);
+      const int shape = quads ? block_shape<K>(f) : kShapeNone;
+      if (shape != kShapeNone) {
+        const QuadTask qt = quad_task<T, K>(f);
+        uint16_t* idw = reinterpret_cast<uint16_t*>(ws.wn);
+        if (lane < G) idw[lane] = quad_ids(f, frames + lane * WW, W, qt);
+        __syncwarp();
+        if (shape == kShapeQuad) quad_sweep<T, K>(ws, c.pI, c.pE, msgs, stride, all, G, qt, idw, 1, lane);
+        else if (shape == kShapeCol) col_sweep<T, K>(ws, c.pI, c.pE, msgs, stride, all, G, qt, idw, 1, lane);
+        else if (shape == kShapeRow) row_sweep<T, K>(ws, c.pI, c.pE, msgs, stride, all, G, qt, idw, 1, lane);
+        else dot_sweep<T, K>(ws, c.pI, c.pE, msgs, stride, all, G, qt, idw, 1, lane);
+      } else {
+        fused_sweep(ws, c, msgs, stride, all, G, frames, f, ls, lane);
+      }
       const int right = J + 1 < nb ? msg_index(c, I, J + 1, kDirL) : -1;
+      // On the grid border the right side has no message.  The node-by-node
+      // path gives missing legs the value 0, so only entry 0 survives; the
+      // register forms treat every node as complete, so their vector is
+      // closed against the border vector instead (1 at a check, whose copy
+      // tensor spans its remaining legs; e_0 at a qubit).
+      int qm_out = 0;
+      if (right < 0 && shape != kShapeNone)
+        for (int u = 0; u < f.h; ++u) {
+          int i, j;
+          f.node(f.ncols - 1, u, &i, &j);
+          if (!((i + j) & 1)) qm_out |= 1 << (f.h - 1 - u);
+        }
 #pragma unroll
       for (int q = 0; q < G; ++q) {
         const T* mq = msgs + q * stride;
-        const T z = right >= 0 ? read_dot(ws.s0 + (q << f.h), mq + right * VEC, 1 << f.h, lane)
-                               : ws.s0[q << f.h];
+        T z;
+        if (right >= 0) {
+          z = read_dot(ws.s0 + (q << f.h), mq + right * VEC, 1 << f.h, lane);
+        } else if (shape != kShapeNone) {
+          const T v = (lane < (1 << f.h) && !(lane & qm_out)) ? ws.s0[(q << f.h) + lane] : T(0);
+          z = warp_sum(v);
+        } else {
+          z = ws.s0[q << f.h];
+        }
         if (lane == 0) {
           ls[q].mul(z < T(0) ? -z : z);
-          rlog[q * per + item] = ls[q].value();
+          if constexpr (sizeof(T) == 4) {   // the factor as mantissa and exponent
+            reinterpret_cast<float*>(rlog + q * per + item)[0] = ls[q].m;
+            reinterpret_cast<int*>(rlog + q * per + item)[1] = ls[q].e;
+          } else {
+            rlog[q * per + item] = ls[q].value();
+          }
           if (!(z > T(0))) atomicOr(&misc[8 + q], kFlagBlock);
         }
       }
@@ -1298,7 +1531,14 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
         const T* mq = msgs + q * stride;
         const T o = read_dot(mq + idx * VEC, mq + other * VEC, 1 << w, lane);
         if (lane == 0) {
-          rlog[q * per + item] = -log(fabs((double)o));
+          if constexpr (sizeof(T) == 4) {
+            LogAcc<float> lo;
+            lo.mul(fabsf(o));
+            reinterpret_cast<float*>(rlog + q * per + item)[0] = lo.m;
+            reinterpret_cast<int*>(rlog + q * per + item)[1] = lo.e;
+          } else {
+            rlog[q * per + item] = -log(fabs((double)o));
+          }
           if (!(o > T(0))) atomicOr(&misc[8 + q], kFlagOverlap);
         }
       }
@@ -1307,8 +1547,31 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
   __syncthreads();
   if (warp < G) {
     double acc = 0.0;
-    for (int i = lane; i < per; i += 32) acc += rlog[warp * per + i];
-    acc = warp_sum(acc);
+    if constexpr (sizeof(T) == 4) {
+      // Products of the block values and of the edge overlaps in a fixed
+      // order (lane-strided, then a fixed tree), one log each.
+      LogAcc<float> pz, po;
+      for (int i = lane; i < per; i += 32) {
+        LogAcc<float> r;
+        r.m = reinterpret_cast<const float*>(rlog + warp * per + i)[0];
+        r.e = reinterpret_cast<const int*>(rlog + warp * per + i)[1];
+        if (i < nblk) pz.mul(r); else po.mul(r);
+      }
+#pragma unroll
+      for (int msk = 16; msk >= 1; msk >>= 1) {
+        LogAcc<float> oz, oo;
+        oz.m = __shfl_xor_sync(kFull, pz.m, msk);
+        oz.e = __shfl_xor_sync(kFull, pz.e, msk);
+        oo.m = __shfl_xor_sync(kFull, po.m, msk);
+        oo.e = __shfl_xor_sync(kFull, po.e, msk);
+        pz.mul(oz);
+        po.mul(oo);
+      }
+      acc = pz.value() - po.value();
+    } else {
+      for (int i = lane; i < per; i += 32) acc += rlog[warp * per + i];
+      acc = warp_sum(acc);
+    }
     double dq = 0.0;
     int iq = 0;
 #pragma unroll

@@ -41,16 +41,16 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 WORKLOADS = {
     # Small case: d = 5, p = 0.10, k = 3, D = 4, 10 fixed iterations, 200 shots.
     "d5": dict(file="oracle_d5_k3_D4_p010.json", d=5, k=3, D=4, p=0.10, max_iter=10, delta0=0.0,
-               seed=synth.workload_seed(1, 0), first_shot=0, shots=200),
+               seed=synth.workload_seed(1, 0), first_shot=0, shots=200, fp32_ref=True),
     # Distance 11, p = 0.10, k = 4, D = 8, 20 fixed iterations.
     "d11": dict(file="oracle_d11_k4_D8_p010.json", d=11, k=4, D=8, p=0.10, max_iter=20, delta0=0.0,
-                seed=synth.workload_seed(2, 2), first_shot=0, shots=200),
+                seed=synth.workload_seed(2, 2), first_shot=0, shots=200, fp32_ref=True),
 }
 # The other noise levels of the d = 11 workload (p index 0, 1, 3, 4).
 for _ip, _p in ((0, 0.05), (1, 0.08), (3, 0.13), (4, 0.15)):
     WORKLOADS[f"d11_p{int(round(_p * 100)):03d}"] = dict(
         file=f"oracle_d11_k4_D8_p{int(round(_p * 100)):03d}.json", d=11, k=4, D=8, p=_p, max_iter=20,
-        delta0=0.0, seed=synth.workload_seed(2, _ip), first_shot=0, shots=50)
+        delta0=0.0, seed=synth.workload_seed(2, _ip), first_shot=0, shots=50, fp32_ref=True)
 
 # The benchmark workload (d = 11, p = 0.10, k = 4, 20 fixed iterations)
 # through the dense fused-block oracle of Remark 9, the reference of the
@@ -67,7 +67,7 @@ for _d in (9, 11):
     for _D in (2, 4):
         WORKLOADS[f"d{_d}_D{_D}"] = dict(
             file=f"oracle_d{_d}_k4_D{_D}_p010.json", d=_d, k=4, D=_D, p=0.10, max_iter=20, delta0=0.0,
-            seed=synth.workload_seed(6, 10 * _d + _D), first_shot=0, shots=24, sensitivity=True)
+            seed=synth.workload_seed(6, 10 * _d + _D), first_shot=0, shots=24, sensitivity=True, fp32_ref=True)
 
 # Distance 31, k = 6 (dense 64-entry messages), 20 fixed iterations, at the
 # two noise levels of the d = 31 workload (p index 0, 1).
@@ -140,6 +140,14 @@ def _one(args):
                flags=[int(x) for x in r["flags"]], decision=int(r["decision"]),
                min_gap=(None if not np.isfinite(st.min_gap) else float(st.min_gap)),
                truncations=int(st.truncations), flops=float(st.flops))
+    if w.get("fp32_ref"):
+        # The same steps in float32 (numpy / LAPACK single precision, relative
+        # cutoff 1e-7 as the GPU's FP32 default): how far single precision
+        # moves the method's own log P on this shot.
+        P32 = bb.Params(d=w["d"], k=w["k"], D=w["D"], p=w["p"], max_iter=w["max_iter"], delta0=w["delta0"],
+                        cutoff=1e-7)
+        r32 = bb.decode(s, P32, dtype=np.float32)
+        row["dlogp_fp32"] = float(np.max(np.abs(np.asarray(r32["logp"]) - np.asarray(r["logp"]))))
     if w.get("sensitivity"):
         # Noise of the size by which two correct decompositions of the same
         # matrix differ: about a thousand units of rounding (unit roundoff
@@ -162,7 +170,7 @@ def make(name: str, procs: int):
     else:
         with ctx.Pool(procs) as pool:
             rows = pool.map(_one, [(w, b, S[b].tolist()) for b in range(w["shots"])])
-    meta = {k: v for k, v in w.items() if k not in ("file", "form", "sensitivity")}
+    meta = {k: v for k, v in w.items() if k not in ("file", "form", "sensitivity", "fp32_ref")}
     if w.get("form") == "fused":
         meta["oracle"] = "dense fused-block blockBP (Remark 9), no truncation"
     meta["eta"], meta["delta1"], meta["cutoff"] = 0.1, 1e-2, 1e-13

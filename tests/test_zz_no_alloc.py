@@ -80,14 +80,14 @@ def test_static_entry_point_refuses_batches_beyond_its_array():
 
 
 def test_static_entry_point_takes_the_shared_memory_shape_when_slots_do_not_fit():
-    # Fused k = 4 at d = 21: the default shape keeps its messages in
-    # workspace slots (600 syndromes: 512 slots of 4 x 440 x 16 floats =
-    # 57.7 MB > 32 MiB), so the static entry point takes the shape that
+    # Fused k = 4 at d = 19: the default shape keeps its messages in
+    # workspace slots (600 syndromes: 512 slots of 4 x 360 x 16 floats =
+    # 47.2 MB > 32 MiB), so the static entry point takes the shape that
     # keeps them in shared memory; the results are those of the allocating
     # entry point bit for bit.
     build()
     dev = torch.device("cuda:0")
-    d, B = 21, 600
+    d, B = 19, 600
     prm = pkg.DecoderParams(d=d, k=4, p=0.1, max_iter=6, delta0=1e-4, precision="fp32", algorithm="fused")
     assert pkg.workspace_bytes(prm, B) > _lib.STATIC_WORKSPACE_BYTES
     _, _, S = synth.sample_syndromes(2121, 0, B, d, 0.1)
