@@ -120,7 +120,8 @@ def fused_flops(d: int, k: int):
     XOR convolution, four multiply-adds per entry of the state.  Check nodes
     are copy tensors (Sec. III.A): they move entries and cost nothing.  Then
     normalisation, damping and overlaps per message, and the Lemma 1
-    read-out (per-column renormalisation, closing dots, edge overlaps)."""
+    read-out (4 x 4 blocks in register form; the others node by node with
+    per-column renormalisation; closing dots, edge overlaps)."""
     W = 2 * d - 1
     rng = [(a, min(a + k, W)) for a in range(0, W, k)]
     nb = len(rng)
@@ -183,7 +184,10 @@ def fused_flops(d: int, k: int):
                 if dr in (0, 2):
                     readout += 2.0 * 2 ** h
             lines = [[(i, j) for i in rows] for j in cols]
-            readout += sweep(qubits(lines), r1 - r0, I > 0, I + 1 < nb, True) + 2.0 * 2 ** (r1 - r0)
+            if r1 - r0 == 4 and c1 - c0 == 4:      # the read-out's register form, then the closing dot
+                readout += 2.0 * 16 * (108 if (r0 + c0) % 2 else 116) + 2.0 * 16
+            else:
+                readout += sweep(qubits(lines), r1 - r0, I > 0, I + 1 < nb, True) + 2.0 * 2 ** (r1 - r0)
     return per_iter, readout
 
 
@@ -610,7 +614,7 @@ def ours(args):
                 "flop_model": "4x4 blocks: the multiply-adds of the register form (116 or 108 per row and "
                               "coset); other blocks: qubit nodes as 2x2 XOR convolutions (4 multiply-adds "
                               "per state entry), check nodes as zero-flop copy tensors, side-message data "
-                              "columns; normalise/damp/overlap; Lemma 1 read-out (node by node)",
+                              "columns; normalise/damp/overlap; Lemma 1 read-out (register form for 4x4 blocks)",
                 "flops_per_syndrome": flops / B}
     if mlp_ms is not None:
         bf16_peak, src = 1900.0, "fallback"

@@ -90,13 +90,19 @@ extern "C" {
  *             CTA (1, 2 or 4; they share the block geometry and, off row 0
  *             and column 0, the node tensors), resident CTAs per SM of
  *             bbp_decode_mixed, and where the messages live (1 shared memory,
- *             2 a workspace slot per resident CTA with a persistent grid).
+ *             2 a workspace slot per resident CTA with a persistent grid,
+ *             3 shared memory with every block update in register form:
+ *             k = 4 at odd d only, where every block is 4 x 4 or one node
+ *             wide; small per-warp buffers, sized for more CTAs per SM; not
+ *             for bbp_decode_mixed).
  *             0 picks the first compiled shape, in order of measured speed,
  *             whose shared memory allows the CTAs per SM its registers are
  *             sized for, else the first that fits; compiled (warps, cosets):
  *             FP32 (8,4) (8,2) (4,2) (4,4) (16,1) (8,1) (4,1), of which (8,4)
- *             and (8,2) also with workspace messages; FP64 (4,2) (8,2) (8,1)
- *             (4,4), (4,2) also with workspace messages; for k = 5, 6
+ *             and (8,2) also with workspace messages and in register-form-only
+ *             variants (3 and 4 CTAs per SM); FP64 (4,2) (8,2) (8,1) (4,4),
+ *             (4,2) also with workspace messages, (4,2) and (8,2) in
+ *             register-form-only variants (4 and 2 CTAs per SM); for k = 5, 6
  *             (workspace messages only): FP32 (6,1) (4,1) (2,1), FP64 (3,1)
  *             (2,1); other requests give BBP_EUNSUPPORTED.
  *   algorithm BBP_ALG_MPS, or BBP_ALG_FUSED: every k x k block fused into one
@@ -121,7 +127,7 @@ typedef struct bbp_params {
   int32_t launch_warps;        /* fused path: warps per CTA (2, 3, 4, 6, 8, 16), 0 = default */
   int32_t launch_ctas_per_sm;  /* bbp_decode_mixed: resident CTAs per SM, 0 = the occupancy limit */
   int32_t launch_cosets;       /* fused path: cosets per CTA (1, 2, 4), 0 = default */
-  int32_t launch_messages;     /* fused path: 1 shared memory, 2 workspace slots, 0 = default */
+  int32_t launch_messages;     /* fused path: 1 shared memory, 2 workspace slots, 3 register form only, 0 = default */
 } bbp_params;
 
 /*

@@ -33,6 +33,9 @@ FUSED_SHAPES = {"fp32": ((8, 4), (8, 2), (4, 2), (4, 4), (16, 1), (8, 1), (4, 1)
                 "fp64": ((4, 2), (8, 2), (8, 1), (4, 4))}
 # ... of which these also with their messages in workspace slots (messages=2)
 FUSED_SHAPES_WS = {"fp32": ((8, 4), (8, 2)), "fp64": ((4, 2),)}
+# ... of which these also in register-form-only variants (messages=3; k = 4
+# with a one-node-wide last block, i.e. odd d), sized for more CTAs per SM.
+FUSED_SHAPES_LEAN = {"fp32": ((8, 4), (8, 2)), "fp64": ((4, 2), (8, 2))}
 # ... and for block sides 5 and 6 (one coset per CTA, messages in the workspace).
 FUSED_SHAPES_K6 = {"fp32": ((6, 1), (4, 1), (2, 1)), "fp64": ((3, 1), (2, 1))}
 BBP_ETOOLARGE = -5
@@ -65,7 +68,7 @@ class DecoderParams:
     warps: int = 0                  # fused launch shape (tuning only): warps per CTA
     ctas_per_sm: int = 0            # persistent mixed launch: resident CTAs per SM (0 = occupancy)
     cosets: int = 0                 # fused launch shape (tuning only): cosets per CTA (1, 2, 4)
-    messages: int = 0               # fused (tuning only): 1 shared memory, 2 workspace slots, 0 = default
+    messages: int = 0               # fused (tuning only): 1 shared memory, 2 workspace slots, 3 register form only, 0 = default
 
     def c(self) -> BbpParams:
         prec = FP64 if self.precision == "fp64" else FP32

@@ -14,7 +14,7 @@ import dataclasses
 
 import torch
 
-from ._lib import FUSED_SHAPES, FUSED_SHAPES_K6, FUSED_SHAPES_WS, BbpError, DecoderParams
+from ._lib import FUSED_SHAPES, FUSED_SHAPES_K6, FUSED_SHAPES_LEAN, FUSED_SHAPES_WS, BbpError, DecoderParams
 from .decoder import decode, decode_mixed
 
 _cache: dict = {}
@@ -36,10 +36,14 @@ def _time(fn, reps=3):
 
 def candidates(prm: DecoderParams):
     """Compiled (warps, cosets, messages) of the fused kernel: messages 1 in
-    shared memory, 2 in workspace slots (always for k = 5, 6)."""
+    shared memory, 2 in workspace slots (always for k = 5, 6), 3 every block
+    update in register form (k = 4 at odd d)."""
     if prm.k > 4:
         return tuple((w, c, 2) for w, c in FUSED_SHAPES_K6[prm.precision])
-    return (tuple((w, c, 1) for w, c in FUSED_SHAPES[prm.precision]) +
+    lean = ()
+    if prm.k == 4 and prm.d % 2 == 1:
+        lean = tuple((w, c, 3) for w, c in FUSED_SHAPES_LEAN[prm.precision])
+    return (lean + tuple((w, c, 1) for w, c in FUSED_SHAPES[prm.precision]) +
             tuple((w, c, 2) for w, c in FUSED_SHAPES_WS[prm.precision]))
 
 

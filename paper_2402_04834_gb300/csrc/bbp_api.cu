@@ -16,12 +16,14 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 // Launch shape of the fused kernel for this request at geometry g; *gm is
 // set when its messages live in the workspace.
-bool shape_of(const bbp_params* p, const Geo& g, int M, int* warps, int* cosets, bool* gm) {
+bool shape_of(const bbp_params* p, const Geo& g, int M, int* warps, int* cosets, bool* gm, bool* lean = nullptr,
+              bool allow_lean = true) {
   *warps = p->launch_warps;
   *cosets = p->launch_cosets;
   int messages = p->launch_messages;
-  const bool ok = bbp::fused_shape(p->precision, g, M, warps, cosets, &messages);
+  const bool ok = bbp::fused_shape(p->precision, g, M, warps, cosets, &messages, allow_lean);
   *gm = messages == 2;
+  if (lean) *lean = messages == 3;
   return ok;
 }
 
@@ -41,7 +43,7 @@ int check_params(const bbp_params* p) {
   if (p->launch_cosets != 0 && p->launch_cosets != 1 && p->launch_cosets != 2 && p->launch_cosets != 4)
     return BBP_EINVAL;
   if (p->launch_ctas_per_sm < 0 || p->launch_ctas_per_sm > 32) return BBP_EINVAL;
-  if (p->launch_messages < 0 || p->launch_messages > 2) return BBP_EINVAL;
+  if (p->launch_messages < 0 || p->launch_messages > 3) return BBP_EINVAL;
   if (p->algorithm == BBP_ALG_FUSED) {
     if (p->k > bbp::kFusedMaxK) return BBP_EUNSUPPORTED;
     const bbp::Geo g = bbp::make_geo(p->d, p->k);
@@ -59,6 +61,7 @@ struct Sizes {
   size_t elem, arena_bytes, io_bytes;
   int warps, cosets;      // fused: launch shape
   bool gm;                // fused: messages in the workspace
+  bool lean;              // fused: every block update in register form
   long long slots;        // fused with gm: message slots in the arena
 };
 
@@ -78,17 +81,24 @@ Sizes sizes_for(const bbp_params* p, int64_t B) {
   s.elem = p->precision == BBP_FP64 ? sizeof(double) : sizeof(float);
   s.slots = 0;
   s.warps = s.cosets = 0;
-  s.gm = false;
+  s.gm = s.lean = false;
   if (p->algorithm != BBP_ALG_FUSED) {
     s.arena_bytes = align256((size_t)B * 4 * (size_t)s.arena_elems * s.elem);
   } else {
     int M1 = 0, ae = 0;
     bbp::count_messages(s.g, 1, &M1, &ae);
     s.arena_bytes = 0;
-    if (shape_of(p, s.g, M1, &s.warps, &s.cosets, &s.gm) && s.gm) {
+    if (shape_of(p, s.g, M1, &s.warps, &s.cosets, &s.gm, &s.lean) && s.gm) {
       s.slots = fused_slots(B, s.cosets);
       s.arena_bytes = align256((size_t)s.slots * fused_slot_bytes(p->k, s.cosets, M1, s.elem));
     }
+    // The default register-form-only shape needs no workspace, but a mixed
+    // batch cannot take it (it may hold any distance): the size returned
+    // also covers the default shape bbp_decode_mixed takes for d_max.
+    int w2 = 0, c2 = 0;
+    bool gm2 = false;
+    if (s.lean && p->launch_messages == 0 && shape_of(p, s.g, M1, &w2, &c2, &gm2, nullptr, false) && gm2)
+      s.arena_bytes = align256((size_t)fused_slots(B, c2) * fused_slot_bytes(p->k, c2, M1, s.elem));
   }
   s.io_bytes = align256((size_t)B * s.m) + align256((size_t)B * 4 * 8) * 2 +
                align256((size_t)B * 4 * 4) * 2 + align256((size_t)B);
@@ -153,8 +163,8 @@ int bbp_decode_batch_ex(const uint8_t* syndromes, int64_t B, const bbp_params* p
   cudaError_t e;
   if (prm->algorithm == BBP_ALG_FUSED) {
     if (s.warps == 0) return BBP_EUNSUPPORTED;
-    e = prm->precision == BBP_FP64 ? bbp::launch_fused_f64(a, s.warps, s.cosets, s.gm, st)
-                                   : bbp::launch_fused_f32(a, s.warps, s.cosets, s.gm, st);
+    e = prm->precision == BBP_FP64 ? bbp::launch_fused_f64(a, s.warps, s.cosets, s.gm, s.lean, st)
+                                   : bbp::launch_fused_f32(a, s.warps, s.cosets, s.gm, s.lean, st);
   } else
     e = prm->precision == BBP_FP64 ? bbp::launch_decode_f64(a, st) : bbp::launch_decode_f32(a, st);
   if (e != cudaSuccess) return BBP_ECUDA;
@@ -202,6 +212,7 @@ int bbp_decode_mixed(const uint8_t* syndromes, const int64_t* offsets, const int
                      int64_t B, int32_t d_max, const bbp_params* prm, double* logp, double* delta, int32_t* iters,
                      int32_t* flags, int8_t* decision, void* workspace, size_t workspace_bytes, void* stream) {
   if (!prm || prm->algorithm != BBP_ALG_FUSED) return BBP_EINVAL;
+  if (prm->launch_messages == 3) return BBP_EUNSUPPORTED;   // a batch may hold any distance
   bbp_params q = *prm;
   q.d = d_max;                                   // validate the largest geometry
   const int rc = check_params(&q);
@@ -225,7 +236,7 @@ int bbp_decode_mixed(const uint8_t* syndromes, const int64_t* offsets, const int
   int Mmax = 0, ae = 0, w = 0, c = 0;
   bool gm = false;
   bbp::count_messages(a.geo, 1, &Mmax, &ae);
-  if (!shape_of(prm, a.geo, Mmax, &w, &c, &gm)) return BBP_EUNSUPPORTED;
+  if (!shape_of(prm, a.geo, Mmax, &w, &c, &gm, nullptr, false)) return BBP_EUNSUPPORTED;
   if (gm) {   // message slots after the counter
     const size_t elem = prm->precision == BBP_FP64 ? sizeof(double) : sizeof(float);
     m.slots = fused_slots(B, c);

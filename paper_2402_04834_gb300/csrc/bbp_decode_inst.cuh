@@ -31,8 +31,8 @@ cudaError_t launch_decode_t(const LaunchArgs& a, cudaStream_t st) {
 }
 
 template <typename T, int K>
-int fused_smem_for(const Geo& g, int M, int warps, int cosets, bool gm = (K > 4)) {
-  return fused_layout<T, K>(g, M, warps, cosets, gm).total;
+int fused_smem_for(const Geo& g, int M, int warps, int cosets, bool gm = (K > 4), bool lean = false) {
+  return fused_layout<T, K>(g, M, warps, cosets, gm, lean).total;
 }
 
 template <typename T>
@@ -70,11 +70,11 @@ cudaError_t persistent_grid(Kern kern, int threads, int smem, int ctas_per_sm, l
 
 // GM: messages in the workspace (a.arena, a.slots slots of G * M * vec
 // scalars), a persistent grid; always for k = 5, 6.
-template <typename T, int NW, int G, int K, bool GM = (K > 4)>
+template <typename T, int NW, int G, int K, bool GM = (K > 4), int LB = 0>
 cudaError_t launch_fused_nw(const LaunchArgs& a, cudaStream_t st) {
   const KArgs<T> k = fused_args<T>(a);
-  const int smem = fused_smem_for<T, K>(a.geo, a.M, NW, G, GM);
-  auto kern = fused_kernel<T, NW, G, K, GM>;
+  const int smem = fused_smem_for<T, K>(a.geo, a.M, NW, G, GM, LB > 0);
+  auto kern = fused_kernel<T, NW, G, K, GM, LB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const long long items = a.B * (4 / G);

@@ -54,22 +54,35 @@ struct FusedWS {   // (sizes for block side K: slot = FusedDim<K>::slot, vec = F
   T* mb;   // side message B in consumption order, vec per coset
 };
 
+// lean: every block update of the kernel runs in register form (k = 4,
+// every block 4 x 4 or one node wide), so the state buffers only hold the
+// outgoing vectors (16 entries per coset).
 template <typename T, int K>
-BBP_HD int fused_ws_bytes(int G) {
-  return align_up((int)sizeof(T) * G * (2 * FusedDim<K>::slot + 16 + 2 * FusedDim<K>::vec), 16);
+BBP_HD int fused_ws_slot(bool lean) {
+  return lean ? FusedDim<K>::vec : FusedDim<K>::slot;
 }
 
 template <typename T, int K>
-__device__ __forceinline__ FusedWS<T> fused_ws_at(unsigned char* base, int G) {
+BBP_HD int fused_ws_bytes(int G, bool lean = false) {
+  return align_up((int)sizeof(T) * G * (2 * fused_ws_slot<T, K>(lean) + 16 + 2 * FusedDim<K>::vec), 16);
+}
+
+template <typename T, int K>
+__device__ __forceinline__ FusedWS<T> fused_ws_at(unsigned char* base, int G, bool lean = false) {
   FusedWS<T> w;
   T* p = reinterpret_cast<T*>(base);
+  const int slot = fused_ws_slot<T, K>(lean);
   w.s0 = p;
-  w.s1 = p + G * FusedDim<K>::slot;
-  w.wn = p + 2 * G * FusedDim<K>::slot;
+  w.s1 = p + G * slot;
+  w.wn = p + 2 * G * slot;
   w.mt = w.wn + 16 * G;
   w.mb = w.mt + FusedDim<K>::vec * G;
   return w;
 }
+
+// Geometries whose every block has a register form at k = 4: the last
+// block row / column is one node wide (W = 4 n + 1, every odd d).
+BBP_HD bool register_form_only(const Geo& g) { return g.k == 4 && g.W % 4 == 1; }
 
 // What a register-form block update needs beyond the messages and the qubit
 // ids, fixed for a syndrome: the incoming message opposite the outgoing
@@ -96,7 +109,7 @@ struct FusedLayout {
 // gm: the messages live in a workspace slot of the CTA (always for k = 5,
 // 6; on request for k <= 4), not in shared memory.
 template <typename T, int K>
-BBP_HD FusedLayout fused_layout(const Geo& g, int M, int nwarps, int G, bool gm = (K > 4)) {
+BBP_HD FusedLayout fused_layout(const Geo& g, int M, int nwarps, int G, bool gm = (K > 4), bool lean = false) {
   FusedLayout L;
   const int m = 2 * g.d * (g.d - 1);
   int o = 0;
@@ -115,7 +128,7 @@ BBP_HD FusedLayout fused_layout(const Geo& g, int M, int nwarps, int G, bool gm 
   L.msgs = o;   // the messages, unless they live in the workspace
   if (!gm) o = align_up(o + (int)sizeof(T) * FusedDim<K>::vec * G * M, 16);
   L.ws = o;
-  L.ws_stride = fused_ws_bytes<T, K>(G);
+  L.ws_stride = fused_ws_bytes<T, K>(G, lean);
   o = align_up(o + nwarps * L.ws_stride, 16);
   L.total = o;
   return L;
@@ -1247,9 +1260,11 @@ __device__ __forceinline__ void quad_sweep(const FusedWS<T>& ws, T pI, T pE, con
 // CTA, 32 warps per SM in FP32 (64 registers a thread) and 16 in FP64; with
 // more cosets per CTA shared memory allows half as many; with k = 6 states
 // (16 KB a buffer in FP32) the shared memory decides.
-template <typename T, int NW, int G, int K> struct FusedMinBlocks {
+// LB > 0: the register-form-only kernel (lean buffers), sized for LB
+// resident CTAs per SM.
+template <typename T, int NW, int G, int K, int LB = 0> struct FusedMinBlocks {
   static constexpr int warps = K > 4 ? NW : (sizeof(T) == 4 ? 32 : 16) / (G > 1 ? 2 : 1);
-  static constexpr int value = warps / NW > 1 ? warps / NW : 1;
+  static constexpr int value = LB > 0 ? LB : (warps / NW > 1 ? warps / NW : 1);
 };
 
 // Cosets c0 .. c0 + G - 1 of one syndrome decoded by the whole CTA: syn_src
@@ -1257,14 +1272,16 @@ template <typename T, int NW, int G, int K> struct FusedMinBlocks {
 // GM: the messages live in gmsgs, this CTA's slot in global memory (the slot
 // is L2-resident and touched only a few times per block sweep); always for
 // k = 5, 6.  Otherwise they live in shared memory and gmsgs is null.
-template <typename T, int NW, int G, int K, bool GM>
+template <typename T, int NW, int G, int K, bool GM, int LB = 0>
 __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const int M, const uint8_t* syn_src,
                                            const long long syn, const int c0, unsigned char* smem, T* gmsgs) {
   const int W = g.W, d = g.d, nb = g.nb, WW = W * W;
   const int m = 2 * d * (d - 1);
   static_assert(K <= 4 || G == 1, "k = 6 states hold one coset per CTA");
   constexpr int VEC = FusedDim<K>::vec;
-  const FusedLayout Lo = fused_layout<T, K>(g, M, NW, G, GM);
+  constexpr bool kLean = LB > 0;
+  static_assert(!kLean || K == 4, "register-form-only kernels are for k = 4");
+  const FusedLayout Lo = fused_layout<T, K>(g, M, NW, G, GM, kLean);
   uint8_t* synd = smem + Lo.synd;
   uint8_t* frames = smem + Lo.frame;
   int16_t* msg_of = reinterpret_cast<int16_t*>(smem + Lo.msg_of);
@@ -1280,7 +1297,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
   const int stride = M * VEC;                                // messages of one coset
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const FusedWS<T> ws = fused_ws_at<T, K>(smem + Lo.ws + warp * Lo.ws_stride, G);
+  const FusedWS<T> ws = fused_ws_at<T, K>(smem + Lo.ws + warp * Lo.ws_stride, G, kLean);
 
   for (int i = tid; i < m; i += NW * 32) synd[i] = syn_src[i];
   __syncthreads();
@@ -1403,11 +1420,13 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
         } else if (shape == kShapeDot) {
           dot_sweep<T, K>(ws, c.pI, c.pE, msgs, stride, cos_of, n, qt, qid + idx, M, lane);
           h = 1;
-        } else {
+        } else if constexpr (!kLean) {
           const int key = meta[idx];
           const Frame f = make_frame(c, key / 4 / nb, (key / 4) % nb, key & 3);
           fused_sweep(ws, c, msgs, stride, cos_of, n, frames, f, (LogAcc<T>*)nullptr, lane);
           h = f.h;
+        } else {   // the host launches this kernel only where every block has a register form
+          if (lane == 0) atomicOr(&misc[8], kFlagCapacity);
         }
         fused_update<T, K>(ws, msgs, stride, cos_of, n, idx, h, eta, one_m_eta, ovl, M, lane);
       }
@@ -1480,8 +1499,10 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
         else if (shape == kShapeCol) col_sweep<T, K>(ws, c.pI, c.pE, msgs, stride, all, G, qt, idw, 1, lane);
         else if (shape == kShapeRow) row_sweep<T, K>(ws, c.pI, c.pE, msgs, stride, all, G, qt, idw, 1, lane);
         else dot_sweep<T, K>(ws, c.pI, c.pE, msgs, stride, all, G, qt, idw, 1, lane);
-      } else {
+      } else if constexpr (!kLean) {
         fused_sweep(ws, c, msgs, stride, all, G, frames, f, ls, lane);
+      } else {
+        if (lane == 0) atomicOr(&misc[8], kFlagCapacity);
       }
       const int right = J + 1 < nb ? msg_index(c, I, J + 1, kDirL) : -1;
       // On the grid border the right side has no message.  The node-by-node
@@ -1593,8 +1614,8 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
 // Messages in shared memory: one CTA per (syndrome, group of G cosets).
 // Messages in the workspace (GM; always for k = 5, 6): a persistent grid,
 // CTA b taking items b, b + gridDim.x, ... with its messages in slot b.
-template <typename T, int NW, int G, int K, bool GM = (K > 4)>
-__global__ void __launch_bounds__(NW * 32, (FusedMinBlocks<T, NW, G, K>::value)) fused_kernel(KArgs<T> a) {
+template <typename T, int NW, int G, int K, bool GM = (K > 4), int LB = 0>
+__global__ void __launch_bounds__(NW * 32, (FusedMinBlocks<T, NW, G, K, LB>::value)) fused_kernel(KArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NG = 4 / G;
   const int m = 2 * a.geo.d * (a.geo.d - 1);
@@ -1602,13 +1623,13 @@ __global__ void __launch_bounds__(NW * 32, (FusedMinBlocks<T, NW, G, K>::value))
     T* gm = a.arena + (long long)blockIdx.x * a.slot_elems;
     for (long long item = blockIdx.x; item < a.n_items; item += gridDim.x) {
       const long long syn = item / NG;
-      fused_item<T, NW, G, K, true>(a, a.geo, a.M, a.synd + syn * m, syn, (int)(item % NG) * G, smem, gm);
+      fused_item<T, NW, G, K, true, LB>(a, a.geo, a.M, a.synd + syn * m, syn, (int)(item % NG) * G, smem, gm);
       __syncthreads();
     }
   } else {
     const long long syn = blockIdx.x / NG;
     const int c0 = (int)(blockIdx.x % NG) * G;
-    fused_item<T, NW, G, K, false>(a, a.geo, a.M, a.synd + syn * m, syn, c0, smem, nullptr);
+    fused_item<T, NW, G, K, false, LB>(a, a.geo, a.M, a.synd + syn * m, syn, c0, smem, nullptr);
   }
 }
 

@@ -4,7 +4,14 @@
 
 namespace bbp {
 
-cudaError_t launch_fused_f32(const LaunchArgs& a, int warps, int cosets, bool gm, cudaStream_t st) {
+cudaError_t launch_fused_f32(const LaunchArgs& a, int warps, int cosets, bool gm, bool lean, cudaStream_t st) {
+  if (lean) {                              // every block update in register form
+    switch (warps * 10 + cosets) {
+      case 84: return launch_fused_nw<float, 8, 4, 4, false, 3>(a, st);
+      case 82: return launch_fused_nw<float, 8, 2, 4, false, 4>(a, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   if (a.geo.k > 4) {                       // block sides 5 and 6
     switch (warps * 10 + cosets) {
       case 21: return launch_fused_nw<float, 2, 1, 6>(a, st);

@@ -4,7 +4,14 @@
 
 namespace bbp {
 
-cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, int cosets, bool gm, cudaStream_t st) {
+cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, int cosets, bool gm, bool lean, cudaStream_t st) {
+  if (lean) {                              // every block update in register form
+    switch (warps * 10 + cosets) {
+      case 42: return launch_fused_nw<double, 4, 2, 4, false, 4>(a, st);
+      case 82: return launch_fused_nw<double, 8, 2, 4, false, 2>(a, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   if (a.geo.k > 4) {
     switch (warps * 10 + cosets) {
       case 21: return launch_fused_nw<double, 2, 1, 6>(a, st);
@@ -47,6 +54,7 @@ namespace {
 struct Shape {
   int warps, cosets;
   bool gm;        // messages in a workspace slot of the CTA instead of shared memory
+  int lean = 0;   // > 0: every block update in register form, sized for this many CTAs per SM
 };
 
 // Compiled shapes in the order the default launch tries them.  Shared-memory
@@ -56,9 +64,11 @@ struct Shape {
 // (GB300, syndromes/s): FP32 (8,4) 85.4k, (8,2) 69.9k, (4,2) 66.3k, (4,4)
 // 56.7k, (16,1) 54.5k, (8,1) 53.2k, (4,1) 51.3k; FP64 (4,2) 16.8k, (8,1)
 // 12.9k, (4,4) 11.9k.
-constexpr Shape kShapesF32[] = {{8, 4, false}, {8, 4, true}, {8, 2, false}, {8, 2, true}, {4, 2, false},
-                                {4, 4, false}, {16, 1, false}, {8, 1, false}, {4, 1, false}};
-constexpr Shape kShapesF64[] = {{4, 2, false}, {4, 2, true}, {8, 2, false}, {8, 1, false}, {4, 4, false}};
+constexpr Shape kShapesF32[] = {{8, 4, false, 3}, {8, 2, false, 4}, {8, 4, false}, {8, 4, true}, {8, 2, false},
+                                {8, 2, true}, {4, 2, false}, {4, 4, false}, {16, 1, false}, {8, 1, false},
+                                {4, 1, false}};
+constexpr Shape kShapesF64[] = {{4, 2, false, 4}, {8, 2, false, 2}, {4, 2, false}, {4, 2, true}, {8, 2, false},
+                                {8, 1, false}, {4, 4, false}};
 
 // Block sides 5 and 6: states of 2^12 entries, one coset per CTA, messages
 // in the workspace; the most warps whose state buffers fit one SM first.
@@ -68,20 +78,21 @@ constexpr Shape kShapesF64K6[] = {{3, 1, true}, {2, 1, true}};
 // Resident CTAs per SM that the register budget of a shape is sized for
 // (the host-side value of FusedMinBlocks).
 int target_blocks(int precision, int k, const Shape& s) {
+  if (s.lean > 0) return s.lean;
   const int warps = k > 4 ? s.warps : (precision == 0 ? 16 : 32) / (s.cosets > 1 ? 2 : 1);
   return warps / s.warps > 1 ? warps / s.warps : 1;
 }
 
 }  // namespace
 
-int fused_smem_bytes(int precision, const Geo& g, int M, int warps, int cosets, bool gm) {
+int fused_smem_bytes(int precision, const Geo& g, int M, int warps, int cosets, bool gm, bool lean) {
   if (g.k > 4)
     return precision == 0 ? fused_smem_for<double, 6>(g, M, warps, cosets) : fused_smem_for<float, 6>(g, M, warps, cosets);
-  return precision == 0 ? fused_smem_for<double, 4>(g, M, warps, cosets, gm)
-                        : fused_smem_for<float, 4>(g, M, warps, cosets, gm);
+  return precision == 0 ? fused_smem_for<double, 4>(g, M, warps, cosets, gm, lean)
+                        : fused_smem_for<float, 4>(g, M, warps, cosets, gm, lean);
 }
 
-bool fused_shape(int precision, const Geo& g, int M, int* warps, int* cosets, int* messages) {
+bool fused_shape(int precision, const Geo& g, int M, int* warps, int* cosets, int* messages, bool allow_lean) {
   const bool k6 = g.k > 4;
   const Shape* sh = k6 ? (precision == 0 ? kShapesF64K6 : kShapesF32K6) : (precision == 0 ? kShapesF64 : kShapesF32);
   const int n = k6 ? (precision == 0 ? (int)(sizeof(kShapesF64K6) / sizeof(Shape)) : (int)(sizeof(kShapesF32K6) / sizeof(Shape)))
@@ -92,13 +103,15 @@ bool fused_shape(int precision, const Geo& g, int M, int* warps, int* cosets, in
     for (int i = 0; i < n; ++i) {
       if (*warps != 0 && sh[i].warps != *warps) continue;
       if (*cosets != 0 && sh[i].cosets != *cosets) continue;
-      if (*messages != 0 && (*messages == 2) != sh[i].gm) continue;
-      const int smem = fused_smem_bytes(precision, g, M, sh[i].warps, sh[i].cosets, sh[i].gm);
+      const int mem = sh[i].lean > 0 ? 3 : (sh[i].gm ? 2 : 1);
+      if (*messages != 0 && *messages != mem) continue;
+      if (sh[i].lean > 0 && (!allow_lean || !register_form_only(g))) continue;
+      const int smem = fused_smem_bytes(precision, g, M, sh[i].warps, sh[i].cosets, sh[i].gm, sh[i].lean > 0);
       if (smem > kMaxSmemBytes) continue;
       if (pass == 0 && kSmemPerSm / (smem + kSmemReservedPerCta) < target_blocks(precision, g.k, sh[i])) continue;
       *warps = sh[i].warps;
       *cosets = sh[i].cosets;
-      *messages = sh[i].gm ? 2 : 1;
+      *messages = mem;
       return true;
     }
   }

@@ -45,12 +45,14 @@ constexpr long long kFusedSlots = 512;
 constexpr int kMaxSmemBytes = 227 * 1024;       // opt-in shared memory of one CTA
 constexpr int kSmemPerSm = 228 * 1024;          // shared memory of one SM
 constexpr int kSmemReservedPerCta = 1024;       // reserved by the runtime per resident CTA
-int fused_smem_bytes(int precision, const Geo& g, int M, int warps, int cosets, bool gm);
+int fused_smem_bytes(int precision, const Geo& g, int M, int warps, int cosets, bool gm, bool lean = false);
 // Launch shape of the fused kernel: *warps / *cosets / *messages (1 shared
-// memory, 2 workspace slots) are requests (0 = any); on success they hold
-// the first compiled shape that matches them, preferring shapes whose
-// shared memory allows the CTAs per SM their registers are sized for.
-bool fused_shape(int precision, const Geo& g, int M, int* warps, int* cosets, int* messages);
+// memory, 2 workspace slots, 3 shared memory with every block update in
+// register form: k = 4 with a one-node-wide last block) are requests
+// (0 = any); on success they hold the first compiled shape that matches
+// them, preferring shapes whose shared memory allows the CTAs per SM their
+// registers are sized for.
+bool fused_shape(int precision, const Geo& g, int M, int* warps, int* cosets, int* messages, bool allow_lean = true);
 
 struct MixedLaunch {
   const int32_t* d_of;
@@ -63,8 +65,8 @@ struct MixedLaunch {
   long long slots = 0;
 };
 
-cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, int cosets, bool gm, cudaStream_t st);
-cudaError_t launch_fused_f32(const LaunchArgs& a, int warps, int cosets, bool gm, cudaStream_t st);
+cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, int cosets, bool gm, bool lean, cudaStream_t st);
+cudaError_t launch_fused_f32(const LaunchArgs& a, int warps, int cosets, bool gm, bool lean, cudaStream_t st);
 cudaError_t launch_fused_mixed_f64(const LaunchArgs& a, const MixedLaunch& mx, int warps, int cosets, bool gm,
                                    cudaStream_t st);
 cudaError_t launch_fused_mixed_f32(const LaunchArgs& a, const MixedLaunch& mx, int warps, int cosets, bool gm,

@@ -51,7 +51,7 @@ def test_workspace_sizes_scale_with_batch(L):
 
 @pytest.mark.parametrize("field,val", [("d", 1), ("k", 0), ("D", 0), ("p", 0.0), ("p", 0.8),
                                        ("eta", 1.0), ("precision", 7), ("max_iter", -1),
-                                       ("launch_warps", 5), ("launch_cosets", 3), ("launch_messages", 3)])
+                                       ("launch_warps", 5), ("launch_cosets", 3), ("launch_messages", 4)])
 def test_invalid_parameters_rejected(L, field, val):
     c = pkg.DecoderParams(d=5, k=3, D=4).c()
     setattr(c, field, val)
@@ -254,3 +254,25 @@ def test_learned_decoder_entry_points_check_arguments_on_the_host(L):
         assert fn(fake, fake, 4, ctypes.byref(cp), 0.1, fake, fake, fake, fake, fake, vp(257), 1 << 40, None) == -1
         assert fn(fake, fake, 4, ctypes.byref(cp), 0.1, fake, fake, fake, fake, fake, fake, 1024, None) == -3
         assert fn(fake, fake, 0, ctypes.byref(cp), 0.1, None, None, None, None, None, None, 0, None) == 0
+
+
+def test_register_form_only_shapes_chosen_where_every_block_has_one(L):
+    # messages = 3 (every block update in register form) exists for k = 4
+    # at odd d (the last block row / column one node wide); at even d the
+    # 3-wide last blocks need the node-by-node path, and bbp_decode_mixed
+    # never takes it (a batch may hold any distance).
+    out = ctypes.c_size_t(0)
+    for d in (5, 11, 13, 21):
+        c = pkg.DecoderParams(d=d, k=4, precision="fp32", algorithm="fused", messages=3).c()
+        assert L.bbp_workspace_bytes(ctypes.byref(c), 10, 0, ctypes.byref(out)) == 0, d
+        assert out.value == 0
+    for d in (6, 12):
+        c = pkg.DecoderParams(d=d, k=4, precision="fp32", algorithm="fused", messages=3).c()
+        assert L.bbp_workspace_bytes(ctypes.byref(c), 10, 0, ctypes.byref(out)) == -4, d
+    c = pkg.DecoderParams(d=11, k=3, precision="fp32", algorithm="fused", messages=3).c()
+    assert L.bbp_workspace_bytes(ctypes.byref(c), 10, 0, ctypes.byref(out)) == -4
+    c = pkg.DecoderParams(d=11, k=4, precision="fp32", algorithm="fused", messages=3).c()
+    vp = ctypes.c_void_p
+    fake = vp(256)
+    assert L.bbp_decode_mixed(fake, fake, fake, None, 4, 11, ctypes.byref(c), fake, fake, fake, fake, fake, fake,
+                              1 << 20, None) == -4

@@ -302,3 +302,29 @@ def test_fused_fp32_against_fp64_at_extreme_noise(dev, p):
     lp = np.sort(np.where(r["fp64"]["flags"] == 0, r["fp64"]["logp"], -np.inf), axis=1)
     sure = (lp[:, -1] - lp[:, -2]) > 1e-2
     assert np.array_equal(r["fp32"]["decision"][sure], r["fp64"]["decision"][sure])
+
+
+@pytest.mark.parametrize("d,precision,warps,cosets", [(11, "fp32", 8, 4), (13, "fp32", 8, 2), (5, "fp32", 8, 4),
+                                                      (11, "fp64", 4, 2), (9, "fp64", 8, 2)])
+def test_register_form_only_kernels_give_the_same_bits(dev, d, precision, warps, cosets):
+    # The register-form-only variants (messages = 3: small per-warp buffers,
+    # more CTAs per SM, no node-by-node code) run the same block updates as
+    # the full kernel: every output bit for bit, early exit, initial and
+    # exported messages included.
+    from paper_2402_04834_gb300 import warmstart as wsm
+    _, _, S = synth.sample_syndromes(1500 + d, 0, 300, d, 0.1)
+    s = torch.from_numpy(S).to(dev)
+    M = wsm.message_count(pkg.DecoderParams(d=d, k=4, algorithm="fused"))
+    init = torch.rand((300 * 4 * M, 16), generator=torch.Generator().manual_seed(d)).to(dev) + 0.01
+    res = {}
+    for mem in (1, 3):
+        prm = pkg.DecoderParams(d=d, k=4, p=0.1, max_iter=15, delta0=1e-4, precision=precision, algorithm="fused",
+                                warps=warps, cosets=cosets, messages=mem)
+        final = torch.empty_like(init)
+        res[mem] = (wsm.decode_ex(s, prm), wsm.decode_ex(s, prm, init_msgs=init, final_msgs=final), final)
+    torch.cuda.synchronize()
+    for i in range(2):
+        for key in ("logp", "delta", "iters", "flags", "decision"):
+            assert torch.equal(res[1][i][key], res[3][i][key]), (i, key)
+    assert torch.equal(res[1][2], res[3][2])
+    assert not torch.any(res[3][0]["flags"] & (1 << 16))     # no block outside the register forms
