@@ -62,9 +62,10 @@ FP64_FMA_PER_SM_CLK = 2
 MLP_FLOPS_PER_ROW = 2 * (256 * 256 + 256 * 256 + 256 * 16)
 # DRAM bytes read + written per unit, from ncu captures (dram__bytes_read.sum
 # + dram__bytes_write.sum) of the current kernels: the fused decode kernel
-# moved 351.7 KB + 356.4 KB for 1024 syndromes (d = 11, 4 cosets per CTA);
-# the network kernel 1.234 GB + 74.6 MB for 1.2 M rows.
-FUSED_DRAM_BYTES_PER_SYNDROME = (351.744e3 + 356.352e3) / 1024
+# moved 335.9 KB + 0 for 1024 syndromes (d = 11, 4 cosets per CTA, the
+# register-form-only variant); the network kernel 1.234 GB + 74.6 MB for
+# 1.2 M rows.
+FUSED_DRAM_BYTES_PER_SYNDROME = (335.872e3 + 0.0) / 1024
 NETWORK_DRAM_BYTES_PER_ROW = (1.234248e9 + 74.605312e6) / 1.2e6
 
 
