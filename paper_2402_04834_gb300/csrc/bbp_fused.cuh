@@ -795,11 +795,18 @@ template <> struct DeltaTerm<float> {
   }
 };
 
+// 1 / sqrt(s), 0 for s = 0: the scale of a unit-norm vector (Remark 3).
+// FP32 takes the hardware reciprocal square root (a scale factor, whose last
+// bit does not matter); FP64 the rounded square root and quotient.
+__device__ __forceinline__ float inv_norm(float s) { return s > 0.f ? rsqrtf(s) : 0.f; }
+__device__ __forceinline__ double inv_norm(double s) { return s > 0.0 ? 1.0 / sqrt(s) : 0.0; }
+__device__ __forceinline__ float2 inv_norm(float2 s) { return make_float2(inv_norm(s.x), inv_norm(s.y)); }
+__device__ __forceinline__ double2 inv_norm(double2 s) { return make_double2(inv_norm(s.x), inv_norm(s.y)); }
+
 // Unit L2 norm (Remark 3) of the vector held by a group of lanes.
 template <typename T>
 __device__ __forceinline__ T group_normalize(T v, int width) {
-  const T nrm = xsqrt(group_sum(v * v, width));
-  return v * (nrm > T(0) ? T(1) / nrm : T(0));
+  return v * inv_norm(group_sum(v * v, width));
 }
 
 // After a sweep: normalise the new messages in ws.s0 (Remark 3), damp them
@@ -975,12 +982,110 @@ __device__ __forceinline__ uint16_t quad_ids(const Frame& f, const uint8_t* fr, 
   return (uint16_t)v;
 }
 
+// Four consecutive scalars at a 16-byte aligned address.
+__device__ __forceinline__ void vcopy4(const float* p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void vcopy4(const double* p, double (&v)[4]) {
+  const double2 q0 = reinterpret_cast<const double2*>(p)[0], q1 = reinterpret_cast<const double2*>(p)[1];
+  v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+}
+__device__ __forceinline__ void vstore4(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void vstore4(double* p, const double (&v)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// Sum over aligned groups of 16 lanes (xor butterfly: every lane of a group
+// gets the same bits).
+// (Adds that are never contracted with the product feeding them, so that
+// every kernel compiled from this gives the same bits.)
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+template <typename T>
+__device__ __forceinline__ T gsum16(T v) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v = radd(v, shx(v, o));
+  return v;
+}
+
+// What the register form needs to finish a message update itself (the
+// steps of fused_update): the messages, the message index, the damping
+// and the Delta terms.
+template <typename T>
+struct QuadUpd {
+  T* msgs;
+  int idx;
+  T eta, one_m_eta;
+  T* ovl;
+  int M;
+};
+
+// The message update (the steps of fused_update: normalisation, Remark 3;
+// damping with the stored message y, Remark 7; normalisation; the Delta
+// term, Remark 4, FP32 as s (2 - s / 2) with s = ||x - y||^2, FP64 as
+// 2 - 2 <x, y>^2) of coset cq's new 16-entry vector, held one entry per
+// lane of a 16-lane group (entry Rn in this lane), from registers.
+template <typename T, int K>
+__device__ __forceinline__ void reg_update16(T out, bool on, int cq, int R, int Rn, int stride, const QuadUpd<T>& up) {
+  T* old = up.msgs + cq * stride + up.idx * FusedDim<K>::vec + Rn;
+  const T y = *old;
+  T x = out * inv_norm(gsum16(out * out));
+  x = fma(up.one_m_eta, x, up.eta * y);
+  x = x * inv_norm(gsum16(x * x));
+  T term;
+  if constexpr (sizeof(T) == 4) {
+    const T t = x - y;
+    const T sq = gsum16(t * t);
+    term = sq * fma(T(-0.5), sq, T(2));
+  } else {
+    const T o = gsum16(x * y);
+    term = fma(T(-2) * o, o, T(2));
+  }
+  if (on) {
+    *old = x;
+    if (R == 0) up.ovl[cq * up.M + up.idx] = term;
+  }
+}
+
+// The same for a 2-entry vector (v0, v1) that every lane of the group
+// holds whole; the writer lane stores it.
+template <typename T, int K>
+__device__ __forceinline__ void reg_update2(T v0, T v1, bool on, int cq, bool writer, int stride,
+                                            const QuadUpd<T>& up) {
+  T* old = up.msgs + cq * stride + up.idx * FusedDim<K>::vec;
+  const T y0 = old[0], y1 = old[1];
+  T inv = inv_norm(radd(v0 * v0, v1 * v1));
+  T x0 = fma(up.one_m_eta, v0 * inv, up.eta * y0), x1 = fma(up.one_m_eta, v1 * inv, up.eta * y1);
+  inv = inv_norm(radd(x0 * x0, x1 * x1));
+  x0 = x0 * inv;
+  x1 = x1 * inv;
+  T term;
+  if constexpr (sizeof(T) == 4) {
+    const T t0 = x0 - y0, t1 = x1 - y1;
+    const T sq = radd(t0 * t0, t1 * t1);
+    term = sq * fma(T(-0.5), sq, T(2));
+  } else {
+    const T o = radd(x0 * y0, x1 * y1);
+    term = fma(T(-2) * o, o, T(2));
+  }
+  __syncwarp();   // every lane has read the stored message
+  if (on && writer) {
+    old[0] = x0;
+    old[1] = x1;
+    up.ovl[cq * up.M + up.idx] = term;
+  }
+}
+
 // Register form of a block of one column of 4 nodes (4 x 1 rotated): the
 // column acts as in quad_sweep's column 0, both side messages have one leg.
-template <typename T, int K>
+template <typename T, int K, bool UPD>
 __device__ __forceinline__ void col_sweep(const FusedWS<T>& ws, T pI, T pE, const T* msgs, int stride,
                                           unsigned cos_of, int n, const QuadTask qt, const uint16_t* qid,
-                                          int qid_stride, int lane) {
+                                          int qid_stride, int lane, const QuadUpd<T> up) {
   constexpr int VEC = FusedDim<K>::vec;
   const bool rev = qt.flags & kQuadRev;
   const int qm_in = qt.masks & 15, qm_up = (qt.masks >> 4) & 15, qm_lo = (qt.masks >> 8) & 15;
@@ -1000,12 +1105,16 @@ __device__ __forceinline__ void col_sweep(const FusedWS<T>& ws, T pI, T pE, cons
     const T bb = qt.lo_idx >= 0 ? mq[qt.lo_idx * VEC + r3] : ((r3 && qm_lo) ? T(0) : T(1));
     T k0, k1, h0, h1, m0, m1;
     qpair(id_lo, r1 ^ r3, pI, pE, k0, k1);
-    const T u = k0 * x + k1 * shx(x, 2);
-    const T up = shx(u, 8);
+    const T u = fma(k1, shx(x, 2), k0 * x);
+    const T uf = shx(u, 8);
     qpair(id_up, r1, pI, pE, h0, h1);          // top leg 0
     qpair(id_up, r1 ^ 1, pI, pE, m0, m1);      // top leg 1
-    const T out = bb * (a0 * (h0 * u + h1 * up) + a1 * (m0 * u + m1 * up));
-    if (on) ws.s0[(slot << 4) | Rn] = out;
+    const T out = bb * fma(a1, fma(m1, uf, m0 * u), a0 * fma(h1, uf, h0 * u));
+    if constexpr (UPD) {
+      reg_update16<T, K>(out, on, cq, R, Rn, stride, up);
+    } else {
+      if (on) ws.s0[(slot << 4) | Rn] = out;
+    }
   }
   __syncwarp();
 }
@@ -1013,10 +1122,10 @@ __device__ __forceinline__ void col_sweep(const FusedWS<T>& ws, T pI, T pE, cons
 // Register form of a block of one row of 4 nodes (1 x 4 rotated): a lane
 // takes one assignment of the four side legs that the two qubits see (the
 // legs at the checks are tied to the row leg), the 16 lanes of a coset sum.
-template <typename T, int K>
+template <typename T, int K, bool UPD>
 __device__ __forceinline__ void row_sweep(const FusedWS<T>& ws, T pI, T pE, const T* msgs, int stride,
                                           unsigned cos_of, int n, const QuadTask qt, const uint16_t* qid,
-                                          int qid_stride, int lane) {
+                                          int qid_stride, int lane, const QuadUpd<T> up) {
   constexpr int VEC = FusedDim<K>::vec;
   const bool chk0 = qt.flags & kQuadRev, srev = qt.flags & kQuadSideRev;
   const int qm_in = qt.masks & 15, qm_up = (qt.masks >> 4) & 15, qm_lo = (qt.masks >> 8) & 15;
@@ -1076,17 +1185,21 @@ __device__ __forceinline__ void row_sweep(const FusedWS<T>& ws, T pI, T pE, cons
       part[0] += shx(part[0], m);
       part[1] += shx(part[1], m);
     }
-    if (on && j < 2) ws.s0[(slot << 1) | j] = j ? part[1] : part[0];
+    if constexpr (UPD) {
+      reg_update2<T, K>(part[0], part[1], on, cq, j == 0, stride, up);
+    } else {
+      if (on && j < 2) ws.s0[(slot << 1) | j] = j ? part[1] : part[0];
+    }
   }
   __syncwarp();
 }
 
 // Register form of a single node (1 x 1): lane (l, a, b, r) of the node's
 // legs, summed over l, a, b.
-template <typename T, int K>
+template <typename T, int K, bool UPD>
 __device__ __forceinline__ void dot_sweep(const FusedWS<T>& ws, T pI, T pE, const T* msgs, int stride,
                                           unsigned cos_of, int n, const QuadTask qt, const uint16_t* qid,
-                                          int qid_stride, int lane) {
+                                          int qid_stride, int lane, const QuadUpd<T> up) {
   constexpr int VEC = FusedDim<K>::vec;
   const bool chk = qt.flags & kQuadRev;
   const int qm_in = qt.masks & 15, qm_up = (qt.masks >> 4) & 15, qm_lo = (qt.masks >> 8) & 15;
@@ -1106,36 +1219,57 @@ __device__ __forceinline__ void dot_sweep(const FusedWS<T>& ws, T pI, T pE, cons
     v += shx(v, 8);
     v += shx(v, 4);
     v += shx(v, 2);
-    if (on && j < 2) ws.s0[(slot << 1) | j] = v;
+    if constexpr (UPD) {
+      const T w = shx(v, 1);                   // the other entry
+      reg_update2<T, K>(r ? w : v, r ? v : w, on, cq, j == 0, stride, up);
+    } else {
+      if (on && j < 2) ws.s0[(slot << 1) | j] = v;
+    }
   }
   __syncwarp();
 }
 
 // The outgoing vectors of a 4 x 4 block (f.h == f.ncols == 4) for the n
 // cosets of cos_of, into ws.s0 (slot s at s << 4), as fused_sweep leaves
-// them.  Columns t = 0..3 hold qubits at chain positions {0, 2} or {1, 3},
+// them; with UPD the message update itself instead (normalisation, Remark
+// 3; damping, Remark 7; the Delta term, Remark 4), from registers.
+// Columns t = 0..3 hold qubits at chain positions {0, 2} or {1, 3},
 // alternating from column to column.  Both node tensors are symmetric in
 // their two chain legs, so reading the chain bottom to top (position
 // s' = 3 - s, the side messages exchanged) turns a block whose column 0
 // starts with a check into one whose column 0 starts with a qubit; only
 // that case is written out.
 // qid[q * qid_stride] holds the qubit ids of coset q (quad_ids).
-template <typename T, int K>
+template <typename T, int K, bool UPD>
 __device__ __forceinline__ void quad_sweep(const FusedWS<T>& ws, T pI, T pE, const T* msgs, int stride,
                                            unsigned cos_of, int n, const QuadTask qt, const uint16_t* qid,
-                                           int qid_stride, int lane) {
+                                           int qid_stride, int lane, const QuadUpd<T> up) {
   constexpr int VEC = FusedDim<K>::vec;
   const bool rev = qt.flags & kQuadRev, srev = qt.flags & kQuadSideRev;
   const int qm_in = qt.masks & 15, qm_up = (qt.masks >> 4) & 15, qm_lo = (qt.masks >> 8) & 15;
   // The side messages in consumption order, the upper one (attached at
-  // s' = 0) in ws.mt and the lower one in ws.mb, slot q at q << 4.  A side
-  // on the grid border has no message: the product vector of its nodes'
-  // missing legs (1 for a check, e_0 for a qubit), bit 3 - t for column t.
-  for (int e = lane; e < (n << 4); e += 32) {
-    const int i = e & 15, jj = srev ? bitrev(i, 4) : i;
-    const T* ms = msgs + slot_coset(cos_of, e >> 4) * stride;
-    ws.mt[e] = qt.up_idx >= 0 ? ms[qt.up_idx * VEC + jj] : ((i & qm_up) ? T(0) : T(1));
-    ws.mb[e] = qt.lo_idx >= 0 ? ms[qt.lo_idx * VEC + jj] : ((i & qm_lo) ? T(0) : T(1));
+  // s' = 0) in ws.mt and the lower one in ws.mb, slot q at q << 4, a lane
+  // per (slot, side, quarter of the vector).  A side on the grid border has
+  // no message: the product vector of its nodes' missing legs (1 for a
+  // check, e_0 for a qubit), bit 3 - t for column t.
+  for (int t = lane; t < (n << 3); t += 32) {
+    const int sl = t >> 3, side = (t >> 2) & 1, i0 = (t & 3) << 2;
+    const int midx = side ? qt.lo_idx : qt.up_idx;
+    const int qm = side ? qm_lo : qm_up;
+    T v[4];
+    if (midx >= 0) {
+      const T* ms = msgs + slot_coset(cos_of, sl) * stride + midx * VEC;
+      if (srev) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = ms[bitrev(i0 + u, 4)];
+      } else {
+        vcopy4(ms + i0, v);
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = ((i0 + u) & qm) ? T(0) : T(1);
+    }
+    vstore4((side ? ws.mb : ws.mt) + (sl << 4) + i0, v);
   }
   __syncwarp();
   const int R = lane & 15, hi = lane >> 4;
@@ -1161,81 +1295,81 @@ __device__ __forceinline__ void quad_sweep(const FusedWS<T>& ws, T pI, T pE, con
     {
       T k0, k1;
       qpair(id[0][1], r1 ^ r3, pI, pE, k0, k1);
-      const T u = k0 * x + k1 * shx(x, 2);
+      const T u = fma(k1, shx(x, 2), k0 * x);
       const T up = shx(u, 8);
 #pragma unroll
       for (int a0 = 0; a0 < 2; ++a0) {
         T h0, h1;
         qpair(id[0][0], a0 ^ r1, pI, pE, h0, h1);
-        S0[a0] = h0 * u + h1 * up;
+        S0[a0] = fma(h1, up, h0 * u);
       }
     }
+    // Column 2's coefficients: the lower qubit (c2k0, c2k1) and the upper
+    // one, g[l0 ^ r0][v ^ r1] for v = 0, 1.
+    T c2k0, c2k1, g00, g01, g10, g11;
+    qpair(id[2][1], r1 ^ r3, pI, pE, c2k0, c2k1);
+    qpair(id[2][0], r1, pI, pE, g00, g10);                   // v = 0
+    qpair(id[2][0], r1 ^ 1, pI, pE, g01, g11);               // v = 1
     // Column 1 (qubits at 1, 3): a1 is tied to r0 by the check at 0; the
-    // lower leg b1 is recorded.  S1[a0][b0][b1].
-    T S1[2][2][2];
-    {
-      T X[2][2];
+    // lower leg b1 is recorded.  S1[b0][b1] for one a0 at a time, folded
+    // into column 2 at once.  Column 2 (qubits at 0, 2) is the data column
+    // of both side messages: the upper leg v is summed against A[a0 a1 v e],
+    // the lower leg w = r3 against B[b0 b1 w f].
+    T h0, h1;
+    qpair(id[1][0], r0 ^ r2, pI, pE, h0, h1);
+    T kk0[2], kk1[2];                                        // [b1], for b0 = 0, 1
 #pragma unroll
-      for (int a0 = 0; a0 < 2; ++a0) {
+    for (int b1 = 0; b1 < 2; ++b1) {
+      T k0, k1;
+      qpair(id[1][1], r2 ^ b1, pI, pE, k0, k1);
+      kk0[b1] = r3 ? k1 : k0;
+      kk1[b1] = r3 ? k0 : k1;
+    }
+    T Y[2][2][2];                                            // [e][b0][b1]
+#pragma unroll
+    for (int a0 = 0; a0 < 2; ++a0) {
+      T S1[2][2];
+      {
         const T o = S0[a0], p = shx(o, 1);
-        X[a0][0] = r3 ? p : o;
-        X[a0][1] = r3 ? o : p;
-      }
-      T h0, h1;
-      qpair(id[1][0], r0 ^ r2, pI, pE, h0, h1);
+        const T X0 = r3 ? p : o, X1 = r3 ? o : p;
 #pragma unroll
-      for (int b1 = 0; b1 < 2; ++b1) {
-        T k0, k1;
-        qpair(id[1][1], r2 ^ b1, pI, pE, k0, k1);
-        const T kk0 = r3 ? k1 : k0, kk1 = r3 ? k0 : k1;       // b0 = 0, 1
-#pragma unroll
-        for (int a0 = 0; a0 < 2; ++a0) {
-          const T y0 = kk0 * X[a0][0], y1 = kk1 * X[a0][1];
-          S1[a0][0][b1] = h0 * y0 + h1 * shx(y0, 4);
-          S1[a0][1][b1] = h0 * y1 + h1 * shx(y1, 4);
+        for (int b1 = 0; b1 < 2; ++b1) {
+          const T y0 = kk0[b1] * X0, y1 = kk1[b1] * X1;
+          S1[0][b1] = fma(h1, shx(y0, 4), h0 * y0);
+          S1[1][b1] = fma(h1, shx(y1, 4), h0 * y1);
         }
       }
-    }
-    // Column 2 (qubits at 0, 2), the data column of both side messages: the
-    // upper leg v is summed against A[a0 a1 v e], the lower leg w = r3
-    // against B[b0 b1 w f].  S2[e][f].
-    T S2[2][2];
-    {
-      T k0, k1;
-      qpair(id[2][1], r1 ^ r3, pI, pE, k0, k1);
-      T g00, g01, g10, g11;                                  // g[l0 ^ r0][v ^ r1] of the upper qubit
-      qpair(id[2][0], r1, pI, pE, g00, g10);                 // v = 0
-      qpair(id[2][0], r1 ^ 1, pI, pE, g01, g11);             // v = 1
-      T Y[2][2][2];                                          // [e][b0][b1]
+      // A0: row bit 0 kept (l0 = r0 = a1), A1: flipped (l0 = a1 = !r0).
+      T m0[4], m1[4];
+      vcopy4(mA + (a0 << 3) + (r0 << 2), m0);
+      vcopy4(mA + (a0 << 3) + ((r0 ^ 1) << 2), m1);
+      const T A00 = fma(m0[2], g01, m0[0] * g00), A01 = fma(m0[3], g01, m0[1] * g00);   // e = 0, 1
+      const T A10 = fma(m1[2], g11, m1[0] * g10), A11 = fma(m1[3], g11, m1[1] * g10);
 #pragma unroll
       for (int b0 = 0; b0 < 2; ++b0)
 #pragma unroll
-        for (int b1 = 0; b1 < 2; ++b1) Y[0][b0][b1] = Y[1][b0][b1] = T(0);
-#pragma unroll
-      for (int a0 = 0; a0 < 2; ++a0) {
-        // A0: row bit 0 kept (l0 = r0 = a1), A1: flipped (l0 = a1 = !r0).
-        const T* m0 = mA + (a0 << 3) + (r0 << 2);
-        const T* m1 = mA + (a0 << 3) + ((r0 ^ 1) << 2);
-        const T A00 = m0[0] * g00 + m0[2] * g01, A01 = m0[1] * g00 + m0[3] * g01;   // e = 0, 1
-        const T A10 = m1[0] * g10 + m1[2] * g11, A11 = m1[1] * g10 + m1[3] * g11;
-#pragma unroll
-        for (int b0 = 0; b0 < 2; ++b0)
-#pragma unroll
-          for (int b1 = 0; b1 < 2; ++b1) {
-            const T s1 = S1[a0][b0][b1];
-            const T u = k0 * s1 + k1 * shx(s1, 2);
-            const T up = shx(u, 8);
-            Y[0][b0][b1] += A00 * u + A10 * up;
-            Y[1][b0][b1] += A01 * u + A11 * up;
+        for (int b1 = 0; b1 < 2; ++b1) {
+          const T s1 = S1[b0][b1];
+          const T u = fma(c2k1, shx(s1, 2), c2k0 * s1);
+          const T up = shx(u, 8);
+          if (a0 == 0) {
+            Y[0][b0][b1] = fma(A00, u, A10 * up);
+            Y[1][b0][b1] = fma(A01, u, A11 * up);
+          } else {
+            Y[0][b0][b1] = fma(A00, u, fma(A10, up, Y[0][b0][b1]));
+            Y[1][b0][b1] = fma(A01, u, fma(A11, up, Y[1][b0][b1]));
           }
-      }
-      const T* mb = mB + (r3 << 1);
+        }
+    }
+    T S2[2][2];
+    {
+      const T* mb = mB + (r3 << 1);                          // B[b0 b1 r3 ff] at mb[4 (2 b0 + b1) + ff]
 #pragma unroll
       for (int e = 0; e < 2; ++e)
 #pragma unroll
         for (int ff = 0; ff < 2; ++ff)
-          S2[e][ff] = mb[ff] * Y[e][0][0] + mb[4 + ff] * Y[e][0][1] + mb[8 + ff] * Y[e][1][0] +
-                      mb[12 + ff] * Y[e][1][1];
+          S2[e][ff] = fma(mb[12 + ff], Y[e][1][1], fma(mb[8 + ff], Y[e][1][0], fma(mb[4 + ff], Y[e][0][1],
+                                                                                mb[ff] * Y[e][0][0])));
     }
     // Column 3 (qubits at 1, 3): the upper leg e is tied to r0, the lower
     // leg f closes against B's expected value.
@@ -1246,12 +1380,16 @@ __device__ __forceinline__ void quad_sweep(const FusedWS<T>& ws, T pI, T pE, con
       T k0, k1, m0, m1;
       qpair(id[3][1], r2, pI, pE, k0, k1);
       qpair(id[3][1], r2 ^ 1, pI, pE, m0, m1);
-      const T uu = k0 * z0 + k1 * p0 + m0 * z1 + m1 * p1;
-      T h0, h1;
-      qpair(id[3][0], r0 ^ r2, pI, pE, h0, h1);
-      out = h0 * uu + h1 * shx(uu, 4);
+      const T uu = fma(m1, p1, fma(m0, z1, fma(k1, p0, k0 * z0)));
+      T g0, g1;
+      qpair(id[3][0], r0 ^ r2, pI, pE, g0, g1);
+      out = fma(g1, shx(uu, 4), g0 * uu);
     }
-    if (on) ws.s0[(slot << 4) | Rn] = out;
+    if constexpr (UPD) {
+      reg_update16<T, K>(out, on, cq, R, Rn, stride, up);
+    } else {
+      if (on) ws.s0[(slot << 4) | Rn] = out;
+    }
   }
   __syncwarp();
 }
@@ -1291,7 +1429,9 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
   QuadTask* qdesc = reinterpret_cast<QuadTask*>(smem + Lo.qdesc);
   uint16_t* qid = reinterpret_cast<uint16_t*>(smem + Lo.qid);
   double* rlog = reinterpret_cast<double*>(smem + Lo.rlog);
-  int* misc = reinterpret_cast<int*>(smem + Lo.misc);      // [0] counter, [2..4] list sizes, [8 + q] flags
+  // misc: [0] counter, [2..4] list sizes, [8 + q] flags, [12 + q] iterations
+  // done; dsh[q]: the sum of coset q's Delta terms at its last iteration.
+  int* misc = reinterpret_cast<int*>(smem + Lo.misc);
   double* dsh = reinterpret_cast<double*>(smem + Lo.misc + 64);
   T* msgs = GM ? gmsgs : reinterpret_cast<T*>(smem + Lo.msgs);
   const int stride = M * VEC;                                // messages of one coset
@@ -1335,7 +1475,11 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
           }
         }
     misc[0] = 0; misc[2] = n0; misc[3] = n1;
-    for (int q = 0; q < 4; ++q) misc[8 + q] = 0;
+    for (int q = 0; q < 4; ++q) {
+      misc[8 + q] = 0;
+      misc[12 + q] = 0;
+      dsh[q] = 0.0;
+    }
   }
   __syncthreads();
 
@@ -1383,10 +1527,6 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
   const T eta = (T)a.eta, one_m_eta = T(1) - eta;
   const double d0sq = (a.delta0 * M) * (a.delta0 * M);
   unsigned act = (1u << G) - 1;                      // cosets still iterating
-  double delta[G];
-  int it_done[G];
-#pragma unroll
-  for (int q = 0; q < G; ++q) { delta[q] = 0.0; it_done[q] = 0; }
   for (int it = 1; it <= a.max_iter && M > 0 && act; ++it) {
     int n = 0;
     unsigned cos_of = 0;
@@ -1403,32 +1543,30 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
         item = __shfl_sync(kFull, item, 0);
         if (item >= nwork) break;
         const int idx = lst[item];
-        int h = 4;
         int shape = kShapeNone;
         QuadTask qt;
         if (quads) {
           qt = qdesc[idx];
           shape = qt.shape;
         }
+        // Register forms finish the update themselves.
+        const QuadUpd<T> up{msgs, idx, eta, one_m_eta, ovl, M};
         if (shape == kShapeQuad) {
-          quad_sweep<T, K>(ws, c.pI, c.pE, msgs, stride, cos_of, n, qt, qid + idx, M, lane);
+          quad_sweep<T, K, true>(ws, c.pI, c.pE, msgs, stride, cos_of, n, qt, qid + idx, M, lane, up);
         } else if (shape == kShapeCol) {
-          col_sweep<T, K>(ws, c.pI, c.pE, msgs, stride, cos_of, n, qt, qid + idx, M, lane);
+          col_sweep<T, K, true>(ws, c.pI, c.pE, msgs, stride, cos_of, n, qt, qid + idx, M, lane, up);
         } else if (shape == kShapeRow) {
-          row_sweep<T, K>(ws, c.pI, c.pE, msgs, stride, cos_of, n, qt, qid + idx, M, lane);
-          h = 1;
+          row_sweep<T, K, true>(ws, c.pI, c.pE, msgs, stride, cos_of, n, qt, qid + idx, M, lane, up);
         } else if (shape == kShapeDot) {
-          dot_sweep<T, K>(ws, c.pI, c.pE, msgs, stride, cos_of, n, qt, qid + idx, M, lane);
-          h = 1;
+          dot_sweep<T, K, true>(ws, c.pI, c.pE, msgs, stride, cos_of, n, qt, qid + idx, M, lane, up);
         } else if constexpr (!kLean) {
           const int key = meta[idx];
           const Frame f = make_frame(c, key / 4 / nb, (key / 4) % nb, key & 3);
           fused_sweep(ws, c, msgs, stride, cos_of, n, frames, f, (LogAcc<T>*)nullptr, lane);
-          h = f.h;
+          fused_update<T, K>(ws, msgs, stride, cos_of, n, idx, f.h, eta, one_m_eta, ovl, M, lane);
         } else {   // the host launches this kernel only where every block has a register form
           if (lane == 0) atomicOr(&misc[8], kFlagCapacity);
         }
-        fused_update<T, K>(ws, msgs, stride, cos_of, n, idx, h, eta, one_m_eta, ovl, M, lane);
       }
       __syncthreads();
       if (tid == 0) misc[0] = 0;
@@ -1446,13 +1584,10 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
 #pragma unroll
     for (int q = 0; q < G; ++q)
       if ((act >> q) & 1u) {
-        delta[q] = dsh[q];
-        it_done[q] = it;
-        if (delta[q] < d0sq) act &= ~(1u << q);
+        if (tid == 0) misc[12 + q] = it;
+        if (dsh[q] < d0sq) act &= ~(1u << q);
       }
   }
-#pragma unroll
-  for (int q = 0; q < G; ++q) delta[q] = M > 0 ? sqrt(delta[q]) / M : 0.0;
 
   if (a.final_msgs)
     for (int e = tid; e < G * stride; e += NW * 32) {
@@ -1495,10 +1630,14 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
         uint16_t* idw = reinterpret_cast<uint16_t*>(ws.wn);
         if (lane < G) idw[lane] = quad_ids(f, frames + lane * WW, W, qt);
         __syncwarp();
-        if (shape == kShapeQuad) quad_sweep<T, K>(ws, c.pI, c.pE, msgs, stride, all, G, qt, idw, 1, lane);
-        else if (shape == kShapeCol) col_sweep<T, K>(ws, c.pI, c.pE, msgs, stride, all, G, qt, idw, 1, lane);
-        else if (shape == kShapeRow) row_sweep<T, K>(ws, c.pI, c.pE, msgs, stride, all, G, qt, idw, 1, lane);
-        else dot_sweep<T, K>(ws, c.pI, c.pE, msgs, stride, all, G, qt, idw, 1, lane);
+        if (shape == kShapeQuad)
+          quad_sweep<T, K, false>(ws, c.pI, c.pE, msgs, stride, all, G, qt, idw, 1, lane, QuadUpd<T>{});
+        else if (shape == kShapeCol)
+          col_sweep<T, K, false>(ws, c.pI, c.pE, msgs, stride, all, G, qt, idw, 1, lane, QuadUpd<T>{});
+        else if (shape == kShapeRow)
+          row_sweep<T, K, false>(ws, c.pI, c.pE, msgs, stride, all, G, qt, idw, 1, lane, QuadUpd<T>{});
+        else
+          dot_sweep<T, K, false>(ws, c.pI, c.pE, msgs, stride, all, G, qt, idw, 1, lane, QuadUpd<T>{});
       } else if constexpr (!kLean) {
         fused_sweep(ws, c, msgs, stride, all, G, frames, f, ls, lane);
       } else {
@@ -1593,11 +1732,8 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
       for (int i = lane; i < per; i += 32) acc += rlog[warp * per + i];
       acc = warp_sum(acc);
     }
-    double dq = 0.0;
-    int iq = 0;
-#pragma unroll
-    for (int q = 0; q < G; ++q)
-      if (q == warp) { dq = delta[q]; iq = it_done[q]; }
+    const double dq = M > 0 ? sqrt(dsh[warp]) / M : 0.0;
+    const int iq = misc[12 + warp];
     if (lane == 0) {
       int fl = misc[8 + warp];
       if (!isfinite(acc)) fl |= kFlagNonfinite;
