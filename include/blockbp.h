@@ -100,9 +100,11 @@ extern "C" {
  *             sized for, else the first that fits; compiled (warps, cosets):
  *             FP32 (8,4) (8,2) (4,2) (4,4) (16,1) (8,1) (4,1), of which (8,4)
  *             and (8,2) also with workspace messages and in register-form-only
- *             variants (3 and 4 CTAs per SM); FP64 (4,2) (8,2) (8,1) (4,4),
- *             (4,2) also with workspace messages, (4,2) and (8,2) in
- *             register-form-only variants (4 and 2 CTAs per SM); for k = 5, 6
+ *             variants ((8,4) sized for 4 and for 3 CTAs per SM, the first
+ *             whose shared memory allows it taken; (8,2) for 4); FP64 (4,2)
+ *             (8,2) (8,1) (4,4), (4,2) also with workspace messages, (4,2) and
+ *             (8,2) in register-form-only variants (4 and 2 CTAs per SM); for
+ *             k = 5, 6
  *             (workspace messages only): FP32 (6,1) (4,1) (2,1), FP64 (3,1)
  *             (2,1); other requests give BBP_EUNSUPPORTED.
  *   algorithm BBP_ALG_MPS, or BBP_ALG_FUSED: every k x k block fused into one

@@ -16,14 +16,15 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 // Launch shape of the fused kernel for this request at geometry g; *gm is
 // set when its messages live in the workspace.
-bool shape_of(const bbp_params* p, const Geo& g, int M, int* warps, int* cosets, bool* gm, bool* lean = nullptr,
+// *lean: 0, or the CTAs per SM the register-form-only kernel is sized for.
+bool shape_of(const bbp_params* p, const Geo& g, int M, int* warps, int* cosets, bool* gm, int* lean = nullptr,
               bool allow_lean = true) {
   *warps = p->launch_warps;
   *cosets = p->launch_cosets;
-  int messages = p->launch_messages;
-  const bool ok = bbp::fused_shape(p->precision, g, M, warps, cosets, &messages, allow_lean);
+  int messages = p->launch_messages, lb = 0;
+  const bool ok = bbp::fused_shape(p->precision, g, M, warps, cosets, &messages, allow_lean, &lb);
   *gm = messages == 2;
-  if (lean) *lean = messages == 3;
+  if (lean) *lean = messages == 3 ? lb : 0;
   return ok;
 }
 
@@ -61,7 +62,7 @@ struct Sizes {
   size_t elem, arena_bytes, io_bytes;
   int warps, cosets;      // fused: launch shape
   bool gm;                // fused: messages in the workspace
-  bool lean;              // fused: every block update in register form
+  int lean;               // fused: every block update in register form (CTAs per SM it is sized for), else 0
   long long slots;        // fused with gm: message slots in the arena
 };
 
@@ -81,7 +82,8 @@ Sizes sizes_for(const bbp_params* p, int64_t B) {
   s.elem = p->precision == BBP_FP64 ? sizeof(double) : sizeof(float);
   s.slots = 0;
   s.warps = s.cosets = 0;
-  s.gm = s.lean = false;
+  s.gm = false;
+  s.lean = 0;
   if (p->algorithm != BBP_ALG_FUSED) {
     s.arena_bytes = align256((size_t)B * 4 * (size_t)s.arena_elems * s.elem);
   } else {

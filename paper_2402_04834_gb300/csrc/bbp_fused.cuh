@@ -1429,8 +1429,9 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
   QuadTask* qdesc = reinterpret_cast<QuadTask*>(smem + Lo.qdesc);
   uint16_t* qid = reinterpret_cast<uint16_t*>(smem + Lo.qid);
   double* rlog = reinterpret_cast<double*>(smem + Lo.rlog);
-  // misc: [0] counter, [2..4] list sizes, [8 + q] flags, [12 + q] iterations
-  // done; dsh[q]: the sum of coset q's Delta terms at its last iteration.
+  // misc: [0] counter, [1] cosets converged (bit q), [2..4] list sizes,
+  // [8 + q] flags, [12 + q] iterations done; dsh[q]: the sum of coset q's
+  // Delta terms at its last iteration.
   int* misc = reinterpret_cast<int*>(smem + Lo.misc);
   double* dsh = reinterpret_cast<double*>(smem + Lo.misc + 64);
   T* msgs = GM ? gmsgs : reinterpret_cast<T*>(smem + Lo.msgs);
@@ -1474,7 +1475,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
             msg_of[key] = -1;
           }
         }
-    misc[0] = 0; misc[2] = n0; misc[3] = n1;
+    misc[0] = 0; misc[1] = 0; misc[2] = n0; misc[3] = n1;
     for (int q = 0; q < 4; ++q) {
       misc[8 + q] = 0;
       misc[12 + q] = 0;
@@ -1518,7 +1519,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
       if (!uniform && lane < VEC) x[lane] = v * (T(1) / nrm);
     }
     if (uniform) {                                   // no (or an unusable) proposal
-      const T u = (T)rsqrt((double)(1 << w));
+      const T u = T(1) / xsqrt(T(1 << w));        // in working precision: no FP64 per message
       for (int i = lane; i < VEC; i += 32) x[i] = i < (1 << w) ? u : T(0);
     }
   }
@@ -1572,21 +1573,23 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
       if (tid == 0) misc[0] = 0;
       __syncthreads();
     }
-    if (warp < G && ((act >> warp) & 1u)) {          // Remark 4, one warp per coset
-      double acc = 0.0;
-      for (int i = lane; i < M; i += 32) acc += (double)ovl[warp * M + i];
+    // Delta = sqrt(sum) / M < delta0 (Remark 4), compared as sum <
+    // (delta0 M)^2 by the coset's warp, which sets the coset's bit in
+    // misc[1]; the square root is taken once, after the loop.  The sum runs
+    // in working precision (FP32 terms, each already rounded to FP32).
+    if (warp < G && ((act >> warp) & 1u)) {
+      T acc = T(0);
+      for (int i = lane; i < M; i += 32) acc += ovl[warp * M + i];
       acc = warp_sum(acc);
-      if (lane == 0) dsh[warp] = fmax(acc, 0.0);
+      if (lane == 0) {
+        const double sum = acc > T(0) ? (double)acc : 0.0;
+        dsh[warp] = sum;
+        misc[12 + warp] = it;
+        if (sum < d0sq) atomicOr(&misc[1], 1 << warp);
+      }
     }
     __syncthreads();
-    // Delta = sqrt(sum) / M < delta0 compared as sum < (delta0 M)^2; the
-    // square root is taken once, after the loop.
-#pragma unroll
-    for (int q = 0; q < G; ++q)
-      if ((act >> q) & 1u) {
-        if (tid == 0) misc[12 + q] = it;
-        if (dsh[q] < d0sq) act &= ~(1u << q);
-      }
+    act &= ~(unsigned)misc[1];
   }
 
   if (a.final_msgs)

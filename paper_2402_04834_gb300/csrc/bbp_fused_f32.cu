@@ -4,11 +4,12 @@
 
 namespace bbp {
 
-cudaError_t launch_fused_f32(const LaunchArgs& a, int warps, int cosets, bool gm, bool lean, cudaStream_t st) {
-  if (lean) {                              // every block update in register form
-    switch (warps * 10 + cosets) {
-      case 84: return launch_fused_nw<float, 8, 4, 4, false, 3>(a, st);
-      case 82: return launch_fused_nw<float, 8, 2, 4, false, 4>(a, st);
+cudaError_t launch_fused_f32(const LaunchArgs& a, int warps, int cosets, bool gm, int lean, cudaStream_t st) {
+  if (lean > 0) {                          // every block update in register form, sized for `lean` CTAs per SM
+    switch (warps * 100 + cosets * 10 + lean) {
+      case 844: return launch_fused_nw<float, 8, 4, 4, false, 4>(a, st);
+      case 843: return launch_fused_nw<float, 8, 4, 4, false, 3>(a, st);
+      case 824: return launch_fused_nw<float, 8, 2, 4, false, 4>(a, st);
       default: return cudaErrorInvalidValue;
     }
   }

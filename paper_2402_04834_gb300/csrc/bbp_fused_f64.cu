@@ -4,11 +4,11 @@
 
 namespace bbp {
 
-cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, int cosets, bool gm, bool lean, cudaStream_t st) {
-  if (lean) {                              // every block update in register form
-    switch (warps * 10 + cosets) {
-      case 42: return launch_fused_nw<double, 4, 2, 4, false, 4>(a, st);
-      case 82: return launch_fused_nw<double, 8, 2, 4, false, 2>(a, st);
+cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, int cosets, bool gm, int lean, cudaStream_t st) {
+  if (lean > 0) {                          // every block update in register form, sized for `lean` CTAs per SM
+    switch (warps * 100 + cosets * 10 + lean) {
+      case 424: return launch_fused_nw<double, 4, 2, 4, false, 4>(a, st);
+      case 822: return launch_fused_nw<double, 8, 2, 4, false, 2>(a, st);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -57,14 +57,16 @@ struct Shape {
   int lean = 0;   // > 0: every block update in register form, sized for this many CTAs per SM
 };
 
-// Compiled shapes in the order the default launch tries them.  Shared-memory
-// messages first where they leave room for the CTAs per SM the register
-// budget is sized for (FusedMinBlocks), then the same shape with its
-// messages in the workspace.  Speeds on the d = 11, p = 0.10 workload
-// (GB300, syndromes/s): FP32 (8,4) 85.4k, (8,2) 69.9k, (4,2) 66.3k, (4,4)
-// 56.7k, (16,1) 54.5k, (8,1) 53.2k, (4,1) 51.3k; FP64 (4,2) 16.8k, (8,1)
-// 12.9k, (4,4) 11.9k.
-constexpr Shape kShapesF32[] = {{8, 4, false, 3}, {8, 2, false, 4}, {8, 4, false}, {8, 4, true}, {8, 2, false},
+// Compiled shapes in the order the default launch tries them: the
+// register-form-only kernels where the geometry allows them, then
+// shared-memory messages where they leave room for the CTAs per SM the
+// register budget is sized for (FusedMinBlocks), then the same shape with
+// its messages in the workspace.  Measured on the d = 11, p = 0.10 workload
+// (GB300, ms per 10^4 syndromes): FP32 register form only (8,4) 16.3 at 3
+// CTAs per SM, (8,2) 18.2; full kernels (8,4) 20.6, (4,2) 30.1, (8,2) 32.7,
+// (4,4) 42.7, (4,1) 44.8, (8,1) 46.7, (16,1) 52.2; FP64 about 150 per 4096
+// syndromes for (4,2) and (8,2), 176 for (4,4).
+constexpr Shape kShapesF32[] = {{8, 4, false, 4}, {8, 4, false, 3}, {8, 2, false, 4}, {8, 4, false}, {8, 4, true}, {8, 2, false},
                                 {8, 2, true}, {4, 2, false}, {4, 4, false}, {16, 1, false}, {8, 1, false},
                                 {4, 1, false}};
 constexpr Shape kShapesF64[] = {{4, 2, false, 4}, {8, 2, false, 2}, {4, 2, false}, {4, 2, true}, {8, 2, false},
@@ -92,7 +94,8 @@ int fused_smem_bytes(int precision, const Geo& g, int M, int warps, int cosets, 
                         : fused_smem_for<float, 4>(g, M, warps, cosets, gm, lean);
 }
 
-bool fused_shape(int precision, const Geo& g, int M, int* warps, int* cosets, int* messages, bool allow_lean) {
+bool fused_shape(int precision, const Geo& g, int M, int* warps, int* cosets, int* messages, bool allow_lean,
+                 int* lean_blocks) {
   const bool k6 = g.k > 4;
   const Shape* sh = k6 ? (precision == 0 ? kShapesF64K6 : kShapesF32K6) : (precision == 0 ? kShapesF64 : kShapesF32);
   const int n = k6 ? (precision == 0 ? (int)(sizeof(kShapesF64K6) / sizeof(Shape)) : (int)(sizeof(kShapesF32K6) / sizeof(Shape)))
@@ -112,6 +115,7 @@ bool fused_shape(int precision, const Geo& g, int M, int* warps, int* cosets, in
       *warps = sh[i].warps;
       *cosets = sh[i].cosets;
       *messages = mem;
+      if (lean_blocks) *lean_blocks = sh[i].lean;
       return true;
     }
   }

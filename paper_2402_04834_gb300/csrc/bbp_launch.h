@@ -51,8 +51,10 @@ int fused_smem_bytes(int precision, const Geo& g, int M, int warps, int cosets, 
 // register form: k = 4 with a one-node-wide last block) are requests
 // (0 = any); on success they hold the first compiled shape that matches
 // them, preferring shapes whose shared memory allows the CTAs per SM their
-// registers are sized for.
-bool fused_shape(int precision, const Geo& g, int M, int* warps, int* cosets, int* messages, bool allow_lean = true);
+// registers are sized for; *lean_blocks (if given) the CTAs per SM a
+// register-form-only kernel is compiled for (0 for the others).
+bool fused_shape(int precision, const Geo& g, int M, int* warps, int* cosets, int* messages, bool allow_lean = true,
+                 int* lean_blocks = nullptr);
 
 struct MixedLaunch {
   const int32_t* d_of;
@@ -65,8 +67,9 @@ struct MixedLaunch {
   long long slots = 0;
 };
 
-cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, int cosets, bool gm, bool lean, cudaStream_t st);
-cudaError_t launch_fused_f32(const LaunchArgs& a, int warps, int cosets, bool gm, bool lean, cudaStream_t st);
+// lean: 0, or the CTAs per SM of the register-form-only kernel to launch.
+cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, int cosets, bool gm, int lean, cudaStream_t st);
+cudaError_t launch_fused_f32(const LaunchArgs& a, int warps, int cosets, bool gm, int lean, cudaStream_t st);
 cudaError_t launch_fused_mixed_f64(const LaunchArgs& a, const MixedLaunch& mx, int warps, int cosets, bool gm,
                                    cudaStream_t st);
 cudaError_t launch_fused_mixed_f32(const LaunchArgs& a, const MixedLaunch& mx, int warps, int cosets, bool gm,

@@ -304,13 +304,14 @@ def test_fused_fp32_against_fp64_at_extreme_noise(dev, p):
     assert np.array_equal(r["fp32"]["decision"][sure], r["fp64"]["decision"][sure])
 
 
-@pytest.mark.parametrize("d,precision,warps,cosets", [(11, "fp32", 8, 4), (13, "fp32", 8, 2), (5, "fp32", 8, 4),
-                                                      (11, "fp64", 4, 2), (9, "fp64", 8, 2)])
+@pytest.mark.parametrize("d,precision,warps,cosets", [(11, "fp32", 8, 4), (13, "fp32", 8, 4), (13, "fp32", 8, 2),
+                                                      (5, "fp32", 8, 4), (11, "fp64", 4, 2), (9, "fp64", 8, 2)])
 def test_register_form_only_kernels_give_the_same_bits(dev, d, precision, warps, cosets):
     # The register-form-only variants (messages = 3: small per-warp buffers,
     # more CTAs per SM, no node-by-node code) run the same block updates as
     # the full kernel: every output bit for bit, early exit, initial and
-    # exported messages included.
+    # exported messages included.  FP32 (8, 4) takes its 4-CTA variant at
+    # d = 5 and 11 and its 3-CTA variant at d = 13 (shared memory).
     from paper_2402_04834_gb300 import warmstart as wsm
     _, _, S = synth.sample_syndromes(1500 + d, 0, 300, d, 0.1)
     s = torch.from_numpy(S).to(dev)
