@@ -5,11 +5,11 @@ planar surface code under depolarizing noise p = 0.10, 10^4 seeded synthetic
 syndromes per GPU, blockBP with 4x4-node blocks, max-iter 20, delta0 = 1e-4,
 delta1 = 1e-2, eta = 0.1 (Sec. IV parameters), D = 8 for the MPS form.
 The headline decoder is the learned + mixed-precision one: features of
-the distinct message rows, the warm-start network on the tensor cores
-(trained first, untimed, on converged messages of seeded decodes) and the
-expansion of its proposals to every coset, then the fused-block form of
-Remark 9 (the form the paper ran for k = 4) in FP32 with FP64 Delta sums
-and read-out, started from the proposals.  Timed beside it on the same
+the distinct message rows (as bits), the warm-start network on the tensor
+cores (trained first, untimed, on converged messages of seeded decodes)
+and the expansion of its proposals to every coset, then the fused-block
+form of Remark 9 (the form the paper ran for k = 4) in FP32 with an FP64
+read-out, started from the proposals.  Timed beside it on the same
 batch: the same decoder from the uniform start (cold), the plain FP64
 blockBP in the fused form (the like-for-like denominator of the metric:
 same algorithm, same results), the FP64 MPS form (a change of algorithm
@@ -62,11 +62,11 @@ FP64_FMA_PER_SM_CLK = 2
 MLP_FLOPS_PER_ROW = 2 * (256 * 256 + 256 * 256 + 256 * 16)
 # DRAM bytes read + written per unit, from ncu captures (dram__bytes_read.sum
 # + dram__bytes_write.sum) of the current kernels: the fused decode kernel
-# moved 335.9 KB + 0 for 1024 syndromes (d = 11, 4 cosets per CTA, the
-# register-form-only variant); the network kernel 1.234 GB + 74.6 MB for
-# 1.2 M rows.
-FUSED_DRAM_BYTES_PER_SYNDROME = (335.872e3 + 0.0) / 1024
-NETWORK_DRAM_BYTES_PER_ROW = (1.234248e9 + 74.605312e6) / 1.2e6
+# moved 326.9 KB + 0 for 1024 syndromes (d = 11, 4 cosets per CTA, the
+# register-form-only variant sized for 4 CTAs per SM).  The network kernel
+# reading feature bits has no capture yet (None: traffic reported null).
+FUSED_DRAM_BYTES_PER_SYNDROME = (326.912e3 + 0.0) / 1024
+NETWORK_DRAM_BYTES_PER_ROW = None
 
 
 def oracle_one(args):
@@ -278,8 +278,10 @@ def mixed_batch_leg(args, dev, pkg):
     packed, offsets, d_of = pack_mixed(shots, device=dev)
     prm = pkg.DecoderParams(d=0, k=K_BLOCK, p=P_NOISE, max_iter=MAX_ITER, eta=ETA, delta0=DELTA0, delta1=DELTA1,
                             precision="fp32", algorithm="fused")
+    # Every distance here is odd, so the register-form-only kernels are candidates too.
+    lean = ((8, 4, 3), (8, 2, 3)) if all(d % 2 == 1 for d in MIXED_DISTANCES) else ()
     prm, table = autotune.tune_mixed(packed, offsets, d_of, prm,
-                                     shapes=((8, 4, 1), (8, 4, 2), (8, 2, 1), (8, 2, 2), (4, 2, 1), (4, 4, 1)),
+                                     shapes=lean + ((8, 4, 1), (8, 4, 2), (8, 2, 1), (8, 2, 2), (4, 2, 1), (4, 4, 1)),
                                      ctas=(0, 1, 2))
     order = torch.argsort(d_of, descending=True, stable=True).to(torch.int32)
     d_max = int(max(MIXED_DISTANCES))
@@ -334,7 +336,8 @@ def mixed_batch_leg(args, dev, pkg):
     return {"value": mixed_val, "unit": "syndromes/s", "batch": n, "distances": list(MIXED_DISTANCES),
             "counts": [int(c) for c in counts], "p": P_NOISE, "precision": "fp32", "algorithm": "fused",
             "launch": "one persistent launch, largest distance first, replayed from a CUDA graph",
-            "shape": {"warps": prm.warps, "cosets": prm.cosets, "messages": "shared" if prm.messages == 1 else "workspace",
+            "shape": {"warps": prm.warps, "cosets": prm.cosets,
+                      "messages": {1: "shared", 2: "workspace", 3: "shared, register form only"}[prm.messages],
                       "ctas_per_sm": prm.ctas_per_sm},
             "autotune_candidates": len(table),
             "mean_iters": float(out["iters"].double().mean().item()),
@@ -446,10 +449,10 @@ def ours(args):
                 ev_dec.append((a, b))
             return out
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
-        feats, lens = wsm.features_rows(S_dev, prm)
+        bits, lens = wsm.feature_bits_rows(S_dev, prm)
         if record:
             evs[0].record(stream)
-        init = wsm.expand_rows(net.infer(feats, lens, alpha=wsm.DEFAULT_ALPHA), B, prm)
+        init = wsm.expand_rows(net.infer_bits(bits, lens, prm.p, alpha=wsm.DEFAULT_ALPHA), B, prm)
         if record:
             evs[1].record(stream)
             evs[2].record(stream)
@@ -626,8 +629,10 @@ def ours(args):
             pass
         mf = rows * MLP_FLOPS_PER_ROW / (mlp_ms / 1e3) / 1e12
         roof_mlp = {"bound": "tensor", "achieved": mf, "peak": bf16_peak, "unit": "TFLOP/s", "frac": mf / bf16_peak,
-                    "traffic": NETWORK_DRAM_BYTES_PER_ROW * rows,
-                    "traffic_source": "ncu DRAM bytes of a 1.2 M-row launch, scaled to the step's rows",
+                    "traffic": None if NETWORK_DRAM_BYTES_PER_ROW is None else NETWORK_DRAM_BYTES_PER_ROW * rows,
+                    "traffic_source": ("ncu DRAM bytes of a 1.2 M-row launch, scaled to the step's rows"
+                                       if NETWORK_DRAM_BYTES_PER_ROW is not None else
+                                       "no capture of the current kernel"),
                     "kernel": "mlp_tc_kernel (+ weight preparation and the expansion to every coset)",
                     "launch_ms": mlp_ms,
                     "rows": rows, "peak_source": src}

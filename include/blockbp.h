@@ -58,6 +58,16 @@ extern "C" {
 #define BBP_FLAG_OVERLAP 2     /* some edge overlap <m_uv|m_vu> <= 0 */
 #define BBP_FLAG_BLOCK 4       /* some block contraction Z_v <= 0 */
 #define BBP_FLAG_NONFINITE 8   /* a norm or a log went non-finite */
+/* An MPS bond outgrew its slot, or a register-form-only kernel met a block
+ * without a register form (neither is expected; the coset's values are not
+ * meaningful). */
+#define BBP_FLAG_CAPACITY (1 << 16)
+/* An index or size checked on the device was out of range and the access was
+ * skipped (the coset's values are not meaningful): a syndrome of a mixed
+ * batch whose distance lies outside 2..d_max (always checked), or, in the
+ * library built with device bounds checks (-DBLOCKBP_CHECKS, whose
+ * bbp_version() says so), any table index the kernels derive. */
+#define BBP_FLAG_CHECK (1 << 17)
 
 /* Algorithms. */
 #define BBP_ALG_MPS 0          /* blockBP with boundary-MPS messages of bond D (Sec. III.D) */
@@ -93,8 +103,8 @@ extern "C" {
  *             2 a workspace slot per resident CTA with a persistent grid,
  *             3 shared memory with every block update in register form:
  *             k = 4 at odd d only, where every block is 4 x 4 or one node
- *             wide; small per-warp buffers, sized for more CTAs per SM; not
- *             for bbp_decode_mixed).
+ *             wide; small per-warp buffers, sized for more CTAs per SM; for
+ *             bbp_decode_mixed only on request, see there).
  *             0 picks the first compiled shape, in order of measured speed,
  *             whose shared memory allows the CTAs per SM its registers are
  *             sized for, else the first that fits; compiled (warps, cosets):
@@ -303,6 +313,16 @@ int bbp_message_features_rows(const uint8_t* syndromes, int64_t B, const bbp_par
                               int32_t U, float* feats, int32_t* lens, void* stream);
 
 /*
+ * bbp_message_feature_bits_rows -- the same rows as bits: bits
+ * [B*U][BBP_WARM_FEATURES / 32] uint32, bit q % 32 of word q / 32 set where
+ * feature q is not zero.  Every feature is 0 or 1 except feature 253 (10 p,
+ * whose bit is set), so the bits and p give the rows back exactly
+ * (bbp_warm_infer_bits); 32 bytes a row instead of 1 KB.
+ */
+int bbp_message_feature_bits_rows(const uint8_t* syndromes, int64_t B, const bbp_params* prm,
+                                  const int32_t* row_key, int32_t U, uint32_t* bits, int32_t* lens, void* stream);
+
+/*
  * bbp_expand_rows -- messages [B][4][M][16] from distinct rows [B*U][16]:
  * msgs[b][c][i] = rows[b*U + uniq_of[c*M + i]] (uniq_of device, from
  * bbp_message_classes).  Asynchronous on ``stream``.
@@ -331,6 +351,16 @@ int bbp_warm_workspace_bytes(int64_t N, size_t* bytes);
  */
 int bbp_warm_infer(const float* theta, const float* feats, const int32_t* lens, int64_t N, float alpha,
                    float* msgs, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * bbp_warm_infer_bits -- bbp_warm_infer from feature bits (as
+ * bbp_message_feature_bits_rows writes them) and the noise rate p of
+ * feature 253: the same BF16 operands, so the same messages bit for bit as
+ * bbp_warm_infer on the FP32 rows.  Arguments and errors otherwise as
+ * bbp_warm_infer (p in (0, 0.75)).
+ */
+int bbp_warm_infer_bits(const float* theta, const uint32_t* bits, const int32_t* lens, int64_t N, double p,
+                        float alpha, float* msgs, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * bbp_warm_infer_syndromes -- bbp_warm_infer for every message of B
@@ -375,9 +405,10 @@ int bbp_decode_batch_ex(const uint8_t* syndromes, int64_t B, const bbp_params* p
 
 /*
  * bbp_decode_warm -- the learned decoder in one call (fused path, k <= 4):
- * features of the distinct message rows (bbp_message_classes,
- * bbp_message_features_rows), the network on the tensor cores
- * (bbp_warm_infer, alpha as there), the expansion of each proposal to the
+ * features of the distinct message rows (bbp_message_classes; the features
+ * of bbp_message_features_rows, held as bits: every feature is 0 or 1 but
+ * 10 p), the network on the tensor cores (bbp_warm_infer, alpha as there;
+ * the same BF16 operands, bit for bit), the expansion of each proposal to the
  * cosets it stands for (bbp_expand_rows), then bbp_decode_batch_ex started
  * from the proposals.  Outputs as bbp_decode_batch.
  *   theta      device, bbp_warm_param_count() floats (trained parameters)
@@ -385,8 +416,8 @@ int bbp_decode_batch_ex(const uint8_t* syndromes, int64_t B, const bbp_params* p
  *   workspace  device, at least bbp_decode_warm_workspace_bytes(prm, B, 0)
  *              bytes, 256-byte aligned: the network's scratch (its status
  *              word at byte BBP_WARM_STATUS_OFFSET, as for bbp_warm_infer),
- *              the class tables, the features of the distinct rows (1 KB
- *              per row; d = 11, k = 4: 154 rows per syndrome), the
+ *              the class tables, the features of the distinct rows (32
+ *              bytes per row; d = 11, k = 4: 154 rows per syndrome), the
  *              proposals, the expanded initial messages (B x 4 x M x 16
  *              floats) and the decode's own workspace
  * Asynchronous on ``stream``.  Errors: BBP_EINVAL for bad arguments,
@@ -418,10 +449,17 @@ int bbp_decode_warm_workspace_bytes(const bbp_params* prm, int64_t B, int includ
  * ``order`` (e.g. largest distance first); outputs are indexed by syndrome.
  *   syndromes  device, packed: syndrome b starts at byte offsets[b] and has
  *              m(d_of[b]) = 2 d (d-1) bytes
- *   offsets    device [B] int64;  d_of  device [B] int32 (2 <= d <= d_max)
- *   order      device [B] int32 permutation of 0..B-1, or NULL (natural order)
+ *   offsets    device [B] int64;  d_of  device [B] int32 (2 <= d <= d_max;
+ *              the kernel checks it: a syndrome outside that range is not
+ *              decoded, its rows get BBP_FLAG_CHECK and NaN)
+ *   order      device [B] int32 permutation of 0..B-1, or NULL (natural order;
+ *              an entry outside 0..B-1 is skipped)
  *   prm        k, p, eta, delta0, delta1, max_iter, precision; d is ignored;
- *              algorithm must be BBP_ALG_FUSED
+ *              algorithm must be BBP_ALG_FUSED; launch_messages = 3 asks for
+ *              the register-form-only kernels: the caller vouches that every
+ *              distance is odd (k = 4, d_max odd, else BBP_EUNSUPPORTED); a
+ *              syndrome of even distance in such a batch gets
+ *              BBP_FLAG_CAPACITY.  The default never takes them.
  *   workspace  device, at least 256 bytes (the work counter); when the launch
  *              shape keeps its messages in the workspace (always for k = 5,
  *              6), 256 + bbp_workspace_bytes of d_max and B (the slots)

@@ -17,6 +17,7 @@ BBP_OK = 0
 FP64, FP32 = 0, 1
 ALG_MPS, ALG_FUSED = 0, 1
 FLAG_UNTRUSTED, FLAG_OVERLAP, FLAG_BLOCK, FLAG_NONFINITE = 1, 2, 4, 8
+FLAG_CAPACITY, FLAG_CHECK = 1 << 16, 1 << 17
 
 # Exported symbols, as declared in include/blockbp.h.
 SYMBOLS = ("bbp_workspace_bytes", "bbp_decode_batch", "bbp_decode_batch_host", "bbp_sample",
@@ -24,7 +25,8 @@ SYMBOLS = ("bbp_workspace_bytes", "bbp_decode_batch", "bbp_decode_batch_host", "
            "bbp_message_features", "bbp_warm_param_count", "bbp_warm_workspace_bytes", "bbp_warm_infer",
            "bbp_warm_train_step", "bbp_decode_batch_ex", "bbp_decode_mixed", "bbp_warm_infer_syndromes",
            "bbp_pure_error", "bbp_message_classes", "bbp_message_features_rows", "bbp_expand_rows",
-           "bbp_decode_warm", "bbp_decode_warm_host", "bbp_decode_warm_workspace_bytes")
+           "bbp_decode_warm", "bbp_decode_warm_host", "bbp_decode_warm_workspace_bytes",
+           "bbp_message_feature_bits_rows", "bbp_warm_infer_bits")
 WARM_F, WARM_H, WARM_O, WARM_MAX_ROWS = 256, 256, 16, 4194240
 WARM_STATUS_OFFSET = 270336       # int32 status word of bbp_warm_infer in its workspace
 WARM_INFER_WS_BYTES = 270592      # workspace of bbp_warm_infer, for any N
@@ -87,15 +89,27 @@ class BbpError(RuntimeError):
 
 
 _lib = None
+_lib_path = LIB_PATH
+
+
+def use_library(path: str | None = None):
+    """Make lib() load the library at ``path`` (None: the default build), e.g.
+    the build with device bounds checks; returns the path used before."""
+    global _lib, _lib_path
+    prev = _lib_path
+    path = path or LIB_PATH
+    if path != _lib_path:
+        _lib, _lib_path = None, path
+    return prev
 
 
 def lib():
     """The loaded library; raises if it has not been built."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise BbpError(f"{LIB_PATH} is missing: build it with paper_2402_04834_gb300.build.build()")
-        L = ctypes.CDLL(LIB_PATH)
+        if not os.path.exists(_lib_path):
+            raise BbpError(f"{_lib_path} is missing: build it with paper_2402_04834_gb300.build.build()")
+        L = ctypes.CDLL(_lib_path)
         vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
         P = ctypes.POINTER(BbpParams)
         L.bbp_workspace_bytes.argtypes = [P, i64, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
@@ -133,6 +147,11 @@ def lib():
         L.bbp_message_classes.restype = ctypes.c_int
         L.bbp_message_features_rows.argtypes = [vp, i64, P, vp, i32, vp, vp, vp]
         L.bbp_message_features_rows.restype = ctypes.c_int
+        L.bbp_message_feature_bits_rows.argtypes = [vp, i64, P, vp, i32, vp, vp, vp]
+        L.bbp_message_feature_bits_rows.restype = ctypes.c_int
+        L.bbp_warm_infer_bits.argtypes = [vp, vp, vp, i64, ctypes.c_double, ctypes.c_float, vp, vp, ctypes.c_size_t,
+                                          vp]
+        L.bbp_warm_infer_bits.restype = ctypes.c_int
         L.bbp_expand_rows.argtypes = [vp, i64, i32, vp, i32, vp, vp]
         L.bbp_expand_rows.restype = ctypes.c_int
         L.bbp_decode_warm.argtypes = [vp, vp, i64, P, ctypes.c_float, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]

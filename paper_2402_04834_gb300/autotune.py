@@ -67,9 +67,15 @@ def tune_uniform(syndromes, prm: DecoderParams, shapes=None):
 
 
 def tune_mixed(packed, offsets, d_of, prm: DecoderParams, shapes=None, ctas=(0, 1, 2, 3, 4)):
-    """Best (warps, cosets, messages, resident CTAs per SM) for a mixed batch; returns (params, table)."""
-    shapes = tuple(shapes or candidates(prm))
+    """Best (warps, cosets, messages, resident CTAs per SM) for a mixed batch; returns (params, table).
+    The register-form-only shapes (messages 3) are candidates when every
+    distance of the batch is odd (k = 4)."""
     sig = tuple(sorted(torch.unique(d_of).tolist()))
+    if shapes is None:
+        shapes = candidates(prm)
+        if prm.k == 4 and all(d % 2 == 1 for d in sig):
+            shapes = tuple((w, c, 3) for w, c in FUSED_SHAPES_LEAN[prm.precision]) + tuple(shapes)
+    shapes = tuple(shapes)
     key = ("mixed", sig, prm.k, prm.precision, prm.max_iter, shapes, tuple(ctas))
     if key in _cache:
         return dataclasses.replace(prm, **_cache[key][0]), _cache[key][1]

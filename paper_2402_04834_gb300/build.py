@@ -15,6 +15,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libblockbp.so")
+# The same sources with device bounds checks (-DBLOCKBP_CHECKS): every table
+# index the kernels derive is tested before use, failures flagged
+# (BBP_FLAG_CHECK) and skipped.  Built on request only.
+BUILD_CHECKS = os.path.join(HERE, "_build_checks")
+LIB_CHECKS = os.path.join(HERE, "libblockbp_checks.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["bbp_api.cu", "bbp_decode_f64.cu", "bbp_decode_f32.cu", "bbp_fused_f32.cu", "bbp_fused_f64.cu",
            "bbp_sample.cu", "bbp_static.cu", "bbp_warm.cu", "bbp_warm_tc.cu",
@@ -36,19 +41,22 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
-    """Compile and link the library; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, force: bool = False, checks: bool = False) -> str:
+    """Compile and link the library (with ``checks``, the variant with device
+    bounds checks); returns its path."""
+    bdir, lib_path = (BUILD_CHECKS, LIB_CHECKS) if checks else (BUILD, LIB)
+    extra = ["-DBLOCKBP_CHECKS"] if checks else []
+    os.makedirs(bdir, exist_ok=True)
     newest = _deps_mtime()
     nvcc = _nvcc()
     procs = []
     objs = []
     for src in SOURCES:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(bdir, src.replace(".cu", ".o"))
         objs.append(obj)
         if not force and os.path.exists(obj) and os.path.getmtime(obj) >= newest:
             continue
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -62,13 +70,13 @@ def build(verbose: bool = False, force: bool = False) -> str:
     if failed:
         msg = "\n".join(f"--- {s}\n{o}" for s, o in failed)
         raise RuntimeError(f"nvcc failed:\n{msg}")
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        cmd = [nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
+    if force or not os.path.exists(lib_path) or os.path.getmtime(lib_path) < max(os.path.getmtime(o) for o in objs):
+        cmd = [nvcc, *ARCH, "-shared", "-o", lib_path, *objs, "-lcudart"]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         subprocess.run(cmd, check=True)
-    return LIB
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(verbose=True, force="--force" in sys.argv))
+    print(build(verbose=True, force="--force" in sys.argv, checks="--checks" in sys.argv))

@@ -111,7 +111,13 @@ Sizes sizes_for(const bbp_params* p, int64_t B) {
 
 extern "C" {
 
-const char* bbp_version(void) { return "blockbp-gb300 0.1 (sm_103a)"; }
+const char* bbp_version(void) {
+#ifdef BLOCKBP_CHECKS
+  return "blockbp-gb300 0.1 (sm_103a, device bounds checks)";
+#else
+  return "blockbp-gb300 0.1 (sm_103a)";
+#endif
+}
 
 const char* bbp_strerror(int code) {
   switch (code) {
@@ -214,7 +220,10 @@ int bbp_decode_mixed(const uint8_t* syndromes, const int64_t* offsets, const int
                      int64_t B, int32_t d_max, const bbp_params* prm, double* logp, double* delta, int32_t* iters,
                      int32_t* flags, int8_t* decision, void* workspace, size_t workspace_bytes, void* stream) {
   if (!prm || prm->algorithm != BBP_ALG_FUSED) return BBP_EINVAL;
-  if (prm->launch_messages == 3) return BBP_EUNSUPPORTED;   // a batch may hold any distance
+  // The register-form-only kernels only on request (launch_messages = 3):
+  // the caller vouches that every distance of the batch is odd.
+  const bool lean_req = prm->launch_messages == 3;
+  if (lean_req && (prm->k != 4 || d_max % 2 == 0)) return BBP_EUNSUPPORTED;
   bbp_params q = *prm;
   q.d = d_max;                                   // validate the largest geometry
   const int rc = check_params(&q);
@@ -235,18 +244,18 @@ int bbp_decode_mixed(const uint8_t* syndromes, const int64_t* offsets, const int
   m.counter = static_cast<unsigned long long*>(workspace);
   m.d_max = d_max; m.ctas_per_sm = prm->launch_ctas_per_sm;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int Mmax = 0, ae = 0, w = 0, c = 0;
+  int Mmax = 0, ae = 0, w = 0, c = 0, lean = 0;
   bool gm = false;
   bbp::count_messages(a.geo, 1, &Mmax, &ae);
-  if (!shape_of(prm, a.geo, Mmax, &w, &c, &gm, nullptr, false)) return BBP_EUNSUPPORTED;
+  if (!shape_of(prm, a.geo, Mmax, &w, &c, &gm, &lean, lean_req)) return BBP_EUNSUPPORTED;
   if (gm) {   // message slots after the counter
     const size_t elem = prm->precision == BBP_FP64 ? sizeof(double) : sizeof(float);
     m.slots = fused_slots(B, c);
     if (workspace_bytes < 256 + (size_t)m.slots * fused_slot_bytes(prm->k, c, Mmax, elem)) return BBP_ENOSPACE;
     m.slot_base = static_cast<char*>(workspace) + 256;
   }
-  cudaError_t e = prm->precision == BBP_FP64 ? bbp::launch_fused_mixed_f64(a, m, w, c, gm, st)
-                                             : bbp::launch_fused_mixed_f32(a, m, w, c, gm, st);
+  cudaError_t e = prm->precision == BBP_FP64 ? bbp::launch_fused_mixed_f64(a, m, w, c, gm, lean, st)
+                                             : bbp::launch_fused_mixed_f32(a, m, w, c, gm, lean, st);
   if (e != cudaSuccess) return BBP_ECUDA;
   e = bbp::launch_decide(a, st);
   return e == cudaSuccess ? BBP_OK : BBP_ECUDA;

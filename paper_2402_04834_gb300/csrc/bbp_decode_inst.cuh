@@ -92,14 +92,14 @@ cudaError_t launch_fused_nw(const LaunchArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <typename T, int NW, int G, int K, bool GM = (K > 4)>
+template <typename T, int NW, int G, int K, bool GM = (K > 4), int LB = 0>
 cudaError_t launch_fused_mixed_nw(const LaunchArgs& a, const MixedLaunch& m, cudaStream_t st) {
   const KArgs<T> k = fused_args<T>(a);
   const Geo gmax = make_geo(m.d_max, a.geo.k);
   int Mmax = 0, ae = 0;
   count_messages(gmax, 1, &Mmax, &ae);
-  const int smem = fused_smem_for<T, K>(gmax, Mmax, NW, G, GM);
-  auto kern = fused_mixed_kernel<T, NW, G, K, GM>;
+  const int smem = fused_smem_for<T, K>(gmax, Mmax, NW, G, GM, LB > 0);
+  auto kern = fused_mixed_kernel<T, NW, G, K, GM, LB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   int per_sm = m.ctas_per_sm;
@@ -114,6 +114,7 @@ cudaError_t launch_fused_mixed_nw(const LaunchArgs& a, const MixedLaunch& m, cud
   MixedArgs mx;
   mx.d_of = m.d_of; mx.offsets = m.offsets; mx.order = m.order; mx.counter = m.counter;
   mx.n_items = a.B * (4 / G); mx.k = a.geo.k;
+  mx.B = a.B; mx.d_max = m.d_max;
   long long grid = (long long)sms * per_sm;
   if (grid > mx.n_items) grid = mx.n_items;
   KArgs<T> kp = k;

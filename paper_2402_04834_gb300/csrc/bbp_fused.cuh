@@ -1481,6 +1481,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
       misc[12 + q] = 0;
       dsh[q] = 0.0;
     }
+    if (!dev_check(idx == M && n0 + n1 == M, &misc[8])) misc[2] = misc[3] = 0;
   }
   __syncthreads();
 
@@ -1496,7 +1497,11 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
       const int q = e / M, idx = e - q * M;
       const int key = meta[idx];
       const Frame f = make_frame(c, key / 4 / nb, (key / 4) % nb, key & 3);
-      const QuadTask qt = quad_task<T, K>(f);
+      QuadTask qt = quad_task<T, K>(f);
+      if (!dev_check(qt.in_idx >= -1 && qt.in_idx < M && qt.up_idx >= -1 && qt.up_idx < M && qt.lo_idx >= -1 &&
+                         qt.lo_idx < M && qt.shape <= kShapeDot,
+                     &misc[8]))
+        qt.shape = kShapeNone;
       if (q == 0) qdesc[idx] = qt;
       qid[e] = quad_ids(f, frames + q * WW, W, qt);
     }
@@ -1526,7 +1531,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
   __syncthreads();
 
   const T eta = (T)a.eta, one_m_eta = T(1) - eta;
-  const double d0sq = (a.delta0 * M) * (a.delta0 * M);
+  const T d0sq = (T)((a.delta0 * M) * (a.delta0 * M));   // the exit threshold in working precision
   unsigned act = (1u << G) - 1;                      // cosets still iterating
   for (int it = 1; it <= a.max_iter && M > 0 && act; ++it) {
     int n = 0;
@@ -1544,6 +1549,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
         item = __shfl_sync(kFull, item, 0);
         if (item >= nwork) break;
         const int idx = lst[item];
+        if (!dev_check(idx >= 0 && idx < M, &misc[8])) continue;
         int shape = kShapeNone;
         QuadTask qt;
         if (quads) {
@@ -1575,15 +1581,16 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
     }
     // Delta = sqrt(sum) / M < delta0 (Remark 4), compared as sum <
     // (delta0 M)^2 by the coset's warp, which sets the coset's bit in
-    // misc[1]; the square root is taken once, after the loop.  The sum runs
-    // in working precision (FP32 terms, each already rounded to FP32).
+    // misc[1]; the square root is taken once, after the loop.  The sum and
+    // the compare run in working precision (FP32 terms, each already rounded
+    // to FP32; no FP64 instruction in the loop of an FP32 kernel).
     if (warp < G && ((act >> warp) & 1u)) {
       T acc = T(0);
       for (int i = lane; i < M; i += 32) acc += ovl[warp * M + i];
       acc = warp_sum(acc);
       if (lane == 0) {
-        const double sum = acc > T(0) ? (double)acc : 0.0;
-        dsh[warp] = sum;
+        const T sum = acc > T(0) ? acc : T(0);
+        dsh[warp] = (double)sum;
         misc[12 + warp] = it;
         if (sum < d0sq) atomicOr(&misc[1], 1 << warp);
       }
@@ -1605,7 +1612,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
       const int dir = meta[idx] & 3;
       if (dir == kDirR || dir == kDirD) work[ne++] = (int16_t)idx;
     }
-    misc[4] = ne;
+    misc[4] = dev_check(ne <= M, &misc[8]) ? ne : 0;
     misc[0] = 0;
   }
   __syncthreads();
@@ -1647,6 +1654,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
         if (lane == 0) atomicOr(&misc[8], kFlagCapacity);
       }
       const int right = J + 1 < nb ? msg_index(c, I, J + 1, kDirL) : -1;
+      if (!dev_check(right >= -1 && right < M, &misc[8])) continue;
       // On the grid border the right side has no message.  The node-by-node
       // path gives missing legs the value 0, so only entry 0 survives; the
       // register forms treat every node as complete, so their vector is
@@ -1685,9 +1693,11 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
       __syncwarp();
     } else {
       const int idx = work[item - nblk];
+      if (!dev_check(idx >= 0 && idx < M, &misc[8])) continue;
       const int key = meta[idx];
       const int I = key / 4 / nb, J = (key / 4) % nb, dir = key & 3;
       const int other = dir == kDirR ? msg_index(c, I, J + 1, kDirL) : msg_index(c, I + 1, J, kDirU);
+      if (!dev_check(other >= 0 && other < M, &misc[8])) continue;
       const int w = g.side_len(I, J, dir);
 #pragma unroll
       for (int q = 0; q < G; ++q) {
@@ -1738,7 +1748,9 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
     const double dq = M > 0 ? sqrt(dsh[warp]) / M : 0.0;
     const int iq = misc[12 + warp];
     if (lane == 0) {
-      int fl = misc[8 + warp];
+      // Capacity and check failures are recorded on the first coset's word
+      // and hold for every coset of the item.
+      int fl = misc[8 + warp] | (misc[8] & (kFlagCapacity | kFlagCheck));
       if (!isfinite(acc)) fl |= kFlagNonfinite;
       if (!(dq < a.delta1)) fl |= kFlagUntrusted;
       const long long row = syn * 4 + c0 + warp;
@@ -1781,11 +1793,13 @@ struct MixedArgs {
   const int32_t* order;         // syndrome order of the items, or null
   unsigned long long* counter;  // zero before the launch
   long long n_items;            // B * (4 / G)
-  int k;
+  long long B;                  // syndromes
+  int k, d_max;                 // shared memory is sized for d_max
 };
 
-template <typename T, int NW, int G, int K, bool GM = (K > 4)>
-__global__ void __launch_bounds__(NW * 32, (FusedMinBlocks<T, NW, G, K>::value))
+// LB > 0: the register-form-only kernel (every distance of the batch odd).
+template <typename T, int NW, int G, int K, bool GM = (K > 4), int LB = 0>
+__global__ void __launch_bounds__(NW * 32, (FusedMinBlocks<T, NW, G, K, LB>::value))
     fused_mixed_kernel(KArgs<T> a, MixedArgs mx) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long item_sh;
@@ -1798,11 +1812,26 @@ __global__ void __launch_bounds__(NW * 32, (FusedMinBlocks<T, NW, G, K>::value))
     if (item >= mx.n_items) break;
     const long long shot = mx.order ? (long long)mx.order[item / NG] : (item / NG);
     const int c0 = (int)(item % NG) * G;
-    const Geo g = make_geo(mx.d_of[shot], mx.k);
+    // The batch comes from device buffers the host cannot read: a syndrome
+    // index outside the batch is skipped, a distance outside 2..d_max (more
+    // than the shared memory holds) gives its rows kFlagCheck and NaN.
+    if (shot < 0 || shot >= mx.B) continue;
+    const int d = mx.d_of[shot];
+    if (d < 2 || d > mx.d_max) {
+      if (threadIdx.x < G) {
+        const long long row = shot * 4 + c0 + threadIdx.x;
+        a.logp[row] = __longlong_as_double(0x7ff8000000000000ll);
+        a.delta[row] = __longlong_as_double(0x7ff8000000000000ll);
+        a.iters[row] = 0;
+        a.flags[row] = kFlagCheck | kFlagNonfinite;
+      }
+      continue;
+    }
+    const Geo g = make_geo(d, mx.k);
     int M = 0, ae = 0;
     count_messages(g, 1, &M, &ae);
-    fused_item<T, NW, G, K, GM>(a, g, M, a.synd + mx.offsets[shot], shot, c0, smem,
-                                GM ? a.arena + (long long)blockIdx.x * a.slot_elems : nullptr);
+    fused_item<T, NW, G, K, GM, LB>(a, g, M, a.synd + mx.offsets[shot], shot, c0, smem,
+                                    GM ? a.arena + (long long)blockIdx.x * a.slot_elems : nullptr);
     __syncthreads();
   }
 }

@@ -41,7 +41,15 @@ cudaError_t launch_fused_f32(const LaunchArgs& a, int warps, int cosets, bool gm
 }
 
 cudaError_t launch_fused_mixed_f32(const LaunchArgs& a, const MixedLaunch& m, int warps, int cosets, bool gm,
-                                   cudaStream_t st) {
+                                   int lean, cudaStream_t st) {
+  if (lean > 0) {                          // every distance odd: every block update in register form
+    switch (warps * 100 + cosets * 10 + lean) {
+      case 844: return launch_fused_mixed_nw<float, 8, 4, 4, false, 4>(a, m, st);
+      case 843: return launch_fused_mixed_nw<float, 8, 4, 4, false, 3>(a, m, st);
+      case 824: return launch_fused_mixed_nw<float, 8, 2, 4, false, 4>(a, m, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   if (a.geo.k > 4) {
     switch (warps * 10 + cosets) {
       case 21: return launch_fused_mixed_nw<float, 2, 1, 6>(a, m, st);

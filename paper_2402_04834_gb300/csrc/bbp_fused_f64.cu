@@ -30,7 +30,14 @@ cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, int cosets, bool gm
 }
 
 cudaError_t launch_fused_mixed_f64(const LaunchArgs& a, const MixedLaunch& m, int warps, int cosets, bool gm,
-                                   cudaStream_t st) {
+                                   int lean, cudaStream_t st) {
+  if (lean > 0) {                          // every distance odd: every block update in register form
+    switch (warps * 100 + cosets * 10 + lean) {
+      case 424: return launch_fused_mixed_nw<double, 4, 2, 4, false, 4>(a, m, st);
+      case 822: return launch_fused_mixed_nw<double, 8, 2, 4, false, 2>(a, m, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   if (a.geo.k > 4) {
     switch (warps * 10 + cosets) {
       case 21: return launch_fused_mixed_nw<double, 2, 1, 6>(a, m, st);

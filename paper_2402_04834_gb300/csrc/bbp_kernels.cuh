@@ -28,6 +28,27 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxSweeps = 48;          // one-sided Jacobi sweep limit
 constexpr int kFlagUntrusted = 1, kFlagOverlap = 2, kFlagBlock = 4, kFlagNonfinite = 8;
 constexpr int kFlagCapacity = 1 << 16;  // a bond exceeded its slot (never expected)
+constexpr int kFlagCheck = 1 << 17;     // a device-checked index or size was out of range
+
+// Device bounds checks.  Built with -DBLOCKBP_CHECKS (a separate library,
+// build(checks=True)), every table index the kernels derive (message
+// indices, list entries, slot offsets, record indices) is tested against
+// its buffer before use; a failed test sets kFlagCheck in *flags and the
+// access is skipped.  The default build compiles the tests away.
+#ifdef BLOCKBP_CHECKS
+constexpr bool kChecks = true;
+#else
+constexpr bool kChecks = false;
+#endif
+__device__ __forceinline__ bool dev_check(bool ok, int* flags) {
+  if constexpr (kChecks) {
+    if (!ok) {
+      atomicOr(flags, kFlagCheck);
+      return false;
+    }
+  }
+  return true;
+}
 
 template <typename T> struct Eps;
 template <> struct Eps<double> { static __device__ __forceinline__ double v() { return 2.220446049250313e-16; } };
@@ -838,6 +859,7 @@ __global__ void __launch_bounds__(NW * 32) decode_kernel(KArgs<T> a) {
         }
     misc[0] = 0; misc[1] = 0; misc[2] = n0; misc[3] = n1;
     e0[0] = T(1); e0[1] = T(0);
+    if (!dev_check(idx == M && n0 + n1 == M && off <= a.arena_elems, &misc[1])) misc[2] = misc[3] = 0;
   }
   __syncthreads();
 
@@ -875,6 +897,7 @@ __global__ void __launch_bounds__(NW * 32) decode_kernel(KArgs<T> a) {
         item = __shfl_sync(kFull, item, 0);
         if (item >= nwork) break;
         const int idx = lst[item];
+        if (!dev_check(idx >= 0 && idx < M, &misc[1])) continue;
         const int key = meta[idx];
         const int I = key / 4 / nb, J = (key / 4) % nb, dir = key & 3;
         const Frame f = make_frame(c, I, J, dir);
@@ -925,6 +948,7 @@ __global__ void __launch_bounds__(NW * 32) decode_kernel(KArgs<T> a) {
       const Frame f = make_frame(c, I, J, kDirR);
       const double ls = block_sweep(ws, c, f, true, lane);
       const int right = J + 1 < nb ? msg_index(c, I, J + 1, kDirL) : -1;
+      if (!dev_check(right >= -1 && right < M, &misc[1])) continue;
       const double z = mps_overlap(ws, f.h, [&](int s) { return psi_site(ws, s); },
                                    [&](int s) { return msg_site(c, right, f.h, s, false); }, lane);
       if (lane == 0) {
@@ -934,9 +958,11 @@ __global__ void __launch_bounds__(NW * 32) decode_kernel(KArgs<T> a) {
     } else {
       const int e = item - nblk;
       const int idx = work[e];
+      if (!dev_check(idx >= 0 && idx < M, &misc[1])) continue;
       const int key = meta[idx];
       const int I = key / 4 / nb, J = (key / 4) % nb, dir = key & 3;
       const int other = dir == kDirR ? msg_index(c, I, J + 1, kDirL) : msg_index(c, I + 1, J, kDirU);
+      if (!dev_check(other >= 0 && other < M, &misc[1])) continue;
       const int w = g.side_len(I, J, dir);
       const double o = mps_overlap(ws, w, [&](int s) { return msg_site(c, idx, w, s, false); },
                                    [&](int s) { return msg_site(c, other, w, s, false); }, lane);

@@ -70,10 +70,11 @@ struct MixedLaunch {
 // lean: 0, or the CTAs per SM of the register-form-only kernel to launch.
 cudaError_t launch_fused_f64(const LaunchArgs& a, int warps, int cosets, bool gm, int lean, cudaStream_t st);
 cudaError_t launch_fused_f32(const LaunchArgs& a, int warps, int cosets, bool gm, int lean, cudaStream_t st);
+// lean as for launch_fused_f32 / _f64 (every distance of the batch odd).
 cudaError_t launch_fused_mixed_f64(const LaunchArgs& a, const MixedLaunch& mx, int warps, int cosets, bool gm,
-                                   cudaStream_t st);
+                                   int lean, cudaStream_t st);
 cudaError_t launch_fused_mixed_f32(const LaunchArgs& a, const MixedLaunch& mx, int warps, int cosets, bool gm,
-                                   cudaStream_t st);
+                                   int lean, cudaStream_t st);
 cudaError_t launch_decode_f64(const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_decode_f32(const LaunchArgs& a, cudaStream_t st);
 cudaError_t launch_decide(const LaunchArgs& a, cudaStream_t st);

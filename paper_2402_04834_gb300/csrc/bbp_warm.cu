@@ -72,9 +72,12 @@ __global__ void features_kernel(Geo g, int M, double p, const uint8_t* synd, flo
 
 // Features of listed rows: row u of syndrome b is (coset, message) =
 // row_key[u] = coset * M + message; one CTA per syndrome holding the four
-// coset frames.  Row (b, u) is written at b * U + u.
+// coset frames.  Row (b, u) is written at b * U + u: 256 floats, or with
+// BITS 256 bits (8 words; bit q of word q / 32 set where feature q is not
+// zero: every feature is 0 or 1 except 10 p, which inference puts back).
+template <bool BITS>
 __global__ void features_rows_kernel(Geo g, int M, double p, const uint8_t* synd, const int32_t* row_key, int U,
-                                     float* feats, int32_t* lens) {
+                                     float* feats, uint32_t* bits, int32_t* lens) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int W = g.W, WW = W * W, d = g.d, nb = g.nb;
   const int m = 2 * d * (d - 1);
@@ -104,14 +107,40 @@ __global__ void features_rows_kernel(Geo g, int M, double p, const uint8_t* synd
     const int mk = meta[idx];
     const MsgGeo f = msg_geo(g, mk / 4 / nb, (mk / 4) % nb, mk & 3);
     const uint8_t* frame = frames + coset * WW;
-    float* out = feats + (shot * U + u) * F;
-    for (int pos = lane; pos < 49; pos += 32) {
-      float c[5];
-      window_node(g, f, pos, frame, s, c);
+    if constexpr (BITS) {
+      // Lane l holds window nodes l and l + 32; each channel's 49 bits come
+      // from two ballots, shifted into place (features ch * 49 + pos).
+      float c0[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, c1[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      window_node(g, f, lane, frame, s, c0);
+      if (lane + 32 < 49) window_node(g, f, lane + 32, frame, s, c1);
+      uint32_t w[9] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
 #pragma unroll
-      for (int ch = 0; ch < 5; ++ch) out[ch * 49 + pos] = c[ch];
+      for (int ch = 0; ch < 5; ++ch)
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          uint32_t b = __ballot_sync(kFull, (half ? c1[ch] : c0[ch]) != 0.f);
+          if (half) b &= (1u << 17) - 1u;                   // nodes 32 .. 48
+          const int q0 = ch * 49 + 32 * half, sh = q0 & 31;
+          w[q0 >> 5] |= b << sh;
+          if (sh) w[(q0 >> 5) + 1] |= b >> (32 - sh);
+        }
+      const uint32_t tb = __ballot_sync(kFull, lane < F - 245 && tail_feature(f, 245 + lane, p10) != 0.f);
+      w[7] |= tb << (245 - 224);
+      if (lane == 0) {
+        uint4* out = reinterpret_cast<uint4*>(bits + (shot * U + u) * 8);
+        out[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        out[1] = make_uint4(w[4], w[5], w[6], w[7]);
+      }
+    } else {
+      float* out = feats + (shot * U + u) * F;
+      for (int pos = lane; pos < 49; pos += 32) {
+        float c[5];
+        window_node(g, f, pos, frame, s, c);
+#pragma unroll
+        for (int ch = 0; ch < 5; ++ch) out[ch * 49 + pos] = c[ch];
+      }
+      if (lane < F - 245) out[245 + lane] = tail_feature(f, 245 + lane, p10);
     }
-    if (lane < F - 245) out[245 + lane] = tail_feature(f, 245 + lane, p10);
     if (lane == 0 && lens) lens[shot * U + u] = 1 << f.h;
   }
 }
@@ -349,9 +378,15 @@ int bbp_message_classes(const bbp_params* prm, int32_t* uniq_of, int32_t* row_ke
   return BBP_OK;
 }
 
-int bbp_message_features_rows(const uint8_t* syndromes, int64_t B, const bbp_params* prm, const int32_t* row_key,
-                              int32_t U, float* feats, int32_t* lens, void* stream) {
-  if (!prm || !syndromes || !row_key || !feats || B < 0 || prm->d < 2 || prm->d > 64 || prm->k < 1 ||
+}  // extern "C"
+
+namespace bbp {
+namespace warm {
+
+// Either output of features_rows_kernel (exactly one of feats, bits).
+int features_rows(const uint8_t* syndromes, int64_t B, const bbp_params* prm, const int32_t* row_key, int32_t U,
+                  float* feats, uint32_t* bits, int32_t* lens, cudaStream_t st) {
+  if (!prm || !syndromes || !row_key || (!feats == !bits) || B < 0 || prm->d < 2 || prm->d > 64 || prm->k < 1 ||
       prm->k > kFusedK || U < 0)
     return BBP_EINVAL;
   if (B == 0 || U == 0) return BBP_OK;
@@ -361,12 +396,30 @@ int bbp_message_features_rows(const uint8_t* syndromes, int64_t B, const bbp_par
   if (U > 4 * M) return BBP_EINVAL;
   const int m = 2 * g.d * (g.d - 1);
   const int smem = align_up(m, 16) + align_up(4 * g.W * g.W, 16) + align_up(2 * M, 16);
-  if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(features_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+  auto kern = bits ? features_rows_kernel<true> : features_rows_kernel<false>;
+  if (smem > 48 * 1024 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
     return BBP_ECUDA;
-  features_rows_kernel<<<(unsigned)B, 256, smem, static_cast<cudaStream_t>(stream)>>>(g, M, prm->p, syndromes,
-                                                                                     row_key, U, feats, lens);
+  kern<<<(unsigned)B, 256, smem, st>>>(g, M, prm->p, syndromes, row_key, U, feats, bits, lens);
   return cudaGetLastError() == cudaSuccess ? BBP_OK : BBP_ECUDA;
+}
+
+}  // namespace warm
+}  // namespace bbp
+
+extern "C" {
+
+int bbp_message_features_rows(const uint8_t* syndromes, int64_t B, const bbp_params* prm, const int32_t* row_key,
+                              int32_t U, float* feats, int32_t* lens, void* stream) {
+  if (!feats) return BBP_EINVAL;
+  return bbp::warm::features_rows(syndromes, B, prm, row_key, U, feats, nullptr, lens,
+                                  static_cast<cudaStream_t>(stream));
+}
+
+int bbp_message_feature_bits_rows(const uint8_t* syndromes, int64_t B, const bbp_params* prm,
+                                  const int32_t* row_key, int32_t U, uint32_t* bits, int32_t* lens, void* stream) {
+  if (!bits) return BBP_EINVAL;
+  return bbp::warm::features_rows(syndromes, B, prm, row_key, U, nullptr, bits, lens,
+                                  static_cast<cudaStream_t>(stream));
 }
 
 int bbp_expand_rows(const float* rows, int64_t B, int32_t U, const int32_t* uniq_of, int32_t M, float* msgs,
@@ -399,6 +452,19 @@ int bbp_warm_infer(const float* theta, const float* feats, const int32_t* lens, 
   if (!workspace || workspace_bytes < infer_tc_workspace_bytes()) return BBP_ENOSPACE;
   if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return BBP_EINVAL;
   return infer_tc(theta, feats, lens, N, alpha, msgs, workspace, static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? BBP_OK
+             : BBP_ECUDA;
+}
+
+int bbp_warm_infer_bits(const float* theta, const uint32_t* bits, const int32_t* lens, int64_t N, double p,
+                        float alpha, float* msgs, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!theta || !bits || !lens || !msgs || N < 0 || N > BBP_WARM_MAX_ROWS) return BBP_EINVAL;
+  if (!(alpha >= 0.f && alpha <= 1.f) || !(p > 0.0 && p < 0.75)) return BBP_EINVAL;
+  if (N == 0) return BBP_OK;
+  if (!workspace || workspace_bytes < infer_tc_workspace_bytes()) return BBP_ENOSPACE;
+  if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return BBP_EINVAL;
+  return infer_tc_bits(theta, bits, lens, N, p, alpha, msgs, workspace, static_cast<cudaStream_t>(stream)) ==
+                 cudaSuccess
              ? BBP_OK
              : BBP_ECUDA;
 }

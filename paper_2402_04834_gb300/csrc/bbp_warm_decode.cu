@@ -88,7 +88,7 @@ int plan_for(const bbp_params* prm, int64_t B, WarmPlan* w) {
   const size_t N = (size_t)B * w->U;
   w->tables = a256(3 * 4 * (size_t)w->M * sizeof(int32_t));   // scan scratch, uniq_of, row_key
   w->infer_ws = a256(infer_ws);
-  w->feats = a256(N * BBP_WARM_FEATURES * sizeof(float));
+  w->feats = a256(N * (BBP_WARM_FEATURES / 32) * sizeof(uint32_t));   // feature bits
   w->lens = a256(N * sizeof(int32_t));
   w->rows = a256(N * BBP_WARM_OUT * sizeof(float));
   w->msgs = a256((size_t)B * 4 * w->M * BBP_WARM_OUT * sizeof(float));
@@ -134,7 +134,7 @@ int bbp_decode_warm(const float* theta, const uint8_t* syndromes, int64_t B, con
   int32_t* uniq_of = off + 4 * w.M;
   int32_t* row_key = uniq_of + 4 * w.M;
   p += w.tables;
-  float* feats = reinterpret_cast<float*>(p);        p += w.feats;
+  uint32_t* bits = reinterpret_cast<uint32_t*>(p);   p += w.feats;
   int32_t* lens = reinterpret_cast<int32_t*>(p);     p += w.lens;
   float* rows = reinterpret_cast<float*>(p);         p += w.rows;
   float* msgs = reinterpret_cast<float*>(p);         p += w.msgs;
@@ -142,12 +142,14 @@ int bbp_decode_warm(const float* theta, const uint8_t* syndromes, int64_t B, con
   const Geo g = bbp::make_geo(prm->d, prm->k);
   classes_kernel<<<1, 256, 0, st>>>(g, w.M, off, uniq_of, row_key);
   if (cudaGetLastError() != cudaSuccess) return BBP_ECUDA;
-  if ((rc = bbp_message_features_rows(syndromes, B, prm, row_key, w.U, feats, lens, stream)) != BBP_OK) return rc;
+  // Features as bits (32 bytes a row instead of 1 KB of FP32), expanded to
+  // the same BF16 operands inside the network kernel.
+  if ((rc = bbp_message_feature_bits_rows(syndromes, B, prm, row_key, w.U, bits, lens, stream)) != BBP_OK) return rc;
   const long long N = (long long)B * w.U;
   for (long long a = 0; a < N; a += BBP_WARM_MAX_ROWS) {
     const long long n = N - a < BBP_WARM_MAX_ROWS ? N - a : BBP_WARM_MAX_ROWS;
-    rc = bbp_warm_infer(theta, feats + a * BBP_WARM_FEATURES, lens + a, n, alpha, rows + a * BBP_WARM_OUT, infer_ws,
-                        w.infer_ws, stream);
+    rc = bbp_warm_infer_bits(theta, bits + a * (BBP_WARM_FEATURES / 32), lens + a, n, prm->p, alpha,
+                             rows + a * BBP_WARM_OUT, infer_ws, w.infer_ws, stream);
     if (rc != BBP_OK) return rc;
   }
   if ((rc = bbp_expand_rows(rows, B, w.U, uniq_of, w.M, msgs, stream)) != BBP_OK) return rc;

@@ -214,8 +214,12 @@ __device__ __forceinline__ void issue_layer(uint32_t d_tmem, const unsigned char
   mma_commit(mbar);
 }
 
+// Where a tile's features come from.
+constexpr int kFromFeats = 0, kFromSyndromes = 1, kFromBits = 2;
+
 struct MlpArgs {
   const float* feats;        // feature rows [N][256] (from a features tensor), or
+  const uint32_t* bits;      //   as bits [N][8] (feature 253 stands for p10), with
   const int32_t* lens;       //   their message lengths;
   const uint8_t* synd;       // syndromes [N / (4 M)][m]: features computed here
   Geo g;
@@ -245,8 +249,9 @@ __host__ __device__ inline int synd_extra_bytes(const Geo& g, int M, int max_pai
          max_pairs * (align_up(m, 16) + align_up(g.W * g.W, 16));
 }
 
-template <bool kSynd>
+template <int kSrc>
 __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(MlpArgs a) {
+  constexpr bool kSynd = kSrc == kFromSyndromes;
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem;                 // operand tile / hidden activations
   unsigned char* sB = smem + kTileA;        // weights of the current layer
@@ -349,6 +354,31 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(MlpArgs a) {
           v = tail_feature(f, q, a.p10);
         }
         xa[core_off(row, q) / 2] = __float2bfloat16_rn(v);
+      }
+    } else if (kSrc == kFromBits) {
+      // X from feature bits: 1 where a bit is set (feature 253: 10 p, the one
+      // feature that is not 0 or 1), rounded to BF16 exactly as the FP32
+      // path rounds the same features (one 32-feature word of one row per
+      // task; consecutive threads, consecutive rows).
+      const uint16_t one = 0x3F80u;
+      const __nv_bfloat16 pb = __float2bfloat16_rn(a.p10);
+      const uint16_t p10b = *reinterpret_cast<const uint16_t*>(&pb);
+#pragma unroll 2
+      for (int task = tid; task < TM * 8; task += kThreads) {
+        const int row = task & (TM - 1), wd = task >> 7;
+        const long long gr = r0 + row;
+        const uint32_t b = gr < N ? a.bits[gr * 8 + wd] : 0u;
+#pragma unroll
+        for (int c8 = 0; c8 < 4; ++c8) {
+          uint32_t h[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int q = 32 * wd + 8 * c8 + j;
+            h[j] = (b >> (8 * c8 + j)) & 1u ? (q == 253 ? p10b : one) : 0u;
+          }
+          *reinterpret_cast<uint4*>(sA + core_off(row, 32 * wd + 8 * c8)) =
+              make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+        }
       }
     } else {
       // X: rows r0 .. r0 + 127 of the FP32 features, rounded to BF16 (one
@@ -467,7 +497,7 @@ size_t infer_tc_workspace_bytes() { return (size_t)kStatusOffset + 256; }
 namespace {
 
 // Weights into the workspace, status cleared, then the persistent kernel.
-template <bool kSynd>
+template <int kSrc>
 cudaError_t launch_mlp(const float* theta, MlpArgs a, int extra_smem, void* workspace, cudaStream_t st) {
   unsigned char* wt = static_cast<unsigned char*>(workspace);
   a.wt = wt;
@@ -481,7 +511,7 @@ cudaError_t launch_mlp(const float* theta, MlpArgs a, int extra_smem, void* work
   if (e != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(a.status, 0, sizeof(int32_t), st)) != cudaSuccess) return e;
   const int smem = kTileA + kTileB + extra_smem;
-  if ((e = cudaFuncSetAttribute(mlp_tc_kernel<kSynd>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
+  if ((e = cudaFuncSetAttribute(mlp_tc_kernel<kSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
       cudaSuccess)
     return e;
   int dev = 0, sms = 0;
@@ -489,7 +519,7 @@ cudaError_t launch_mlp(const float* theta, MlpArgs a, int extra_smem, void* work
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   const long long ntiles = (a.N + TM - 1) / TM;
   const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
-  mlp_tc_kernel<kSynd><<<grid, kThreads, smem, st>>>(a);
+  mlp_tc_kernel<kSrc><<<grid, kThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -499,7 +529,15 @@ cudaError_t infer_tc(const float* theta, const float* feats, const int32_t* lens
                      float* msgs, void* workspace, cudaStream_t st) {
   MlpArgs a{};
   a.feats = feats; a.lens = lens; a.N = N; a.alpha = alpha; a.msgs = msgs;
-  return launch_mlp<false>(theta, a, 0, workspace, st);
+  return launch_mlp<kFromFeats>(theta, a, 0, workspace, st);
+}
+
+cudaError_t infer_tc_bits(const float* theta, const uint32_t* bits, const int32_t* lens, long long N, double p,
+                          float alpha, float* msgs, void* workspace, cudaStream_t st) {
+  MlpArgs a{};
+  a.bits = bits; a.lens = lens; a.N = N; a.alpha = alpha; a.msgs = msgs;
+  a.p10 = (float)(10.0 * p);
+  return launch_mlp<kFromBits>(theta, a, 0, workspace, st);
 }
 
 int infer_tc_syndromes_smem(const Geo& g, int M) {
@@ -513,7 +551,7 @@ cudaError_t infer_tc_syndromes(const float* theta, const uint8_t* synd, long lon
   a.synd = synd; a.g = g; a.M = M; a.max_pairs = (TM - 1) / M + 2;
   a.p10 = (float)(10.0 * p);
   a.N = B * 4 * (long long)M; a.alpha = alpha; a.msgs = msgs;
-  return launch_mlp<true>(theta, a, synd_extra_bytes(g, M, a.max_pairs), workspace, st);
+  return launch_mlp<kFromSyndromes>(theta, a, synd_extra_bytes(g, M, a.max_pairs), workspace, st);
 }
 
 }  // namespace warm

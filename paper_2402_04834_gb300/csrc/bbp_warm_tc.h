@@ -24,6 +24,16 @@ size_t infer_tc_workspace_bytes();
 cudaError_t infer_tc(const float* theta, const float* feats, const int32_t* lens, long long N, float alpha,
                      float* msgs, void* workspace, cudaStream_t st);
 
+// The same from feature bits [N x 8 words] (bbp_warm.cu's features_rows with
+// bits): bit q set where feature q is not zero; feature 253 is 10 p.
+cudaError_t infer_tc_bits(const float* theta, const uint32_t* bits, const int32_t* lens, long long N, double p,
+                          float alpha, float* msgs, void* workspace, cudaStream_t st);
+
+// Features of the listed rows (bbp_message_features_rows), as FP32 rows
+// [B*U x 256] (feats) or as bits [B*U x 8 words] (bits); exactly one of them.
+int features_rows(const uint8_t* syndromes, int64_t B, const bbp_params* prm, const int32_t* row_key, int32_t U,
+                  float* feats, uint32_t* bits, int32_t* lens, cudaStream_t st);
+
 // Shared memory the syndrome-fed kernel needs at geometry g (bytes).
 int infer_tc_syndromes_smem(const Geo& g, int M);
 

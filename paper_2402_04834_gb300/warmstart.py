@@ -75,6 +75,21 @@ def features_rows(syndromes: torch.Tensor, prm: DecoderParams, stream=None):
     return feats, lens
 
 
+def feature_bits_rows(syndromes: torch.Tensor, prm: DecoderParams, stream=None):
+    """The rows of ``features_rows`` as bits [B*U, 8] int32 (bit q % 32 of word
+    q // 32 set where feature q is not zero; feature 253 stands for 10 p)
+    and the lengths [B*U]."""
+    B = syndromes.shape[0]
+    _, rk = message_classes(prm, syndromes.device)
+    U = rk.numel()
+    bits = torch.empty(B * U, WARM_F // 32, dtype=torch.int32, device=syndromes.device)
+    lens = torch.empty(B * U, dtype=torch.int32, device=syndromes.device)
+    cp = prm.c()
+    check(lib().bbp_message_feature_bits_rows(_ptr(syndromes.contiguous()), B, ctypes.byref(cp), _ptr(rk), U,
+                                              _ptr(bits), _ptr(lens), _stream(stream)))
+    return bits, lens
+
+
 def expand_rows(rows: torch.Tensor, B: int, prm: DecoderParams, out=None, stream=None):
     """Messages [B*4*M, 16] (rows ordered syndrome, coset, message) from the
     distinct rows [B*U, 16]."""
@@ -144,6 +159,19 @@ class WarmStart:
             b = min(N, a + step)
             check(lib().bbp_warm_infer(_ptr(self.theta), _ptr(feats[a:b]), _ptr(lens[a:b]), b - a, alpha,
                                        _ptr(out[a:b]), _ptr(ws), ws.numel(), _stream(stream)))
+        return out
+
+    def infer_bits(self, bits, lens, p, out=None, stream=None, alpha=1.0):
+        """``infer`` from feature bits [N, 8] (``feature_bits_rows``) and the
+        noise rate of feature 253: the same messages bit for bit."""
+        N = bits.shape[0]
+        out = out if out is not None else torch.empty(N, WARM_O, dtype=torch.float32, device=bits.device)
+        step = max(1, min(N, WARM_MAX_ROWS))
+        ws = self.infer_ws.get(WARM_INFER_WS_BYTES, self.device)
+        for a in range(0, N, step):
+            b = min(N, a + step)
+            check(lib().bbp_warm_infer_bits(_ptr(self.theta), _ptr(bits[a:b]), _ptr(lens[a:b]), b - a, p, alpha,
+                                            _ptr(out[a:b]), _ptr(ws), ws.numel(), _stream(stream)))
         return out
 
     def infer_syndromes(self, syndromes, prm: DecoderParams, out=None, stream=None, alpha=1.0):
@@ -352,7 +380,8 @@ def time_inference(syndromes_n=2500, d=11, p=0.10, k=4, seed=5000, reps=3):
     """Features, tensor-core inference from them, and inference with the
     features computed in its kernel, for an untrained network over the
     messages of ``syndromes_n`` seeded syndromes (4 M rows per syndrome);
-    returns the rows and the best times in ms."""
+    then the same for the distinct rows only, from FP32 rows and from
+    feature bits; returns the rows and the best times in ms."""
     from .decoder import sample
     dev = torch.device("cuda")
     _, _, s, _ = sample(seed, 0, syndromes_n, d, p, device=dev, with_errors=False)
@@ -360,9 +389,17 @@ def time_inference(syndromes_n=2500, d=11, p=0.10, k=4, seed=5000, reps=3):
     net = WarmStart(device=dev, seed=0)
     feats, lens = features(s, prm)
     out = net.infer(feats, lens)
-    res = {"rows": int(feats.shape[0])}
+    # The distinct rows only (what the decoder runs), as FP32 rows and as bits.
+    rfeats, rlens = features_rows(s, prm)
+    bits, blens = feature_bits_rows(s, prm)
+    rout = net.infer(rfeats, rlens)
+    res = {"rows": int(feats.shape[0]), "distinct_rows": int(rfeats.shape[0])}
     for name, fn in (("features_ms", lambda: features(s, prm)), ("infer_ms", lambda: net.infer(feats, lens, out=out)),
-                     ("infer_from_syndromes_ms", lambda: net.infer_syndromes(s, prm, out=out))):
+                     ("infer_from_syndromes_ms", lambda: net.infer_syndromes(s, prm, out=out)),
+                     ("features_rows_ms", lambda: features_rows(s, prm)),
+                     ("infer_rows_ms", lambda: net.infer(rfeats, rlens, out=rout)),
+                     ("feature_bits_rows_ms", lambda: feature_bits_rows(s, prm)),
+                     ("infer_bits_ms", lambda: net.infer_bits(bits, blens, p, out=rout))):
         best = float("inf")
         for _ in range(reps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

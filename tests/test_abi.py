@@ -150,6 +150,16 @@ def test_warm_start_arguments_checked_on_the_host(L):
     assert L.bbp_warm_infer(big, big, big, 10, 0.1, big, big, _lib.WARM_INFER_WS_BYTES - 1, None) == -3
     assert L.bbp_warm_infer(big, big, big, _lib.WARM_MAX_ROWS + 1, 0.1, big, big, 1 << 20, None) == -1
     assert L.bbp_warm_infer(big, big, big, 0, 0.1, big, None, 0, None) == 0
+    # the feature-bits forms
+    assert L.bbp_warm_infer_bits(big, None, big, 10, 0.1, 0.1, big, big, 1 << 20, None) == -1
+    assert L.bbp_warm_infer_bits(big, big, big, 10, 0.0, 0.1, big, big, 1 << 20, None) == -1     # p outside (0, 0.75)
+    assert L.bbp_warm_infer_bits(big, big, big, 10, 0.1, 1.5, big, big, 1 << 20, None) == -1     # alpha
+    assert L.bbp_warm_infer_bits(big, big, big, _lib.WARM_MAX_ROWS + 1, 0.1, 0.1, big, big, 1 << 20, None) == -1
+    assert L.bbp_warm_infer_bits(big, big, big, 10, 0.1, 0.1, big, big, _lib.WARM_INFER_WS_BYTES - 1, None) == -3
+    assert L.bbp_warm_infer_bits(big, big, big, 0, 0.1, 0.1, big, None, 0, None) == 0
+    assert L.bbp_message_feature_bits_rows(big, 4, ctypes.byref(c), big, 10, None, big, None) == -1
+    assert L.bbp_message_feature_bits_rows(big, 4, ctypes.byref(c), big, 4 * 120 + 1, big, big, None) == -1
+    assert L.bbp_message_feature_bits_rows(big, 0, ctypes.byref(c), big, 10, big, big, None) == 0
 
 
 def _window_logicals(d, k, I, J, dr):
@@ -232,9 +242,11 @@ def test_learned_decoder_entry_points_check_arguments_on_the_host(L):
     dev_bytes = out.value
     assert L.bbp_decode_warm_workspace_bytes(ctypes.byref(cp), 100, 1, ctypes.byref(out)) == 0
     assert out.value > dev_bytes
-    # Room for the features of the distinct rows (154 per syndrome, 1 KB each)
-    # and the expanded initial messages (480 x 16 floats per syndrome).
-    assert dev_bytes >= 100 * (154 * 1024 + 480 * 64)
+    # Room for the feature bits of the distinct rows (154 per syndrome, 32
+    # bytes each), their proposals (16 floats) and the expanded initial
+    # messages (480 x 16 floats per syndrome); no FP32 feature rows.
+    assert dev_bytes >= 100 * (154 * (32 + 64) + 480 * 64)
+    assert dev_bytes < 100 * (154 * 1024 + 480 * 64)
     for bad in (pkg.DecoderParams(d=11, k=4, algorithm="mps"),
                 pkg.DecoderParams(d=11, k=6, precision="fp32", algorithm="fused"),
                 pkg.DecoderParams(d=1, k=4, algorithm="fused")):
@@ -259,8 +271,9 @@ def test_learned_decoder_entry_points_check_arguments_on_the_host(L):
 def test_register_form_only_shapes_chosen_where_every_block_has_one(L):
     # messages = 3 (every block update in register form) exists for k = 4
     # at odd d (the last block row / column one node wide); at even d the
-    # 3-wide last blocks need the node-by-node path, and bbp_decode_mixed
-    # never takes it (a batch may hold any distance).
+    # 3-wide last blocks need the node-by-node path.  bbp_decode_mixed takes
+    # it only on request, and refuses the request for an even d_max or
+    # k != 4 before any CUDA call.
     out = ctypes.c_size_t(0)
     for d in (5, 11, 13, 21):
         c = pkg.DecoderParams(d=d, k=4, precision="fp32", algorithm="fused", messages=3).c()
@@ -273,6 +286,9 @@ def test_register_form_only_shapes_chosen_where_every_block_has_one(L):
     assert L.bbp_workspace_bytes(ctypes.byref(c), 10, 0, ctypes.byref(out)) == -4
     c = pkg.DecoderParams(d=11, k=4, precision="fp32", algorithm="fused", messages=3).c()
     vp = ctypes.c_void_p
-    fake = vp(256)
-    assert L.bbp_decode_mixed(fake, fake, fake, None, 4, 11, ctypes.byref(c), fake, fake, fake, fake, fake, fake,
+    fake = vp(256)                                  # never dereferenced: both calls return first
+    assert L.bbp_decode_mixed(fake, fake, fake, None, 4, 12, ctypes.byref(c), fake, fake, fake, fake, fake, fake,
+                              1 << 20, None) == -4
+    c3 = pkg.DecoderParams(d=11, k=3, precision="fp32", algorithm="fused", messages=3).c()
+    assert L.bbp_decode_mixed(fake, fake, fake, None, 4, 11, ctypes.byref(c3), fake, fake, fake, fake, fake, fake,
                               1 << 20, None) == -4

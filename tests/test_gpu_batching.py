@@ -188,3 +188,48 @@ def test_mixed_workload_4096_over_five_distances(dev):
         torch.cuda.synchronize()
         assert torch.equal(out["logp"][torch.from_numpy(idx).to(dev)], ref["logp"])
     assert (out["decision"] >= 0).all() and (out["decision"] < 4).all()
+
+
+@pytest.mark.parametrize("precision,warps,cosets", [("fp32", 8, 4), ("fp32", 8, 2), ("fp64", 4, 2)])
+def test_register_form_only_mixed_batch_of_odd_distances(dev, precision, warps, cosets):
+    # A batch whose distances are all odd may take the register-form-only
+    # kernels (launch_messages = 3): the same bits as per-distance decodes.
+    p = 0.1
+    ds, shots = mixed_batch(120, [5, 7, 9, 11, 13], p, 41)
+    packed, offsets, d_of = pack_mixed(shots, device=dev)
+    prm = pkg.DecoderParams(d=0, k=4, p=p, max_iter=12, delta0=1e-4, precision=precision, algorithm="fused",
+                            warps=warps, cosets=cosets, messages=3)
+    out = decode_mixed(packed, offsets, d_of, prm)
+    torch.cuda.synchronize()
+    for d in sorted(set(ds.tolist())):
+        idx = np.nonzero(ds == d)[0]
+        S = np.stack([shots[i] for i in idx])
+        ref = pkg.decode(torch.from_numpy(S).to(dev), pkg.DecoderParams(**{**prm.__dict__, "d": int(d),
+                                                                            "messages": 0, "warps": 0, "cosets": 0}))
+        torch.cuda.synchronize()
+        for key in ("logp", "delta", "iters", "flags", "decision"):
+            assert torch.equal(out[key][torch.from_numpy(idx).to(dev)], ref[key]), (d, key)
+
+
+def test_register_form_only_mixed_batch_flags_an_even_distance(dev):
+    # The caller vouches for odd distances; a syndrome of even distance in
+    # such a batch is flagged (BBP_FLAG_CAPACITY), the others are decoded as
+    # usual; an even d_max is refused on the host.
+    from paper_2402_04834_gb300 import _lib
+    p = 0.1
+    ds = [7, 8, 9, 7, 9, 8]
+    shots = [synth.sample_syndromes(43, i, 1, d, p)[2][0] for i, d in enumerate(ds)]
+    packed, offsets, d_of = pack_mixed(shots, device=dev)
+    lean = pkg.DecoderParams(d=0, k=4, p=p, max_iter=12, delta0=1e-4, precision="fp32", algorithm="fused",
+                             messages=3)
+    out = decode_mixed(packed, offsets, d_of, lean)
+    full = decode_mixed(packed, offsets, d_of, pkg.DecoderParams(**{**lean.__dict__, "messages": 0}))
+    torch.cuda.synchronize()
+    even = np.array(ds) % 2 == 0
+    fl = out["flags"].cpu().numpy()
+    assert np.all(fl[even] & _lib.FLAG_CAPACITY)
+    assert not np.any(fl[~even] & _lib.FLAG_CAPACITY)
+    for key in ("logp", "delta", "iters", "decision"):
+        assert np.array_equal(out[key].cpu().numpy()[~even], full[key].cpu().numpy()[~even]), key
+    with pytest.raises(pkg.BbpError):
+        decode_mixed(packed, offsets, d_of, lean, d_max=10)

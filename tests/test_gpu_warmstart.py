@@ -316,3 +316,30 @@ def test_trained_network_saves_iterations_and_keeps_the_error_rate(dev):
     assert warm <= cold + 3.0 * np.sqrt(max(cold, 1)), ev
     assert ev["decision_agreement"] > 0.99
     assert net.status() == 0
+
+
+@pytest.mark.parametrize("d,k,p", [(11, 4, 0.10), (7, 3, 0.13), (5, 2, 0.05)])
+def test_feature_bits_give_the_same_proposals(dev, d, k, p):
+    # The one-call decoder holds the features as bits (32 bytes a row): the
+    # bits are exactly the nonzero pattern of the FP32 rows, every feature
+    # but 253 (10 p) is 0 or 1, and inference from the bits gives the
+    # messages of inference from the FP32 rows bit for bit.
+    _, _, S = synth.sample_syndromes(synth.workload_seed(2, 3), 0, 300, d, p)
+    s = torch.from_numpy(S).to(dev)
+    prm = pkg.DecoderParams(d=d, k=k, p=p, precision="fp32", algorithm="fused")
+    feats, lens = wsm.features_rows(s, prm)
+    bits, lens_b = wsm.feature_bits_rows(s, prm)
+    torch.cuda.synchronize()
+    f = feats.cpu().numpy()
+    b = bits.cpu().numpy().view(np.uint32)
+    unpacked = ((b[:, :, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(-1, 256)
+    assert np.array_equal(unpacked.astype(bool), f != 0)
+    assert np.all(np.isin(np.delete(f, 253, axis=1), [0.0, 1.0]))
+    assert np.allclose(f[:, 253], 10 * p)
+    assert torch.equal(lens, lens_b)
+    net = wsm.WarmStart(device=dev, seed=4)
+    ref = net.infer(feats, lens, alpha=0.4)
+    got = net.infer_bits(bits, lens_b, p, alpha=0.4)
+    torch.cuda.synchronize()
+    assert torch.equal(ref, got)
+    assert net.status() == 0
