@@ -50,8 +50,8 @@ struct FusedWS {   // (sizes for block side K: slot = FusedDim<K>::slot, vec = F
   T* s0;   // state, G * slot
   T* s1;   // state, G * slot
   T* wn;   // node tensors, 16 per coset
-  T* mt;   // side message A in consumption order, vec per coset
-  T* mb;   // side message B in consumption order, vec per coset
+  T* mt;   // side message A in consumption order, vec per coset (at k = 4 at least two)
+  T* mb;   // side message B in consumption order, vec per coset (at k = 4 at least two)
 };
 
 // lean: every block update of the kernel runs in register form (k = 4,
@@ -62,9 +62,16 @@ BBP_HD int fused_ws_slot(bool lean) {
   return lean ? FusedDim<K>::vec : FusedDim<K>::slot;
 }
 
+// Side-message vectors each of ws.mt / ws.mb holds: one per coset, and at
+// k = 4 at least two (the two half-warp jobs of a register-form pass).
+template <int K>
+BBP_HD int fused_side_vecs(int G) { return K == 4 && G < 2 ? 2 : G; }
+
 template <typename T, int K>
 BBP_HD int fused_ws_bytes(int G, bool lean = false) {
-  return align_up((int)sizeof(T) * G * (2 * fused_ws_slot<T, K>(lean) + 16 + 2 * FusedDim<K>::vec), 16);
+  return align_up((int)sizeof(T) * (G * (2 * fused_ws_slot<T, K>(lean) + 16) +
+                                    2 * fused_side_vecs<K>(G) * FusedDim<K>::vec),
+                  16);
 }
 
 template <typename T, int K>
@@ -76,7 +83,7 @@ __device__ __forceinline__ FusedWS<T> fused_ws_at(unsigned char* base, int G, bo
   w.s1 = p + G * slot;
   w.wn = p + 2 * G * slot;
   w.mt = w.wn + 16 * G;
-  w.mb = w.mt + FusedDim<K>::vec * G;
+  w.mb = w.mt + FusedDim<K>::vec * fused_side_vecs<K>(G);
   return w;
 }
 
@@ -1012,13 +1019,11 @@ __device__ __forceinline__ T gsum16(T v) {
   return v;
 }
 
-// What the register form needs to finish a message update itself (the
-// steps of fused_update): the messages, the message index, the damping
-// and the Delta terms.
+// What the register forms need to finish a message update themselves (the
+// steps of fused_update): the messages, the damping and the Delta terms.
 template <typename T>
 struct QuadUpd {
   T* msgs;
-  int idx;
   T eta, one_m_eta;
   T* ovl;
   int M;
@@ -1027,11 +1032,13 @@ struct QuadUpd {
 // The message update (the steps of fused_update: normalisation, Remark 3;
 // damping with the stored message y, Remark 7; normalisation; the Delta
 // term, Remark 4, FP32 as s (2 - s / 2) with s = ||x - y||^2, FP64 as
-// 2 - 2 <x, y>^2) of coset cq's new 16-entry vector, held one entry per
-// lane of a 16-lane group (entry Rn in this lane), from registers.
+// 2 - 2 <x, y>^2) of coset cq's new 16-entry vector of message idx, held
+// one entry per lane of a 16-lane group (entry Rn in this lane), from
+// registers.
 template <typename T, int K>
-__device__ __forceinline__ void reg_update16(T out, bool on, int cq, int R, int Rn, int stride, const QuadUpd<T>& up) {
-  T* old = up.msgs + cq * stride + up.idx * FusedDim<K>::vec + Rn;
+__device__ __forceinline__ void reg_update16(T out, bool on, int cq, int idx, int R, int Rn, int stride,
+                                             const QuadUpd<T>& up) {
+  T* old = up.msgs + cq * stride + idx * FusedDim<K>::vec + Rn;
   const T y = *old;
   T x = out * inv_norm(gsum16(out * out));
   x = fma(up.one_m_eta, x, up.eta * y);
@@ -1047,16 +1054,16 @@ __device__ __forceinline__ void reg_update16(T out, bool on, int cq, int R, int 
   }
   if (on) {
     *old = x;
-    if (R == 0) up.ovl[cq * up.M + up.idx] = term;
+    if (R == 0) up.ovl[cq * up.M + idx] = term;
   }
 }
 
 // The same for a 2-entry vector (v0, v1) that every lane of the group
 // holds whole; the writer lane stores it.
 template <typename T, int K>
-__device__ __forceinline__ void reg_update2(T v0, T v1, bool on, int cq, bool writer, int stride,
+__device__ __forceinline__ void reg_update2(T v0, T v1, bool on, int cq, int idx, bool writer, int stride,
                                             const QuadUpd<T>& up) {
-  T* old = up.msgs + cq * stride + up.idx * FusedDim<K>::vec;
+  T* old = up.msgs + cq * stride + idx * FusedDim<K>::vec;
   const T y0 = old[0], y1 = old[1];
   T inv = inv_norm(radd(v0 * v0, v1 * v1));
   T x0 = fma(up.one_m_eta, v0 * inv, up.eta * y0), x1 = fma(up.one_m_eta, v1 * inv, up.eta * y1);
@@ -1076,183 +1083,34 @@ __device__ __forceinline__ void reg_update2(T v0, T v1, bool on, int cq, bool wr
   if (on && writer) {
     old[0] = x0;
     old[1] = x1;
-    up.ovl[cq * up.M + up.idx] = term;
+    up.ovl[cq * up.M + idx] = term;
   }
 }
 
-// Register form of a block of one column of 4 nodes (4 x 1 rotated): the
-// column acts as in quad_sweep's column 0, both side messages have one leg.
-template <typename T, int K, bool UPD>
-__device__ __forceinline__ void col_sweep(const FusedWS<T>& ws, T pI, T pE, const T* msgs, int stride,
-                                          unsigned cos_of, int n, const QuadTask qt, const uint16_t* qid,
-                                          int qid_stride, int lane, const QuadUpd<T> up) {
-  constexpr int VEC = FusedDim<K>::vec;
-  const bool rev = qt.flags & kQuadRev;
-  const int qm_in = qt.masks & 15, qm_up = (qt.masks >> 4) & 15, qm_lo = (qt.masks >> 8) & 15;
-  const int R = lane & 15, hi = lane >> 4;
-  const int r1 = (R >> 2) & 1, r3 = R & 1;
-  const int Rn = rev ? bitrev(R, 4) : R;
-  for (int sp = 0; sp < n; sp += 2) {
-    const int slot = sp + hi;
-    const bool on = slot < n;
-    const int cq = slot_coset(cos_of, on ? slot : sp);
-    const T* mq = msgs + cq * stride;
-    const unsigned idv = qid[cq * qid_stride];
-    const int id_up = (int)(idv & 3u), id_lo = (int)((idv >> 2) & 3u);
-    const T x = qt.in_idx >= 0 ? mq[qt.in_idx * VEC + Rn] : ((Rn & qm_in) ? T(0) : T(1));
-    const T a0 = qt.up_idx >= 0 ? mq[qt.up_idx * VEC] : T(1);
-    const T a1 = qt.up_idx >= 0 ? mq[qt.up_idx * VEC + 1] : (qm_up ? T(0) : T(1));
-    const T bb = qt.lo_idx >= 0 ? mq[qt.lo_idx * VEC + r3] : ((r3 && qm_lo) ? T(0) : T(1));
-    T k0, k1, h0, h1, m0, m1;
-    qpair(id_lo, r1 ^ r3, pI, pE, k0, k1);
-    const T u = fma(k1, shx(x, 2), k0 * x);
-    const T uf = shx(u, 8);
-    qpair(id_up, r1, pI, pE, h0, h1);          // top leg 0
-    qpair(id_up, r1 ^ 1, pI, pE, m0, m1);      // top leg 1
-    const T out = bb * fma(a1, fma(m1, uf, m0 * u), a0 * fma(h1, uf, h0 * u));
-    if constexpr (UPD) {
-      reg_update16<T, K>(out, on, cq, R, Rn, stride, up);
-    } else {
-      if (on) ws.s0[(slot << 4) | Rn] = out;
-    }
-  }
-  __syncwarp();
-}
+// One half-warp job of the register forms: coset cq of message idx, with
+// the message's descriptor qt and the coset's qubit ids idv.  Lanes
+// 16 h .. 16 h + 15 of a warp run the job of their half h; a half without a
+// job of the warp's shape repeats the other half's job with on = false (it
+// keeps the warp's shuffles company and stores nothing).  slot: where the
+// read-out takes the outgoing vector (ws.s0, slot << h); sside: the slot of
+// the job's staged side messages in ws.mt / ws.mb (sside << 4).
+struct HalfJob {
+  QuadTask qt;
+  int cq, idx, slot, sside;
+  unsigned idv;
+  bool on;
+};
 
-// Register form of a block of one row of 4 nodes (1 x 4 rotated): a lane
-// takes one assignment of the four side legs that the two qubits see (the
-// legs at the checks are tied to the row leg), the 16 lanes of a coset sum.
-template <typename T, int K, bool UPD>
-__device__ __forceinline__ void row_sweep(const FusedWS<T>& ws, T pI, T pE, const T* msgs, int stride,
-                                          unsigned cos_of, int n, const QuadTask qt, const uint16_t* qid,
-                                          int qid_stride, int lane, const QuadUpd<T> up) {
+// The side messages of the n cosets of cos_of for one message (descriptor
+// qt), staged for the quad and row forms at slot s << 4 of ws.mt / ws.mb:
+// the same contents stage_sides gives one job.
+template <typename T, int K>
+__device__ __forceinline__ void stage_all_sides(const FusedWS<T>& ws, const T* msgs, int stride, const QuadTask& qt,
+                                                unsigned cos_of, int n, int lane) {
   constexpr int VEC = FusedDim<K>::vec;
-  const bool chk0 = qt.flags & kQuadRev, srev = qt.flags & kQuadSideRev;
-  const int qm_in = qt.masks & 15, qm_up = (qt.masks >> 4) & 15, qm_lo = (qt.masks >> 8) & 15;
-  for (int e = lane; e < (n << 4); e += 32) {
-    const int i = e & 15, jj = srev ? bitrev(i, 4) : i;
-    const T* ms = msgs + slot_coset(cos_of, e >> 4) * stride;
-    ws.mt[e] = qt.up_idx >= 0 ? ms[qt.up_idx * VEC + jj] : ((i & qm_up) ? T(0) : T(1));
-    ws.mb[e] = qt.lo_idx >= 0 ? ms[qt.lo_idx * VEC + jj] : ((i & qm_lo) ? T(0) : T(1));
-  }
-  __syncwarp();
-  const int j = lane & 15, hi = lane >> 4;
-  const int x0 = (j >> 3) & 1, x2 = (j >> 2) & 1, y0 = (j >> 1) & 1, y2 = j & 1;
-  for (int sp = 0; sp < n; sp += 2) {
-    const int slot = sp + hi;
-    const bool on = slot < n;
-    const int sl = on ? slot : sp;
-    const int cq = slot_coset(cos_of, sl);
-    const T* mq = msgs + cq * stride;
-    const T* mA = ws.mt + (sl << 4);
-    const T* mB = ws.mb + (sl << 4);
-    const unsigned idv = qid[cq * qid_stride];
-    const int ia = (int)(idv & 3u), ib = (int)((idv >> 2) & 3u);
-    const T in0 = qt.in_idx >= 0 ? mq[qt.in_idx * VEC] : T(1);
-    const T in1 = qt.in_idx >= 0 ? mq[qt.in_idx * VEC + 1] : (qm_in ? T(0) : T(1));
-    T part[2];
-    if (!chk0) {
-      // qubit, check, qubit, check: the lane's legs are (a0, a2, b0, b2);
-      // the checks tie a1 = b1 to the row leg l1 and a3 = b3 to r.
-#pragma unroll
-      for (int r = 0; r < 2; ++r) part[r] = T(0);
-#pragma unroll
-      for (int l1 = 0; l1 < 2; ++l1) {
-        T g0, g1;
-        qpair(ia, x0 ^ y0, pI, pE, g0, g1);
-        const T hh = l1 ? in0 * g1 + in1 * g0 : in0 * g0 + in1 * g1;
-#pragma unroll
-        for (int r = 0; r < 2; ++r)
-          part[r] += hh * mA[(x0 << 3) | (l1 << 2) | (x2 << 1) | r] * mB[(y0 << 3) | (l1 << 2) | (y2 << 1) | r] *
-                     qval(ib, l1 ^ r, x2 ^ y2, pI, pE);
-      }
-    } else {
-      // check, qubit, check, qubit: the lane's legs are (a1, a3, b1, b3); the
-      // checks tie a0 = b0 = l0 and a2 = b2 = l2.
-      part[0] = part[1] = T(0);
-#pragma unroll
-      for (int l0 = 0; l0 < 2; ++l0)
-#pragma unroll
-        for (int l2 = 0; l2 < 2; ++l2) {
-          const T w = (l0 ? in1 : in0) * mA[(l0 << 3) | (x0 << 2) | (l2 << 1) | x2] *
-                      mB[(l0 << 3) | (y0 << 2) | (l2 << 1) | y2] * qval(ia, l0 ^ l2, x0 ^ y0, pI, pE);
-          part[0] += w * qval(ib, l2, x2 ^ y2, pI, pE);
-          part[1] += w * qval(ib, l2 ^ 1, x2 ^ y2, pI, pE);
-        }
-    }
-#pragma unroll
-    for (int m = 8; m >= 1; m >>= 1) {
-      part[0] += shx(part[0], m);
-      part[1] += shx(part[1], m);
-    }
-    if constexpr (UPD) {
-      reg_update2<T, K>(part[0], part[1], on, cq, j == 0, stride, up);
-    } else {
-      if (on && j < 2) ws.s0[(slot << 1) | j] = j ? part[1] : part[0];
-    }
-  }
-  __syncwarp();
-}
-
-// Register form of a single node (1 x 1): lane (l, a, b, r) of the node's
-// legs, summed over l, a, b.
-template <typename T, int K, bool UPD>
-__device__ __forceinline__ void dot_sweep(const FusedWS<T>& ws, T pI, T pE, const T* msgs, int stride,
-                                          unsigned cos_of, int n, const QuadTask qt, const uint16_t* qid,
-                                          int qid_stride, int lane, const QuadUpd<T> up) {
-  constexpr int VEC = FusedDim<K>::vec;
-  const bool chk = qt.flags & kQuadRev;
-  const int qm_in = qt.masks & 15, qm_up = (qt.masks >> 4) & 15, qm_lo = (qt.masks >> 8) & 15;
-  const int j = lane & 15, hi = lane >> 4;
-  const int l = (j >> 3) & 1, a = (j >> 2) & 1, b = (j >> 1) & 1, r = j & 1;
-  for (int sp = 0; sp < n; sp += 2) {
-    const int slot = sp + hi;
-    const bool on = slot < n;
-    const int cq = slot_coset(cos_of, on ? slot : sp);
-    const T* mq = msgs + cq * stride;
-    const int id = (int)(qid[cq * qid_stride] & 3u);
-    const T mi = qt.in_idx >= 0 ? mq[qt.in_idx * VEC + l] : ((l && qm_in) ? T(0) : T(1));
-    const T ma = qt.up_idx >= 0 ? mq[qt.up_idx * VEC + a] : ((a && qm_up) ? T(0) : T(1));
-    const T mb = qt.lo_idx >= 0 ? mq[qt.lo_idx * VEC + b] : ((b && qm_lo) ? T(0) : T(1));
-    const T nv = chk ? ((l == r && a == r && b == r) ? T(1) : T(0)) : qval(id, l ^ r, a ^ b, pI, pE);
-    T v = mi * ma * mb * nv;
-    v += shx(v, 8);
-    v += shx(v, 4);
-    v += shx(v, 2);
-    if constexpr (UPD) {
-      const T w = shx(v, 1);                   // the other entry
-      reg_update2<T, K>(r ? w : v, r ? v : w, on, cq, j == 0, stride, up);
-    } else {
-      if (on && j < 2) ws.s0[(slot << 1) | j] = v;
-    }
-  }
-  __syncwarp();
-}
-
-// The outgoing vectors of a 4 x 4 block (f.h == f.ncols == 4) for the n
-// cosets of cos_of, into ws.s0 (slot s at s << 4), as fused_sweep leaves
-// them; with UPD the message update itself instead (normalisation, Remark
-// 3; damping, Remark 7; the Delta term, Remark 4), from registers.
-// Columns t = 0..3 hold qubits at chain positions {0, 2} or {1, 3},
-// alternating from column to column.  Both node tensors are symmetric in
-// their two chain legs, so reading the chain bottom to top (position
-// s' = 3 - s, the side messages exchanged) turns a block whose column 0
-// starts with a check into one whose column 0 starts with a qubit; only
-// that case is written out.
-// qid[q * qid_stride] holds the qubit ids of coset q (quad_ids).
-template <typename T, int K, bool UPD>
-__device__ __forceinline__ void quad_sweep(const FusedWS<T>& ws, T pI, T pE, const T* msgs, int stride,
-                                           unsigned cos_of, int n, const QuadTask qt, const uint16_t* qid,
-                                           int qid_stride, int lane, const QuadUpd<T> up) {
-  constexpr int VEC = FusedDim<K>::vec;
-  const bool rev = qt.flags & kQuadRev, srev = qt.flags & kQuadSideRev;
-  const int qm_in = qt.masks & 15, qm_up = (qt.masks >> 4) & 15, qm_lo = (qt.masks >> 8) & 15;
-  // The side messages in consumption order, the upper one (attached at
-  // s' = 0) in ws.mt and the lower one in ws.mb, slot q at q << 4, a lane
-  // per (slot, side, quarter of the vector).  A side on the grid border has
-  // no message: the product vector of its nodes' missing legs (1 for a
-  // check, e_0 for a qubit), bit 3 - t for column t.
-  for (int t = lane; t < (n << 3); t += 32) {
+  const bool srev = qt.flags & kQuadSideRev;
+  const int qm_up = (qt.masks >> 4) & 15, qm_lo = (qt.masks >> 8) & 15;
+  for (int t = lane; t < (n << 3); t += 32) {            // a lane per (slot, side, quarter)
     const int sl = t >> 3, side = (t >> 2) & 1, i0 = (t & 3) << 2;
     const int midx = side ? qt.lo_idx : qt.up_idx;
     const int qm = side ? qm_lo : qm_up;
@@ -1272,126 +1130,358 @@ __device__ __forceinline__ void quad_sweep(const FusedWS<T>& ws, T pI, T pE, con
     vstore4((side ? ws.mb : ws.mt) + (sl << 4) + i0, v);
   }
   __syncwarp();
+}
+
+// The side messages of a job in consumption order, the upper one (attached
+// at s' = 0) in ws.mt and the lower one in ws.mb, half h at h << 4, entries
+// 4 u .. 4 u + 3 per lane (lanes 0 .. 7 of the half; messages and buffers
+// are 16-byte aligned).  A side on the grid border has no message: the
+// product vector of its nodes' missing legs (1 for a check, e_0 for a
+// qubit), bit n - 1 - t for node t.
+template <typename T, int K>
+__device__ __forceinline__ void stage_sides(const FusedWS<T>& ws, const T* msgs, int stride, const HalfJob& jb,
+                                            int lane) {
+  constexpr int VEC = FusedDim<K>::vec;
+  const int t = lane & 15, hi = lane >> 4;
+  if (t < 8) {
+    const bool srev = jb.qt.flags & kQuadSideRev;
+    const int side = t >> 2, i0 = (t & 3) << 2;
+    const int midx = side ? jb.qt.lo_idx : jb.qt.up_idx;
+    const int qm = side ? (jb.qt.masks >> 8) & 15 : (jb.qt.masks >> 4) & 15;
+    T v[4];
+    if (midx >= 0) {
+      const T* ms = msgs + jb.cq * stride + midx * VEC;
+      if (srev) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = ms[bitrev(i0 + u, 4)];
+      } else {
+        vcopy4(ms + i0, v);
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = ((i0 + u) & qm) ? T(0) : T(1);
+    }
+    vstore4((side ? ws.mb : ws.mt) + (hi << 4) + i0, v);
+  }
+  __syncwarp();
+}
+
+// Register form of a block of one column of 4 nodes (4 x 1 rotated): the
+// column acts as in quad_pass's column 0, both side messages have one leg.
+template <typename T, int K, bool UPD>
+__device__ __forceinline__ void col_pass(const FusedWS<T>& ws, T pI, T pE, const T* msgs, int stride,
+                                         const HalfJob& jb, int lane, const QuadUpd<T>& upd) {
+  constexpr int VEC = FusedDim<K>::vec;
+  const QuadTask& qt = jb.qt;
+  const bool rev = qt.flags & kQuadRev;
+  const int qm_in = qt.masks & 15, qm_up = (qt.masks >> 4) & 15, qm_lo = (qt.masks >> 8) & 15;
+  const int R = lane & 15;
+  const int r1 = (R >> 2) & 1, r3 = R & 1;
+  const int Rn = rev ? bitrev(R, 4) : R;
+  const T* mq = msgs + jb.cq * stride;
+  const int id_up = (int)(jb.idv & 3u), id_lo = (int)((jb.idv >> 2) & 3u);
+  const T x = qt.in_idx >= 0 ? mq[qt.in_idx * VEC + Rn] : ((Rn & qm_in) ? T(0) : T(1));
+  const T a0 = qt.up_idx >= 0 ? mq[qt.up_idx * VEC] : T(1);
+  const T a1 = qt.up_idx >= 0 ? mq[qt.up_idx * VEC + 1] : (qm_up ? T(0) : T(1));
+  const T bb = qt.lo_idx >= 0 ? mq[qt.lo_idx * VEC + r3] : ((r3 && qm_lo) ? T(0) : T(1));
+  T k0, k1, h0, h1, m0, m1;
+  qpair(id_lo, r1 ^ r3, pI, pE, k0, k1);
+  const T u = fma(k1, shx(x, 2), k0 * x);
+  const T uf = shx(u, 8);
+  qpair(id_up, r1, pI, pE, h0, h1);          // top leg 0
+  qpair(id_up, r1 ^ 1, pI, pE, m0, m1);      // top leg 1
+  const T out = bb * fma(a1, fma(m1, uf, m0 * u), a0 * fma(h1, uf, h0 * u));
+  if constexpr (UPD) {
+    reg_update16<T, K>(out, jb.on, jb.cq, jb.idx, R, Rn, stride, upd);
+  } else {
+    if (jb.on) ws.s0[(jb.slot << 4) | Rn] = out;
+  }
+  __syncwarp();
+}
+
+// Register form of a block of one row of 4 nodes (1 x 4 rotated): a lane
+// takes one assignment of the four side legs that the two qubits see (the
+// legs at the checks are tied to the row leg), the 16 lanes of a coset sum.
+template <typename T, int K, bool UPD, bool STAGE>
+__device__ __forceinline__ void row_pass(const FusedWS<T>& ws, T pI, T pE, const T* msgs, int stride,
+                                         const HalfJob& jb, int lane, const QuadUpd<T>& upd) {
+  constexpr int VEC = FusedDim<K>::vec;
+  const QuadTask& qt = jb.qt;
+  const bool chk0 = qt.flags & kQuadRev, srev = qt.flags & kQuadSideRev;
+  const int qm_in = qt.masks & 15, qm_up = (qt.masks >> 4) & 15, qm_lo = (qt.masks >> 8) & 15;
+  const int j = lane & 15, hi = lane >> 4;
+  const T* mq = msgs + jb.cq * stride;
+  if constexpr (STAGE) {                     // this job's side messages at slot hi
+    const int jj = srev ? bitrev(j, 4) : j;
+    ws.mt[(hi << 4) | j] = qt.up_idx >= 0 ? mq[qt.up_idx * VEC + jj] : ((j & qm_up) ? T(0) : T(1));
+    ws.mb[(hi << 4) | j] = qt.lo_idx >= 0 ? mq[qt.lo_idx * VEC + jj] : ((j & qm_lo) ? T(0) : T(1));
+    __syncwarp();
+  }
+  const int x0 = (j >> 3) & 1, x2 = (j >> 2) & 1, y0 = (j >> 1) & 1, y2 = j & 1;
+  const T* mA = ws.mt + (jb.sside << 4);
+  const T* mB = ws.mb + (jb.sside << 4);
+  const int ia = (int)(jb.idv & 3u), ib = (int)((jb.idv >> 2) & 3u);
+  const T in0 = qt.in_idx >= 0 ? mq[qt.in_idx * VEC] : T(1);
+  const T in1 = qt.in_idx >= 0 ? mq[qt.in_idx * VEC + 1] : (qm_in ? T(0) : T(1));
+  T part[2];
+  if (!chk0) {
+    // qubit, check, qubit, check: the lane's legs are (a0, a2, b0, b2);
+    // the checks tie a1 = b1 to the row leg l1 and a3 = b3 to r.
+#pragma unroll
+    for (int r = 0; r < 2; ++r) part[r] = T(0);
+#pragma unroll
+    for (int l1 = 0; l1 < 2; ++l1) {
+      T g0, g1;
+      qpair(ia, x0 ^ y0, pI, pE, g0, g1);
+      const T hh = l1 ? in0 * g1 + in1 * g0 : in0 * g0 + in1 * g1;
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+        part[r] += hh * mA[(x0 << 3) | (l1 << 2) | (x2 << 1) | r] * mB[(y0 << 3) | (l1 << 2) | (y2 << 1) | r] *
+                   qval(ib, l1 ^ r, x2 ^ y2, pI, pE);
+    }
+  } else {
+    // check, qubit, check, qubit: the lane's legs are (a1, a3, b1, b3); the
+    // checks tie a0 = b0 = l0 and a2 = b2 = l2.
+    part[0] = part[1] = T(0);
+#pragma unroll
+    for (int l0 = 0; l0 < 2; ++l0)
+#pragma unroll
+      for (int l2 = 0; l2 < 2; ++l2) {
+        const T w = (l0 ? in1 : in0) * mA[(l0 << 3) | (x0 << 2) | (l2 << 1) | x2] *
+                    mB[(l0 << 3) | (y0 << 2) | (l2 << 1) | y2] * qval(ia, l0 ^ l2, x0 ^ y0, pI, pE);
+        part[0] += w * qval(ib, l2, x2 ^ y2, pI, pE);
+        part[1] += w * qval(ib, l2 ^ 1, x2 ^ y2, pI, pE);
+      }
+  }
+#pragma unroll
+  for (int m = 8; m >= 1; m >>= 1) {
+    part[0] += shx(part[0], m);
+    part[1] += shx(part[1], m);
+  }
+  if constexpr (UPD) {
+    reg_update2<T, K>(part[0], part[1], jb.on, jb.cq, jb.idx, j == 0, stride, upd);
+  } else {
+    if (jb.on && j < 2) ws.s0[(jb.slot << 1) | j] = j ? part[1] : part[0];
+  }
+  __syncwarp();
+}
+
+// Register form of a single node (1 x 1): lane (l, a, b, r) of the node's
+// legs, summed over l, a, b.
+template <typename T, int K, bool UPD>
+__device__ __forceinline__ void dot_pass(const FusedWS<T>& ws, T pI, T pE, const T* msgs, int stride,
+                                         const HalfJob& jb, int lane, const QuadUpd<T>& upd) {
+  constexpr int VEC = FusedDim<K>::vec;
+  const QuadTask& qt = jb.qt;
+  const bool chk = qt.flags & kQuadRev;
+  const int qm_in = qt.masks & 15, qm_up = (qt.masks >> 4) & 15, qm_lo = (qt.masks >> 8) & 15;
+  const int j = lane & 15;
+  const int l = (j >> 3) & 1, a = (j >> 2) & 1, b = (j >> 1) & 1, r = j & 1;
+  const T* mq = msgs + jb.cq * stride;
+  const int id = (int)(jb.idv & 3u);
+  const T mi = qt.in_idx >= 0 ? mq[qt.in_idx * VEC + l] : ((l && qm_in) ? T(0) : T(1));
+  const T ma = qt.up_idx >= 0 ? mq[qt.up_idx * VEC + a] : ((a && qm_up) ? T(0) : T(1));
+  const T mb = qt.lo_idx >= 0 ? mq[qt.lo_idx * VEC + b] : ((b && qm_lo) ? T(0) : T(1));
+  const T nv = chk ? ((l == r && a == r && b == r) ? T(1) : T(0)) : qval(id, l ^ r, a ^ b, pI, pE);
+  T v = mi * ma * mb * nv;
+  v += shx(v, 8);
+  v += shx(v, 4);
+  v += shx(v, 2);
+  if constexpr (UPD) {
+    const T w = shx(v, 1);                     // the other entry
+    reg_update2<T, K>(r ? w : v, r ? v : w, jb.on, jb.cq, jb.idx, j == 0, stride, upd);
+  } else {
+    if (jb.on && j < 2) ws.s0[(jb.slot << 1) | j] = v;
+  }
+  __syncwarp();
+}
+
+// The outgoing vector of a 4 x 4 block (f.h == f.ncols == 4) for a job,
+// into ws.s0 at the job's slot (slot << 4), as fused_sweep leaves it; with
+// UPD the message update itself instead (normalisation, Remark 3; damping,
+// Remark 7; the Delta term, Remark 4), from registers.  Columns t = 0..3
+// hold qubits at chain positions {0, 2} or {1, 3}, alternating from column
+// to column.  Both node tensors are symmetric in their two chain legs, so
+// reading the chain bottom to top (position s' = 3 - s, the side messages
+// exchanged) turns a block whose column 0 starts with a check into one
+// whose column 0 starts with a qubit; only that case is written out.
+template <typename T, int K, bool UPD, bool STAGE>
+__device__ __forceinline__ void quad_pass(const FusedWS<T>& ws, T pI, T pE, const T* msgs, int stride,
+                                          const HalfJob& jb, int lane, const QuadUpd<T>& upd) {
+  constexpr int VEC = FusedDim<K>::vec;
+  const QuadTask& qt = jb.qt;
+  if constexpr (STAGE) stage_sides<T, K>(ws, msgs, stride, jb, lane);   // at slot hi
+  const bool rev = qt.flags & kQuadRev;
+  const int qm_in = qt.masks & 15;
   const int R = lane & 15, hi = lane >> 4;
   const int r0 = (R >> 3) & 1, r1 = (R >> 2) & 1, r2 = (R >> 1) & 1, r3 = R & 1;
   const int Rn = rev ? bitrev(R, 4) : R;                     // the lane's row in the block's own order
-  for (int sp = 0; sp < n; sp += 2) {
-    const int slot = sp + hi;
-    const bool on = slot < n;
-    const int sl = on ? slot : sp;
-    const int cq = slot_coset(cos_of, sl);
-    const T* mA = ws.mt + (sl << 4);
-    const T* mB = ws.mb + (sl << 4);
-    const unsigned idv = qid[cq * qid_stride];
-    int id[4][2];
+  const int cq = jb.cq;
+  const T* mA = ws.mt + (jb.sside << 4);
+  const T* mB = ws.mb + (jb.sside << 4);
+  int id[4][2];
 #pragma unroll
-    for (int t = 0; t < 4; ++t)
+  for (int t = 0; t < 4; ++t)
 #pragma unroll
-      for (int u = 0; u < 2; ++u) id[t][u] = (int)((idv >> (2 * (2 * t + u))) & 3u);
-    const T x = qt.in_idx >= 0 ? msgs[cq * stride + qt.in_idx * VEC + Rn] : ((Rn & qm_in) ? T(0) : T(1));
-    // Column 0 (qubits at 0, 2): the upper leg a0 is recorded, the lower leg
-    // b0 is tied to r3 by the check at 3.
-    T S0[2];
-    {
-      T k0, k1;
-      qpair(id[0][1], r1 ^ r3, pI, pE, k0, k1);
-      const T u = fma(k1, shx(x, 2), k0 * x);
-      const T up = shx(u, 8);
-#pragma unroll
-      for (int a0 = 0; a0 < 2; ++a0) {
-        T h0, h1;
-        qpair(id[0][0], a0 ^ r1, pI, pE, h0, h1);
-        S0[a0] = fma(h1, up, h0 * u);
-      }
-    }
-    // Column 2's coefficients: the lower qubit (c2k0, c2k1) and the upper
-    // one, g[l0 ^ r0][v ^ r1] for v = 0, 1.
-    T c2k0, c2k1, g00, g01, g10, g11;
-    qpair(id[2][1], r1 ^ r3, pI, pE, c2k0, c2k1);
-    qpair(id[2][0], r1, pI, pE, g00, g10);                   // v = 0
-    qpair(id[2][0], r1 ^ 1, pI, pE, g01, g11);               // v = 1
-    // Column 1 (qubits at 1, 3): a1 is tied to r0 by the check at 0; the
-    // lower leg b1 is recorded.  S1[b0][b1] for one a0 at a time, folded
-    // into column 2 at once.  Column 2 (qubits at 0, 2) is the data column
-    // of both side messages: the upper leg v is summed against A[a0 a1 v e],
-    // the lower leg w = r3 against B[b0 b1 w f].
-    T h0, h1;
-    qpair(id[1][0], r0 ^ r2, pI, pE, h0, h1);
-    T kk0[2], kk1[2];                                        // [b1], for b0 = 0, 1
-#pragma unroll
-    for (int b1 = 0; b1 < 2; ++b1) {
-      T k0, k1;
-      qpair(id[1][1], r2 ^ b1, pI, pE, k0, k1);
-      kk0[b1] = r3 ? k1 : k0;
-      kk1[b1] = r3 ? k0 : k1;
-    }
-    T Y[2][2][2];                                            // [e][b0][b1]
+    for (int u = 0; u < 2; ++u) id[t][u] = (int)((jb.idv >> (2 * (2 * t + u))) & 3u);
+  const T x = qt.in_idx >= 0 ? msgs[cq * stride + qt.in_idx * VEC + Rn] : ((Rn & qm_in) ? T(0) : T(1));
+  // Column 0 (qubits at 0, 2): the upper leg a0 is recorded, the lower leg
+  // b0 is tied to r3 by the check at 3.
+  T S0[2];
+  {
+    T k0, k1;
+    qpair(id[0][1], r1 ^ r3, pI, pE, k0, k1);
+    const T u = fma(k1, shx(x, 2), k0 * x);
+    const T uf = shx(u, 8);
 #pragma unroll
     for (int a0 = 0; a0 < 2; ++a0) {
-      T S1[2][2];
-      {
-        const T o = S0[a0], p = shx(o, 1);
-        const T X0 = r3 ? p : o, X1 = r3 ? o : p;
-#pragma unroll
-        for (int b1 = 0; b1 < 2; ++b1) {
-          const T y0 = kk0[b1] * X0, y1 = kk1[b1] * X1;
-          S1[0][b1] = fma(h1, shx(y0, 4), h0 * y0);
-          S1[1][b1] = fma(h1, shx(y1, 4), h0 * y1);
-        }
-      }
-      // A0: row bit 0 kept (l0 = r0 = a1), A1: flipped (l0 = a1 = !r0).
-      T m0[4], m1[4];
-      vcopy4(mA + (a0 << 3) + (r0 << 2), m0);
-      vcopy4(mA + (a0 << 3) + ((r0 ^ 1) << 2), m1);
-      const T A00 = fma(m0[2], g01, m0[0] * g00), A01 = fma(m0[3], g01, m0[1] * g00);   // e = 0, 1
-      const T A10 = fma(m1[2], g11, m1[0] * g10), A11 = fma(m1[3], g11, m1[1] * g10);
-#pragma unroll
-      for (int b0 = 0; b0 < 2; ++b0)
-#pragma unroll
-        for (int b1 = 0; b1 < 2; ++b1) {
-          const T s1 = S1[b0][b1];
-          const T u = fma(c2k1, shx(s1, 2), c2k0 * s1);
-          const T up = shx(u, 8);
-          if (a0 == 0) {
-            Y[0][b0][b1] = fma(A00, u, A10 * up);
-            Y[1][b0][b1] = fma(A01, u, A11 * up);
-          } else {
-            Y[0][b0][b1] = fma(A00, u, fma(A10, up, Y[0][b0][b1]));
-            Y[1][b0][b1] = fma(A01, u, fma(A11, up, Y[1][b0][b1]));
-          }
-        }
-    }
-    T S2[2][2];
-    {
-      const T* mb = mB + (r3 << 1);                          // B[b0 b1 r3 ff] at mb[4 (2 b0 + b1) + ff]
-#pragma unroll
-      for (int e = 0; e < 2; ++e)
-#pragma unroll
-        for (int ff = 0; ff < 2; ++ff)
-          S2[e][ff] = fma(mb[12 + ff], Y[e][1][1], fma(mb[8 + ff], Y[e][1][0], fma(mb[4 + ff], Y[e][0][1],
-                                                                                mb[ff] * Y[e][0][0])));
-    }
-    // Column 3 (qubits at 1, 3): the upper leg e is tied to r0, the lower
-    // leg f closes against B's expected value.
-    T out;
-    {
-      const T z0 = r0 ? S2[1][0] : S2[0][0], z1 = r0 ? S2[1][1] : S2[0][1];
-      const T p0 = shx(z0, 1), p1 = shx(z1, 1);
-      T k0, k1, m0, m1;
-      qpair(id[3][1], r2, pI, pE, k0, k1);
-      qpair(id[3][1], r2 ^ 1, pI, pE, m0, m1);
-      const T uu = fma(m1, p1, fma(m0, z1, fma(k1, p0, k0 * z0)));
-      T g0, g1;
-      qpair(id[3][0], r0 ^ r2, pI, pE, g0, g1);
-      out = fma(g1, shx(uu, 4), g0 * uu);
-    }
-    if constexpr (UPD) {
-      reg_update16<T, K>(out, on, cq, R, Rn, stride, up);
-    } else {
-      if (on) ws.s0[(slot << 4) | Rn] = out;
+      T h0, h1;
+      qpair(id[0][0], a0 ^ r1, pI, pE, h0, h1);
+      S0[a0] = fma(h1, uf, h0 * u);
     }
   }
+  // Column 2's coefficients: the lower qubit (c2k0, c2k1) and the upper
+  // one, g[l0 ^ r0][v ^ r1] for v = 0, 1.
+  T c2k0, c2k1, g00, g01, g10, g11;
+  qpair(id[2][1], r1 ^ r3, pI, pE, c2k0, c2k1);
+  qpair(id[2][0], r1, pI, pE, g00, g10);                   // v = 0
+  qpair(id[2][0], r1 ^ 1, pI, pE, g01, g11);               // v = 1
+  // Column 1 (qubits at 1, 3): a1 is tied to r0 by the check at 0; the
+  // lower leg b1 is recorded.  S1[b0][b1] for one a0 at a time, folded
+  // into column 2 at once.  Column 2 (qubits at 0, 2) is the data column
+  // of both side messages: the upper leg v is summed against A[a0 a1 v e],
+  // the lower leg w = r3 against B[b0 b1 w f].
+  T h0, h1;
+  qpair(id[1][0], r0 ^ r2, pI, pE, h0, h1);
+  T kk0[2], kk1[2];                                        // [b1], for b0 = 0, 1
+#pragma unroll
+  for (int b1 = 0; b1 < 2; ++b1) {
+    T k0, k1;
+    qpair(id[1][1], r2 ^ b1, pI, pE, k0, k1);
+    kk0[b1] = r3 ? k1 : k0;
+    kk1[b1] = r3 ? k0 : k1;
+  }
+  T Y[2][2][2];                                            // [e][b0][b1]
+#pragma unroll
+  for (int a0 = 0; a0 < 2; ++a0) {
+    T S1[2][2];
+    {
+      const T o = S0[a0], p = shx(o, 1);
+      const T X0 = r3 ? p : o, X1 = r3 ? o : p;
+#pragma unroll
+      for (int b1 = 0; b1 < 2; ++b1) {
+        const T y0 = kk0[b1] * X0, y1 = kk1[b1] * X1;
+        S1[0][b1] = fma(h1, shx(y0, 4), h0 * y0);
+        S1[1][b1] = fma(h1, shx(y1, 4), h0 * y1);
+      }
+    }
+    // A0: row bit 0 kept (l0 = r0 = a1), A1: flipped (l0 = a1 = !r0).
+    T m0[4], m1[4];
+    vcopy4(mA + (a0 << 3) + (r0 << 2), m0);
+    vcopy4(mA + (a0 << 3) + ((r0 ^ 1) << 2), m1);
+    const T A00 = fma(m0[2], g01, m0[0] * g00), A01 = fma(m0[3], g01, m0[1] * g00);   // e = 0, 1
+    const T A10 = fma(m1[2], g11, m1[0] * g10), A11 = fma(m1[3], g11, m1[1] * g10);
+#pragma unroll
+    for (int b0 = 0; b0 < 2; ++b0)
+#pragma unroll
+      for (int b1 = 0; b1 < 2; ++b1) {
+        const T s1 = S1[b0][b1];
+        const T u = fma(c2k1, shx(s1, 2), c2k0 * s1);
+        const T uf = shx(u, 8);
+        if (a0 == 0) {
+          Y[0][b0][b1] = fma(A00, u, A10 * uf);
+          Y[1][b0][b1] = fma(A01, u, A11 * uf);
+        } else {
+          Y[0][b0][b1] = fma(A00, u, fma(A10, uf, Y[0][b0][b1]));
+          Y[1][b0][b1] = fma(A01, u, fma(A11, uf, Y[1][b0][b1]));
+        }
+      }
+  }
+  T S2[2][2];
+  {
+    const T* mb = mB + (r3 << 1);                          // B[b0 b1 r3 ff] at mb[4 (2 b0 + b1) + ff]
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+#pragma unroll
+      for (int ff = 0; ff < 2; ++ff)
+        S2[e][ff] = fma(mb[12 + ff], Y[e][1][1], fma(mb[8 + ff], Y[e][1][0], fma(mb[4 + ff], Y[e][0][1],
+                                                                              mb[ff] * Y[e][0][0])));
+  }
+  // Column 3 (qubits at 1, 3): the upper leg e is tied to r0, the lower
+  // leg f closes against B's expected value.
+  T out;
+  {
+    const T z0 = r0 ? S2[1][0] : S2[0][0], z1 = r0 ? S2[1][1] : S2[0][1];
+    const T p0 = shx(z0, 1), p1 = shx(z1, 1);
+    T k0, k1, m0, m1;
+    qpair(id[3][1], r2, pI, pE, k0, k1);
+    qpair(id[3][1], r2 ^ 1, pI, pE, m0, m1);
+    const T uu = fma(m1, p1, fma(m0, z1, fma(k1, p0, k0 * z0)));
+    T g0, g1;
+    qpair(id[3][0], r0 ^ r2, pI, pE, g0, g1);
+    out = fma(g1, shx(uu, 4), g0 * uu);
+  }
+  if constexpr (UPD) {
+    reg_update16<T, K>(out, jb.on, cq, jb.idx, R, Rn, stride, upd);
+  } else {
+    if (jb.on) ws.s0[(jb.slot << 4) | Rn] = out;
+  }
   __syncwarp();
+}
+
+// Every iterating coset of one message in passes of two (cosets sp + h in
+// half h), the side messages staged by the caller (stage_all_sides); the
+// shape is dispatched once, outside the passes.
+template <typename T, int K, int SHAPE, bool UPD>
+__device__ __forceinline__ void msg_passes(const FusedWS<T>& ws, T pI, T pE, const T* msgs, int stride,
+                                           const QuadTask& qt, int idx, unsigned cos_of, int n, const uint16_t* qid,
+                                           int qid_stride, int lane, const QuadUpd<T>& upd) {
+  const int hi = lane >> 4;
+  for (int sp = 0; sp < n; sp += 2) {
+    HalfJob jb;
+    jb.on = sp + hi < n;
+    const int sl = jb.on ? sp + hi : sp;
+    jb.cq = slot_coset(cos_of, sl);
+    jb.idx = idx;
+    jb.slot = jb.sside = sl;
+    jb.qt = qt;
+    jb.idv = qid[jb.cq * qid_stride];
+    if constexpr (SHAPE == kShapeQuad) quad_pass<T, K, UPD, false>(ws, pI, pE, msgs, stride, jb, lane, upd);
+    else if constexpr (SHAPE == kShapeCol) col_pass<T, K, UPD>(ws, pI, pE, msgs, stride, jb, lane, upd);
+    else if constexpr (SHAPE == kShapeRow) row_pass<T, K, UPD, false>(ws, pI, pE, msgs, stride, jb, lane, upd);
+    else dot_pass<T, K, UPD>(ws, pI, pE, msgs, stride, jb, lane, upd);
+  }
+}
+
+template <typename T, int K, bool UPD>
+__device__ __forceinline__ void msg_register_form(int shape, const FusedWS<T>& ws, T pI, T pE, const T* msgs,
+                                                  int stride, const QuadTask& qt, int idx, unsigned cos_of, int n,
+                                                  const uint16_t* qid, int qid_stride, int lane,
+                                                  const QuadUpd<T>& upd) {
+  if (shape == kShapeQuad || shape == kShapeRow) stage_all_sides<T, K>(ws, msgs, stride, qt, cos_of, n, lane);
+  if (shape == kShapeQuad)
+    msg_passes<T, K, kShapeQuad, UPD>(ws, pI, pE, msgs, stride, qt, idx, cos_of, n, qid, qid_stride, lane, upd);
+  else if (shape == kShapeCol)
+    msg_passes<T, K, kShapeCol, UPD>(ws, pI, pE, msgs, stride, qt, idx, cos_of, n, qid, qid_stride, lane, upd);
+  else if (shape == kShapeRow)
+    msg_passes<T, K, kShapeRow, UPD>(ws, pI, pE, msgs, stride, qt, idx, cos_of, n, qid, qid_stride, lane, upd);
+  else
+    msg_passes<T, K, kShapeDot, UPD>(ws, pI, pE, msgs, stride, qt, idx, cos_of, n, qid, qid_stride, lane, upd);
+}
+
+// Message item of coset job j when every message has n jobs.
+__device__ __forceinline__ int job_item(int j, int n) { return n == 4 ? j >> 2 : n == 2 ? j >> 1 : n == 1 ? j : j / 3; }
+
+// A job of any register form (shape: the warp's, the same in both halves).
+// STAGE: the quad and row forms stage the job's side messages themselves
+// (at slot hi, sside = hi); else the caller has (stage_all_sides).
+template <typename T, int K, bool UPD, bool STAGE>
+__device__ __forceinline__ void reg_pass(int shape, const FusedWS<T>& ws, T pI, T pE, const T* msgs, int stride,
+                                         const HalfJob& jb, int lane, const QuadUpd<T>& upd) {
+  if (shape == kShapeQuad) quad_pass<T, K, UPD, STAGE>(ws, pI, pE, msgs, stride, jb, lane, upd);
+  else if (shape == kShapeCol) col_pass<T, K, UPD>(ws, pI, pE, msgs, stride, jb, lane, upd);
+  else if (shape == kShapeRow) row_pass<T, K, UPD, STAGE>(ws, pI, pE, msgs, stride, jb, lane, upd);
+  else dot_pass<T, K, UPD>(ws, pI, pE, msgs, stride, jb, lane, upd);
 }
 
 // Resident CTAs per SM the register budget is sized for: with one coset per
@@ -1437,7 +1527,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
   T* msgs = GM ? gmsgs : reinterpret_cast<T*>(smem + Lo.msgs);
   const int stride = M * VEC;                                // messages of one coset
 
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, hi = lane >> 4;
   const FusedWS<T> ws = fused_ws_at<T, K>(smem + Lo.ws + warp * Lo.ws_stride, G, kLean);
 
   for (int i = tid; i < m; i += NW * 32) synd[i] = syn_src[i];
@@ -1507,6 +1597,37 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
     }
     __syncthreads();
   }
+  // Each colour's list: the messages of the register forms first, grouped
+  // by shape (a warp pass pairs two coset jobs of one shape), their count
+  // in misc[5 + colour]; then those of the node-by-node path.  The order
+  // within a colour does not matter: its messages read only the other
+  // colour's (Remark 8).
+  if (tid == 0) {
+    for (int color = 0; color < 2; ++color) {
+      int16_t* lst = work + color * M;
+      const int nw = misc[2 + color];
+      int nreg = 0;
+      if (quads && G == 4) {             // passes per message: register forms first, both orders kept
+        for (int i = 0; i < nw; ++i)
+          if (qdesc[lst[i]].shape != kShapeNone) {
+            const int16_t t = lst[i];
+            for (int j = i; j > nreg; --j) lst[j] = lst[j - 1];
+            lst[nreg++] = t;
+          }
+      } else if (quads) {
+        for (int sh = kShapeQuad; sh <= kShapeDot; ++sh)
+          for (int i = nreg; i < nw; ++i)
+            if (qdesc[lst[i]].shape == sh) {
+              const int16_t t = lst[i];
+              lst[i] = lst[nreg];
+              lst[nreg++] = t;
+            }
+      }
+      misc[5 + color] = nreg;
+    }
+    misc[7] = 0;
+  }
+  __syncthreads();
 
   // Remark 2: uniform messages of unit norm, unless initial messages are
   // given (learned warm start): those are renormalised on entry.
@@ -1540,43 +1661,92 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
     for (int q = 0; q < G; ++q)
       if ((act >> q) & 1u) { cos_of |= (unsigned)q << (2 * n); ++n; }
     c.frame = frames + (cos_of & 3u) * WW;
+    const QuadUpd<T> upd{msgs, eta, one_m_eta, ovl, M};
     for (int color = 0; color < 2; ++color) {       // Remark 8
-      const int nwork = misc[2 + color];
+      const int nwork = misc[2 + color], nreg = misc[5 + color];
       const int16_t* lst = work + color * M;
-      for (;;) {
-        int item = 0;
-        if (lane == 0) item = atomicAdd(&misc[0], 1);
-        item = __shfl_sync(kFull, item, 0);
-        if (item >= nwork) break;
-        const int idx = lst[item];
-        if (!dev_check(idx >= 0 && idx < M, &misc[8])) continue;
-        int shape = kShapeNone;
-        QuadTask qt;
-        if (quads) {
-          qt = qdesc[idx];
-          shape = qt.shape;
+      // The register forms.  Four cosets per CTA: a warp takes a message,
+      // stages its side messages for every iterating coset once and runs
+      // passes of two cosets (measured faster than pairing single coset
+      // jobs, whose passes each stage and fetch for themselves).
+      if constexpr (K == 4 && G == 4) {
+        for (;;) {
+          int item = 0;
+          if (lane == 0) item = atomicAdd(&misc[0], 1);
+          item = __shfl_sync(kFull, item, 0);
+          if (item >= nreg) break;
+          const int idx = lst[item];
+          if (!dev_check(idx >= 0 && idx < M, &misc[8])) continue;
+          const QuadTask qt = qdesc[idx];
+          msg_register_form<T, K, true>(qt.shape, ws, c.pI, c.pE, msgs, stride, qt, idx, cos_of, n, qid + idx, M,
+                                        lane, upd);
         }
-        // Register forms finish the update themselves.
-        const QuadUpd<T> up{msgs, idx, eta, one_m_eta, ovl, M};
-        if (shape == kShapeQuad) {
-          quad_sweep<T, K, true>(ws, c.pI, c.pE, msgs, stride, cos_of, n, qt, qid + idx, M, lane, up);
-        } else if (shape == kShapeCol) {
-          col_sweep<T, K, true>(ws, c.pI, c.pE, msgs, stride, cos_of, n, qt, qid + idx, M, lane, up);
-        } else if (shape == kShapeRow) {
-          row_sweep<T, K, true>(ws, c.pI, c.pE, msgs, stride, cos_of, n, qt, qid + idx, M, lane, up);
-        } else if (shape == kShapeDot) {
-          dot_sweep<T, K, true>(ws, c.pI, c.pE, msgs, stride, cos_of, n, qt, qid + idx, M, lane, up);
-        } else if constexpr (!kLean) {
+      }
+      // One or two cosets per CTA: coset jobs (message, coset), the n jobs of
+      // a message consecutive, two per warp pass (one per half-warp), so that
+      // no half idles when one coset of a message is iterating.
+      const int njobs = nreg * n;
+      for (;;) {
+        if constexpr (K != 4 || G == 4) break;      // block sides 5, 6: no register forms
+        int j0 = 0;
+        if (lane == 0) j0 = atomicAdd(&misc[0], 2);
+        j0 = __shfl_sync(kFull, j0, 0);
+        if (j0 >= njobs) break;
+        HalfJob jb;
+        jb.on = j0 + hi < njobs;
+        const int jm = jb.on ? j0 + hi : j0;       // a half without a job repeats the other's
+        const int item = job_item(jm, n), sl = jm - item * n;
+        jb.idx = lst[item];
+        if (!dev_check(jb.idx >= 0 && jb.idx < M, &misc[8])) {
+          jb.idx = 0;
+          jb.on = false;
+        }
+        jb.cq = slot_coset(cos_of, sl);
+        jb.slot = sl;
+        jb.sside = hi;
+        jb.qt = qdesc[jb.idx];
+        jb.idv = qid[jb.cq * M + jb.idx];
+        const int shp = jb.qt.shape;
+        if (shp == __shfl_xor_sync(kFull, shp, 16)) {
+          reg_pass<T, K, true, true>(shp, ws, c.pI, c.pE, msgs, stride, jb, lane, upd);
+        } else {
+          // The halves' jobs have different shapes (the boundary of two
+          // shape groups): one shape at a time, the other half keeping company.
+          for (int r = 0; r < 2; ++r) {
+            HalfJob jr;
+            jr.idx = __shfl_sync(kFull, jb.idx, 16 * r);
+            jr.cq = __shfl_sync(kFull, jb.cq, 16 * r);
+            jr.slot = 0;
+            jr.sside = hi;
+            jr.qt = qdesc[jr.idx];
+            jr.idv = qid[jr.cq * M + jr.idx];
+            jr.on = jb.on && hi == r;
+            reg_pass<T, K, true, true>(jr.qt.shape, ws, c.pI, c.pE, msgs, stride, jr, lane, upd);
+          }
+        }
+      }
+      // The node-by-node path: whole messages, every coset at once.
+      if constexpr (!kLean) {
+        for (;;) {
+          int item = 0;
+          if (lane == 0) item = atomicAdd(&misc[7], 1);
+          item = __shfl_sync(kFull, item, 0) + nreg;
+          if (item >= nwork) break;
+          const int idx = lst[item];
+          if (!dev_check(idx >= 0 && idx < M, &misc[8])) continue;
           const int key = meta[idx];
           const Frame f = make_frame(c, key / 4 / nb, (key / 4) % nb, key & 3);
           fused_sweep(ws, c, msgs, stride, cos_of, n, frames, f, (LogAcc<T>*)nullptr, lane);
           fused_update<T, K>(ws, msgs, stride, cos_of, n, idx, f.h, eta, one_m_eta, ovl, M, lane);
-        } else {   // the host launches this kernel only where every block has a register form
-          if (lane == 0) atomicOr(&misc[8], kFlagCapacity);
         }
+      } else {   // the host launches this kernel only where every block has a register form
+        if (tid == 0 && nwork > nreg) atomicOr(&misc[8], kFlagCapacity);
       }
       __syncthreads();
-      if (tid == 0) misc[0] = 0;
+      if (tid == 0) {
+        misc[0] = 0;
+        misc[7] = 0;
+      }
       __syncthreads();
     }
     // Delta = sqrt(sum) / M < delta0 (Remark 4), compared as sum <
@@ -1640,14 +1810,9 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
         uint16_t* idw = reinterpret_cast<uint16_t*>(ws.wn);
         if (lane < G) idw[lane] = quad_ids(f, frames + lane * WW, W, qt);
         __syncwarp();
-        if (shape == kShapeQuad)
-          quad_sweep<T, K, false>(ws, c.pI, c.pE, msgs, stride, all, G, qt, idw, 1, lane, QuadUpd<T>{});
-        else if (shape == kShapeCol)
-          col_sweep<T, K, false>(ws, c.pI, c.pE, msgs, stride, all, G, qt, idw, 1, lane, QuadUpd<T>{});
-        else if (shape == kShapeRow)
-          row_sweep<T, K, false>(ws, c.pI, c.pE, msgs, stride, all, G, qt, idw, 1, lane, QuadUpd<T>{});
-        else
-          dot_sweep<T, K, false>(ws, c.pI, c.pE, msgs, stride, all, G, qt, idw, 1, lane, QuadUpd<T>{});
+        // Every coset q (slot q: the read-out's identity mapping `all`).
+        msg_register_form<T, K, false>(shape, ws, c.pI, c.pE, msgs, stride, qt, 0, all, G, idw, 1, lane,
+                                       QuadUpd<T>{});
       } else if constexpr (!kLean) {
         fused_sweep(ws, c, msgs, stride, all, G, frames, f, ls, lane);
       } else {
