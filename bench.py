@@ -62,11 +62,12 @@ FP64_FMA_PER_SM_CLK = 2
 MLP_FLOPS_PER_ROW = 2 * (256 * 256 + 256 * 256 + 256 * 16)
 # DRAM bytes read + written per unit, from ncu captures (dram__bytes_read.sum
 # + dram__bytes_write.sum) of the current kernels: the fused decode kernel
-# moved 326.9 KB + 0 for 1024 syndromes (d = 11, 4 cosets per CTA, the
-# register-form-only variant sized for 4 CTAs per SM).  The network kernel
-# reading feature bits has no capture yet (None: traffic reported null).
-FUSED_DRAM_BYTES_PER_SYNDROME = (326.912e3 + 0.0) / 1024
-NETWORK_DRAM_BYTES_PER_ROW = None
+# moved 327.2 KB + 0 for 1024 syndromes (d = 11, 4 cosets per CTA, the
+# register-form-only variant sized for 4 CTAs per SM); the network kernel
+# fed by feature bits 14.17 MB + 0 for 385,000 rows (its 64-byte output
+# rows stay in L2 during the launch).
+FUSED_DRAM_BYTES_PER_SYNDROME = (327.168e3 + 0.0) / 1024
+NETWORK_DRAM_BYTES_PER_ROW = (14.172928e6 + 0.0) / 385000
 
 
 def oracle_one(args):
@@ -630,7 +631,7 @@ def ours(args):
         mf = rows * MLP_FLOPS_PER_ROW / (mlp_ms / 1e3) / 1e12
         roof_mlp = {"bound": "tensor", "achieved": mf, "peak": bf16_peak, "unit": "TFLOP/s", "frac": mf / bf16_peak,
                     "traffic": None if NETWORK_DRAM_BYTES_PER_ROW is None else NETWORK_DRAM_BYTES_PER_ROW * rows,
-                    "traffic_source": ("ncu DRAM bytes of a 1.2 M-row launch, scaled to the step's rows"
+                    "traffic_source": ("ncu DRAM bytes of a 385,000-row launch, scaled to the step's rows"
                                        if NETWORK_DRAM_BYTES_PER_ROW is not None else
                                        "no capture of the current kernel"),
                     "kernel": "mlp_tc_kernel (+ weight preparation and the expansion to every coset)",
