@@ -100,38 +100,41 @@ __global__ void features_rows_kernel(Geo g, int M, double p, const uint8_t* synd
   }
   __syncthreads();
   const float p10 = (float)(10.0 * p);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int u = warp; u < U; u += nw) {
-    const int key = row_key[u];
-    const int coset = key / M, idx = key - coset * M;
-    const int mk = meta[idx];
-    const MsgGeo f = msg_geo(g, mk / 4 / nb, (mk / 4) % nb, mk & 3);
-    const uint8_t* frame = frames + coset * WW;
-    if constexpr (BITS) {
-      // Lane l holds window nodes l and l + 32; each channel's 49 bits come
-      // from two ballots, shifted into place (features ch * 49 + pos).
-      float c0[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, c1[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-      window_node(g, f, lane, frame, s, c0);
-      if (lane + 32 < 49) window_node(g, f, lane + 32, frame, s, c1);
-      uint32_t w[9] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+  if constexpr (BITS) {
+    // A thread per row: its 49 window nodes in turn, each channel's bit set
+    // in place (feature ch * 49 + pos; the loops unrolled so that the eight
+    // words stay in registers), then the tail features.
+    for (int u = threadIdx.x; u < U; u += blockDim.x) {
+      const int key = row_key[u];
+      const int coset = key / M, idx = key - coset * M;
+      const int mk = meta[idx];
+      const MsgGeo f = msg_geo(g, mk / 4 / nb, (mk / 4) % nb, mk & 3);
+      const uint8_t* frame = frames + coset * WW;
+      uint32_t w[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
 #pragma unroll
-      for (int ch = 0; ch < 5; ++ch)
+      for (int pos = 0; pos < 49; ++pos) {
+        float c[5];
+        window_node(g, f, pos, frame, s, c);
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          uint32_t b = __ballot_sync(kFull, (half ? c1[ch] : c0[ch]) != 0.f);
-          if (half) b &= (1u << 17) - 1u;                   // nodes 32 .. 48
-          const int q0 = ch * 49 + 32 * half, sh = q0 & 31;
-          w[q0 >> 5] |= b << sh;
-          if (sh) w[(q0 >> 5) + 1] |= b >> (32 - sh);
-        }
-      const uint32_t tb = __ballot_sync(kFull, lane < F - 245 && tail_feature(f, 245 + lane, p10) != 0.f);
-      w[7] |= tb << (245 - 224);
-      if (lane == 0) {
-        uint4* out = reinterpret_cast<uint4*>(bits + (shot * U + u) * 8);
-        out[0] = make_uint4(w[0], w[1], w[2], w[3]);
-        out[1] = make_uint4(w[4], w[5], w[6], w[7]);
+        for (int ch = 0; ch < 5; ++ch)
+          if (c[ch] != 0.f) w[(ch * 49 + pos) >> 5] |= 1u << ((ch * 49 + pos) & 31);
       }
-    } else {
+#pragma unroll
+      for (int q = 245; q < F; ++q)
+        if (tail_feature(f, q, p10) != 0.f) w[q >> 5] |= 1u << (q & 31);
+      uint4* out = reinterpret_cast<uint4*>(bits + (shot * U + u) * 8);
+      out[0] = make_uint4(w[0], w[1], w[2], w[3]);
+      out[1] = make_uint4(w[4], w[5], w[6], w[7]);
+      if (lens) lens[shot * U + u] = 1 << f.h;
+    }
+  } else {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int u = warp; u < U; u += nw) {
+      const int key = row_key[u];
+      const int coset = key / M, idx = key - coset * M;
+      const int mk = meta[idx];
+      const MsgGeo f = msg_geo(g, mk / 4 / nb, (mk / 4) % nb, mk & 3);
+      const uint8_t* frame = frames + coset * WW;
       float* out = feats + (shot * U + u) * F;
       for (int pos = lane; pos < 49; pos += 32) {
         float c[5];
@@ -140,8 +143,8 @@ __global__ void features_rows_kernel(Geo g, int M, double p, const uint8_t* synd
         for (int ch = 0; ch < 5; ++ch) out[ch * 49 + pos] = c[ch];
       }
       if (lane < F - 245) out[245 + lane] = tail_feature(f, 245 + lane, p10);
+      if (lane == 0 && lens) lens[shot * U + u] = 1 << f.h;
     }
-    if (lane == 0 && lens) lens[shot * U + u] = 1 << f.h;
   }
 }
 
