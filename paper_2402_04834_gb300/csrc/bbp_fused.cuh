@@ -1581,7 +1581,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
   c.frame = frames; c.msg_of = msg_of; c.msg_off = nullptr; c.dims = nullptr;
   c.arena = nullptr; c.e0 = nullptr; c.cta_flags = &misc[8];
 
-  const bool quads = K == 4 && g.k == 4;   // 4 x 4 blocks take quad_sweep
+  const bool quads = K == 4 && g.k == 4;   // 4 x 4 blocks take quad_pass
   if (quads) {                              // their descriptors
     for (int e = tid; e < G * M; e += NW * 32) {
       const int q = e / M, idx = e - q * M;
