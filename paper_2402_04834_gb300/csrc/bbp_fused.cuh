@@ -271,9 +271,9 @@ template <> struct LogAcc<float> {
 // s at s << h.  For the read-out (ls not null) every column's state is
 // renormalised per coset and the norms taken out go to ls[slot] (lane 0).
 template <typename T, int K>
-__device__ __noinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K>& c, const T* msgs, int stride,
-                                         unsigned cos_of, int n, const uint8_t* frames, const Frame& f,
-                                         LogAcc<T>* ls, int lane) {
+__device__ __forceinline__ void fused_sweep_body(const FusedWS<T>& ws, const Ctx<T, K>& c, const T* msgs, int stride,
+                                                 unsigned cos_of, int n, const uint8_t* frames, const Frame& f,
+                                                 LogAcc<T>* ls, int lane) {
   using V2 = typename Vec2<T>::type;
   const int h = f.h, nc = f.ncols;
   T* cur = ws.s0;
@@ -761,6 +761,24 @@ __device__ __noinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K>& 
     for (int e = lane; e < (n << h); e += 32) ws.s0[e] = cur[e];
     __syncwarp();
   }
+}
+
+// Block sides up to 4: one out-of-line copy (the kernels that also hold the
+// register forms keep their hot loop small in the instruction cache);
+// block sides 5 and 6 inline it (their loop is this sweep).
+template <typename T, int K>
+__device__ __noinline__ void fused_sweep_call(const FusedWS<T>& ws, const Ctx<T, K>& c, const T* msgs, int stride,
+                                              unsigned cos_of, int n, const uint8_t* frames, const Frame& f,
+                                              LogAcc<T>* ls, int lane) {
+  fused_sweep_body<T, K>(ws, c, msgs, stride, cos_of, n, frames, f, ls, lane);
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void fused_sweep(const FusedWS<T>& ws, const Ctx<T, K>& c, const T* msgs, int stride,
+                                            unsigned cos_of, int n, const uint8_t* frames, const Frame& f,
+                                            LogAcc<T>* ls, int lane) {
+  if constexpr (K <= 4) fused_sweep_call<T, K>(ws, c, msgs, stride, cos_of, n, frames, f, ls, lane);
+  else fused_sweep_body<T, K>(ws, c, msgs, stride, cos_of, n, frames, f, ls, lane);
 }
 
 // <x, y> over n <= 64 entries for the read-out, in the working precision.

@@ -43,7 +43,8 @@ constexpr int kCore = 128;                    // one core matrix: 8 rows x 16 by
 constexpr int kTileA = TM * KD * 2;           // 64 KB: BF16 operand tile
 constexpr int kTileB = NH * KD * 2;           // 128 KB: one hidden layer's BF16 weights
 constexpr int kTileB3 = NO * KD * 2;          // 8 KB: the output layer's weights
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;                 // 16 warps: four per TMEM lane quarter
+constexpr int kParts = kThreads / 128;        // column parts of a lane quarter in the epilogues
 constexpr uint32_t kLBO = kCore;              // K-adjacent core matrices
 constexpr uint32_t kSBO = (KD / 8) * kCore;   // 8-row groups
 constexpr uint32_t kTmemCols = 512;
@@ -176,14 +177,16 @@ __device__ __forceinline__ void load_weights(unsigned char* dst, const unsigned 
 
 // Accumulators of a hidden layer (TMEM columns [0, 256)) -> + bias, GELU,
 // BF16 -> the operand tile.  Warp w reads TMEM lanes 32 (w % 4) .. (its
-// rows) and columns 128 (w / 4) .. + 127.
+// rows; a warp reaches only its own lane quarter) and columns
+// (256 / kParts) (w / 4) .. + 256 / kParts - 1.
 __device__ __forceinline__ void hidden_epilogue(uint32_t tmem, unsigned char* sA, const float* bias, int warp,
                                                 int lane) {
-  const int q = warp & 3, half = warp >> 2;
+  constexpr int kCols = NH / kParts;
+  const int q = warp & 3, part = warp >> 2;
   const int row = 32 * q + lane;
 #pragma unroll 1
-  for (int ch = 0; ch < 4; ++ch) {
-    const int col0 = 128 * half + 32 * ch;
+  for (int ch = 0; ch < kCols / 32; ++ch) {
+    const int col0 = kCols * part + 32 * ch;
     uint32_t v[32];
     tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col0, v);
     tmem_wait_ld();
