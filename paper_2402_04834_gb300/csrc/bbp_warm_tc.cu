@@ -126,21 +126,23 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// erf by the rational approximation of Abramowitz & Stegun, Handbook of
-// Mathematical Functions, formula 7.1.26 (|error| <= 1.5e-7 for x >= 0;
-// odd extension), with the hardware reciprocal and exponential: below
-// 1e-6 in all in FP32, far below the BF16 rounding of the activations the
-// epilogue writes.  Fewer instructions than the library erf, which matters
-// here: the two hidden epilogues are most of the kernel's instructions.
-__device__ __forceinline__ float erf_as(float x) {
+// GELU(x) = x Phi(x) = 0.5 x (1 + erf(x / sqrt 2)), with erf by the
+// rational approximation of Abramowitz & Stegun, Handbook of Mathematical
+// Functions, formula 7.1.26: 1 - erf(z) = poly(t) exp(-z^2), t = 1 / (1 +
+// p z), |error| <= 1.5e-7 for z >= 0 (odd in z).  With z = |x| / sqrt 2
+// and h = 0.5 |x| poly(t) exp(-x^2 / 2): GELU(x) = max(x, 0) - h for either
+// sign of x.  The hardware reciprocal and exponential keep it below 1e-6 in
+// FP32, far below the BF16 rounding of the activations the epilogue
+// writes, in fewer instructions than the library erf; the two hidden
+// epilogues are most of the kernel's instructions.
+__device__ __forceinline__ float gelu_f(float x) {
   const float ax = fabsf(x);
-  const float t = __fdividef(1.f, fmaf(0.3275911f, ax, 1.f));
+  const float t = __fdividef(1.f, fmaf(0.3275911f * 0.70710678118654752f, ax, 1.f));
   const float poly =
       t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
-  return copysignf(fmaf(-poly, __expf(-ax * ax), 1.f), x);
+  const float h = 0.5f * ax * poly * __expf(-0.5f * x * x);
+  return fmaxf(x, 0.f) - h;
 }
-
-__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.f + erf_as(x * 0.70710678118654752f)); }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
