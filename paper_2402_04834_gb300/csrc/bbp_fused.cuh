@@ -1487,6 +1487,40 @@ __device__ __forceinline__ void msg_register_form(int shape, const FusedWS<T>& w
     msg_passes<T, K, kShapeDot, UPD>(ws, pI, pE, msgs, stride, qt, idx, cos_of, n, qid, qid_stride, lane, upd);
 }
 
+// 2^-e exactly (0 <= e < 126), from the exponent bits.
+template <typename T> __device__ __forceinline__ T pow2_neg(int e);
+template <> __device__ __forceinline__ float pow2_neg<float>(int e) { return __int_as_float((127 - e) << 23); }
+template <> __device__ __forceinline__ double pow2_neg<double>(int e) {
+  return __longlong_as_double((long long)(1023 - e) << 52);
+}
+
+// Stable compaction by the whole CTA: items 0 .. n - 1 in order, emit(i, r)
+// for every item with flag(i), r its rank among them; returns their count.
+// scratch: NW ints of shared memory.  Every thread of the CTA calls it.
+template <int NW, typename Flag, typename Emit>
+__device__ __forceinline__ int cta_compact(int n, int* scratch, Flag flag, Emit emit) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int base = 0;
+  for (int c0 = 0; c0 < n; c0 += NW * 32) {
+    const int i = c0 + tid;
+    const bool f = i < n && flag(i);
+    const unsigned b = __ballot_sync(kFull, f);
+    if (lane == 0) scratch[warp] = __popc(b);
+    __syncthreads();
+    int off = base, tot = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      const int cw = scratch[w];
+      off += w < warp ? cw : 0;
+      tot += cw;
+    }
+    if (f) emit(i, off + __popc(b & ((1u << lane) - 1u)));
+    __syncthreads();
+    base += tot;
+  }
+  return base;
+}
+
 // Message item of coset job j when every message has n jobs.
 __device__ __forceinline__ int job_item(int j, int n) { return n == 4 ? j >> 2 : n == 2 ? j >> 1 : n == 1 ? j : j / 3; }
 
@@ -1549,49 +1583,65 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
   const FusedWS<T> ws = fused_ws_at<T, K>(smem + Lo.ws + warp * Lo.ws_stride, G, kLean);
 
   for (int i = tid; i < m; i += NW * 32) synd[i] = syn_src[i];
-  __syncthreads();
-  // Pauli frame f_s L of each coset: pure error strings from the syndrome
-  // plus the logical string (X on row 0, Z on column 0).
-  for (int e = tid; e < G * WW; e += NW * 32) {
-    const int q = e / WW, ij = e - q * WW;
-    const int coset = c0 + q;
-    const int bx = (coset == 1 || coset == 2), bz = (coset == 2 || coset == 3);
-    const int i = ij / W, j = ij % W;
-    int fx = 0, fz = 0;
-    if ((i & 1) == 0 && (j & 1) == 0) {
-      const int r = i >> 1, cc = j >> 1;
-      for (int c2 = 0; c2 < cc; ++c2) fx ^= synd[r * (d - 1) + c2];
-      for (int r2 = 0; r2 < r; ++r2) fz ^= synd[d * (d - 1) + r2 * d + cc];
-      if (bx && r == 0) fx ^= 1;
-      if (bz && cc == 0) fz ^= 1;
-    }
-    frames[e] = (uint8_t)(fx | (fz << 1));
-  }
   if (tid == 0) {
-    int idx = 0, n0 = 0, n1 = 0;
-    for (int I = 0; I < nb; ++I)
-      for (int J = 0; J < nb; ++J)
-        for (int dir = 0; dir < 4; ++dir) {
-          const int key = (I * nb + J) * 4 + dir;
-          if (g.has(I, J, dir)) {
-            msg_of[key] = (int16_t)idx;
-            meta[idx] = (int16_t)key;
-            if (((I + J) & 1) == 0) work[n0++] = (int16_t)idx;
-            else work[M + n1++] = (int16_t)idx;
-            ++idx;
-          } else {
-            msg_of[key] = -1;
-          }
-        }
-    misc[0] = 0; misc[1] = 0; misc[2] = n0; misc[3] = n1;
+    misc[0] = 0; misc[1] = 0; misc[4] = 0; misc[7] = 0;
     for (int q = 0; q < 4; ++q) {
       misc[8 + q] = 0;
       misc[12 + q] = 0;
       dsh[q] = 0.0;
     }
-    if (!dev_check(idx == M && n0 + n1 == M, &misc[8])) misc[2] = misc[3] = 0;
+  }
+  // Pauli frame f_s L of each coset (Algorithm 1): the pure error's bits as
+  // running XORs, a thread per row of horizontal-edge qubits for x (the
+  // flagged sites to its left) and one per column for z (the flagged
+  // plaquettes above), built in the last frame slot; then every coset's
+  // frame, that one with the logical strings (X on row 0, Z on column 0).
+  // Frames are zero off the horizontal-edge qubits.
+  uint8_t* fr_s = frames + (G - 1) * WW;
+  for (int e = tid; e < WW; e += NW * 32) fr_s[e] = 0;
+  __syncthreads();
+  if (tid < d) {
+    int x = 0;
+    for (int cc = 0; cc < d; ++cc) {
+      fr_s[(2 * tid) * W + 2 * cc] = (uint8_t)x;
+      if (cc < d - 1) x ^= synd[tid * (d - 1) + cc];
+    }
   }
   __syncthreads();
+  if (tid < d) {
+    int z = 0;
+    for (int r = 0; r < d; ++r) {
+      fr_s[(2 * r) * W + 2 * tid] |= (uint8_t)(z << 1);
+      if (r < d - 1) z ^= synd[d * (d - 1) + r * d + tid];
+    }
+  }
+  __syncthreads();
+  for (int pass = 0; pass < 2; ++pass) {      // the other slots first, then the last one in place
+    const int q0 = pass == 0 ? 0 : G - 1, q1 = pass == 0 ? G - 1 : G;
+    for (int e = tid; e < (q1 - q0) * WW; e += NW * 32) {
+      const int q = q0 + e / WW, ij = e % WW;
+      const int i = ij / W, j = ij - (ij / W) * W;
+      const int coset = c0 + q;
+      const bool bx = coset == 1 || coset == 2, bz = coset == 2 || coset == 3;
+      const bool hq = ((i | j) & 1) == 0;
+      frames[q * WW + ij] =
+          (uint8_t)(fr_s[ij] ^ ((bx && hq && i == 0) ? 1 : 0) ^ ((bz && hq && j == 0) ? 2 : 0));
+    }
+    __syncthreads();
+  }
+  // Message table by stable compaction in (I, J, dir) order: each directed
+  // block edge's index and key.  The first per-warp buffers serve as the
+  // compactions' scratch (NW ints) until the message updates start.
+  int* scr = reinterpret_cast<int*>(smem + Lo.ws);
+  const int NK = nb * nb * 4;
+  for (int key = tid; key < NK; key += NW * 32) msg_of[key] = -1;
+  __syncthreads();
+  auto has_key = [&](int key) { return g.has(key / 4 / nb, (key / 4) % nb, key & 3); };
+  auto color_of = [&](int key) { return (key / 4 / nb + (key / 4) % nb) & 1; };
+  const int nmsg = cta_compact<NW>(NK, scr, has_key, [&](int key, int r) {
+    msg_of[key] = (int16_t)r;
+    meta[r] = (int16_t)key;
+  });
 
   Ctx<T, K> c;
   c.g = g; c.D = 0; c.cutoff2 = T(0);
@@ -1600,9 +1650,8 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
   c.arena = nullptr; c.e0 = nullptr; c.cta_flags = &misc[8];
 
   const bool quads = K == 4 && g.k == 4;   // 4 x 4 blocks take quad_pass
-  if (quads) {                              // their descriptors
-    for (int e = tid; e < G * M; e += NW * 32) {
-      const int q = e / M, idx = e - q * M;
+  if (quads) {                              // their descriptors (geometry) and qubit ids (per coset)
+    for (int idx = tid; idx < M; idx += NW * 32) {
       const int key = meta[idx];
       const Frame f = make_frame(c, key / 4 / nb, (key / 4) % nb, key & 3);
       QuadTask qt = quad_task<T, K>(f);
@@ -1610,40 +1659,37 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
                          qt.lo_idx < M && qt.shape <= kShapeDot,
                      &misc[8]))
         qt.shape = kShapeNone;
-      if (q == 0) qdesc[idx] = qt;
-      qid[e] = quad_ids(f, frames + q * WW, W, qt);
+      qdesc[idx] = qt;
+      for (int q = 0; q < G; ++q) qid[q * M + idx] = quad_ids(f, frames + q * WW, W, qt);
     }
     __syncthreads();
   }
-  // Each colour's list: the messages of the register forms first, grouped
-  // by shape (a warp pass pairs two coset jobs of one shape), their count
-  // in misc[5 + colour]; then those of the node-by-node path.  The order
-  // within a colour does not matter: its messages read only the other
-  // colour's (Remark 8).
-  if (tid == 0) {
-    for (int color = 0; color < 2; ++color) {
-      int16_t* lst = work + color * M;
-      const int nw = misc[2 + color];
-      int nreg = 0;
-      if (quads && G == 4) {             // passes per message: register forms first, both orders kept
-        for (int i = 0; i < nw; ++i)
-          if (qdesc[lst[i]].shape != kShapeNone) {
-            const int16_t t = lst[i];
-            for (int j = i; j > nreg; --j) lst[j] = lst[j - 1];
-            lst[nreg++] = t;
-          }
-      } else if (quads) {
-        for (int sh = kShapeQuad; sh <= kShapeDot; ++sh)
-          for (int i = nreg; i < nw; ++i)
-            if (qdesc[lst[i]].shape == sh) {
-              const int16_t t = lst[i];
-              lst[i] = lst[nreg];
-              lst[nreg++] = t;
-            }
-      }
-      misc[5 + color] = nreg;
+  // Each colour's list (Remark 8): the messages of the register forms
+  // first, grouped by shape (a warp pass pairs two coset jobs of one
+  // shape), their count in misc[5 + colour]; then those of the node-by-node
+  // path; key order within a group.  The order within a colour does not
+  // matter for the results: its messages read only the other colour's.
+  int ncol[2];
+  for (int color = 0; color < 2; ++color) {
+    int placed = 0, nreg = 0;
+    const int ngroups = quads ? 5 : 1;
+    for (int gi = 0; gi < ngroups; ++gi) {
+      const int sh = gi < 4 ? kShapeQuad + gi : kShapeNone;
+      placed += cta_compact<NW>(
+          NK, scr,
+          [&](int key) {
+            return has_key(key) && color_of(key) == color && (!quads || qdesc[msg_of[key]].shape == sh);
+          },
+          [&](int key, int r) { work[color * M + placed + r] = msg_of[key]; });
+      if (gi == 3) nreg = placed;
     }
-    misc[7] = 0;
+    ncol[color] = placed;
+    if (tid == 0) misc[5 + color] = quads ? nreg : 0;
+  }
+  if (tid == 0) {
+    misc[2] = ncol[0];
+    misc[3] = ncol[1];
+    if (!dev_check(nmsg == M && ncol[0] + ncol[1] == M, &misc[8])) misc[2] = misc[3] = 0;
   }
   __syncthreads();
 
@@ -1663,7 +1709,8 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
       if (!uniform && lane < VEC) x[lane] = v * (T(1) / nrm);
     }
     if (uniform) {                                   // no (or an unusable) proposal
-      const T u = T(1) / xsqrt(T(1 << w));        // in working precision: no FP64 per message
+      // 1 / sqrt(2^w): a power of two, times the rounded 1 / sqrt 2 for odd w.
+      const T u = ((w & 1) ? T(0.70710678118654752440) : T(1)) * pow2_neg<T>(w >> 1);
       for (int i = lane; i < VEC; i += 32) x[i] = i < (1 << w) ? u : T(0);
     }
   }
@@ -1794,17 +1841,13 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
     }
 
   // Lemma 1 read-out, all G cosets of a block (or edge) at once.
-  if (tid == 0) {
-    int ne = 0;
-    for (int idx = 0; idx < M; ++idx) {
-      const int dir = meta[idx] & 3;
-      if (dir == kDirR || dir == kDirD) work[ne++] = (int16_t)idx;
-    }
-    misc[4] = dev_check(ne <= M, &misc[8]) ? ne : 0;
-    misc[0] = 0;
-  }
+  // The undirected edges, each as its rightward / downward message, in
+  // index order (the read-out's product order does not depend on the launch).
+  const int nedge = cta_compact<NW>(
+      M, scr, [&](int idx) { const int dir = meta[idx] & 3; return dir == kDirR || dir == kDirD; },
+      [&](int idx, int r) { work[r] = (int16_t)idx; });
+  if (tid == 0) misc[0] = 0;
   __syncthreads();
-  const int nedge = misc[4];
   const int nblk = nb * nb;
   const int per = nblk + nedge;
   const unsigned all = G == 1 ? 0u : (G == 2 ? 0x4u : 0xE4u);    // slot q holds coset q
