@@ -471,39 +471,79 @@ __device__ __noinline__ void svd_step(WarpWS<T, K, DM>& ws, const Ctx<T, K>& c, 
   __syncwarp();
 }
 
-// Divide the last site by its Frobenius norm; return log(norm).
+// Divide the last site by its Frobenius norm; return log(norm) when
+// want_log (only the read-out keeps the scale; the log is an FP64 call,
+// which GB300 issues at 1/64 of the FP32 rate), else 0.
 template <typename T, int K, int DM>
-__device__ double normalize_last(WarpWS<T, K, DM>& ws, int h, int lane) {
+__device__ double normalize_last(WarpWS<T, K, DM>& ws, int h, int lane, bool want_log) {
   const int n = ws.bond[h - 1] * 2 * ws.bond[h];
   T* A = ws.psi[h - 1];
   T acc = 0;
   for (int e = lane; e < n; e += 32) acc += A[e] * A[e];
   acc = warp_sum(acc);
   const T nrm = xsqrt(acc);
-  if (nrm > T(0) && isfinite((double)nrm)) {
+  if (nrm > T(0) && isfinite(nrm)) {
     const T inv = T(1) / nrm;
     for (int e = lane; e < n; e += 32) A[e] *= inv;
   }
   __syncwarp();
-  return log((double)nrm);
+  return want_log ? log((double)nrm) : 0.0;
 }
 
 // MPS compression (Sec. III.A): QR sweep right to left, truncated SVD sweep
-// left to right, normalisation (Remark 3).  Returns the log of the norm.
+// left to right, normalisation (Remark 3).  Returns the log of the norm
+// when want_log.
 template <typename T, int K, int DM>
-__device__ __noinline__ double compress(WarpWS<T, K, DM>& ws, const Ctx<T, K>& c, int h, int lane) {
+__device__ __noinline__ double compress(WarpWS<T, K, DM>& ws, const Ctx<T, K>& c, int h, int lane, bool want_log) {
   for (int s = h - 1; s >= 1; --s) lq_step(ws, s, lane);
   for (int s = 0; s + 1 < h; ++s) svd_step(ws, c, s, lane);
-  return normalize_last(ws, h, lane);
+  return normalize_last(ws, h, lane, want_log);
 }
 
-// <A|B> of two MPS views with end bonds 1, accumulated in double; the
-// transfer matrices live in the (tmp, mat) pair reinterpreted as doubles.
+// Accumulation of the overlaps' transfer matrices: double in FP64 kernels;
+// in FP32 kernels a float pair (head + tail, about 48 bits), whose
+// multiply-adds run on the FP32 pipe: native FP64 there would issue at
+// 1/64 of the rate, and the overlap must hold 1 - <m|m'> of converged
+// messages (1e-7 and below) for Delta (Remark 4).
+struct F2 {
+  float h, l;
+};
+template <typename T> struct OvAcc;
+template <> struct OvAcc<double> {
+  using V = double;
+  static __device__ __forceinline__ V zero() { return 0.0; }
+  static __device__ __forceinline__ V one() { return 1.0; }
+  static __device__ __forceinline__ V mac(V acc, V x, double y) { return fma(x, y, acc); }
+  static __device__ __forceinline__ double value(V v) { return v; }
+};
+template <> struct OvAcc<float> {
+  using V = F2;
+  static __device__ __forceinline__ V zero() { return F2{0.f, 0.f}; }
+  static __device__ __forceinline__ V one() { return F2{1.f, 0.f}; }
+  // acc + x y with x a pair and y a float: the head product exactly (its
+  // rounding error by fma), the tail product, then a two-sum into acc.
+  static __device__ __forceinline__ V mac(V acc, V x, float y) {
+    const float ph = __fmul_rn(x.h, y);
+    const float pl = __fmaf_rn(x.l, y, __fmaf_rn(x.h, y, -ph));
+    const float s = __fadd_rn(acc.h, ph);
+    const float bv = __fsub_rn(s, acc.h);
+    const float e = __fadd_rn(__fadd_rn(__fsub_rn(acc.h, __fsub_rn(s, bv)), __fsub_rn(ph, bv)), __fadd_rn(acc.l, pl));
+    const float hh = __fadd_rn(s, e);
+    return F2{hh, __fsub_rn(e, __fsub_rn(hh, s))};
+  }
+  static __device__ __forceinline__ double value(V v) { return (double)v.h + (double)v.l; }
+};
+
+// <A|B> of two MPS views with end bonds 1, the transfer matrices
+// accumulated as OvAcc<T> (8 bytes an entry) in the (tmp, mat) pair.
 template <typename T, int K, int DM, typename FA, typename FB>
 __device__ double mps_overlap(WarpWS<T, K, DM>& ws, int h, FA sa, FB sb, int lane) {
-  double* E = reinterpret_cast<double*>(ws.tmp);
-  double* F = E + 2 * DM * DM;        // E <= (2D x D), F <= D x 2 x 2D
-  if (lane == 0) E[0] = 1.0;
+  using Acc = OvAcc<T>;
+  using V = typename Acc::V;
+  static_assert(sizeof(V) == sizeof(double), "transfer matrices of 8-byte entries");
+  V* E = reinterpret_cast<V*>(ws.tmp);
+  V* F = E + 2 * DM * DM;             // E <= (2D x D), F <= D x 2 x 2D
+  if (lane == 0) E[0] = Acc::one();
   int ea = 1, eb = 1;
   __syncwarp();
   for (int s = 0; s < h; ++s) {
@@ -513,8 +553,8 @@ __device__ double mps_overlap(WarpWS<T, K, DM>& ws, int h, FA sa, FB sb, int lan
     const FastDiv dA(A.nb);
     for (int e = lane; e < nF; e += 32) {
       const int q = dA.quo(e), cc = e - q * A.nb, b = q >> 1, p = q & 1;
-      double acc = 0;
-      for (int a = 0; a < ea; ++a) acc += E[a * eb + b] * (double)A.at(a, p, cc);
+      V acc = Acc::zero();
+      for (int a = 0; a < ea; ++a) acc = Acc::mac(acc, E[a * eb + b], A.at(a, p, cc));
       F[e] = acc;
     }
     __syncwarp();
@@ -523,16 +563,16 @@ __device__ double mps_overlap(WarpWS<T, K, DM>& ws, int h, FA sa, FB sb, int lan
     const FastDiv dB(B.nb);
     for (int e = lane; e < nE; e += 32) {
       const int cc = dB.quo(e), dd = e - cc * B.nb;
-      double acc = 0;
+      V acc = Acc::zero();
       for (int b = 0; b < eb; ++b)
-        for (int p = 0; p < 2; ++p) acc += F[(b * 2 + p) * A.nb + cc] * (double)B.at(b, p, dd);
+        for (int p = 0; p < 2; ++p) acc = Acc::mac(acc, F[(b * 2 + p) * A.nb + cc], B.at(b, p, dd));
       E[e] = acc;
     }
     ea = A.nb;
     eb = B.nb;
     __syncwarp();
   }
-  return E[0];
+  return Acc::value(E[0]);
 }
 
 // ---------------------------------------------------------------------------
@@ -721,7 +761,7 @@ __device__ __noinline__ double block_sweep(WarpWS<T, K, DM>& ws, const Ctx<T, K>
   double log_scale = 0.0;
   for (int t = 0; t < f.ncols; ++t) {
     absorb(ws, c, f, t, lane);
-    if (!readout || t + 1 < f.ncols) log_scale += compress(ws, c, f.h, lane);
+    if (!readout || t + 1 < f.ncols) log_scale += compress(ws, c, f.h, lane, readout);
   }
   return log_scale;
 }
@@ -770,7 +810,7 @@ __device__ __noinline__ void damp(WarpWS<T, K, DM>& ws, const Ctx<T, K>& c, int 
       for (int s = 0; s <= w; ++s) ws.bond[s] = nb_new[s];
     __syncwarp();
   }
-  compress(ws, c, w, lane);
+  compress(ws, c, w, lane, false);
 }
 
 // Store psi as message idx (bond dims checked against the slot bounds).
