@@ -917,6 +917,15 @@ __device__ __forceinline__ void qpair(int id, int be, T pI, T pE, T& g0, T& g1) 
   g1 = (hit && hi) ? pI : pE;
 }
 
+// Coefficient v (0 .. 3) of the qubit in field f of t = ids ^ lane pattern:
+// pI where the field equals v.  With the lane's bit be at the field's beta
+// position, the field is (alpha, beta ^ be): g[0][be], g[1][be] are
+// v = 0, 2 and g[0][be ^ 1], g[1][be ^ 1] are v = 1, 3.
+template <typename T>
+__device__ __forceinline__ T qco(unsigned t, int f, unsigned v, T pI, T pE) {
+  return ((t >> (2 * f)) & 3u) == v ? pI : pE;
+}
+
 template <typename T>
 __device__ __forceinline__ T qval(int id, int al, int be, T pI, T pE) {
   return ((al << 1) | be) == id ? pI : pE;
@@ -1197,17 +1206,18 @@ __device__ __forceinline__ void col_pass(const FusedWS<T>& ws, T pI, T pE, const
   const int r1 = (R >> 2) & 1, r3 = R & 1;
   const int Rn = rev ? bitrev(R, 4) : R;
   const T* mq = msgs + jb.cq * stride;
-  const int id_up = (int)(jb.idv & 3u), id_lo = (int)((jb.idv >> 2) & 3u);
+  // Ids against the lane's row bits (qco): the top qubit (field 0) with be
+  // = r1, the lower one (field 1) with be = r1 ^ r3.
+  const unsigned tq = jb.idv ^ (((unsigned)r1 * 5u) ^ ((unsigned)r3 * 4u));
   const T x = qt.in_idx >= 0 ? mq[qt.in_idx * VEC + Rn] : ((Rn & qm_in) ? T(0) : T(1));
   const T a0 = qt.up_idx >= 0 ? mq[qt.up_idx * VEC] : T(1);
   const T a1 = qt.up_idx >= 0 ? mq[qt.up_idx * VEC + 1] : (qm_up ? T(0) : T(1));
   const T bb = qt.lo_idx >= 0 ? mq[qt.lo_idx * VEC + r3] : ((r3 && qm_lo) ? T(0) : T(1));
-  T k0, k1, h0, h1, m0, m1;
-  qpair(id_lo, r1 ^ r3, pI, pE, k0, k1);
+  const T k0 = qco(tq, 1, 0u, pI, pE), k1 = qco(tq, 1, 2u, pI, pE);
   const T u = fma(k1, shx(x, 2), k0 * x);
   const T uf = shx(u, 8);
-  qpair(id_up, r1, pI, pE, h0, h1);          // top leg 0
-  qpair(id_up, r1 ^ 1, pI, pE, m0, m1);      // top leg 1
+  const T h0 = qco(tq, 0, 0u, pI, pE), h1 = qco(tq, 0, 2u, pI, pE);   // top leg 0
+  const T m0 = qco(tq, 0, 1u, pI, pE), m1 = qco(tq, 0, 3u, pI, pE);   // top leg 1
   const T out = bb * fma(a1, fma(m1, uf, m0 * u), a0 * fma(h1, uf, h0 * u));
   if constexpr (UPD) {
     reg_update16<T, K>(out, jb.on, jb.cq, jb.idx, R, Rn, stride, upd);
@@ -1337,47 +1347,44 @@ __device__ __forceinline__ void quad_pass(const FusedWS<T>& ws, T pI, T pE, cons
   const int cq = jb.cq;
   const T* mA = ws.mt + (jb.sside << 4);
   const T* mB = ws.mb + (jb.sside << 4);
-  int id[4][2];
-#pragma unroll
-  for (int t = 0; t < 4; ++t)
-#pragma unroll
-    for (int u = 0; u < 2; ++u) id[t][u] = (int)((jb.idv >> (2 * (2 * t + u))) & 3u);
+  // The qubit ids (field 2 t + u: the upper, u = 0, or lower qubit of
+  // column t) against the lane's row bits: be of each field's first use,
+  // r1 (0, 0), r1 ^ r3 (0, 1), r0 ^ r2 (1, 0), r2 (1, 1), r1 (2, 0),
+  // r1 ^ r3 (2, 1), r0 ^ r2 (3, 0), r2 (3, 1); and r3 at the alpha bit of
+  // (1, 1), whose coefficients the lanes of odd rows take swapped.
+  const unsigned lq = ((unsigned)r0 * 0x1010u) ^ ((unsigned)r1 * 0x0505u) ^ ((unsigned)r2 * 0x5050u) ^
+                      ((unsigned)r3 * 0x0484u);
+  const unsigned tq = jb.idv ^ lq;
   const T x = qt.in_idx >= 0 ? msgs[cq * stride + qt.in_idx * VEC + Rn] : ((Rn & qm_in) ? T(0) : T(1));
   // Column 0 (qubits at 0, 2): the upper leg a0 is recorded, the lower leg
   // b0 is tied to r3 by the check at 3.
   T S0[2];
   {
-    T k0, k1;
-    qpair(id[0][1], r1 ^ r3, pI, pE, k0, k1);
+    const T k0 = qco(tq, 1, 0u, pI, pE), k1 = qco(tq, 1, 2u, pI, pE);
     const T u = fma(k1, shx(x, 2), k0 * x);
     const T uf = shx(u, 8);
 #pragma unroll
     for (int a0 = 0; a0 < 2; ++a0) {
-      T h0, h1;
-      qpair(id[0][0], a0 ^ r1, pI, pE, h0, h1);
+      const T h0 = qco(tq, 0, (unsigned)a0, pI, pE), h1 = qco(tq, 0, 2u + a0, pI, pE);
       S0[a0] = fma(h1, uf, h0 * u);
     }
   }
   // Column 2's coefficients: the lower qubit (c2k0, c2k1) and the upper
   // one, g[l0 ^ r0][v ^ r1] for v = 0, 1.
-  T c2k0, c2k1, g00, g01, g10, g11;
-  qpair(id[2][1], r1 ^ r3, pI, pE, c2k0, c2k1);
-  qpair(id[2][0], r1, pI, pE, g00, g10);                   // v = 0
-  qpair(id[2][0], r1 ^ 1, pI, pE, g01, g11);               // v = 1
+  const T c2k0 = qco(tq, 5, 0u, pI, pE), c2k1 = qco(tq, 5, 2u, pI, pE);
+  const T g00 = qco(tq, 4, 0u, pI, pE), g10 = qco(tq, 4, 2u, pI, pE);   // v = 0
+  const T g01 = qco(tq, 4, 1u, pI, pE), g11 = qco(tq, 4, 3u, pI, pE);   // v = 1
   // Column 1 (qubits at 1, 3): a1 is tied to r0 by the check at 0; the
   // lower leg b1 is recorded.  S1[b0][b1] for one a0 at a time, folded
   // into column 2 at once.  Column 2 (qubits at 0, 2) is the data column
   // of both side messages: the upper leg v is summed against A[a0 a1 v e],
   // the lower leg w = r3 against B[b0 b1 w f].
-  T h0, h1;
-  qpair(id[1][0], r0 ^ r2, pI, pE, h0, h1);
-  T kk0[2], kk1[2];                                        // [b1], for b0 = 0, 1
+  const T h0 = qco(tq, 2, 0u, pI, pE), h1 = qco(tq, 2, 2u, pI, pE);
+  T kk0[2], kk1[2];                                        // [b1]: g[r3][r2 ^ b1], g[!r3][r2 ^ b1]
 #pragma unroll
   for (int b1 = 0; b1 < 2; ++b1) {
-    T k0, k1;
-    qpair(id[1][1], r2 ^ b1, pI, pE, k0, k1);
-    kk0[b1] = r3 ? k1 : k0;
-    kk1[b1] = r3 ? k0 : k1;
+    kk0[b1] = qco(tq, 3, (unsigned)b1, pI, pE);
+    kk1[b1] = qco(tq, 3, 2u + b1, pI, pE);
   }
   T Y[2][2][2];                                            // [e][b0][b1]
 #pragma unroll
@@ -1431,12 +1438,10 @@ __device__ __forceinline__ void quad_pass(const FusedWS<T>& ws, T pI, T pE, cons
   {
     const T z0 = r0 ? S2[1][0] : S2[0][0], z1 = r0 ? S2[1][1] : S2[0][1];
     const T p0 = shx(z0, 1), p1 = shx(z1, 1);
-    T k0, k1, m0, m1;
-    qpair(id[3][1], r2, pI, pE, k0, k1);
-    qpair(id[3][1], r2 ^ 1, pI, pE, m0, m1);
+    const T k0 = qco(tq, 7, 0u, pI, pE), k1 = qco(tq, 7, 2u, pI, pE);
+    const T m0 = qco(tq, 7, 1u, pI, pE), m1 = qco(tq, 7, 3u, pI, pE);
     const T uu = fma(m1, p1, fma(m0, z1, fma(k1, p0, k0 * z0)));
-    T g0, g1;
-    qpair(id[3][0], r0 ^ r2, pI, pE, g0, g1);
+    const T g0 = qco(tq, 6, 0u, pI, pE), g1 = qco(tq, 6, 2u, pI, pE);
     out = fma(g1, shx(uu, 4), g0 * uu);
   }
   if constexpr (UPD) {
