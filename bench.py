@@ -110,6 +110,15 @@ def run_oracle_sample(first_shot: int, n: int, procs: int, algorithm: str):
     return dt, res
 
 
+# Multiply-adds of the 4 x 4 register form per (row, coset): column 0's two
+# butterflies 6; per upper leg a0 of column 0 (two): column 1's products 4
+# and butterflies 8, the upper side message's entries 4, column 2's
+# butterflies and data column 16; the lower side message's data column 8;
+# column 3 6.  Only the entries with column 3's upper leg e equal to the
+# row's bit r0 (the check at its top ties them) are formed.
+REGISTER_FORM_MADDS = 84
+
+
 def fused_flops(d: int, k: int):
     """Algorithmic arithmetic of the fused-block update (multiply-adds count 2), per coset.
 
@@ -176,18 +185,17 @@ def fused_flops(d: int, k: int):
                 if h == 4 and len(lines) == 4:
                     # 4 x 4 blocks: the register form of the update (butterflies
                     # over single row bits, side messages contracted where their
-                    # legs enter), per (row, coset) entry 116 multiply-adds when
-                    # column 0 starts with a qubit and 108 when it starts with a
-                    # check.
-                    i0, j0 = lines[0][0]
-                    per_iter += 2.0 * 16 * (108 if (i0 + j0) % 2 else 116) + 12.0 * 2 ** h
+                    # legs enter), 84 multiply-adds per (row, coset) entry
+                    # whichever node column 0 starts with (a chain starting with
+                    # a check is read bottom to top).
+                    per_iter += 2.0 * 16 * REGISTER_FORM_MADDS + 12.0 * 2 ** h
                 else:
                     per_iter += sweep(qubits(lines), h, ha, hb, False) + 12.0 * 2 ** h
                 if dr in (0, 2):
                     readout += 2.0 * 2 ** h
             lines = [[(i, j) for i in rows] for j in cols]
             if r1 - r0 == 4 and c1 - c0 == 4:      # the read-out's register form, then the closing dot
-                readout += 2.0 * 16 * (108 if (r0 + c0) % 2 else 116) + 2.0 * 16
+                readout += 2.0 * 16 * REGISTER_FORM_MADDS + 2.0 * 16
             else:
                 readout += sweep(qubits(lines), r1 - r0, I > 0, I + 1 < nb, True) + 2.0 * 2 ** (r1 - r0)
     return per_iter, readout
@@ -616,7 +624,7 @@ def ours(args):
                 "launch_ms": dec_ms,
                 "peak_source": (f"derived: {per_clk} {'FP32 lanes' if fp else 'FP64 FMA/clk'} per SM x 2 x "
                                 f"{n_sm} SMs x {sm_mhz:.0f} MHz (max SM clock)"),
-                "flop_model": "4x4 blocks: the multiply-adds of the register form (116 or 108 per row and "
+                "flop_model": "4x4 blocks: the multiply-adds of the register form (84 per row and "
                               "coset); other blocks: qubit nodes as 2x2 XOR convolutions (4 multiply-adds "
                               "per state entry), check nodes as zero-flop copy tensors, side-message data "
                               "columns; normalise/damp/overlap; Lemma 1 read-out (register form for 4x4 blocks)",

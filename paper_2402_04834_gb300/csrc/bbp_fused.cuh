@@ -1386,7 +1386,9 @@ __device__ __forceinline__ void quad_pass(const FusedWS<T>& ws, T pI, T pE, cons
     kk0[b1] = qco(tq, 3, (unsigned)b1, pI, pE);
     kk1[b1] = qco(tq, 3, 2u + b1, pI, pE);
   }
-  T Y[2][2][2];                                            // [e][b0][b1]
+  // Column 3's upper leg e is tied to r0 by its check: only e = r0 of
+  // A[a0 a1 v e] and of everything after it reaches this lane's output.
+  T Y[2][2];                                               // [b0][b1], e = r0
 #pragma unroll
   for (int a0 = 0; a0 < 2; ++a0) {
     T S1[2][2];
@@ -1400,12 +1402,11 @@ __device__ __forceinline__ void quad_pass(const FusedWS<T>& ws, T pI, T pE, cons
         S1[1][b1] = fma(h1, shx(y1, 4), h0 * y1);
       }
     }
-    // A0: row bit 0 kept (l0 = r0 = a1), A1: flipped (l0 = a1 = !r0).
-    T m0[4], m1[4];
-    vcopy4(mA + (a0 << 3) + (r0 << 2), m0);
-    vcopy4(mA + (a0 << 3) + ((r0 ^ 1) << 2), m1);
-    const T A00 = fma(m0[2], g01, m0[0] * g00), A01 = fma(m0[3], g01, m0[1] * g00);   // e = 0, 1
-    const T A10 = fma(m1[2], g11, m1[0] * g10), A11 = fma(m1[3], g11, m1[1] * g10);
+    // A0: row bit 0 kept (l0 = r0 = a1), A1: flipped (l0 = a1 = !r0); v
+    // summed against column 2's upper qubit, e = r0.
+    const T* ma = mA + (a0 << 3) + r0;
+    const T A0 = fma(ma[(r0 << 2) + 2], g01, ma[r0 << 2] * g00);
+    const T A1 = fma(ma[((r0 ^ 1) << 2) + 2], g11, ma[(r0 ^ 1) << 2] * g10);
 #pragma unroll
     for (int b0 = 0; b0 < 2; ++b0)
 #pragma unroll
@@ -1413,30 +1414,21 @@ __device__ __forceinline__ void quad_pass(const FusedWS<T>& ws, T pI, T pE, cons
         const T s1 = S1[b0][b1];
         const T u = fma(c2k1, shx(s1, 2), c2k0 * s1);
         const T uf = shx(u, 8);
-        if (a0 == 0) {
-          Y[0][b0][b1] = fma(A00, u, A10 * uf);
-          Y[1][b0][b1] = fma(A01, u, A11 * uf);
-        } else {
-          Y[0][b0][b1] = fma(A00, u, fma(A10, uf, Y[0][b0][b1]));
-          Y[1][b0][b1] = fma(A01, u, fma(A11, uf, Y[1][b0][b1]));
-        }
+        Y[b0][b1] = a0 == 0 ? fma(A0, u, A1 * uf) : fma(A0, u, fma(A1, uf, Y[b0][b1]));
       }
   }
-  T S2[2][2];
+  T S2[2];                                                 // [ff], e = r0
   {
     const T* mb = mB + (r3 << 1);                          // B[b0 b1 r3 ff] at mb[4 (2 b0 + b1) + ff]
 #pragma unroll
-    for (int e = 0; e < 2; ++e)
-#pragma unroll
-      for (int ff = 0; ff < 2; ++ff)
-        S2[e][ff] = fma(mb[12 + ff], Y[e][1][1], fma(mb[8 + ff], Y[e][1][0], fma(mb[4 + ff], Y[e][0][1],
-                                                                              mb[ff] * Y[e][0][0])));
+    for (int ff = 0; ff < 2; ++ff)
+      S2[ff] = fma(mb[12 + ff], Y[1][1], fma(mb[8 + ff], Y[1][0], fma(mb[4 + ff], Y[0][1], mb[ff] * Y[0][0])));
   }
   // Column 3 (qubits at 1, 3): the upper leg e is tied to r0, the lower
   // leg f closes against B's expected value.
   T out;
   {
-    const T z0 = r0 ? S2[1][0] : S2[0][0], z1 = r0 ? S2[1][1] : S2[0][1];
+    const T z0 = S2[0], z1 = S2[1];
     const T p0 = shx(z0, 1), p1 = shx(z1, 1);
     const T k0 = qco(tq, 7, 0u, pI, pE), k1 = qco(tq, 7, 2u, pI, pE);
     const T m0 = qco(tq, 7, 1u, pI, pE), m1 = qco(tq, 7, 3u, pI, pE);
