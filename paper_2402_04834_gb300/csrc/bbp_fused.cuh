@@ -923,7 +923,7 @@ __device__ __forceinline__ void qpair(int id, int be, T pI, T pE, T& g0, T& g1) 
 // v = 0, 2 and g[0][be ^ 1], g[1][be ^ 1] are v = 1, 3.
 template <typename T>
 __device__ __forceinline__ T qco(unsigned t, int f, unsigned v, T pI, T pE) {
-  return ((t >> (2 * f)) & 3u) == v ? pI : pE;
+  return ((t ^ (v << (2 * f))) & (3u << (2 * f))) == 0u ? pI : pE;   // constant masks: one logic op
 }
 
 template <typename T>
@@ -1444,6 +1444,182 @@ __device__ __forceinline__ void quad_pass(const FusedWS<T>& ws, T pI, T pE, cons
   __syncwarp();
 }
 
+// Sum over aligned groups of 8 lanes, every lane of a group getting the
+// same bits.
+template <typename T>
+__device__ __forceinline__ T gsum8(T v) {
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) v = radd(v, shx(v, o));
+  return v;
+}
+
+// reg_update16 for a lane holding two entries of the 16-entry vector,
+// out[q] at Rn[q] (the rows differing in row bit 0), over groups of 8
+// lanes: the same sums in the same order (the first level of gsum16 adds a
+// lane's value to its row-bit-0 partner's, here the lane's own pair).
+template <typename T, int K>
+__device__ __forceinline__ void reg_update16x2(const T (&out)[2], bool on, int cq, int idx, bool writer,
+                                               const int (&Rn)[2], int stride, const QuadUpd<T>& up) {
+  T* old = up.msgs + cq * stride + idx * FusedDim<K>::vec;
+  const T y0 = old[Rn[0]], y1 = old[Rn[1]];
+  const T i1 = inv_norm(gsum8(radd(out[0] * out[0], out[1] * out[1])));
+  T x0 = out[0] * i1, x1 = out[1] * i1;
+  x0 = fma(up.one_m_eta, x0, up.eta * y0);
+  x1 = fma(up.one_m_eta, x1, up.eta * y1);
+  const T i2 = inv_norm(gsum8(radd(x0 * x0, x1 * x1)));
+  x0 = x0 * i2;
+  x1 = x1 * i2;
+  T term;
+  if constexpr (sizeof(T) == 4) {
+    const T t0 = x0 - y0, t1 = x1 - y1;
+    const T sq = gsum8(radd(t0 * t0, t1 * t1));
+    term = sq * fma(T(-0.5), sq, T(2));
+  } else {
+    const T o = gsum8(radd(x0 * y0, x1 * y1));
+    term = fma(T(-2) * o, o, T(2));
+  }
+  if (on) {
+    old[Rn[0]] = x0;
+    old[Rn[1]] = x1;
+    if (writer) up.ovl[cq * up.M + idx] = term;
+  }
+}
+
+// quad_pass for up to four cosets of one message at once: lane (slot
+// c = lane >> 3, j = lane & 7) holds rows R = 8 q + j, q = 0, 1, of coset
+// slot c, so row bit r0 = q lives in registers (quad_pass's exchanges
+// with lane ^ 8 become register swaps; its other shuffles stay inside the
+// 8-lane group).  Slots >= n repeat slot 0 and store nothing.  The side
+// messages are staged for slots 0 .. n - 1 (stage_all_sides).  Every value
+// is quad_pass's, bit for bit.
+template <typename T, int K, bool UPD>
+__device__ __forceinline__ void quad_pass4(const FusedWS<T>& ws, T pI, T pE, const T* msgs, int stride,
+                                           const QuadTask& qt, int idx, unsigned cos_of, int n, const uint16_t* qid,
+                                           int qid_stride, int lane, const QuadUpd<T>& upd) {
+  constexpr int VEC = FusedDim<K>::vec;
+  const int c = lane >> 3, j = lane & 7;
+  const bool on = c < n;
+  const int sl = on ? c : 0;
+  const int cq = slot_coset(cos_of, sl);
+  const bool rev = qt.flags & kQuadRev;
+  const int qm_in = qt.masks & 15;
+  const int r1 = (j >> 2) & 1, r2 = (j >> 1) & 1, r3 = j & 1;
+  int Rn[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) Rn[q] = rev ? bitrev((q << 3) | j, 4) : ((q << 3) | j);
+  const T* mA = ws.mt + (sl << 4);
+  const T* mB = ws.mb + (sl << 4);
+  // quad_pass's lane pattern at r0 = 0; r0 = 1 flips the beta bits of
+  // fields 2 and 6 (be = r0 ^ r2), the only ones depending on r0.
+  const unsigned tq = (unsigned)qid[cq * qid_stride] ^ (((unsigned)r1 * 0x0505u) ^ ((unsigned)r2 * 0x5050u) ^
+                                                        ((unsigned)r3 * 0x0484u));
+  unsigned tr[2];
+  tr[0] = tq;
+  tr[1] = tq ^ 0x1010u;
+  T x[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+    x[q] = qt.in_idx >= 0 ? msgs[cq * stride + qt.in_idx * VEC + Rn[q]] : ((Rn[q] & qm_in) ? T(0) : T(1));
+  // Column 0.
+  T S0[2][2];                                              // [a0][q]
+  {
+    const T k0 = qco(tq, 1, 0u, pI, pE), k1 = qco(tq, 1, 2u, pI, pE);
+    T u[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) u[q] = fma(k1, shx(x[q], 2), k0 * x[q]);
+#pragma unroll
+    for (int a0 = 0; a0 < 2; ++a0) {
+      const T h0 = qco(tq, 0, (unsigned)a0, pI, pE), h1 = qco(tq, 0, 2u + a0, pI, pE);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) S0[a0][q] = fma(h1, u[q ^ 1], h0 * u[q]);
+    }
+  }
+  const T c2k0 = qco(tq, 5, 0u, pI, pE), c2k1 = qco(tq, 5, 2u, pI, pE);
+  const T g00 = qco(tq, 4, 0u, pI, pE), g10 = qco(tq, 4, 2u, pI, pE);
+  const T g01 = qco(tq, 4, 1u, pI, pE), g11 = qco(tq, 4, 3u, pI, pE);
+  T h0[2], h1[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    h0[q] = qco(tr[q], 2, 0u, pI, pE);
+    h1[q] = qco(tr[q], 2, 2u, pI, pE);
+  }
+  T kk0[2], kk1[2];
+#pragma unroll
+  for (int b1 = 0; b1 < 2; ++b1) {
+    kk0[b1] = qco(tq, 3, (unsigned)b1, pI, pE);
+    kk1[b1] = qco(tq, 3, 2u + b1, pI, pE);
+  }
+  T Y[2][2][2];                                            // [b0][b1][q], e = r0 = q
+#pragma unroll
+  for (int a0 = 0; a0 < 2; ++a0) {
+    T S1[2][2][2];                                         // [b0][b1][q]
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const T o = S0[a0][q], p = shx(o, 1);
+      const T X0 = r3 ? p : o, X1 = r3 ? o : p;
+#pragma unroll
+      for (int b1 = 0; b1 < 2; ++b1) {
+        const T y0 = kk0[b1] * X0, y1 = kk1[b1] * X1;
+        S1[0][b1][q] = fma(h1[q], shx(y0, 4), h0[q] * y0);
+        S1[1][b1][q] = fma(h1[q], shx(y1, 4), h0[q] * y1);
+      }
+    }
+    // A[a0 a1 v e] at mA[8 a0 + 4 a1 + 2 v + e]: row q takes e = q, A0 with
+    // a1 = q and A1 with a1 = !q.
+    T lo[4], hi4[4];
+    vcopy4(mA + (a0 << 3), lo);                            // a1 = 0: [2 v + e]
+    vcopy4(mA + (a0 << 3) + 4, hi4);                       // a1 = 1
+    T A0[2], A1[2];
+    A0[0] = fma(lo[2], g01, lo[0] * g00);
+    A1[0] = fma(hi4[2], g11, hi4[0] * g10);
+    A0[1] = fma(hi4[3], g01, hi4[1] * g00);
+    A1[1] = fma(lo[3], g11, lo[1] * g10);
+#pragma unroll
+    for (int b0 = 0; b0 < 2; ++b0)
+#pragma unroll
+      for (int b1 = 0; b1 < 2; ++b1) {
+        T u[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const T s1 = S1[b0][b1][q];
+          u[q] = fma(c2k1, shx(s1, 2), c2k0 * s1);
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+          Y[b0][b1][q] = a0 == 0 ? fma(A0[q], u[q], A1[q] * u[q ^ 1])
+                                 : fma(A0[q], u[q], fma(A1[q], u[q ^ 1], Y[b0][b1][q]));
+      }
+  }
+  T out[2];
+  {
+    const T* mb = mB + (r3 << 1);                          // B[b0 b1 r3 ff] at mb[4 (2 b0 + b1) + ff]
+    const T k0 = qco(tq, 7, 0u, pI, pE), k1 = qco(tq, 7, 2u, pI, pE);
+    const T m0 = qco(tq, 7, 1u, pI, pE), m1 = qco(tq, 7, 3u, pI, pE);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      T S2[2];
+#pragma unroll
+      for (int ff = 0; ff < 2; ++ff)
+        S2[ff] = fma(mb[12 + ff], Y[1][1][q], fma(mb[8 + ff], Y[1][0][q], fma(mb[4 + ff], Y[0][1][q],
+                                                                             mb[ff] * Y[0][0][q])));
+      const T z0 = S2[0], z1 = S2[1];
+      const T p0 = shx(z0, 1), p1 = shx(z1, 1);
+      const T uu = fma(m1, p1, fma(m0, z1, fma(k1, p0, k0 * z0)));
+      const T g0 = qco(tr[q], 6, 0u, pI, pE), g1 = qco(tr[q], 6, 2u, pI, pE);
+      out[q] = fma(g1, shx(uu, 4), g0 * uu);
+    }
+  }
+  if constexpr (UPD) {
+    reg_update16x2<T, K>(out, on, cq, idx, j == 0, Rn, stride, upd);
+  } else {
+    if (on) {
+      ws.s0[(sl << 4) | Rn[0]] = out[0];
+      ws.s0[(sl << 4) | Rn[1]] = out[1];
+    }
+  }
+  __syncwarp();
+}
+
 // Every iterating coset of one message in passes of two (cosets sp + h in
 // half h), the side messages staged by the caller (stage_all_sides); the
 // shape is dispatched once, outside the passes.
@@ -1451,6 +1627,12 @@ template <typename T, int K, int SHAPE, bool UPD>
 __device__ __forceinline__ void msg_passes(const FusedWS<T>& ws, T pI, T pE, const T* msgs, int stride,
                                            const QuadTask& qt, int idx, unsigned cos_of, int n, const uint16_t* qid,
                                            int qid_stride, int lane, const QuadUpd<T>& upd) {
+  if constexpr (SHAPE == kShapeQuad) {
+    if (n > 2) {                              // three or four cosets: one pass, 8 lanes each
+      quad_pass4<T, K, UPD>(ws, pI, pE, msgs, stride, qt, idx, cos_of, n, qid, qid_stride, lane, upd);
+      return;
+    }
+  }
   const int hi = lane >> 4;
   for (int sp = 0; sp < n; sp += 2) {
     HalfJob jb;
