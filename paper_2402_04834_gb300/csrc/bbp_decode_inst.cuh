@@ -21,6 +21,7 @@ cudaError_t launch_decode_t(const LaunchArgs& a, cudaStream_t st) {
   k.logp = a.logp; k.delta = a.delta; k.iters = a.iters; k.flags = a.flags;
   k.init_msgs = nullptr; k.final_msgs = nullptr;
   k.n_items = 0; k.slot_elems = 0;
+  set_working(k);
   const int smem = smem_bytes_for<T>(a.geo, a.M);
   auto kern = decode_kernel<T, kMaxK, kMaxD, kWarps>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -44,6 +45,7 @@ KArgs<T> fused_args(const LaunchArgs& a) {
   k.logp = a.logp; k.delta = a.delta; k.iters = a.iters; k.flags = a.flags;
   k.init_msgs = a.init_msgs; k.final_msgs = a.final_msgs;
   k.n_items = 0; k.slot_elems = 0;
+  set_working(k);
   return k;
 }
 

@@ -1824,7 +1824,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
 
   Ctx<T, K> c;
   c.g = g; c.D = 0; c.cutoff2 = T(0);
-  c.pI = (T)(1.0 - a.p); c.pE = (T)(a.p / 3.0);
+  c.pI = a.pI_w; c.pE = a.pE_w;
   c.frame = frames; c.msg_of = msg_of; c.msg_off = nullptr; c.dims = nullptr;
   c.arena = nullptr; c.e0 = nullptr; c.cta_flags = &misc[8];
 
@@ -1895,8 +1895,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
   }
   __syncthreads();
 
-  const T eta = (T)a.eta, one_m_eta = T(1) - eta;
-  const T d0sq = (T)((a.delta0 * M) * (a.delta0 * M));   // the exit threshold in working precision
+  const T eta = a.eta_w, one_m_eta = a.one_m_eta_w;
   unsigned act = (1u << G) - 1;                      // cosets still iterating
   for (int it = 1; it <= a.max_iter && M > 0 && act; ++it) {
     int n = 0;
@@ -2003,6 +2002,7 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
       for (int i = lane; i < M; i += 32) acc += ovl[warp * M + i];
       acc = warp_sum(acc);
       if (lane == 0) {
+        const T d0sq = (T)((a.delta0 * M) * (a.delta0 * M));   // the exit threshold in working precision
         const T sum = acc > T(0) ? acc : T(0);
         dsh[warp] = (double)sum;
         misc[12 + warp] = it;

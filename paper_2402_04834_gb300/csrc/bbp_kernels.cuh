@@ -110,7 +110,24 @@ struct KArgs {
   float* final_msgs;        // fused path: [cta][M][16] messages after the BP loop, or null
   long long n_items;        // fused path, messages in the workspace: (syndrome, coset group) items
   long long slot_elems;     // fused path, messages in the workspace: scalars of one CTA's slot in arena
+  // The constants above in working precision, rounded once by the host
+  // (set_working): kernels read them as arguments, so no FP64 instruction
+  // recomputes them inside an FP32 kernel's loops.
+  T pI_w, pE_w;             // pi(I) = 1 - p, pi(X) = p / 3
+  T eta_w, one_m_eta_w;     // eta, 1 - eta (the latter in working precision)
+  T cutoff2_w;              // cutoff^2
 };
+
+// Fill KArgs' working-precision constants from its double parameters (the
+// host's IEEE double arithmetic and rounding to T).
+template <typename T>
+inline void set_working(KArgs<T>& k) {
+  k.pI_w = (T)(1.0 - k.p);
+  k.pE_w = (T)(k.p / 3.0);
+  k.eta_w = (T)k.eta;
+  k.one_m_eta_w = T(1) - k.eta_w;
+  k.cutoff2_w = (T)(k.cutoff * k.cutoff);
+}
 
 // Everything a warp needs to reach the CTA's shared tables.
 template <typename T, int K>
@@ -905,8 +922,8 @@ __global__ void __launch_bounds__(NW * 32) decode_kernel(KArgs<T> a) {
 
   Ctx<T, K> c;
   c.g = g; c.D = a.D;
-  c.cutoff2 = (T)(a.cutoff * a.cutoff);
-  c.pI = (T)(1.0 - a.p); c.pE = (T)(a.p / 3.0);
+  c.cutoff2 = a.cutoff2_w;
+  c.pI = a.pI_w; c.pE = a.pE_w;
   c.frame = frame; c.msg_of = msg_of; c.msg_off = msg_off; c.dims = dims;
   c.arena = arena; c.e0 = e0; c.cta_flags = &misc[1];
 
@@ -942,7 +959,7 @@ __global__ void __launch_bounds__(NW * 32) decode_kernel(KArgs<T> a) {
         const int I = key / 4 / nb, J = (key / 4) % nb, dir = key & 3;
         const Frame f = make_frame(c, I, J, dir);
         block_sweep(ws, c, f, false, lane);
-        damp(ws, c, idx, f.h, (T)a.eta, lane);
+        damp(ws, c, idx, f.h, a.eta_w, lane);
         const double o = mps_overlap(ws, f.h, [&](int s) { return psi_site(ws, s); },
                                      [&](int s) { return msg_site(c, idx, f.h, s, false); }, lane);
         store_msg(ws, c, idx, f.h, lane);
