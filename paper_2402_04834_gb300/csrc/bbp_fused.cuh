@@ -1874,6 +1874,39 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
 
   // Remark 2: uniform messages of unit norm, unless initial messages are
   // given (learned warm start): those are renormalised on entry.
+  if constexpr (K <= 4) {
+    // A message per half-warp, two per half in flight (the proposals come
+    // from HBM); the norm's sum in gsum16's order, which is group_sum's
+    // over 32 lanes for vectors of at most 16 entries.
+    const int sub = lane & 15;
+    for (int b0 = 2 * warp; b0 < G * M; b0 += 4 * NW) {   // the same trip count in both halves (shuffles)
+      const int q0 = b0 + hi;
+      T v[2];
+      int w[2];
+      T* x[2];
+      bool ok[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int qi = q0 + u * 2 * NW;
+        ok[u] = qi < G * M;
+        const int qq = ok[u] ? qi : 0;
+        const int q = qq / M, idx = qq - q * M;
+        const int key = meta[idx];
+        w[u] = g.side_len(key / 4 / nb, (key / 4) % nb, key & 3);
+        x[u] = msgs + q * stride + idx * VEC;
+        v[u] = (a.init_msgs && ok[u] && sub < (1 << w[u]))
+                   ? (T)a.init_msgs[((syn * 4 + c0 + q) * M + idx) * VEC + sub] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const T nrm = xsqrt(gsum16(v[u] * v[u]));
+        const bool uniform = !a.init_msgs || !(nrm > T(0));
+        // 1 / sqrt(2^w): a power of two, times the rounded 1 / sqrt 2 for odd w.
+        const T un = ((w[u] & 1) ? T(0.70710678118654752440) : T(1)) * pow2_neg<T>(w[u] >> 1);
+        if (ok[u] && sub < VEC) x[u][sub] = uniform ? (sub < (1 << w[u]) ? un : T(0)) : v[u] * (T(1) / nrm);
+      }
+    }
+  } else
   for (int qi = warp; qi < G * M; qi += NW) {
     const int q = qi / M, idx = qi - q * M;
     const int key = meta[idx];
@@ -2145,14 +2178,14 @@ __device__ __forceinline__ void fused_item(const KArgs<T>& a, const Geo g, const
         pz.mul(oz);
         po.mul(oo);
       }
-      acc = pz.value() - po.value();
+      if (lane == 0) acc = pz.value() - po.value();   // FP64 logs on one lane (2 FP64 lanes a cycle per SM)
     } else {
       for (int i = lane; i < per; i += 32) acc += rlog[warp * per + i];
       acc = warp_sum(acc);
     }
-    const double dq = M > 0 ? sqrt(dsh[warp]) / M : 0.0;
-    const int iq = misc[12 + warp];
     if (lane == 0) {
+      const double dq = M > 0 ? sqrt(dsh[warp]) / M : 0.0;
+      const int iq = misc[12 + warp];
       // Capacity and check failures are recorded on the first coset's word
       // and hold for every coset of the item.
       int fl = misc[8 + warp] | (misc[8] & (kFlagCapacity | kFlagCheck));
