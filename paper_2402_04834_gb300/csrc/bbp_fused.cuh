@@ -1620,6 +1620,124 @@ __device__ __forceinline__ void quad_pass4(const FusedWS<T>& ws, T pI, T pE, con
   __syncwarp();
 }
 
+// col_pass for up to four cosets of one message at once, lane and rows as
+// in quad_pass4; every value is col_pass's, bit for bit.
+template <typename T, int K, bool UPD>
+__device__ __forceinline__ void col_pass4(const FusedWS<T>& ws, T pI, T pE, const T* msgs, int stride,
+                                          const QuadTask& qt, int idx, unsigned cos_of, int n, const uint16_t* qid,
+                                          int qid_stride, int lane, const QuadUpd<T>& upd) {
+  constexpr int VEC = FusedDim<K>::vec;
+  const int c = lane >> 3, j = lane & 7;
+  const bool on = c < n;
+  const int sl = on ? c : 0;
+  const int cq = slot_coset(cos_of, sl);
+  const bool rev = qt.flags & kQuadRev;
+  const int qm_in = qt.masks & 15, qm_up = (qt.masks >> 4) & 15, qm_lo = (qt.masks >> 8) & 15;
+  const int r1 = (j >> 2) & 1, r3 = j & 1;
+  int Rn[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) Rn[q] = rev ? bitrev((q << 3) | j, 4) : ((q << 3) | j);
+  const T* mq = msgs + cq * stride;
+  const unsigned tq = (unsigned)qid[cq * qid_stride] ^ (((unsigned)r1 * 5u) ^ ((unsigned)r3 * 4u));
+  T x[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+    x[q] = qt.in_idx >= 0 ? mq[qt.in_idx * VEC + Rn[q]] : ((Rn[q] & qm_in) ? T(0) : T(1));
+  const T a0 = qt.up_idx >= 0 ? mq[qt.up_idx * VEC] : T(1);
+  const T a1 = qt.up_idx >= 0 ? mq[qt.up_idx * VEC + 1] : (qm_up ? T(0) : T(1));
+  const T bb = qt.lo_idx >= 0 ? mq[qt.lo_idx * VEC + r3] : ((r3 && qm_lo) ? T(0) : T(1));
+  const T k0 = qco(tq, 1, 0u, pI, pE), k1 = qco(tq, 1, 2u, pI, pE);
+  const T h0 = qco(tq, 0, 0u, pI, pE), h1 = qco(tq, 0, 2u, pI, pE);
+  const T m0 = qco(tq, 0, 1u, pI, pE), m1 = qco(tq, 0, 3u, pI, pE);
+  T u[2], out[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) u[q] = fma(k1, shx(x[q], 2), k0 * x[q]);
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const T uf = u[q ^ 1];
+    out[q] = bb * fma(a1, fma(m1, uf, m0 * u[q]), a0 * fma(h1, uf, h0 * u[q]));
+  }
+  if constexpr (UPD) {
+    reg_update16x2<T, K>(out, on, cq, idx, j == 0, Rn, stride, upd);
+  } else {
+    if (on) {
+      ws.s0[(sl << 4) | Rn[0]] = out[0];
+      ws.s0[(sl << 4) | Rn[1]] = out[1];
+    }
+  }
+  __syncwarp();
+}
+
+// row_pass for up to four cosets of one message at once: lane (slot c,
+// j = lane & 7) takes the side-leg assignments (x0, x2, y0, y2) with
+// (x2, y0, y2) = j and x0 = 0, 1 in registers; the two are added first, as
+// row_pass's first butterfly level adds them (x0 is its lane bit 3).  The
+// side messages are staged for slots 0 .. n - 1.
+template <typename T, int K, bool UPD>
+__device__ __forceinline__ void row_pass4(const FusedWS<T>& ws, T pI, T pE, const T* msgs, int stride,
+                                          const QuadTask& qt, int idx, unsigned cos_of, int n, const uint16_t* qid,
+                                          int qid_stride, int lane, const QuadUpd<T>& upd) {
+  constexpr int VEC = FusedDim<K>::vec;
+  const int c = lane >> 3, j = lane & 7;
+  const bool on = c < n;
+  const int sl = on ? c : 0;
+  const int cq = slot_coset(cos_of, sl);
+  const bool chk0 = qt.flags & kQuadRev;
+  const int qm_in = qt.masks & 15;
+  const T* mq = msgs + cq * stride;
+  const int x2 = (j >> 2) & 1, y0 = (j >> 1) & 1, y2 = j & 1;
+  const T* mA = ws.mt + (sl << 4);
+  const T* mB = ws.mb + (sl << 4);
+  const unsigned idv = qid[cq * qid_stride];
+  const int ia = (int)(idv & 3u), ib = (int)((idv >> 2) & 3u);
+  const T in0 = qt.in_idx >= 0 ? mq[qt.in_idx * VEC] : T(1);
+  const T in1 = qt.in_idx >= 0 ? mq[qt.in_idx * VEC + 1] : (qm_in ? T(0) : T(1));
+  T pq[2][2];                                              // [x0][r]
+#pragma unroll
+  for (int x0 = 0; x0 < 2; ++x0) {
+    T* part = pq[x0];
+    if (!chk0) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r) part[r] = T(0);
+#pragma unroll
+      for (int l1 = 0; l1 < 2; ++l1) {
+        T g0, g1;
+        qpair(ia, x0 ^ y0, pI, pE, g0, g1);
+        const T hh = l1 ? in0 * g1 + in1 * g0 : in0 * g0 + in1 * g1;
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+          part[r] += hh * mA[(x0 << 3) | (l1 << 2) | (x2 << 1) | r] * mB[(y0 << 3) | (l1 << 2) | (y2 << 1) | r] *
+                     qval(ib, l1 ^ r, x2 ^ y2, pI, pE);
+      }
+    } else {
+      part[0] = part[1] = T(0);
+#pragma unroll
+      for (int l0 = 0; l0 < 2; ++l0)
+#pragma unroll
+        for (int l2 = 0; l2 < 2; ++l2) {
+          const T w = (l0 ? in1 : in0) * mA[(l0 << 3) | (x0 << 2) | (l2 << 1) | x2] *
+                      mB[(l0 << 3) | (y0 << 2) | (l2 << 1) | y2] * qval(ia, l0 ^ l2, x0 ^ y0, pI, pE);
+          part[0] += w * qval(ib, l2, x2 ^ y2, pI, pE);
+          part[1] += w * qval(ib, l2 ^ 1, x2 ^ y2, pI, pE);
+        }
+    }
+  }
+  T part[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) part[r] = pq[0][r] + pq[1][r];
+#pragma unroll
+  for (int m = 4; m >= 1; m >>= 1) {
+    part[0] += shx(part[0], m);
+    part[1] += shx(part[1], m);
+  }
+  if constexpr (UPD) {
+    reg_update2<T, K>(part[0], part[1], on, cq, idx, j == 0, stride, upd);
+  } else {
+    if (on && j < 2) ws.s0[(sl << 1) | j] = j ? part[1] : part[0];
+  }
+  __syncwarp();
+}
+
 // Every iterating coset of one message in passes of two (cosets sp + h in
 // half h), the side messages staged by the caller (stage_all_sides); the
 // shape is dispatched once, outside the passes.
@@ -1627,9 +1745,15 @@ template <typename T, int K, int SHAPE, bool UPD>
 __device__ __forceinline__ void msg_passes(const FusedWS<T>& ws, T pI, T pE, const T* msgs, int stride,
                                            const QuadTask& qt, int idx, unsigned cos_of, int n, const uint16_t* qid,
                                            int qid_stride, int lane, const QuadUpd<T>& upd) {
-  if constexpr (SHAPE == kShapeQuad) {
-    if (n > 2) {                              // three or four cosets: one pass, 8 lanes each
+  if (n > 2) {                                // three or four cosets: one pass, 8 lanes each
+    if constexpr (SHAPE == kShapeQuad) {
       quad_pass4<T, K, UPD>(ws, pI, pE, msgs, stride, qt, idx, cos_of, n, qid, qid_stride, lane, upd);
+      return;
+    } else if constexpr (SHAPE == kShapeCol) {
+      col_pass4<T, K, UPD>(ws, pI, pE, msgs, stride, qt, idx, cos_of, n, qid, qid_stride, lane, upd);
+      return;
+    } else if constexpr (SHAPE == kShapeRow) {
+      row_pass4<T, K, UPD>(ws, pI, pE, msgs, stride, qt, idx, cos_of, n, qid, qid_stride, lane, upd);
       return;
     }
   }
