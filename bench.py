@@ -61,13 +61,17 @@ FP64_FMA_PER_SM_CLK = 2
 # Warm-start network: 256 -> 256 -> 256 -> 16, two flops per multiply-add.
 MLP_FLOPS_PER_ROW = 2 * (256 * 256 + 256 * 256 + 256 * 16)
 # DRAM bytes read + written per unit, from ncu captures (dram__bytes_read.sum
-# + dram__bytes_write.sum) of the current kernels: the fused decode kernel
-# moved 327.2 KB + 0 for 1024 syndromes (d = 11, 4 cosets per CTA, the
-# register-form-only variant sized for 4 CTAs per SM); the network kernel
-# fed by feature bits 14.17 MB + 0 for 385,000 rows (its 64-byte output
-# rows stay in L2 during the launch).
-FUSED_DRAM_BYTES_PER_SYNDROME = (327.168e3 + 0.0) / 1024
-NETWORK_DRAM_BYTES_PER_ROW = (14.172928e6 + 0.0) / 385000
+# + dram__bytes_write.sum) of the current kernels at d = 11 (4 cosets per
+# CTA, the register-form-only variant sized for 4 CTAs per SM).  The timed
+# launches of the benchmark step (one-pass capture of the NVTX range
+# "timed", 10^4 syndromes, mean of its two launches): the decode from the
+# network's proposals moved 310.09 MB + 0.87 MB (it reads every proposed
+# message: 4 cosets x 120 messages x 16 floats per syndrome), the network
+# kernel fed by feature bits 55.76 MB + 39.68 MB for its 1.54 M rows.  The
+# decode from the uniform start moved 363.0 KB + 0 for 1024 syndromes.
+FUSED_DRAM_BYTES_PER_SYNDROME_WARM = (310.087e6 + 0.871e6) / 10000
+FUSED_DRAM_BYTES_PER_SYNDROME = (363.008e3 + 0.0) / 1024
+NETWORK_DRAM_BYTES_PER_ROW = (55.761e6 + 39.677e6) / 1540000
 
 
 def oracle_one(args):
@@ -616,11 +620,15 @@ def ours(args):
         f_it, f_ro = fused_flops(D_CODE, K_BLOCK)
         flops = float(out["iters"].double().sum().item()) * f_it + B * 4 * f_ro
         achieved = flops / (dec_ms / 1e3) / 1e12
-        traffic = None if FUSED_DRAM_BYTES_PER_SYNDROME is None else FUSED_DRAM_BYTES_PER_SYNDROME * B
+        warm_launch = mlp_ms is not None            # the decode reads the network's proposals
+        per_syn = FUSED_DRAM_BYTES_PER_SYNDROME_WARM if warm_launch else FUSED_DRAM_BYTES_PER_SYNDROME
+        traffic = per_syn * B
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": "fused_kernel",
-                "traffic_source": ("ncu DRAM bytes of a 1024-syndrome launch, scaled to the batch"
-                                   if traffic is not None else "no capture of the current kernel"),
+                "traffic_source": ("ncu DRAM bytes of the timed 10^4-syndrome launch reading the proposals, "
+                                   "per syndrome, scaled to the batch" if warm_launch else
+                                   "ncu DRAM bytes of a 1024-syndrome launch from the uniform start, "
+                                   "scaled to the batch"),
                 "launch_ms": dec_ms,
                 "peak_source": (f"derived: {per_clk} {'FP32 lanes' if fp else 'FP64 FMA/clk'} per SM x 2 x "
                                 f"{n_sm} SMs x {sm_mhz:.0f} MHz (max SM clock)"),
@@ -639,7 +647,7 @@ def ours(args):
         mf = rows * MLP_FLOPS_PER_ROW / (mlp_ms / 1e3) / 1e12
         roof_mlp = {"bound": "tensor", "achieved": mf, "peak": bf16_peak, "unit": "TFLOP/s", "frac": mf / bf16_peak,
                     "traffic": None if NETWORK_DRAM_BYTES_PER_ROW is None else NETWORK_DRAM_BYTES_PER_ROW * rows,
-                    "traffic_source": ("ncu DRAM bytes of a 385,000-row launch, scaled to the step's rows"
+                    "traffic_source": ("ncu DRAM bytes of the timed 1.54 M-row launch, scaled to the step's rows"
                                        if NETWORK_DRAM_BYTES_PER_ROW is not None else
                                        "no capture of the current kernel"),
                     "kernel": "mlp_tc_kernel (+ weight preparation and the expansion to every coset)",
