@@ -65,13 +65,13 @@ MLP_FLOPS_PER_ROW = 2 * (256 * 256 + 256 * 256 + 256 * 16)
 # CTA, the register-form-only variant sized for 4 CTAs per SM).  The timed
 # launches of the benchmark step (one-pass capture of the NVTX range
 # "timed", 10^4 syndromes, mean of its two launches): the decode from the
-# network's proposals moved 310.09 MB + 0.87 MB (it reads every proposed
+# network's proposals moved 310.29 MB + 1.35 MB (it reads every proposed
 # message: 4 cosets x 120 messages x 16 floats per syndrome), the network
-# kernel fed by feature bits 55.76 MB + 39.68 MB for its 1.54 M rows.  The
-# decode from the uniform start moved 363.0 KB + 0 for 1024 syndromes.
-FUSED_DRAM_BYTES_PER_SYNDROME_WARM = (310.087e6 + 0.871e6) / 10000
-FUSED_DRAM_BYTES_PER_SYNDROME = (363.008e3 + 0.0) / 1024
-NETWORK_DRAM_BYTES_PER_ROW = (55.761e6 + 39.677e6) / 1540000
+# kernel fed by feature bits 55.78 MB + 39.71 MB for its 1.54 M rows.  The
+# decode from the uniform start moved 362.0 KB + 0 for 1024 syndromes.
+FUSED_DRAM_BYTES_PER_SYNDROME_WARM = (310.29e6 + 1.35e6) / 10000
+FUSED_DRAM_BYTES_PER_SYNDROME = (361.984e3 + 0.0) / 1024
+NETWORK_DRAM_BYTES_PER_ROW = (55.78e6 + 39.71e6) / 1540000
 
 
 def oracle_one(args):
@@ -115,12 +115,13 @@ def run_oracle_sample(first_shot: int, n: int, procs: int, algorithm: str):
 
 
 # Multiply-adds of the 4 x 4 register form per (row, coset): column 0's two
-# butterflies 6; per upper leg a0 of column 0 (two): column 1's products 4
-# and butterflies 8, the upper side message's entries 4, column 2's
-# butterflies and data column 16; the lower side message's data column 8;
-# column 3 6.  Only the entries with column 3's upper leg e equal to the
-# row's bit r0 (the check at its top ties them) are formed.
-REGISTER_FORM_MADDS = 84
+# butterflies 6; per upper leg a0 of column 0 (two): column 1's upper-qubit
+# butterflies 4 and lower-qubit products 4, the upper side message's
+# entries 4, column 2's butterflies and data column 16; the lower side
+# message's data column 8; column 3 6.  Only the entries with column 3's
+# upper leg e equal to the row's bit r0 (the check at its top ties them)
+# are formed.
+REGISTER_FORM_MADDS = 76
 
 
 def fused_flops(d: int, k: int):
@@ -189,7 +190,7 @@ def fused_flops(d: int, k: int):
                 if h == 4 and len(lines) == 4:
                     # 4 x 4 blocks: the register form of the update (butterflies
                     # over single row bits, side messages contracted where their
-                    # legs enter), 84 multiply-adds per (row, coset) entry
+                    # legs enter), 76 multiply-adds per (row, coset) entry
                     # whichever node column 0 starts with (a chain starting with
                     # a check is read bottom to top).
                     per_iter += 2.0 * 16 * REGISTER_FORM_MADDS + 12.0 * 2 ** h
@@ -632,7 +633,7 @@ def ours(args):
                 "launch_ms": dec_ms,
                 "peak_source": (f"derived: {per_clk} {'FP32 lanes' if fp else 'FP64 FMA/clk'} per SM x 2 x "
                                 f"{n_sm} SMs x {sm_mhz:.0f} MHz (max SM clock)"),
-                "flop_model": "4x4 blocks: the multiply-adds of the register form (84 per row and "
+                "flop_model": "4x4 blocks: the multiply-adds of the register form (76 per row and "
                               "coset); other blocks: qubit nodes as 2x2 XOR convolutions (4 multiply-adds "
                               "per state entry), check nodes as zero-flop copy tensors, side-message data "
                               "columns; normalise/damp/overlap; Lemma 1 read-out (register form for 4x4 blocks)",

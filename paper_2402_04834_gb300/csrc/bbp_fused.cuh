@@ -1395,11 +1395,13 @@ __device__ __forceinline__ void quad_pass(const FusedWS<T>& ws, T pI, T pE, cons
     {
       const T o = S0[a0], p = shx(o, 1);
       const T X0 = r3 ? p : o, X1 = r3 ? o : p;
+      // The upper qubit's butterfly over r1 first: the lower qubit's
+      // coefficients (r2, r3) are the same in both lanes it pairs.
+      const T T0 = fma(h1, shx(X0, 4), h0 * X0), T1 = fma(h1, shx(X1, 4), h0 * X1);
 #pragma unroll
       for (int b1 = 0; b1 < 2; ++b1) {
-        const T y0 = kk0[b1] * X0, y1 = kk1[b1] * X1;
-        S1[0][b1] = fma(h1, shx(y0, 4), h0 * y0);
-        S1[1][b1] = fma(h1, shx(y1, 4), h0 * y1);
+        S1[0][b1] = kk0[b1] * T0;
+        S1[1][b1] = kk1[b1] * T1;
       }
     }
     // A0: row bit 0 kept (l0 = r0 = a1), A1: flipped (l0 = a1 = !r0); v
@@ -1557,11 +1559,11 @@ __device__ __forceinline__ void quad_pass4(const FusedWS<T>& ws, T pI, T pE, con
     for (int q = 0; q < 2; ++q) {
       const T o = S0[a0][q], p = shx(o, 1);
       const T X0 = r3 ? p : o, X1 = r3 ? o : p;
+      const T T0 = fma(h1[q], shx(X0, 4), h0[q] * X0), T1 = fma(h1[q], shx(X1, 4), h0[q] * X1);
 #pragma unroll
       for (int b1 = 0; b1 < 2; ++b1) {
-        const T y0 = kk0[b1] * X0, y1 = kk1[b1] * X1;
-        S1[0][b1][q] = fma(h1[q], shx(y0, 4), h0[q] * y0);
-        S1[1][b1][q] = fma(h1[q], shx(y1, 4), h0[q] * y1);
+        S1[0][b1][q] = kk0[b1] * T0;
+        S1[1][b1][q] = kk1[b1] * T1;
       }
     }
     // A[a0 a1 v e] at mA[8 a0 + 4 a1 + 2 v + e]: row q takes e = q, A0 with

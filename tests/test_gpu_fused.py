@@ -272,6 +272,33 @@ def test_messages_in_workspace_or_shared_memory_give_the_same_bits(dev, d, preci
     assert torch.equal(res[1][2], res[2][2])
 
 
+@pytest.mark.parametrize("d,precision", [(9, "fp64"), (11, "fp64"), (11, "fp32")])
+def test_four_coset_passes_give_the_two_coset_bits(dev, d, precision):
+    # With four cosets per CTA the register forms run one pass over the
+    # three or four iterating cosets of a message (8 lanes per coset, two
+    # rows per lane), and passes of two once one or two iterate; with one or
+    # two cosets per CTA every pass holds two coset jobs of 16 lanes each.
+    # delta0 = 1e-4 lets the cosets of a syndrome stop at different
+    # iterations, so every pass width runs, and odd d brings in the edge
+    # blocks' forms: every output of every compiled shape is the same bits.
+    _, _, S = synth.sample_syndromes(1700 + d, 0, 256, d, 0.1)
+    s = torch.from_numpy(S).to(dev)
+    res = {}
+    for w, c in pkg.FUSED_SHAPES[precision]:
+        prm = pkg.DecoderParams(d=d, k=4, p=0.1, max_iter=15, delta0=1e-4, precision=precision,
+                                algorithm="fused", warps=w, cosets=c, messages=1)
+        res[(w, c)] = pkg.decode(s, prm)
+    torch.cuda.synchronize()
+    shapes = list(res)
+    assert any(c == 4 for _, c in shapes) and any(c < 4 for _, c in shapes)
+    ref = res[shapes[0]]
+    for sh in shapes[1:]:
+        for key in ("logp", "delta", "iters", "flags", "decision"):
+            assert torch.equal(res[sh][key], ref[key]), (sh, key)
+    its = ref["iters"].view(-1, 4)
+    assert bool((its.max(1).values != its.min(1).values).any())   # cosets stop at different iterations
+
+
 @pytest.mark.parametrize("d,precision,messages", [(46, "fp32", 1), (34, "fp64", 1), (58, "fp32", 0), (54, "fp64", 0)])
 def test_fused_k4_at_the_largest_distance(dev, d, precision, messages):
     # The largest distances with the messages in shared memory (46 / 34) and
